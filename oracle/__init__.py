@@ -1,0 +1,344 @@
+"""Python face of the reference oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It never imports the CUDA library's
+package, and the CUDA library never imports it.
+
+``build()`` compiles ``dpf_oracle.cpp`` with the host C++ compiler into
+``oracle/_build/``; everything else marshals numpy arrays through ctypes.
+The arithmetic lives in the C++ file: the plain definition of the query
+result (Sec. 3.1, Kernels #1-#3) evaluated row at a time, and encoders and
+decoders written from the page-format definition (Sec. 3.4.1, 3.4.2, 4.1,
+4.2).  See the header of ``dpf_oracle.cpp`` for what pins each part.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dpf_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CODECS = {"for": 1, "delta": 2, "dict": 3, "str": 4}
+PRED_OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7,
+            "prefix": 8}
+AGG_OPS = {"count": 0, "sum": 1, "sum_mul": 2, "sum_sub": 3}
+
+RECORD_DTYPE = np.dtype([("key", np.int32, (2,)), ("count", np.int64), ("val", np.int64, (4,))])
+
+
+def build(force=False):
+    """Compile the oracle library (host compiler, plain -O2)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Column(C.Structure):
+    _fields_ = [("is_str", C.c_int32), ("v", C.c_void_p), ("bytes", C.c_void_p),
+                ("offsets", C.c_void_p)]
+
+
+class _Table(C.Structure):
+    _fields_ = [("n", C.c_uint64), ("ncols", C.c_int32), ("cols", C.POINTER(_Column))]
+
+
+class _Pred(C.Structure):
+    _fields_ = [("col", C.c_int32), ("op", C.c_int32), ("nargs", C.c_int32),
+                ("pfx_len", C.c_int32), ("args", C.c_int64 * 16), ("pfx", C.c_void_p)]
+
+
+class _Join(C.Structure):
+    _fields_ = [("fk_col", C.c_int32), ("dim", C.POINTER(_Table)), ("key_col", C.c_int32),
+                ("npreds", C.c_int32), ("preds", C.POINTER(_Pred)), ("npay", C.c_int32),
+                ("pay_cols", C.c_int32 * 2)]
+
+
+class _Key(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("col", C.c_int32), ("join", C.c_int32),
+                ("field", C.c_int32)]
+
+
+class _Agg(C.Structure):
+    _fields_ = [("op", C.c_int32), ("a", C.c_int32), ("b", C.c_int32)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P = C.c_void_p
+            L.orc_encode_int.restype = C.c_int64
+            L.orc_encode_int.argtypes = [C.c_uint32, P, C.c_uint64, C.c_uint32, P, C.c_uint64,
+                                         P, P, P, C.c_uint64, P]
+            L.orc_decode_int.restype = C.c_int64
+            L.orc_decode_int.argtypes = [C.c_uint32, P, P, C.c_uint64, C.c_uint64, C.c_uint32,
+                                         P, C.c_uint64, P]
+            L.orc_decode_int_row.restype = C.c_int64
+            L.orc_decode_int_row.argtypes = [C.c_uint32, P, P, P, C.c_uint64, P, C.c_uint64,
+                                             C.c_uint64, P]
+            L.orc_encode_str.restype = C.c_int64
+            L.orc_encode_str.argtypes = [P, P, C.c_uint64, C.c_uint32, P, C.c_uint64, P, P]
+            L.orc_decode_str.restype = C.c_int64
+            L.orc_decode_str.argtypes = [P, P, C.c_uint64, C.c_uint64, C.c_uint32, P, P,
+                                         C.c_uint64]
+            L.orc_query.restype = C.c_int64
+            L.orc_query.argtypes = [C.POINTER(_Table), C.c_int32, C.POINTER(_Pred), C.c_int32,
+                                    C.POINTER(_Join), C.c_int32, C.POINTER(_Key), C.c_int32,
+                                    C.POINTER(_Agg), P, C.c_uint64]
+            _lib = L
+    return _lib
+
+
+class use_library:
+    """Context manager that routes every call to another build of the
+    oracle (used by the tests that plant a mistake in a copy of it)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self._saved = lib()
+        L = C.CDLL(self.path)
+        for name in ("orc_encode_int", "orc_decode_int", "orc_decode_int_row",
+                     "orc_encode_str", "orc_decode_str", "orc_query"):
+            f, g = getattr(L, name), getattr(self._saved, name)
+            f.restype, f.argtypes = g.restype, g.argtypes
+        _lib = L
+        return L
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
+
+
+def _ptr(a):
+    return a.ctypes.data if a is not None and a.size else None
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise OracleError(f"{what} failed with status {rc}")
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# Encoding / decoding
+# ---------------------------------------------------------------------------
+
+def encode_column(col, page_rows):
+    """Encode one column dict (see ``synth``) into the page format.
+
+    Returns ``{"codec", "rows", "page_rows", "blob", "page_off", "row_prefix",
+    "dict"}`` with numpy arrays.
+    """
+    L = lib()
+    codec = col["codec"]
+    if codec == "str":
+        offsets = np.ascontiguousarray(col["offsets"], dtype=np.uint64)
+        data = np.ascontiguousarray(col["bytes"], dtype=np.uint8)
+        n = offsets.size - 1
+        npages = (n + page_rows - 1) // page_rows
+        page_off = np.zeros(npages + 1, np.uint64)
+        row_prefix = np.zeros(npages, np.uint64)
+        size = _check(L.orc_encode_str(_ptr(data), _ptr(offsets), n, page_rows, None, 0,
+                                       _ptr(page_off), _ptr(row_prefix)), "encode_str")
+        blob = np.zeros(size, np.uint8)
+        _check(L.orc_encode_str(_ptr(data), _ptr(offsets), n, page_rows, _ptr(blob), size,
+                                _ptr(page_off), _ptr(row_prefix)), "encode_str")
+        return {"codec": codec, "rows": n, "page_rows": page_rows, "blob": blob,
+                "page_off": page_off, "row_prefix": row_prefix, "dict": None}
+    v = np.ascontiguousarray(col["values"], dtype=np.int32)
+    n = v.size
+    npages = (n + page_rows - 1) // page_rows
+    page_off = np.zeros(npages + 1, np.uint64)
+    row_prefix = np.zeros(npages, np.uint64)
+    dict_n = np.zeros(1, np.uint64)
+    size = _check(L.orc_encode_int(CODECS[codec], _ptr(v), n, page_rows, None, 0,
+                                   _ptr(page_off), _ptr(row_prefix), None, 0, _ptr(dict_n)),
+                  "encode_int")
+    blob = np.zeros(size, np.uint8)
+    dct = np.zeros(max(int(dict_n[0]), 1), np.int32) if codec == "dict" else None
+    _check(L.orc_encode_int(CODECS[codec], _ptr(v), n, page_rows, _ptr(blob), size,
+                            _ptr(page_off), _ptr(row_prefix), _ptr(dct),
+                            0 if dct is None else dct.size, _ptr(dict_n)), "encode_int")
+    if dct is not None:
+        dct = dct[: int(dict_n[0])]
+    return {"codec": codec, "rows": n, "page_rows": page_rows, "blob": blob,
+            "page_off": page_off, "row_prefix": row_prefix, "dict": dct}
+
+
+def decode_column(enc):
+    """Decode a whole encoded column: int32 values, or (bytes, offsets)."""
+    L = lib()
+    n, npages = enc["rows"], enc["page_off"].size - 1
+    if enc["codec"] == "str":
+        # byte count = blob bytes is an upper bound on the string bytes
+        offsets = np.zeros(n + 1, np.uint64)
+        data = np.zeros(max(enc["blob"].size, 1), np.uint8)
+        _check(L.orc_decode_str(_ptr(enc["blob"]), _ptr(enc["page_off"]), npages, n,
+                                enc["page_rows"], _ptr(offsets), _ptr(data), data.size),
+               "decode_str")
+        return data[: int(offsets[-1])].copy(), offsets
+    out = np.zeros(n, np.int32)
+    dct = enc["dict"]
+    _check(L.orc_decode_int(CODECS[enc["codec"]], _ptr(enc["blob"]), _ptr(enc["page_off"]),
+                            npages, n, enc["page_rows"], _ptr(dct),
+                            0 if dct is None else dct.size, _ptr(out)), "decode_int")
+    return out
+
+
+def decode_row(enc, r):
+    """Decode the single value at row ``r`` through the RID index."""
+    L = lib()
+    out = np.zeros(1, np.int32)
+    dct = enc["dict"]
+    _check(L.orc_decode_int_row(CODECS[enc["codec"]], _ptr(enc["blob"]), _ptr(enc["page_off"]),
+                                _ptr(enc["row_prefix"]), enc["page_off"].size - 1, _ptr(dct),
+                                0 if dct is None else dct.size, int(r), _ptr(out)),
+           "decode_int_row")
+    return int(out[0])
+
+
+# ---------------------------------------------------------------------------
+# Query evaluation
+# ---------------------------------------------------------------------------
+
+def _make_pred(pred, names):
+    p = _Pred()
+    p.col = names.index(pred["col"])
+    p.op = PRED_OPS[pred["op"]]
+    if pred["op"] == "prefix":
+        pfx = bytes(pred["args"][0])
+        buf = C.create_string_buffer(pfx, max(len(pfx), 1))
+        p.pfx = C.cast(buf, C.c_void_p)
+        p.pfx_len = len(pfx)
+        p.nargs = 0
+        return p, buf
+    args = [int(a) for a in pred["args"]]
+    if len(args) > 16:
+        raise ValueError("at most 16 predicate operands")
+    p.nargs = len(args)
+    for i, a in enumerate(args):
+        p.args[i] = a
+    return p, None
+
+
+def _table(cols, n):
+    names = list(cols)
+    arr = (_Column * max(len(names), 1))()
+    keep = []
+    for i, name in enumerate(names):
+        c = cols[name]
+        if isinstance(c, tuple):
+            data, offs = c
+            data = np.ascontiguousarray(data, np.uint8)
+            offs = np.ascontiguousarray(offs, np.uint64)
+            keep += [data, offs]
+            arr[i].is_str = 1
+            arr[i].bytes = _ptr(data) if data.size else offs.ctypes.data  # never read when empty
+            arr[i].offsets = _ptr(offs)
+        else:
+            v = np.ascontiguousarray(c, np.int32)
+            keep.append(v)
+            arr[i].is_str = 0
+            arr[i].v = _ptr(v)
+    t = _Table(n, len(names), C.cast(arr, C.POINTER(_Column)))
+    keep.append(arr)
+    return t, names, keep
+
+
+def decoded_tables(workload, from_encoded=True):
+    """Every table's columns, decoded through the oracle's own encoder and
+    decoder (``from_encoded``) or taken raw from the generator."""
+    out = {}
+    for tname, t in workload["tables"].items():
+        cols = {}
+        for cname, c in t["cols"].items():
+            if from_encoded:
+                enc = encode_column(c, t["page_rows"])
+                d = decode_column(enc)
+                cols[cname] = d if c["codec"] == "str" else d
+            else:
+                cols[cname] = (c["bytes"], c["offsets"]) if c["codec"] == "str" else c["values"]
+        out[tname] = {"rows": t["rows"], "cols": cols}
+    return out
+
+
+def run_query(workload, from_encoded=True, tables=None):
+    """Evaluate ``workload['query']``; returns an array of RECORD_DTYPE."""
+    L = lib()
+    q = workload["query"]
+    if tables is None:
+        tables = decoded_tables(workload, from_encoded)
+    fact = tables[workload["fact"]]
+    ft, fnames, keep = _table(fact["cols"], fact["rows"])
+    preds = (_Pred * max(len(q["preds"]), 1))()
+    for i, pr in enumerate(q["preds"]):
+        preds[i], buf = _make_pred(pr, fnames)
+        keep.append(buf)
+    joins = (_Join * max(len(q["joins"]), 1))()
+    dim_tables = []
+    for i, j in enumerate(q["joins"]):
+        d = tables[j["dim"]]
+        dt, dnames, dkeep = _table(d["cols"], d["rows"])
+        keep += dkeep
+        dim_tables.append(dt)
+        dp = (_Pred * max(len(j["preds"]), 1))()
+        for k, pr in enumerate(j["preds"]):
+            dp[k], buf = _make_pred(pr, dnames)
+            keep.append(buf)
+        keep.append(dp)
+        joins[i].fk_col = fnames.index(j["fk"])
+        joins[i].dim = C.pointer(dt)
+        joins[i].key_col = dnames.index(j["key"])
+        joins[i].npreds = len(j["preds"])
+        joins[i].preds = C.cast(dp, C.POINTER(_Pred))
+        joins[i].npay = len(j["payload"])
+        for f, pc in enumerate(j["payload"]):
+            joins[i].pay_cols[f] = dnames.index(pc)
+    keys = (_Key * max(len(q["group"]), 1))()
+    for i, g in enumerate(q["group"]):
+        if "col" in g:
+            keys[i].kind, keys[i].col = 0, fnames.index(g["col"])
+        else:
+            keys[i].kind, keys[i].join, keys[i].field = 1, g["join"], g["field"]
+    aggs = (_Agg * max(len(q["aggs"]), 1))()
+    for i, a in enumerate(q["aggs"]):
+        aggs[i].op = AGG_OPS[a["op"]]
+        cols = a.get("cols", [])
+        aggs[i].a = fnames.index(cols[0]) if cols else 0
+        aggs[i].b = fnames.index(cols[1]) if len(cols) > 1 else 0
+    cap = 1 << 16
+    out = np.zeros(cap, RECORD_DTYPE)
+    n = _check(L.orc_query(C.pointer(ft), len(q["preds"]), preds, len(q["joins"]), joins,
+                           len(q["group"]), keys, len(q["aggs"]), aggs, _ptr(out), cap),
+               "query")
+    if n > cap:
+        out = np.zeros(n, RECORD_DTYPE)
+        n = _check(L.orc_query(C.pointer(ft), len(q["preds"]), preds, len(q["joins"]), joins,
+                               len(q["group"]), keys, len(q["aggs"]), aggs, _ptr(out), n),
+                   "query")
+    del keep, dim_tables
+    return out[:n].copy()

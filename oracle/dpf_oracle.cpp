@@ -1,0 +1,568 @@
+// Reference oracle for the fused query path -- TEST INFRASTRUCTURE ONLY.
+//
+// Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+// load this library.  It shares no code, header or constant generator with
+// the CUDA library: every layout constant below is restated here from the
+// storage-format definition (Sec. 3.4.1 fixed-length page layout with
+// mini blocks carrying a frame-of-reference base, a bit width and a byte
+// offset; Sec. 3.4.2 variable-length pages with a RID index that is a
+// prefix sum of per-page record counts; Sec. 4.1 integer decompression;
+// Sec. 4.2 data-loader metadata: page offsets and per-page row prefix).
+//
+// What it computes (Sec. 3.1, Kernels #1-#3): an exact relational result
+//   SELECT keys, COUNT(*), aggs FROM fact JOIN dims WHERE conj GROUP BY keys
+// with inner equi-joins on unique dimension keys and every aggregate held
+// in int64 after sign-extending the int32 inputs (Sec. 4.3, DECIMAL stored
+// as 32-bit and processed as 64-bit).  The evaluator is deliberately plain:
+// it decodes whole columns first (page by page, mini block by mini block,
+// bit by bit), then walks the fact rows one at a time, looks dimension keys
+// up in std::unordered_map built from the rows that pass the dimension
+// predicates (the build side of Kernel #1), and accumulates groups in a
+// std::map ordered by the key tuple (the record-format result of Kernel #3).
+//
+// Parity status of every function here: pinned by the tests under
+// tests/test_oracle_*.py (hand-worked golden bytes, encode/decode round
+// trips on edge cases, an independent numpy evaluator on small tables,
+// invariants).  None is "parity unpinned".
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <unordered_map>
+#include <vector>
+
+namespace {
+
+// ---- storage-format constants, restated from the format definition ----
+constexpr uint32_t kMiniBlock = 128;           // values per mini block
+constexpr uint32_t kPageHeaderBytes = 16;      // magic|codec, nrows, payload_off, extra_off
+constexpr uint32_t kMagic = 0x00465044u;       // 'D' 'P' 'F' in the low three bytes
+enum Codec : uint32_t { FOR = 1, DELTA = 2, DICT = 3, STR = 4 };
+
+enum Status : int64_t {
+  OK = 0,
+  EINVAL = -1,
+  ETRUNC = -7,
+  EDUPKEY = -4,
+  ECORRUPT = -9,
+};
+
+uint64_t align16(uint64_t x) { return (x + 15u) & ~uint64_t(15); }
+
+// Bits needed to hold span = max - min (0 when all values are equal).
+uint32_t bits_for_span(uint64_t span) {
+  uint32_t b = 0;
+  while (b < 64 && (span >> b) != 0) ++b;
+  return b;
+}
+
+uint32_t mb_header_bytes(uint32_t codec) { return codec == DELTA ? 16u : 8u; }
+
+// Writes p[0..127] at bit j*bw (bit b of the stream is bit b%32 of word b/32),
+// one bit at a time.
+void pack_bits(const uint32_t* p, uint32_t bw, uint32_t* words) {
+  for (uint32_t w = 0; w < 4 * bw; ++w) words[w] = 0;
+  for (uint32_t j = 0; j < kMiniBlock; ++j)
+    for (uint32_t b = 0; b < bw; ++b)
+      if ((p[j] >> b) & 1u) {
+        uint64_t bit = uint64_t(j) * bw + b;
+        words[bit / 32] |= 1u << (bit % 32);
+      }
+}
+
+// Reads the bw-bit field j, one bit at a time.
+uint32_t unpack_bits(const uint32_t* words, uint32_t bw, uint32_t j) {
+  uint32_t v = 0;
+  for (uint32_t b = 0; b < bw; ++b) {
+    uint64_t bit = uint64_t(j) * bw + b;
+    v |= ((words[bit / 32] >> (bit % 32)) & 1u) << b;
+  }
+  return v;
+}
+
+struct PageLayout {
+  uint32_t nrows, nmb, hdr_bytes, payload_off, payload_bytes, extra_off;
+  uint64_t extra_bytes, page_bytes;
+};
+
+// Frame-of-reference plan of one mini block of already-transformed values
+// q[0..cnt): returns (base, bw).  Missing trailing rows repeat the base.
+void for_plan(const int64_t* q, uint32_t cnt, int64_t* base, uint32_t* bw) {
+  int64_t mn = q[0], mx = q[0];
+  for (uint32_t j = 1; j < cnt; ++j) { mn = std::min(mn, q[j]); mx = std::max(mx, q[j]); }
+  *base = mn;
+  *bw = bits_for_span(uint64_t(mx - mn));
+}
+
+}  // namespace
+
+extern "C" {
+
+// ---------------------------------------------------------------------------
+// Integer column encoding (FOR, DELTA, DICT codes).
+//
+// values[0..n) -> blob.  page_off[npages+1] receives each page's byte offset
+// (the last entry is the blob size); row_prefix[npages] receives the RID
+// index (cumulative rows up to and including page i).  For DICT, dict_out
+// receives the sorted distinct values (capacity dict_cap) and *dict_n their
+// count.  With out == nullptr only the sizes are computed.  Returns the blob
+// size in bytes or a negative status.
+// ---------------------------------------------------------------------------
+int64_t orc_encode_int(uint32_t codec, const int32_t* values, uint64_t n, uint32_t page_rows,
+                       uint8_t* out, uint64_t cap, uint64_t* page_off, uint64_t* row_prefix,
+                       int32_t* dict_out, uint64_t dict_cap, uint64_t* dict_n) {
+  if (n == 0 || page_rows == 0 || page_rows % kMiniBlock != 0 || page_rows > (1u << 20))
+    return EINVAL;
+  if (codec != FOR && codec != DELTA && codec != DICT) return EINVAL;
+
+  // DICT: codes are ranks in the sorted distinct values.
+  std::vector<int32_t> dict;
+  std::vector<int64_t> src(n);
+  if (codec == DICT) {
+    dict.assign(values, values + n);
+    std::sort(dict.begin(), dict.end());
+    dict.erase(std::unique(dict.begin(), dict.end()), dict.end());
+    if (dict.size() > 65536) return EINVAL;
+    for (uint64_t r = 0; r < n; ++r)
+      src[r] = std::lower_bound(dict.begin(), dict.end(), values[r]) - dict.begin();
+    if (dict_n) *dict_n = dict.size();
+    if (dict_out) {
+      if (dict.size() > dict_cap) return ETRUNC;
+      std::copy(dict.begin(), dict.end(), dict_out);
+    }
+  } else {
+    for (uint64_t r = 0; r < n; ++r) src[r] = values[r];
+  }
+
+  const uint64_t npages = (n + page_rows - 1) / page_rows;
+  uint64_t off = 0;
+  for (uint64_t p = 0; p < npages; ++p) {
+    const uint64_t r0 = p * page_rows;
+    const uint32_t rows = uint32_t(std::min<uint64_t>(page_rows, n - r0));
+    const uint32_t nmb = (rows + kMiniBlock - 1) / kMiniBlock;
+    const uint32_t hb = mb_header_bytes(codec);
+    const uint32_t payload_off = uint32_t(align16(kPageHeaderBytes + uint64_t(nmb) * hb));
+    // plan every mini block
+    std::vector<int64_t> q(kMiniBlock);
+    std::vector<uint32_t> bws(nmb);
+    std::vector<int64_t> bases(nmb), firsts(nmb);
+    uint64_t words = 0;
+    for (uint32_t m = 0; m < nmb; ++m) {
+      const uint64_t a = r0 + uint64_t(m) * kMiniBlock;
+      const uint32_t cnt = uint32_t(std::min<uint64_t>(kMiniBlock, r0 + rows - a));
+      if (codec == DELTA) {
+        // d_0 = 0, d_j = x_j - x_{j-1} taken as a wrapped 32-bit signed difference
+        q[0] = 0;
+        for (uint32_t j = 1; j < cnt; ++j)
+          q[j] = int32_t(uint32_t(src[a + j]) - uint32_t(src[a + j - 1]));
+        firsts[m] = src[a];
+      } else {
+        for (uint32_t j = 0; j < cnt; ++j) q[j] = src[a + j];
+      }
+      for_plan(q.data(), cnt, &bases[m], &bws[m]);
+      if (bws[m] > 32) return EINVAL;
+      words += 4ull * bws[m];
+    }
+    if (words >= (1ull << 24)) return EINVAL;
+    const uint64_t page_bytes = align16(payload_off + words * 4);
+    if (page_off) page_off[p] = off;
+    if (row_prefix) row_prefix[p] = r0 + rows;
+    if (out) {
+      if (off + page_bytes > cap) return ETRUNC;
+      uint8_t* pg = out + off;
+      std::memset(pg, 0, page_bytes);
+      const uint32_t hdr[4] = {kMagic | (codec << 24), rows, payload_off, 0};
+      std::memcpy(pg, hdr, sizeof hdr);
+      uint32_t* pay = reinterpret_cast<uint32_t*>(pg + payload_off);
+      uint32_t woff = 0;
+      std::vector<uint32_t> pk(kMiniBlock);
+      for (uint32_t m = 0; m < nmb; ++m) {
+        const uint64_t a = r0 + uint64_t(m) * kMiniBlock;
+        const uint32_t cnt = uint32_t(std::min<uint64_t>(kMiniBlock, r0 + rows - a));
+        for (uint32_t j = 0; j < kMiniBlock; ++j) {
+          int64_t t;
+          if (j >= cnt) t = bases[m];                               // padding: offset 0
+          else if (codec == DELTA) t = j == 0 ? 0 : int32_t(uint32_t(src[a + j]) - uint32_t(src[a + j - 1]));
+          else t = src[a + j];
+          pk[j] = uint32_t(uint64_t(t - bases[m]));
+        }
+        pack_bits(pk.data(), bws[m], pay + woff);
+        uint8_t* h = pg + kPageHeaderBytes + uint64_t(m) * mb_header_bytes(codec);
+        const uint32_t wob = (woff << 8) | bws[m];
+        if (codec == DELTA) {
+          const int32_t f = int32_t(firsts[m]), dmin = int32_t(bases[m]);
+          const uint32_t zero = 0;
+          std::memcpy(h, &f, 4);
+          std::memcpy(h + 4, &dmin, 4);
+          std::memcpy(h + 8, &wob, 4);
+          std::memcpy(h + 12, &zero, 4);
+        } else {
+          const int32_t b = int32_t(bases[m]);
+          std::memcpy(h, &b, 4);
+          std::memcpy(h + 4, &wob, 4);
+        }
+        woff += 4 * bws[m];
+      }
+    }
+    off += page_bytes;
+  }
+  if (page_off) page_off[npages] = off;
+  return int64_t(off);
+}
+
+// Decodes every row of an integer column.  For DICT the result is the
+// dictionary value (codes are looked up in dict[0..dict_n)).  Returns 0 or a
+// negative status (ECORRUPT on a bad page header or mini block header).
+int64_t orc_decode_int(uint32_t codec, const uint8_t* blob, const uint64_t* page_off,
+                       uint64_t npages, uint64_t n, uint32_t page_rows, const int32_t* dict,
+                       uint64_t dict_n, int32_t* out) {
+  uint64_t r = 0;
+  for (uint64_t p = 0; p < npages; ++p) {
+    const uint8_t* pg = blob + page_off[p];
+    uint32_t hdr[4];
+    std::memcpy(hdr, pg, sizeof hdr);
+    if (hdr[0] != (kMagic | (codec << 24))) return ECORRUPT;
+    const uint32_t rows = hdr[1];
+    if (rows == 0 || rows > page_rows || r + rows > n) return ECORRUPT;
+    const uint32_t nmb = (rows + kMiniBlock - 1) / kMiniBlock;
+    const uint32_t* pay = reinterpret_cast<const uint32_t*>(pg + hdr[2]);
+    const uint64_t pay_words = (page_off[p + 1] - page_off[p] - hdr[2]) / 4;
+    for (uint32_t m = 0; m < nmb; ++m) {
+      const uint8_t* h = pg + kPageHeaderBytes + uint64_t(m) * mb_header_bytes(codec);
+      int32_t base, first = 0;
+      uint32_t wob;
+      if (codec == DELTA) {
+        std::memcpy(&first, h, 4);
+        std::memcpy(&base, h + 4, 4);
+        std::memcpy(&wob, h + 8, 4);
+      } else {
+        std::memcpy(&base, h, 4);
+        std::memcpy(&wob, h + 4, 4);
+      }
+      const uint32_t bw = wob & 0xffu, woff = wob >> 8;
+      if (bw > 32 || uint64_t(woff) + 4ull * bw > pay_words) return ECORRUPT;
+      const uint32_t cnt = std::min<uint32_t>(kMiniBlock, rows - m * kMiniBlock);
+      uint32_t running = uint32_t(first);
+      for (uint32_t j = 0; j < cnt; ++j) {
+        const uint32_t f = unpack_bits(pay + woff, bw, j);
+        int32_t v;
+        if (codec == DELTA) {
+          // v_j = first + sum_{i<=j} (dmin + p_i), all modulo 2^32
+          running += uint32_t(base) + f;
+          v = int32_t(running);
+        } else {
+          v = int32_t(uint32_t(base) + f);
+        }
+        if (codec == DICT) {
+          if (uint32_t(v) >= dict_n) return ECORRUPT;
+          v = dict[uint32_t(v)];
+        }
+        out[r + j] = v;
+      }
+      r += cnt;
+    }
+  }
+  return r == n ? OK : ECORRUPT;
+}
+
+// Row lookup through the RID index: binary search for the first page whose
+// cumulative row count exceeds r, then decode that single value.
+int64_t orc_decode_int_row(uint32_t codec, const uint8_t* blob, const uint64_t* page_off,
+                           const uint64_t* row_prefix, uint64_t npages, const int32_t* dict,
+                           uint64_t dict_n, uint64_t r, int32_t* out) {
+  uint64_t lo = 0, hi = npages;
+  while (lo < hi) {
+    uint64_t mid = (lo + hi) / 2;
+    if (row_prefix[mid] > r) hi = mid; else lo = mid + 1;
+  }
+  if (lo >= npages) return EINVAL;
+  const uint64_t page_first = lo == 0 ? 0 : row_prefix[lo - 1];
+  const uint8_t* pg = blob + page_off[lo];
+  uint32_t hdr[4];
+  std::memcpy(hdr, pg, sizeof hdr);
+  if (hdr[0] != (kMagic | (codec << 24))) return ECORRUPT;
+  const uint32_t i = uint32_t(r - page_first);
+  const uint32_t m = i / kMiniBlock, j = i % kMiniBlock;
+  const uint8_t* h = pg + kPageHeaderBytes + uint64_t(m) * mb_header_bytes(codec);
+  const uint32_t* pay = reinterpret_cast<const uint32_t*>(pg + hdr[2]);
+  int32_t base, first = 0;
+  uint32_t wob;
+  if (codec == DELTA) {
+    std::memcpy(&first, h, 4);
+    std::memcpy(&base, h + 4, 4);
+    std::memcpy(&wob, h + 8, 4);
+  } else {
+    std::memcpy(&base, h, 4);
+    std::memcpy(&wob, h + 4, 4);
+  }
+  const uint32_t bw = wob & 0xffu, woff = wob >> 8;
+  if (bw > 32) return ECORRUPT;
+  uint32_t v;
+  if (codec == DELTA) {
+    v = uint32_t(first);
+    for (uint32_t k = 0; k <= j; ++k) v += uint32_t(base) + unpack_bits(pay + woff, bw, k);
+  } else {
+    v = uint32_t(base) + unpack_bits(pay + woff, bw, j);
+  }
+  if (codec == DICT) {
+    if (v >= dict_n) return ECORRUPT;
+    v = uint32_t(dict[v]);
+  }
+  *out = int32_t(v);
+  return OK;
+}
+
+// ---------------------------------------------------------------------------
+// Variable-length strings (Sec. 3.4.2 with the offsets delta-coded): per page
+// the string lengths are FOR-packed in mini blocks of 128, each mini block
+// also records the byte offset of its first string inside the page's byte
+// region, and the raw bytes follow.  offsets[0..n] are the caller's byte
+// offsets into bytes (offsets[r+1] - offsets[r] = length of row r).
+// ---------------------------------------------------------------------------
+int64_t orc_encode_str(const uint8_t* bytes, const uint64_t* offsets, uint64_t n,
+                       uint32_t page_rows, uint8_t* out, uint64_t cap, uint64_t* page_off,
+                       uint64_t* row_prefix) {
+  if (n == 0 || page_rows == 0 || page_rows % kMiniBlock != 0 || page_rows > (1u << 20))
+    return EINVAL;
+  const uint64_t npages = (n + page_rows - 1) / page_rows;
+  uint64_t off = 0;
+  std::vector<int64_t> q(kMiniBlock);
+  std::vector<uint32_t> pk(kMiniBlock);
+  for (uint64_t p = 0; p < npages; ++p) {
+    const uint64_t r0 = p * page_rows;
+    const uint32_t rows = uint32_t(std::min<uint64_t>(page_rows, n - r0));
+    const uint32_t nmb = (rows + kMiniBlock - 1) / kMiniBlock;
+    const uint32_t payload_off = uint32_t(align16(kPageHeaderBytes + uint64_t(nmb) * 12));
+    std::vector<uint32_t> bws(nmb), starts(nmb);
+    std::vector<int64_t> bases(nmb);
+    uint64_t words = 0, nbytes = 0;
+    for (uint32_t m = 0; m < nmb; ++m) {
+      const uint64_t a = r0 + uint64_t(m) * kMiniBlock;
+      const uint32_t cnt = uint32_t(std::min<uint64_t>(kMiniBlock, r0 + rows - a));
+      if (nbytes >= (1ull << 32)) return EINVAL;
+      starts[m] = uint32_t(nbytes);
+      for (uint32_t j = 0; j < cnt; ++j) {
+        const uint64_t len = offsets[a + j + 1] - offsets[a + j];
+        if (len > 0x7fffffffu) return EINVAL;
+        q[j] = int64_t(len);
+        nbytes += len;
+      }
+      for_plan(q.data(), cnt, &bases[m], &bws[m]);
+      words += 4ull * bws[m];
+    }
+    if (words >= (1ull << 24) || nbytes >= (1ull << 32)) return EINVAL;
+    const uint32_t extra_off = uint32_t(align16(payload_off + words * 4));
+    const uint64_t page_bytes = align16(extra_off + nbytes);
+    if (page_off) page_off[p] = off;
+    if (row_prefix) row_prefix[p] = r0 + rows;
+    if (out) {
+      if (off + page_bytes > cap) return ETRUNC;
+      uint8_t* pg = out + off;
+      std::memset(pg, 0, page_bytes);
+      const uint32_t hdr[4] = {kMagic | (uint32_t(STR) << 24), rows, payload_off, extra_off};
+      std::memcpy(pg, hdr, sizeof hdr);
+      uint32_t* pay = reinterpret_cast<uint32_t*>(pg + payload_off);
+      uint32_t woff = 0;
+      for (uint32_t m = 0; m < nmb; ++m) {
+        const uint64_t a = r0 + uint64_t(m) * kMiniBlock;
+        const uint32_t cnt = uint32_t(std::min<uint64_t>(kMiniBlock, r0 + rows - a));
+        for (uint32_t j = 0; j < kMiniBlock; ++j) {
+          const int64_t len = j < cnt ? int64_t(offsets[a + j + 1] - offsets[a + j]) : bases[m];
+          pk[j] = uint32_t(uint64_t(len - bases[m]));
+        }
+        pack_bits(pk.data(), bws[m], pay + woff);
+        uint8_t* h = pg + kPageHeaderBytes + uint64_t(m) * 8;
+        const int32_t b = int32_t(bases[m]);
+        const uint32_t wob = (woff << 8) | bws[m];
+        std::memcpy(h, &b, 4);
+        std::memcpy(h + 4, &wob, 4);
+        std::memcpy(pg + kPageHeaderBytes + uint64_t(nmb) * 8 + uint64_t(m) * 4, &starts[m], 4);
+        woff += 4 * bws[m];
+      }
+      std::memcpy(pg + extra_off, bytes + offsets[r0], offsets[r0 + rows] - offsets[r0]);
+    }
+    off += page_bytes;
+  }
+  if (page_off) page_off[npages] = off;
+  return int64_t(off);
+}
+
+// Decodes a string column back into byte offsets (n+1 entries, starting at
+// 0) and the concatenated bytes (capacity bytes_cap).
+int64_t orc_decode_str(const uint8_t* blob, const uint64_t* page_off, uint64_t npages, uint64_t n,
+                       uint32_t page_rows, uint64_t* offsets, uint8_t* bytes, uint64_t bytes_cap) {
+  uint64_t r = 0, pos = 0;
+  offsets[0] = 0;
+  for (uint64_t p = 0; p < npages; ++p) {
+    const uint8_t* pg = blob + page_off[p];
+    uint32_t hdr[4];
+    std::memcpy(hdr, pg, sizeof hdr);
+    if (hdr[0] != (kMagic | (uint32_t(STR) << 24))) return ECORRUPT;
+    const uint32_t rows = hdr[1];
+    if (rows == 0 || rows > page_rows || r + rows > n) return ECORRUPT;
+    const uint32_t nmb = (rows + kMiniBlock - 1) / kMiniBlock;
+    const uint32_t* pay = reinterpret_cast<const uint32_t*>(pg + hdr[2]);
+    const uint8_t* region = pg + hdr[3];
+    const uint64_t region_bytes = page_off[p + 1] - page_off[p] - hdr[3];
+    for (uint32_t m = 0; m < nmb; ++m) {
+      int32_t base;
+      uint32_t wob, start;
+      std::memcpy(&base, pg + kPageHeaderBytes + uint64_t(m) * 8, 4);
+      std::memcpy(&wob, pg + kPageHeaderBytes + uint64_t(m) * 8 + 4, 4);
+      std::memcpy(&start, pg + kPageHeaderBytes + uint64_t(nmb) * 8 + uint64_t(m) * 4, 4);
+      const uint32_t bw = wob & 0xffu, woff = wob >> 8;
+      if (bw > 32) return ECORRUPT;
+      const uint32_t cnt = std::min<uint32_t>(kMiniBlock, rows - m * kMiniBlock);
+      uint64_t s = start;
+      for (uint32_t j = 0; j < cnt; ++j) {
+        const uint32_t len = uint32_t(base) + unpack_bits(pay + woff, bw, j);
+        if (s + len > region_bytes || pos + len > bytes_cap) return ECORRUPT;
+        std::memcpy(bytes + pos, region + s, len);
+        s += len;
+        pos += len;
+        offsets[r + j + 1] = pos;
+      }
+      r += cnt;
+    }
+  }
+  return r == n ? OK : ECORRUPT;
+}
+
+// ---------------------------------------------------------------------------
+// Query evaluation over decoded columns.
+// ---------------------------------------------------------------------------
+
+enum PredOp : int32_t { LT = 0, LE, GT, GE, EQ, NE, BETWEEN, IN, PREFIX };
+enum AggOp : int32_t { COUNT = 0, SUM, SUM_MUL, SUM_SUB };
+
+struct OrcColumn {          // one decoded column
+  int32_t is_str;
+  const int32_t* v;         // int columns
+  const uint8_t* bytes;     // string columns
+  const uint64_t* offsets;  // n+1 byte offsets
+};
+
+struct OrcTable {
+  uint64_t n;
+  int32_t ncols;
+  const OrcColumn* cols;
+};
+
+struct OrcPred {
+  int32_t col, op, nargs, pfx_len;
+  int64_t args[16];
+  const uint8_t* pfx;
+};
+
+struct OrcJoin {
+  int32_t fk_col;                 // column of the fact table
+  const OrcTable* dim;
+  int32_t key_col;                // column of dim
+  int32_t npreds;
+  const OrcPred* preds;           // on dim
+  int32_t npay;
+  int32_t pay_cols[2];            // columns of dim
+};
+
+struct OrcKey {
+  int32_t kind;                   // 0: fact column, 1: join payload
+  int32_t col, join, field;
+};
+
+struct OrcAgg {
+  int32_t op, a, b;
+};
+
+struct OrcRecord {
+  int32_t key[2];
+  int64_t count;
+  int64_t val[4];
+};
+
+static bool eval_pred(const OrcTable& t, const OrcPred& p, uint64_t r) {
+  const OrcColumn& c = t.cols[p.col];
+  if (p.op == PREFIX) {
+    const uint64_t len = c.offsets[r + 1] - c.offsets[r];
+    if (len < uint64_t(p.pfx_len)) return false;
+    return std::memcmp(c.bytes + c.offsets[r], p.pfx, size_t(p.pfx_len)) == 0;
+  }
+  const int64_t x = c.v[r];
+  switch (p.op) {
+    case LT: return x < p.args[0];
+    case LE: return x <= p.args[0];
+    case GT: return x > p.args[0];
+    case GE: return x >= p.args[0];
+    case EQ: return x == p.args[0];
+    case NE: return x != p.args[0];
+    case BETWEEN: return p.args[0] <= x && x <= p.args[1];
+    case IN:
+      for (int32_t i = 0; i < p.nargs; ++i)
+        if (x == p.args[i]) return true;
+      return false;
+  }
+  return false;
+}
+
+// Evaluates the query.  Writes at most cap records (sorted ascending by key
+// tuple, groups with zero rows omitted, an ungrouped query always yields one
+// record) and returns the number of records, or a negative status.
+int64_t orc_query(const OrcTable* fact, int32_t npreds, const OrcPred* preds, int32_t njoins,
+                  const OrcJoin* joins, int32_t nkeys, const OrcKey* keys, int32_t naggs,
+                  const OrcAgg* aggs, OrcRecord* out, uint64_t cap) {
+  if (njoins > 8 || nkeys > 2 || naggs > 4) return EINVAL;
+  // Build side: key -> payload values of the dimension rows that pass.
+  std::vector<std::unordered_map<int32_t, std::vector<int32_t>>> maps(njoins);
+  for (int32_t j = 0; j < njoins; ++j) {
+    const OrcJoin& J = joins[j];
+    for (uint64_t r = 0; r < J.dim->n; ++r) {
+      bool ok = true;
+      for (int32_t k = 0; k < J.npreds && ok; ++k) ok = eval_pred(*J.dim, J.preds[k], r);
+      if (!ok) continue;
+      std::vector<int32_t> pay;
+      for (int32_t f = 0; f < J.npay; ++f) pay.push_back(J.dim->cols[J.pay_cols[f]].v[r]);
+      const int32_t key = J.dim->cols[J.key_col].v[r];
+      if (!maps[j].emplace(key, pay).second) return EDUPKEY;
+    }
+  }
+  std::map<std::pair<int32_t, int32_t>, OrcRecord> groups;
+  for (uint64_t r = 0; r < fact->n; ++r) {
+    bool ok = true;
+    for (int32_t k = 0; k < npreds && ok; ++k) ok = eval_pred(*fact, preds[k], r);
+    if (!ok) continue;
+    std::vector<const std::vector<int32_t>*> hit(njoins);
+    for (int32_t j = 0; j < njoins && ok; ++j) {
+      auto it = maps[j].find(fact->cols[joins[j].fk_col].v[r]);
+      if (it == maps[j].end()) ok = false; else hit[j] = &it->second;
+    }
+    if (!ok) continue;
+    int32_t kv[2] = {0, 0};
+    for (int32_t k = 0; k < nkeys; ++k)
+      kv[k] = keys[k].kind == 0 ? fact->cols[keys[k].col].v[r] : (*hit[keys[k].join])[keys[k].field];
+    auto ins = groups.emplace(std::make_pair(kv[0], kv[1]), OrcRecord{});
+    OrcRecord& g = ins.first->second;
+    if (ins.second) { g.key[0] = kv[0]; g.key[1] = kv[1]; }
+    g.count += 1;
+    for (int32_t a = 0; a < naggs; ++a) {
+      const int64_t x = aggs[a].op == COUNT ? 0 : int64_t(fact->cols[aggs[a].a].v[r]);
+      const int64_t y = (aggs[a].op == SUM_MUL || aggs[a].op == SUM_SUB) ? int64_t(fact->cols[aggs[a].b].v[r]) : 0;
+      int64_t add = 0;
+      switch (aggs[a].op) {
+        case COUNT: add = 1; break;
+        case SUM: add = x; break;
+        case SUM_MUL: add = int64_t(uint64_t(x) * uint64_t(y)); break;
+        case SUM_SUB: add = x - y; break;
+      }
+      g.val[a] = int64_t(uint64_t(g.val[a]) + uint64_t(add));   // two's-complement wrap
+    }
+  }
+  if (nkeys == 0 && groups.empty()) groups.emplace(std::make_pair(0, 0), OrcRecord{});
+  uint64_t i = 0;
+  for (const auto& kv : groups) {
+    if (i < cap) out[i] = kv.second;
+    ++i;
+  }
+  return int64_t(i);
+}
+
+}  // extern "C"

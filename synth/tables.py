@@ -1,0 +1,356 @@
+"""Seeded table generators and query descriptions for the five workloads.
+
+A *workload* is a plain dict::
+
+    {"name": str,
+     "tables": {table_name: {"rows": int, "page_rows": int,
+                             "cols": {col_name: column}}},
+     "fact": table_name,
+     "query": query}
+
+where a column is either ``{"codec": "for"|"delta"|"dict", "values":
+int32 ndarray}`` or ``{"codec": "str", "bytes": uint8 ndarray, "offsets":
+uint64 ndarray of rows+1}``.  The codec names the storage encoding the
+column is to be loaded with; the generator never encodes anything itself.
+
+A *query* is a description of the SQL it stands for::
+
+    {"preds":  [{"col": c, "op": op, "args": [...]}, ...],   # on the fact table
+     "joins":  [{"fk": c, "dim": t, "key": c,
+                 "preds": [...],                              # on the dimension
+                 "payload": [c, ...]}, ...],                  # dimension columns carried
+     "group":  [{"col": c} | {"join": j, "field": f}, ...],   # <= 2 keys
+     "aggs":   [{"op": "count"} | {"op": "sum", "cols": [a]}
+                | {"op": "sum_mul", "cols": [a, b]}
+                | {"op": "sum_sub", "cols": [a, b]}, ...]}    # <= 4
+
+Predicate ops: ``lt le gt ge eq ne between in prefix`` (``between`` is
+inclusive at both ends; ``prefix`` takes one ``bytes`` argument).
+
+Shapes, sizes and value distributions follow the workloads the method is
+evaluated on: star-schema fact tables with uniform foreign keys into small
+dimensions, a dense date dimension of seven calendar years, low-cardinality
+dimension attributes, Zipf-skewed dictionary keys and short strings over a
+27-symbol alphabet.
+"""
+
+from __future__ import annotations
+
+import datetime
+
+import numpy as np
+
+ALPHABET = np.frombuffer(b"abcdefghijklmnopqrstuvwxyz ", dtype=np.uint8)
+
+DEFAULT_PAGE_ROWS = 65536
+
+
+def _rng(seed):
+    return np.random.default_rng(np.random.SeedSequence(int(seed)))
+
+
+def date_keys(first=datetime.date(1992, 1, 1), days=2556):
+    """yyyymmdd keys of ``days`` consecutive calendar days from ``first``."""
+    out = np.empty(days, dtype=np.int32)
+    d = first
+    one = datetime.timedelta(days=1)
+    for i in range(days):
+        out[i] = d.year * 10000 + d.month * 100 + d.day
+        d += one
+    return out
+
+
+def _int_col(values, codec="for"):
+    return {"codec": codec, "values": np.ascontiguousarray(values, dtype=np.int32)}
+
+
+def _distinct_values(rng, count, lo, hi):
+    """``count`` distinct sorted int32 values drawn from [lo, hi)."""
+    vals = rng.choice(np.arange(lo, hi, dtype=np.int64), size=count, replace=False)
+    return np.sort(vals).astype(np.int32)
+
+
+# ---------------------------------------------------------------------------
+# Workload 1: scan - filter - aggregate over one fact table
+# ---------------------------------------------------------------------------
+
+def scan_filter_aggregate(rows=1 << 20, seed=1, page_rows=DEFAULT_PAGE_ROWS,
+                          a_lt=25, b_lo=1, b_hi=3):
+    """SUM(int64(c) * d) WHERE a < a_lt AND b BETWEEN b_lo AND b_hi."""
+    rng = _rng(seed)
+    cols = {
+        "a": _int_col(rng.integers(1, 51, rows, dtype=np.int32)),
+        "b": _int_col(rng.integers(1, 51, rows, dtype=np.int32)),
+        "c": _int_col(rng.integers(1, 11, rows, dtype=np.int32)),
+        "d": _int_col(rng.integers(900, 105001, rows, dtype=np.int32)),
+    }
+    query = {
+        "preds": [{"col": "a", "op": "lt", "args": [a_lt]},
+                  {"col": "b", "op": "between", "args": [b_lo, b_hi]}],
+        "joins": [],
+        "group": [],
+        "aggs": [{"op": "sum_mul", "cols": ["c", "d"]}],
+    }
+    return {"name": f"scan_filter_aggregate_{rows}",
+            "tables": {"fact": {"rows": rows, "page_rows": page_rows, "cols": cols}},
+            "fact": "fact", "query": query}
+
+
+# ---------------------------------------------------------------------------
+# Workload 2: star join, 4 dimensions, group by (dimension attribute, year)
+# ---------------------------------------------------------------------------
+
+def _star_dimensions(rng, dim_rows=(2000, 30000, 200000), page_rows=DEFAULT_PAGE_ROWS):
+    n1, n2, n3 = dim_rows
+    a1_vals = _distinct_values(rng, 10, 0, 1000)
+    a2_vals = _distinct_values(rng, 25, 0, 1000)
+    a3_vals = _distinct_values(rng, 25, 0, 1000)
+    b3_vals = _distinct_values(rng, 5, 0, 100)
+    dims = {
+        "dim1": {"rows": n1, "page_rows": page_rows, "cols": {
+            "k": _int_col(rng.permutation(np.arange(1, n1 + 1, dtype=np.int32))),
+            "A1": _int_col(a1_vals[rng.integers(0, 10, n1)], "dict"),
+        }},
+        "dim2": {"rows": n2, "page_rows": page_rows, "cols": {
+            "k": _int_col(rng.permutation(np.arange(1, n2 + 1, dtype=np.int32))),
+            "A2": _int_col(a2_vals[rng.integers(0, 25, n2)], "dict"),
+        }},
+        "dim3": {"rows": n3, "page_rows": page_rows, "cols": {
+            "k": _int_col(rng.permutation(np.arange(1, n3 + 1, dtype=np.int32))),
+            "A3": _int_col(a3_vals[rng.integers(0, 25, n3)], "dict"),
+            "B3": _int_col(b3_vals[rng.integers(0, 5, n3)], "dict"),
+        }},
+    }
+    dk = date_keys()
+    perm = rng.permutation(dk.size)
+    dims["date"] = {"rows": int(dk.size), "page_rows": page_rows, "cols": {
+        "k": _int_col(dk[perm]),
+        "year": _int_col((dk[perm] // 10000).astype(np.int32), "dict"),
+    }}
+    attrs = {"A1": a1_vals, "A2": a2_vals, "A3": a3_vals, "B3": b3_vals}
+    return dims, attrs
+
+
+def _star_query(rng, attrs):
+    v1 = int(attrs["A1"][rng.integers(0, attrs["A1"].size)])
+    v2 = int(attrs["A2"][rng.integers(0, attrs["A2"].size)])
+    i3 = int(rng.integers(0, attrs["A3"].size - 1))
+    return {
+        "preds": [],
+        "joins": [
+            {"fk": "fk1", "dim": "dim1", "key": "k",
+             "preds": [{"col": "A1", "op": "eq", "args": [v1]}], "payload": []},
+            {"fk": "fk2", "dim": "dim2", "key": "k",
+             "preds": [{"col": "A2", "op": "eq", "args": [v2]}], "payload": []},
+            {"fk": "fk3", "dim": "dim3", "key": "k",
+             "preds": [{"col": "A3", "op": "in",
+                        "args": [int(attrs["A3"][i3]), int(attrs["A3"][i3 + 1])]}],
+             "payload": ["B3"]},
+            {"fk": "fkd", "dim": "date", "key": "k", "preds": [], "payload": ["year"]},
+        ],
+        "group": [{"join": 2, "field": 0}, {"join": 3, "field": 0}],
+        "aggs": [{"op": "sum", "cols": ["m1"]}],
+    }
+
+
+def star_join(rows=1 << 26, seed=2, page_rows=DEFAULT_PAGE_ROWS, clustered=True,
+              dim_rows=(2000, 30000, 200000)):
+    """Fact table with 4 uniform foreign keys and 2 measures, 4 dimensions.
+
+    Filters three dimensions (10 %, 4 %, 8 %), joins all four and groups by
+    (dim3.B3, date.year) computing SUM(int64 m1).  With ``clustered`` the
+    fact rows are ordered by date key (a sorted load) and the date key is
+    stored delta-coded; otherwise it is stored frame-of-reference coded.
+    """
+    rng = _rng(seed)
+    dims, attrs = _star_dimensions(rng, dim_rows, page_rows)
+    dk = np.sort(dims["date"]["cols"]["k"]["values"])
+    n1, n2, n3 = dim_rows
+    fk1 = rng.integers(1, n1 + 1, rows, dtype=np.int32)
+    fk2 = rng.integers(1, n2 + 1, rows, dtype=np.int32)
+    fk3 = rng.integers(1, n3 + 1, rows, dtype=np.int32)
+    fkd = dk[rng.integers(0, dk.size, rows)]
+    m1 = rng.integers(1, 10_000_000, rows, dtype=np.int32)
+    m2 = rng.integers(1, 100_000, rows, dtype=np.int32)
+    if clustered:
+        order = np.argsort(fkd, kind="stable")
+        fk1, fk2, fk3, fkd, m1, m2 = (x[order] for x in (fk1, fk2, fk3, fkd, m1, m2))
+    fact = {"rows": rows, "page_rows": page_rows, "cols": {
+        "fk1": _int_col(fk1), "fk2": _int_col(fk2), "fk3": _int_col(fk3),
+        "fkd": _int_col(fkd, "delta" if clustered else "for"),
+        "m1": _int_col(m1), "m2": _int_col(m2),
+    }}
+    tables = dict(dims)
+    tables["fact"] = fact
+    return {"name": f"star_join_{rows}{'_clustered' if clustered else ''}",
+            "tables": tables, "fact": "fact", "query": _star_query(rng, attrs)}
+
+
+# ---------------------------------------------------------------------------
+# Workload 3: variable-length strings, prefix filter, Zipf dictionary key
+# ---------------------------------------------------------------------------
+
+def _zipf_codes(rng, rows, n_keys=1024, s=1.1):
+    """Ranks 0..n_keys-1 with P(rank k) proportional to (k+1)^-s (inverse CDF)."""
+    w = np.arange(1, n_keys + 1, dtype=np.float64) ** (-s)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    u = rng.random(rows)
+    return np.minimum(np.searchsorted(cdf, u, side="right"), n_keys - 1)
+
+
+def random_strings(rng, rows, min_len=10, max_len=44):
+    lengths = rng.integers(min_len, max_len + 1, rows, dtype=np.int64)
+    offsets = np.zeros(rows + 1, dtype=np.uint64)
+    np.cumsum(lengths, out=offsets[1:])
+    total = int(offsets[-1])
+    data = ALPHABET[rng.integers(0, ALPHABET.size, total, dtype=np.uint8)]
+    return np.ascontiguousarray(data), offsets
+
+
+def strings(rows=1 << 25, seed=3, page_rows=DEFAULT_PAGE_ROWS, prefix=b"q",
+            n_keys=1024):
+    """COUNT(*), SUM(int64 m) WHERE s LIKE 'prefix%' GROUP BY key."""
+    rng = _rng(seed)
+    data, offsets = random_strings(rng, rows)
+    key_values = rng.choice(np.arange(-32768, 32768, dtype=np.int32), size=n_keys,
+                            replace=False).astype(np.int32)
+    key = key_values[_zipf_codes(rng, rows, n_keys)]
+    m = rng.integers(1, 1_000_001, rows, dtype=np.int32)
+    fact = {"rows": rows, "page_rows": page_rows, "cols": {
+        "s": {"codec": "str", "bytes": data, "offsets": offsets},
+        "key": _int_col(key, "dict"),
+        "m": _int_col(m),
+    }}
+    query = {
+        "preds": [{"col": "s", "op": "prefix", "args": [bytes(prefix)]}],
+        "joins": [],
+        "group": [{"col": "key"}],
+        "aggs": [{"op": "count"}, {"op": "sum", "cols": ["m"]}],
+    }
+    return {"name": f"strings_{rows}", "tables": {"fact": fact}, "fact": "fact",
+            "query": query}
+
+
+# ---------------------------------------------------------------------------
+# Workload 4: a batch of queries of the three shapes over uneven tables
+# ---------------------------------------------------------------------------
+
+def batched_workloads(n_queries=64, seed=4, log2_lo=16.0, log2_hi=26.0,
+                      page_rows=DEFAULT_PAGE_ROWS, max_rows=None):
+    """``n_queries`` workloads; shape uniform over the three above, fact rows
+    round(2^U(log2_lo, log2_hi)), predicate constants drawn per query."""
+    rng = _rng(seed)
+    out = []
+    for q in range(n_queries):
+        shape = int(rng.integers(1, 4))
+        rows = int(round(2.0 ** rng.uniform(log2_lo, log2_hi)))
+        if max_rows is not None:
+            rows = min(rows, int(max_rows))
+        sub_seed = int(rng.integers(1, 2**31))
+        if shape == 1:
+            sub = _rng(sub_seed)
+            w = scan_filter_aggregate(rows, sub_seed, page_rows,
+                                      a_lt=int(sub.integers(2, 50)),
+                                      b_lo=int(sub.integers(1, 10)),
+                                      b_hi=int(sub.integers(10, 20)))
+        elif shape == 2:
+            w = star_join(rows, sub_seed, page_rows, clustered=bool(rng.integers(0, 2)))
+        else:
+            sub = _rng(sub_seed)
+            pfx = bytes(ALPHABET[sub.integers(0, ALPHABET.size, int(sub.integers(1, 3)))])
+            w = strings(rows, sub_seed, page_rows, prefix=pfx)
+        w["name"] = f"q{q:02d}_{w['name']}"
+        out.append(w)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Small random workloads for property tests
+# ---------------------------------------------------------------------------
+
+def tiny_random_workload(seed, rows=None, page_rows=None):
+    """A random small star-join-with-strings workload mixing every operator.
+
+    Values are drawn with ranges that exercise bit widths 0..32, negative
+    numbers, ragged tails and empty results.
+    """
+    rng = _rng(1000 + seed)
+    if page_rows is None:
+        page_rows = int(rng.choice([128, 256, 1024, 4096]))
+    if rows is None:
+        rows = int(rng.integers(1, 6 * page_rows))
+    spans = [(0, 1), (0, 2), (-5, 5), (1, 50), (-(2**31), 2**31 - 1), (900, 105001)]
+
+    def draw(n):
+        lo, hi = spans[int(rng.integers(0, len(spans)))]
+        return rng.integers(lo, hi, n, dtype=np.int64, endpoint=True).astype(np.int32)
+
+    nd = int(rng.integers(1, 300))
+    dim = {"rows": nd, "page_rows": page_rows, "cols": {
+        "k": _int_col(rng.permutation(np.arange(1, nd + 1, dtype=np.int32))),
+        "A": _int_col(rng.integers(0, 7, nd, dtype=np.int32) * 3 - 4, "dict"),
+        "B": _int_col(rng.integers(0, 4, nd, dtype=np.int32) + 100, "dict"),
+    }}
+    data, offsets = random_strings(rng, rows, 0, int(rng.integers(1, 12)))
+    fk = rng.integers(1, nd + 2, rows, dtype=np.int32)  # nd+1 never matches
+    x = draw(rows)
+    y = draw(rows)
+    g = rng.integers(0, 5, rows, dtype=np.int32) * 7 - 10
+    clustered = bool(rng.integers(0, 2))
+    if clustered:
+        order = np.argsort(fk, kind="stable")
+        fk, x, y, g = fk[order], x[order], y[order], g[order]
+        starts = offsets[:-1][order]
+        lens = (offsets[1:] - offsets[:-1])[order]
+        new_off = np.zeros(rows + 1, dtype=np.uint64)
+        np.cumsum(lens, out=new_off[1:])
+        data = np.concatenate([data[int(s):int(s + l)] for s, l in zip(starts, lens)]
+                              or [np.zeros(0, np.uint8)]).astype(np.uint8)
+        offsets = new_off
+    fact = {"rows": rows, "page_rows": page_rows, "cols": {
+        "fk": _int_col(fk, "delta" if clustered else "for"),
+        "x": _int_col(x, "for"),
+        "y": _int_col(y, "delta" if rng.integers(0, 2) else "for"),
+        "g": _int_col(g, "dict"),
+        "s": {"codec": "str", "bytes": data, "offsets": offsets},
+    }}
+    ops = ["lt", "le", "gt", "ge", "eq", "ne", "between", "in"]
+    preds = []
+    for _ in range(int(rng.integers(0, 3))):
+        col = str(rng.choice(["x", "y", "g"]))
+        op = str(rng.choice(ops))
+        src = fact["cols"][col]["values"]
+        pick = lambda: int(src[int(rng.integers(0, rows))])  # noqa: E731
+        if op == "between":
+            lo, hi = sorted((pick(), pick()))
+            args = [lo, hi]
+        elif op == "in":
+            args = [pick() for _ in range(int(rng.integers(1, 5)))]
+        else:
+            args = [pick()]
+        preds.append({"col": col, "op": op, "args": args})
+    if rng.integers(0, 2):
+        plen = int(rng.integers(0, 3))
+        preds.append({"col": "s", "op": "prefix",
+                      "args": [bytes(ALPHABET[rng.integers(0, 27, plen)])]})
+    joins = []
+    group = []
+    if rng.integers(0, 2):
+        dpreds = []
+        if rng.integers(0, 2):
+            dpreds.append({"col": "A", "op": "le", "args": [int(rng.integers(-4, 15))]})
+        joins.append({"fk": "fk", "dim": "dim", "key": "k", "preds": dpreds,
+                      "payload": ["B", "A"]})
+        if rng.integers(0, 2):
+            group.append({"join": 0, "field": int(rng.integers(0, 2))})
+    if rng.integers(0, 2):
+        group.append({"col": "g"})
+    aggs = [{"op": "count"}]
+    for _ in range(int(rng.integers(0, 4))):
+        op = str(rng.choice(["sum", "sum_mul", "sum_sub"]))
+        cols = ["x"] if op == "sum" else [str(rng.choice(["x", "y"])), str(rng.choice(["x", "y"]))]
+        aggs.append({"op": op, "cols": cols})
+    query = {"preds": preds, "joins": joins, "group": group, "aggs": aggs}
+    return {"name": f"tiny_{seed}", "tables": {"fact": fact, "dim": dim},
+            "fact": "fact", "query": query}
