@@ -1,0 +1,284 @@
+/*
+ * dpf.h -- C ABI of the GB300 fused columnar query library.
+ *
+ * The library implements the data path of Data Path Fusion (arxiv 2605.10511):
+ * compressed columnar pages are taken through decompression, predicates,
+ * hash-join probes and hash aggregation inside ONE persistent GPU kernel per
+ * query batch, without materialising intermediates in global memory and
+ * without host intervention during execution (Sec. 3.1, Sec. 3.2).
+ *
+ * Conventions for every call:
+ *   - Return value: 0 (DPF_OK) or a negative dpf_status.  No C++ exception
+ *     crosses the ABI.  After an error, dpf_last_error() returns a message
+ *     (thread-local, valid until the next call on the same thread).
+ *   - Pointers named `host` are host memory, `device` are device memory;
+ *     `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - The library never frees or retains caller memory: inputs are copied
+ *     or consumed before the call returns (asynchronous calls copy what they
+ *     need at call time).
+ *   - A context is bound to one CUDA device.  Calls on one context are
+ *     serialised by an internal mutex; objects are not shared across
+ *     contexts.
+ */
+#ifndef DPF_H
+#define DPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+typedef int32_t dpf_status;
+#define DPF_OK 0
+#define DPF_EINVAL (-1)     /* bad argument, unknown id, type mismatch         */
+#define DPF_ENOMEM (-2)     /* allocation failed or the memory budget is spent */
+#define DPF_ECUDA (-3)      /* a CUDA runtime call failed                      */
+#define DPF_EDUPKEY (-4)    /* duplicate key in a hash-table build             */
+#define DPF_EBUSY (-5)      /* admission refused (serving)                     */
+#define DPF_ETIMEOUT (-6)   /* result not ready within the timeout             */
+#define DPF_ETRUNC (-7)     /* caller buffer too small; *n_out = needed count  */
+#define DPF_ENOTFOUND (-8)  /* unknown or already fetched query id             */
+#define DPF_ECORRUPT (-9)   /* a page or mini block header failed validation   */
+#define DPF_EINTERNAL (-10) /* device-side invariant violated (bounded probe)  */
+
+typedef struct dpf_ctx dpf_ctx;
+typedef int32_t dpf_col_id;
+typedef int32_t dpf_ht_id;
+typedef int64_t dpf_query_id;
+typedef int32_t dpf_prep_id;
+
+/* Thread-local description of the last error on this thread. */
+const char* dpf_last_error(void);
+
+/* ----------------------------------------------------------- context */
+/* Device-memory hooks (e.g. a framework's caching allocator).  alloc must
+ * return 256-byte aligned device memory usable from any stream of the
+ * context's device, or NULL on failure.  NULL hooks = cudaMalloc/cudaFree. */
+typedef struct dpf_alloc_hooks {
+  void* (*alloc)(uint64_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} dpf_alloc_hooks;
+
+/* Creates a context on `device`.  hbm_budget caps the device bytes the
+ * context may hold (0 = no cap); allocations beyond it fail with
+ * DPF_ENOMEM (Sec. 4.3: the build side must fit in GPU memory). */
+dpf_status dpf_create(dpf_ctx** out, int32_t device, uint64_t hbm_budget,
+                      const dpf_alloc_hooks* hooks);
+/* Waits for the context's work, frees every object it owns. */
+dpf_status dpf_destroy(dpf_ctx* ctx);
+/* Device bytes currently held by the context. */
+dpf_status dpf_memory_used(dpf_ctx* ctx, uint64_t* bytes);
+
+/* ----------------------------------------------------------- columns */
+/* Storage encodings (Sec. 3.4, Sec. 4.1).  Every encoding splits a column
+ * into pages of `page_rows` rows and pages into mini blocks of 128 values,
+ * each mini block preceded by metadata {FOR base, bit width, offset}
+ * (Sec. 3.4.1).  Page byte layout: see the storage-format section of the
+ * repository's design notes; it is identical for host and device. */
+enum dpf_codec {
+  DPF_CODEC_FOR = 1,   /* int32: frame of reference + bit packing (GPU-FOR)          */
+  DPF_CODEC_DELTA = 2, /* int32: deltas of consecutive rows, FOR-packed (sorted keys) */
+  DPF_CODEC_DICT = 3,  /* int32 with <= 65536 distinct values: sorted dictionary,
+                          FOR-packed ranks (Sec. 3.4.1, short CHAR as integers)       */
+  DPF_CODEC_STR = 4    /* bytes: FOR-packed lengths + per-mini-block start + raw bytes
+                          (Sec. 3.4.2 variable-length page)                           */
+};
+/* Where a column's pages live: device HBM, or pinned host memory read by
+ * the kernel directly through the host link (oversize tables). */
+enum dpf_placement { DPF_PLACE_DEVICE = 0, DPF_PLACE_HOST_PINNED = 1 };
+
+typedef struct dpf_column_desc {
+  int32_t codec;      /* enum dpf_codec                                           */
+  int32_t placement;  /* enum dpf_placement                                       */
+  uint32_t page_rows; /* rows per page: multiple of 128 in [128, 2^20]; 0 = 65536 */
+  int32_t table;      /* caller's table id: columns scanned together by one plan
+                         must share table, row count and page_rows                */
+} dpf_column_desc;
+
+/* Host-side encoder (the data loader of Sec. 4.2), no device work.
+ *   values: host int32[nrows] (FOR/DELTA/DICT) or host bytes (STR)
+ *   str_offsets: host uint64[nrows+1] byte offsets into values (STR only,
+ *                str_offsets[0] may be non-zero), else NULL
+ *   out: host buffer of `cap` bytes for the page images, or NULL to size
+ *   page_off: host uint64[npages+1] (npages = ceil(nrows/page_rows)), filled
+ *   row_prefix: host uint64[npages] RID index (cumulative rows, Sec. 3.4.2)
+ *   dict/dict_cap/dict_n: DICT only: sorted distinct values (may be NULL
+ *                to size), *dict_n receives their count
+ *   size_out: receives the encoded byte size
+ * Errors: DPF_EINVAL (nrows = 0, bad codec/page_rows, > 65536 distinct for
+ * DICT, a page too large for the format), DPF_ETRUNC (cap or dict_cap too
+ * small; *size_out / *dict_n hold the needed sizes). */
+dpf_status dpf_encode_column(const dpf_column_desc* desc, const void* values,
+                             const uint64_t* str_offsets, uint64_t nrows, uint8_t* out,
+                             uint64_t cap, uint64_t* page_off, uint64_t* row_prefix,
+                             int32_t* dict, uint64_t dict_cap, uint64_t* dict_n,
+                             uint64_t* size_out);
+
+/* Uploads already encoded pages (host memory, layout as produced by
+ * dpf_encode_column) to the column's placement; validates every page header.
+ * Errors: DPF_EINVAL, DPF_ECORRUPT (bad page), DPF_ENOMEM, DPF_ECUDA. */
+dpf_status dpf_load_encoded(dpf_ctx* ctx, const dpf_column_desc* desc, const uint8_t* pages,
+                            uint64_t size, const uint64_t* page_off, const uint64_t* row_prefix,
+                            uint64_t nrows, const int32_t* dict, uint64_t dict_n,
+                            dpf_col_id* out);
+
+/* Encodes on the host (dpf_encode_column) and uploads (dpf_load_encoded).
+ * The caller keeps ownership of `values` / `str_offsets`. */
+dpf_status dpf_load_column(dpf_ctx* ctx, const dpf_column_desc* desc, const void* values,
+                           const uint64_t* str_offsets, uint64_t nrows, dpf_col_id* out);
+
+/* Rows, encoded bytes (page images) and raw bytes (4/row, or string bytes
+ * + 8/row of offsets) of a loaded column; any out pointer may be NULL. */
+dpf_status dpf_column_info(dpf_ctx* ctx, dpf_col_id col, uint64_t* rows,
+                           uint64_t* encoded_bytes, uint64_t* raw_bytes);
+
+/* Copies `bytes` of a column's page images starting at byte `offset` back
+ * to host memory (inspection and tests). */
+dpf_status dpf_column_read(dpf_ctx* ctx, dpf_col_id col, uint64_t offset, uint64_t bytes,
+                           uint8_t* host_out);
+
+dpf_status dpf_drop_column(dpf_ctx* ctx, dpf_col_id col);
+
+/* --------------------------------------------------------- predicates */
+enum dpf_op {
+  DPF_OP_LT = 0, DPF_OP_LE = 1, DPF_OP_GT = 2, DPF_OP_GE = 3, DPF_OP_EQ = 4,
+  DPF_OP_NE = 5,
+  DPF_OP_BETWEEN = 6, /* v[0] <= x <= v[1], both ends inclusive                 */
+  DPF_OP_IN = 7,      /* x in {v[0..n)}, 1 <= n <= DPF_MAX_IN                     */
+  DPF_OP_PREFIX = 8   /* STR: string starts with prefix[0..prefix_len); a prefix
+                         longer than the string does not match; an empty prefix
+                         matches every row (Sec. 4.1 variable-length scan)        */
+};
+#define DPF_MAX_IN 8
+#define DPF_MAX_PREFIX 32
+
+typedef struct dpf_pred {
+  dpf_col_id col;          /* column of the scanned table                          */
+  int32_t op;              /* enum dpf_op                                          */
+  int32_t n;               /* IN: number of operands                               */
+  int32_t prefix_len;      /* PREFIX: 0..DPF_MAX_PREFIX                            */
+  int64_t v[DPF_MAX_IN];   /* operands, compared with the int32 value as int64;
+                              for DICT columns they are dictionary values          */
+  uint8_t prefix[DPF_MAX_PREFIX];
+} dpf_pred;
+
+/* --------------------------------------------------------- hash tables */
+/* Kernel #1 of Sec. 3.1: scans a dimension table's key column and payload
+ * columns, keeps the rows passing every predicate (conjunction) and inserts
+ * key -> payload into an open-addressing hash table in device memory.
+ *   key_col: FOR, DELTA or DICT column; keys must be unique among the rows
+ *            kept and differ from INT32_MIN
+ *   payload_cols: 0..2 DICT columns of the same table; field f of a probe hit
+ *            is the dictionary code of payload_cols[f]
+ * Asynchronous on `stream` except for one device-to-host read of the kept
+ * row count (the table is sized from it).  Errors: DPF_EINVAL,
+ * DPF_EDUPKEY, DPF_ENOMEM, DPF_ECUDA. */
+dpf_status dpf_build_hash(dpf_ctx* ctx, dpf_col_id key_col, const dpf_col_id* payload_cols,
+                          int32_t n_payload, const dpf_pred* preds, int32_t n_preds,
+                          void* stream, dpf_ht_id* out);
+/* Entries and slot capacity of a built table. */
+dpf_status dpf_hash_info(dpf_ctx* ctx, dpf_ht_id ht, uint64_t* entries, uint64_t* capacity);
+dpf_status dpf_drop_hash(dpf_ctx* ctx, dpf_ht_id ht);
+
+/* ---------------------------------------------------------------- plans */
+/* One pipeline ending in hash aggregation (Kernel #3 of Sec. 3.1):
+ *   SELECT keys, COUNT(*), aggs FROM fact JOIN dims WHERE preds GROUP BY keys
+ * All fact columns named by a plan belong to one table.  Aggregates are
+ * int64 over sign-extended int32 inputs (Sec. 4.3), wrapping on overflow. */
+typedef struct dpf_join {
+  dpf_col_id fk_col; /* fact column probed (FOR/DELTA/DICT)  */
+  dpf_ht_id ht;      /* table built by dpf_build_hash        */
+} dpf_join;
+
+enum dpf_key_kind { DPF_KEY_COLUMN = 0, DPF_KEY_PAYLOAD = 1 };
+typedef struct dpf_key {
+  int32_t kind;      /* DPF_KEY_COLUMN: fact DICT column `col`;
+                        DPF_KEY_PAYLOAD: field `field` of join `join`      */
+  dpf_col_id col;
+  int32_t join;
+  int32_t field;
+} dpf_key;
+
+enum dpf_agg_op {
+  DPF_AGG_COUNT = 0,   /* COUNT(*)              */
+  DPF_AGG_SUM = 1,     /* SUM(int64 a)          */
+  DPF_AGG_SUM_MUL = 2, /* SUM(int64 a * b)      */
+  DPF_AGG_SUM_SUB = 3  /* SUM(int64 a - b)      */
+};
+typedef struct dpf_agg {
+  int32_t op;
+  dpf_col_id a, b;     /* FOR/DELTA columns of the fact table (b unused for SUM) */
+} dpf_agg;
+
+#define DPF_MAX_PREDS 8
+#define DPF_MAX_JOINS 4
+#define DPF_MAX_KEYS 2
+#define DPF_MAX_AGGS 4
+#define DPF_MAX_GROUPS 65536  /* product of the key dictionary sizes */
+
+typedef struct dpf_plan {
+  int32_t n_preds;  const dpf_pred* preds;  /* on fact columns, conjunction */
+  int32_t n_joins;  const dpf_join* joins;  /* inner equi-joins, in order   */
+  int32_t n_keys;   const dpf_key* keys;    /* group keys, <= 2             */
+  int32_t n_aggs;   const dpf_agg* aggs;    /* <= 4                         */
+} dpf_plan;
+
+/* Launch configuration; 0 in a field = chosen by the library (tuning cache,
+ * then defaults). */
+enum dpf_ht_place { DPF_HT_AUTO = 0, DPF_HT_SMEM = 1, DPF_HT_GLOBAL = 2 };
+typedef struct dpf_tuning {
+  uint32_t chunk_rows;   /* rows per scheduling chunk: multiple of 2048          */
+  uint32_t threads;      /* threads per CTA: 128, 256 or 512                      */
+  int32_t ht_placement;  /* enum dpf_ht_place                                     */
+  uint32_t ctas_per_sm;  /* persistent CTAs per SM                                */
+} dpf_tuning;
+
+/* Result record: keys are dictionary values (0 when unused); count = rows
+ * in the group; val[i] = aggregate i (COUNT repeats count). */
+typedef struct dpf_record {
+  int32_t key[2];
+  int64_t count;
+  int64_t val[4];
+} dpf_record;
+
+/* Prepares a batch of n plans for repeated launches: validates them,
+ * compiles them to the device plan format, allocates accumulators and
+ * result buffers.  Errors: DPF_EINVAL (type mismatch, unknown id, a group
+ * domain above DPF_MAX_GROUPS), DPF_ENOMEM, DPF_ECUDA. */
+dpf_status dpf_prepare(dpf_ctx* ctx, const dpf_plan* plans, int32_t n, const dpf_tuning* tuning,
+                       dpf_prep_id* out);
+/* Enqueues ONE persistent fused kernel for all plans of the batch on
+ * `stream` (no host synchronisation, capturable into a CUDA graph).  The
+ * kernel leaves its scratch state zeroed, so launches can be replayed. */
+dpf_status dpf_launch(dpf_ctx* ctx, dpf_prep_id prep, void* stream);
+/* Captures dpf_launch into a CUDA graph owned by the prepared batch;
+ * dpf_launch_graph replays it on `stream`. */
+dpf_status dpf_capture_graph(dpf_ctx* ctx, dpf_prep_id prep, void* stream);
+dpf_status dpf_launch_graph(dpf_ctx* ctx, dpf_prep_id prep, void* stream);
+/* Waits (up to timeout_ms; < 0 = forever) for the last launch of `prep`
+ * and copies query i's records, ascending by key tuple, to host `buf`.
+ * DPF_ETRUNC if cap < needed (*n_out = needed).  Device status words turn
+ * into DPF_ECORRUPT / DPF_EINTERNAL. */
+dpf_status dpf_read_result(dpf_ctx* ctx, dpf_prep_id prep, int32_t i, dpf_record* buf,
+                           uint64_t cap, uint64_t* n_out, int32_t timeout_ms);
+/* Tuning the batch will launch with (after defaults and cache lookup). */
+dpf_status dpf_prep_tuning(dpf_ctx* ctx, dpf_prep_id prep, dpf_tuning* out);
+dpf_status dpf_release(dpf_ctx* ctx, dpf_prep_id prep);
+
+/* One-shot form (Sec. 3.1): prepare + launch on `stream`; out_ids[i]
+ * names plan i's result.  n > 1 runs every plan in one persistent launch. */
+dpf_status dpf_execute_plan(dpf_ctx* ctx, const dpf_plan* plans, int32_t n, void* stream,
+                            dpf_query_id* out_ids);
+/* Blocks up to timeout_ms for a query of dpf_execute_plan and copies its
+ * records (the "record format returned to the host" of Sec. 3.1).  On
+ * DPF_ETRUNC nothing is consumed; on success the id is freed. */
+dpf_status dpf_fetch_result(dpf_ctx* ctx, dpf_query_id id, dpf_record* buf, uint64_t cap,
+                            uint64_t* n_out, int32_t timeout_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPF_H */

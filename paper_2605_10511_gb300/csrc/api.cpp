@@ -1,0 +1,1082 @@
+// Host side of the C ABI: context and memory accounting, column loading and
+// page validation, the plan compiler (SQL-like plan -> device steps), hash
+// builds and the prepared-batch launch / result path.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "dpf_internal.h"
+#include "host_common.h"
+#include "kernels.h"
+
+namespace dpf {
+
+static thread_local std::string t_last_error;
+
+dpf_status fail(dpf_status st, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return st;
+}
+
+unsigned host_threads() {
+  const unsigned n = std::thread::hardware_concurrency();
+  return std::max(1u, std::min(n == 0 ? 4u : n, 32u));
+}
+
+}  // namespace dpf
+
+using namespace dpf;
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess) return fail(DPF_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct Column {
+  int32_t id = 0, codec = 0, placement = 0, table = 0;
+  uint32_t page_rows = 0;
+  uint64_t nrows = 0, npages = 0, bytes = 0, raw_bytes = 0;
+  uint8_t* blob = nullptr;        // address the kernel reads (device or mapped host)
+  uint8_t* host_blob = nullptr;   // pinned host allocation (HOST_PINNED)
+  uint64_t* d_page_off = nullptr;
+  int32_t* d_dict = nullptr;
+  std::vector<uint64_t> page_off, row_prefix;
+  std::vector<int32_t> dict;
+};
+
+struct HashTable {
+  int32_t id = 0, table = 0, npay = 0;
+  uint2* slots = nullptr;
+  uint32_t capacity = 0;
+  uint64_t entries = 0;
+  uint32_t pay_dom[2] = {0, 0};
+  const int32_t* pay_dict[2] = {nullptr, nullptr};
+};
+
+struct Prep {
+  int32_t id = 0;
+  int nq = 0;
+  std::vector<DevQuery> hq;
+  DevQuery* dq = nullptr;
+  uint64_t* dqbegin = nullptr;
+  Sched* sched = nullptr;
+  uint8_t* scratch = nullptr;     // accumulators, counters, outputs of all queries
+  FusedLaunch L{};
+  dpf_tuning tuning{};
+  cudaEvent_t ev = nullptr;
+  bool launched = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool oneshot = false;
+  std::vector<char> fetched;
+};
+
+struct dpf_ctx {
+  int device = 0;
+  uint64_t budget = 0, used = 0;
+  dpf_alloc_hooks hooks{};
+  bool has_hooks = false;
+  std::recursive_mutex mu;
+  std::map<void*, uint64_t> dev_sizes;
+  std::map<int32_t, Column> cols;
+  std::map<int32_t, HashTable> hts;
+  std::map<int32_t, std::unique_ptr<Prep>> preps;
+  int32_t next_col = 1, next_ht = 1, next_prep = 1;
+  cudaStream_t io = nullptr;      // private non-blocking stream for copies
+  Sched* bsched = nullptr;        // status word of hash builds
+  unsigned long long* bcount = nullptr;
+  int num_sms = 0;
+  int smem_optin = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+dpf_status dev_alloc(dpf_ctx* c, uint64_t bytes, void** out) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~uint64_t(255);
+  if (c->budget && c->used + bytes > c->budget)
+    return fail(DPF_ENOMEM, "device budget exceeded: %llu used + %llu > %llu", (unsigned long long)c->used,
+                (unsigned long long)bytes, (unsigned long long)c->budget);
+  void* p = nullptr;
+  if (c->has_hooks) {
+    p = c->hooks.alloc(bytes, c->hooks.user);
+    if (!p) return fail(DPF_ENOMEM, "allocation hook failed for %llu bytes", (unsigned long long)bytes);
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DPF_ENOMEM, "cudaMalloc(%llu): %s", (unsigned long long)bytes, cudaGetErrorString(e));
+    }
+  }
+  c->dev_sizes[p] = bytes;
+  c->used += bytes;
+  *out = p;
+  return DPF_OK;
+}
+
+void dev_free(dpf_ctx* c, void* p) {
+  if (!p) return;
+  auto it = c->dev_sizes.find(p);
+  if (it == c->dev_sizes.end()) return;
+  c->used -= it->second;
+  c->dev_sizes.erase(it);
+  if (c->has_hooks) c->hooks.free(p, c->hooks.user);
+  else cudaFree(p);
+}
+
+template <class T>
+dpf_status dev_alloc_t(dpf_ctx* c, uint64_t count, T** out) {
+  void* p;
+  dpf_status st = dev_alloc(c, count * sizeof(T), &p);
+  *out = static_cast<T*>(p);
+  return st;
+}
+
+dpf_status upload(dpf_ctx* c, void* dst, const void* src, uint64_t bytes) {
+  CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->io));
+  CUDA_TRY(cudaStreamSynchronize(c->io));
+  return DPF_OK;
+}
+
+void free_column(dpf_ctx* c, Column& col) {
+  if (col.placement == DPF_PLACE_HOST_PINNED) {
+    if (col.host_blob) cudaFreeHost(col.host_blob);
+  } else {
+    dev_free(c, col.blob);
+  }
+  dev_free(c, col.d_page_off);
+  dev_free(c, col.d_dict);
+  col.blob = col.host_blob = nullptr;
+}
+
+// ---------------------------------------------------------------- validation
+inline uint32_t rd32(const uint8_t* p) {
+  uint32_t x;
+  std::memcpy(&x, p, 4);
+  return x;
+}
+
+// Checks every page and mini block header so that the kernels can trust
+// offsets and widths (they still guard bit widths and group ids).
+dpf_status validate_pages(uint32_t codec, const uint8_t* pages, uint64_t size, const uint64_t* page_off,
+                          uint64_t npages, uint64_t nrows, uint32_t P, uint64_t dict_n) {
+  if (page_off[0] != 0 || page_off[npages] != size) return fail(DPF_ECORRUPT, "page_off does not span the pages");
+  bool bad = false;
+  uint64_t bad_page = 0;
+  std::mutex m;
+  parallel_for(npages, [&](uint64_t p) {
+    auto flag = [&] {
+      std::lock_guard<std::mutex> g(m);
+      if (!bad || p < bad_page) bad_page = p;
+      bad = true;
+    };
+    const uint64_t a = page_off[p], b = page_off[p + 1];
+    if (a % 16 || b < a || b - a < kPageHdr || b > size) return flag();
+    const uint8_t* pg = pages + a;
+    const uint64_t pbytes = b - a;
+    const uint32_t rows = uint32_t(std::min<uint64_t>(P, nrows - p * uint64_t(P)));
+    if (rd32(pg) != (kMagic | (codec << 24)) || rd32(pg + 4) != rows) return flag();
+    const uint32_t poff = rd32(pg + 8), extra = rd32(pg + 12);
+    if (poff != payload_offset(codec, rows) || poff > pbytes) return flag();
+    const uint64_t pay_end = codec == C_STR ? extra : pbytes;
+    if (codec == C_STR && (extra < poff || extra > pbytes || extra % 16)) return flag();
+    const uint64_t pay_words = (pay_end - poff) / 4;
+    const uint32_t nmb = (rows + kMB - 1) / kMB;
+    for (uint32_t m2 = 0; m2 < nmb; ++m2) {
+      const uint8_t* h = pg + kPageHdr + uint64_t(m2) * mb_hdr_bytes(codec);
+      const uint32_t wob = codec == C_DELTA ? rd32(h + 8) : rd32(h + 4);
+      const uint32_t bw = wob & 0xffu, woff = wob >> 8;
+      if (bw > 32 || uint64_t(woff) + 4ull * bw > pay_words) return flag();
+      if (codec == C_DICT) {
+        const int32_t base = int32_t(rd32(h));
+        if (base < 0 || uint64_t(base) >= dict_n) return flag();
+      }
+      if (codec == C_STR) {
+        // lengths of the mini block must stay inside the page's byte region
+        const uint32_t start = rd32(pg + kPageHdr + uint64_t(nmb) * 8 + uint64_t(m2) * 4);
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(pg + poff) + woff;
+        const uint32_t base = rd32(h);
+        const uint32_t cnt = std::min<uint32_t>(kMB, rows - m2 * kMB);
+        uint64_t sum = 0;
+        for (uint32_t j = 0; j < cnt; ++j) {
+          uint32_t f = 0;
+          if (bw) {
+            const uint64_t bit = uint64_t(j) * bw;
+            uint64_t win = w[bit >> 5];
+            if ((bit & 31) + bw > 32) win |= uint64_t(w[(bit >> 5) + 1]) << 32;
+            f = uint32_t((win >> (bit & 31)) & (bw == 32 ? 0xffffffffull : ((1ull << bw) - 1)));
+          }
+          sum += uint64_t(base) + f;
+        }
+        if (uint64_t(start) + sum > pbytes - extra) return flag();
+      }
+    }
+  });
+  if (bad) return fail(DPF_ECORRUPT, "page %llu failed validation", (unsigned long long)bad_page);
+  return DPF_OK;
+}
+
+// ---------------------------------------------------------------- plans
+dpf_status compile_pred(const Column& c, const dpf_pred& p, DevStep& S, int col_index) {
+  std::memset(&S, 0, sizeof S);
+  S.col = uint8_t(col_index);
+  S.ht_smem = -1;
+  if (p.op == DPF_OP_PREFIX) {
+    if (c.codec != C_STR) return fail(DPF_EINVAL, "PREFIX needs a STR column (column %d)", c.id);
+    if (p.prefix_len < 0 || p.prefix_len > DPF_MAX_PREFIX) return fail(DPF_EINVAL, "prefix_len %d out of range", p.prefix_len);
+    S.kind = ST_PREFIX;
+    S.plen = uint8_t(p.prefix_len);
+    std::memcpy(S.pfx, p.prefix, size_t(p.prefix_len));
+    return DPF_OK;
+  }
+  if (c.codec == C_STR) return fail(DPF_EINVAL, "only PREFIX applies to STR column %d", c.id);
+  const int64_t MN = INT32_MIN, MX = INT32_MAX;
+  int64_t lo, hi;
+  bool neg = false;
+  switch (p.op) {
+    case DPF_OP_LT: lo = MN; hi = p.v[0] - 1; break;
+    case DPF_OP_LE: lo = MN; hi = p.v[0]; break;
+    case DPF_OP_GT: lo = p.v[0] + 1; hi = MX; break;
+    case DPF_OP_GE: lo = p.v[0]; hi = MX; break;
+    case DPF_OP_EQ: lo = hi = p.v[0]; break;
+    case DPF_OP_NE: lo = hi = p.v[0]; neg = true; break;
+    case DPF_OP_BETWEEN: lo = p.v[0]; hi = p.v[1]; break;
+    case DPF_OP_IN: {
+      if (p.n < 1 || p.n > DPF_MAX_IN) return fail(DPF_EINVAL, "IN takes 1..%d operands", DPF_MAX_IN);
+      std::vector<int32_t> vals;
+      for (int i = 0; i < p.n; ++i) {
+        const int64_t x = p.v[i];
+        if (c.codec == C_DICT) {
+          auto it = std::lower_bound(c.dict.begin(), c.dict.end(), x,
+                                     [](int32_t a, int64_t b) { return int64_t(a) < b; });
+          if (it != c.dict.end() && int64_t(*it) == x) vals.push_back(int32_t(it - c.dict.begin()));
+        } else if (x >= MN && x <= MX) {
+          vals.push_back(int32_t(x));
+        }
+      }
+      if (vals.empty()) { S.kind = ST_FALSE; return DPF_OK; }
+      S.kind = ST_IN;
+      S.nin = uint8_t(vals.size());
+      for (size_t i = 0; i < vals.size(); ++i) S.in[i] = vals[i];
+      return DPF_OK;
+    }
+    default: return fail(DPF_EINVAL, "unknown predicate op %d", p.op);
+  }
+  if (c.codec == C_DICT) {
+    // value interval -> code interval over the sorted dictionary
+    auto lb = [&](int64_t x) {
+      return int64_t(std::lower_bound(c.dict.begin(), c.dict.end(), x,
+                                      [](int32_t a, int64_t b) { return int64_t(a) < b; }) - c.dict.begin());
+    };
+    const int64_t clo = lb(lo);
+    const int64_t chi = hi == INT64_MAX ? int64_t(c.dict.size()) - 1 : lb(hi + 1) - 1;
+    if (neg) {
+      if (clo > chi) { S.kind = ST_RANGE; S.lo = INT32_MIN; S.hi = INT32_MAX; return DPF_OK; }
+      S.kind = ST_NOTRANGE; S.lo = int32_t(clo); S.hi = int32_t(chi);
+      return DPF_OK;
+    }
+    if (clo > chi) { S.kind = ST_FALSE; return DPF_OK; }
+    S.kind = ST_RANGE; S.lo = int32_t(clo); S.hi = int32_t(chi);
+    return DPF_OK;
+  }
+  lo = std::max(lo, MN);
+  hi = std::min(hi, MX);
+  if (neg) {
+    if (lo > hi) { S.kind = ST_RANGE; S.lo = INT32_MIN; S.hi = INT32_MAX; return DPF_OK; }
+    S.kind = ST_NOTRANGE; S.lo = int32_t(lo); S.hi = int32_t(hi);
+    return DPF_OK;
+  }
+  if (lo > hi) { S.kind = ST_FALSE; return DPF_OK; }
+  S.kind = ST_RANGE; S.lo = int32_t(lo); S.hi = int32_t(hi);
+  return DPF_OK;
+}
+
+struct ColumnSet {
+  dpf_ctx* c;
+  DevQuery& Q;
+  std::vector<int32_t> ids;
+  int32_t table = -1;
+  uint64_t nrows = 0;
+  uint32_t page_rows = 0;
+  bool host = false;
+  dpf_status add(int32_t id, int* idx) {
+    auto it = c->cols.find(id);
+    if (it == c->cols.end()) return fail(DPF_EINVAL, "unknown column %d", id);
+    const Column& col = it->second;
+    for (size_t i = 0; i < ids.size(); ++i)
+      if (ids[i] == id) { *idx = int(i); return DPF_OK; }
+    if (ids.empty()) {
+      table = col.table; nrows = col.nrows; page_rows = col.page_rows;
+    } else if (col.table != table || col.nrows != nrows || col.page_rows != page_rows) {
+      return fail(DPF_EINVAL, "column %d is not in the same table (table/rows/page_rows differ)", id);
+    }
+    if (ids.size() >= size_t(kMaxCols)) return fail(DPF_EINVAL, "a plan may touch at most %d columns", kMaxCols);
+    DevColumn& d = Q.cols[ids.size()];
+    d.blob = col.blob;
+    d.page_off = col.d_page_off;
+    d.nrows = col.nrows;
+    d.codec = uint32_t(col.codec);
+    d.page_rows = col.page_rows;
+    host |= col.placement == DPF_PLACE_HOST_PINNED;
+    *idx = int(ids.size());
+    ids.push_back(id);
+    Q.ncols = uint32_t(ids.size());
+    return DPF_OK;
+  }
+};
+
+dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
+                        std::vector<const HashTable*>& probes) {
+  std::memset(&Q, 0, sizeof Q);
+  ColumnSet cs{c, Q};
+  if (P.n_preds < 0 || P.n_preds > DPF_MAX_PREDS || P.n_joins < 0 || P.n_joins > DPF_MAX_JOINS ||
+      P.n_keys < 0 || P.n_keys > DPF_MAX_KEYS || P.n_aggs < 0 || P.n_aggs > DPF_MAX_AGGS)
+    return fail(DPF_EINVAL, "plan sizes out of range");
+  if ((P.n_preds && !P.preds) || (P.n_joins && !P.joins) || (P.n_keys && !P.keys) || (P.n_aggs && !P.aggs))
+    return fail(DPF_EINVAL, "plan array pointer is NULL");
+  std::vector<DevStep> steps;
+  for (int i = 0; i < P.n_preds; ++i) {
+    int idx;
+    dpf_status st = cs.add(P.preds[i].col, &idx);
+    if (st) return st;
+    DevStep S;
+    st = compile_pred(c->cols[P.preds[i].col], P.preds[i], S, idx);
+    if (st) return st;
+    steps.push_back(S);
+  }
+  probes.clear();
+  std::vector<size_t> probe_step;
+  for (int j = 0; j < P.n_joins; ++j) {
+    const dpf_join& J = P.joins[j];
+    auto ht = c->hts.find(J.ht);
+    if (ht == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", J.ht);
+    int idx;
+    dpf_status st = cs.add(J.fk_col, &idx);
+    if (st) return st;
+    const int codec = c->cols[J.fk_col].codec;
+    if (codec != C_FOR && codec != C_DELTA) return fail(DPF_EINVAL, "join column %d must be FOR or DELTA", J.fk_col);
+    DevStep S;
+    std::memset(&S, 0, sizeof S);
+    S.kind = ST_PROBE;
+    S.col = uint8_t(idx);
+    S.ht = ht->second.slots;
+    S.ht_mask = ht->second.capacity - 1;
+    S.ht_smem = -1;
+    probe_step.push_back(steps.size());
+    steps.push_back(S);
+    probes.push_back(&ht->second);
+  }
+  // group keys: dense ids in lexicographic (first key most significant) order
+  uint64_t dom[2] = {1, 1};
+  for (int k = 0; k < P.n_keys; ++k) {
+    const dpf_key& K = P.keys[k];
+    if (K.kind == DPF_KEY_COLUMN) {
+      auto it = c->cols.find(K.col);
+      if (it == c->cols.end() || it->second.codec != C_DICT) return fail(DPF_EINVAL, "group key column %d must be a DICT column", K.col);
+      dom[k] = it->second.dict.size();
+      Q.key_dict[k] = it->second.d_dict;
+    } else if (K.kind == DPF_KEY_PAYLOAD) {
+      if (K.join < 0 || K.join >= P.n_joins) return fail(DPF_EINVAL, "group key %d names join %d", k, K.join);
+      const HashTable& h = *probes[K.join];
+      if (K.field < 0 || K.field >= h.npay) return fail(DPF_EINVAL, "hash table %d has no payload field %d", h.id, K.field);
+      dom[k] = h.pay_dom[K.field];
+      Q.key_dict[k] = h.pay_dict[K.field];
+    } else {
+      return fail(DPF_EINVAL, "unknown key kind %d", K.kind);
+    }
+    if (dom[k] == 0) return fail(DPF_EINVAL, "group key %d has an empty domain", k);
+  }
+  const uint64_t domain = dom[0] * dom[1];
+  if (domain > DPF_MAX_GROUPS) return fail(DPF_EINVAL, "group domain %llu exceeds %d", (unsigned long long)domain, DPF_MAX_GROUPS);
+  Q.nkeys = uint32_t(P.n_keys);
+  Q.domain = uint32_t(domain);
+  for (int k = 0; k < 2; ++k) {
+    Q.key_dom[k] = uint32_t(dom[k]);
+    Q.key_div[k] = (k == 0 && P.n_keys == 2) ? uint32_t(dom[1]) : 1u;
+  }
+  for (int k = 0; k < P.n_keys; ++k) {
+    const dpf_key& K = P.keys[k];
+    if (K.kind == DPF_KEY_PAYLOAD) {
+      DevStep& S = steps[probe_step[K.join]];
+      if (K.field == 0) S.mul0 += Q.key_div[k]; else S.mul1 += Q.key_div[k];
+    } else {
+      int idx;
+      dpf_status st = cs.add(K.col, &idx);
+      if (st) return st;
+      DevStep S;
+      std::memset(&S, 0, sizeof S);
+      S.kind = ST_KEY;
+      S.col = uint8_t(idx);
+      S.key_mul = Q.key_div[k];
+      S.ht_smem = -1;
+      steps.push_back(S);
+    }
+  }
+  Q.naggs = uint32_t(P.n_aggs);
+  for (int a = 0; a < P.n_aggs; ++a) {
+    const dpf_agg& A = P.aggs[a];
+    if (A.op < DPF_AGG_COUNT || A.op > DPF_AGG_SUM_SUB) return fail(DPF_EINVAL, "unknown aggregate op %d", A.op);
+    Q.agg_op[a] = uint8_t(A.op);
+    const int need = A.op == DPF_AGG_COUNT ? 0 : (A.op == DPF_AGG_SUM ? 1 : 2);
+    const dpf_col_id ab[2] = {A.a, A.b};
+    for (int i = 0; i < need; ++i) {
+      auto it = c->cols.find(ab[i]);
+      if (it == c->cols.end()) return fail(DPF_EINVAL, "unknown aggregate column %d", ab[i]);
+      if (it->second.codec != C_FOR && it->second.codec != C_DELTA)
+        return fail(DPF_EINVAL, "aggregate column %d must be FOR or DELTA", ab[i]);
+      int idx;
+      dpf_status st = cs.add(ab[i], &idx);
+      if (st) return st;
+      (i == 0 ? Q.agg_a : Q.agg_b)[a] = uint8_t(idx);
+    }
+  }
+  if (cs.ids.empty()) return fail(DPF_EINVAL, "plan names no column of the scanned table");
+  if (steps.size() > size_t(kMaxSteps)) return fail(DPF_EINVAL, "plan compiles to more than %d steps", kMaxSteps);
+  Q.nsteps = uint32_t(steps.size());
+  for (size_t i = 0; i < steps.size(); ++i) Q.steps[i] = steps[i];
+  Q.nrows = cs.nrows;
+  Q.page_rows = cs.page_rows;
+  *host = cs.host;
+  return DPF_OK;
+}
+
+void fill_tuning_defaults(dpf_ctx* c, dpf_tuning& t) {
+  (void)c;
+  if (t.chunk_rows == 0) t.chunk_rows = 16384;
+  if (t.threads == 0) t.threads = 256;
+  if (t.ht_placement == 0) t.ht_placement = DPF_HT_AUTO;
+}
+
+dpf_status release_prep(dpf_ctx* c, Prep* p) {
+  if (p->launched && p->ev) cudaEventSynchronize(p->ev);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->ev) cudaEventDestroy(p->ev);
+  dev_free(c, p->dq);
+  dev_free(c, p->dqbegin);
+  dev_free(c, p->sched);
+  dev_free(c, p->scratch);
+  return DPF_OK;
+}
+
+dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tuning* tuning, Prep** out) {
+  if (!plans || n < 1 || n > 4096) return fail(DPF_EINVAL, "need 1..4096 plans");
+  auto p = std::make_unique<Prep>();
+  p->nq = n;
+  p->hq.resize(size_t(n));
+  dpf_tuning t{};
+  if (tuning) t = *tuning;
+  fill_tuning_defaults(c, t);
+  if (t.chunk_rows % 2048 != 0 || t.chunk_rows > (1u << 24)) return fail(DPF_EINVAL, "chunk_rows %u must be a multiple of 2048", t.chunk_rows);
+  if (t.threads != 128 && t.threads != 256 && t.threads != 512) return fail(DPF_EINVAL, "threads must be 128, 256 or 512");
+  bool host = false;
+  uint64_t tickets = 0;
+  std::vector<uint64_t> qbegin(size_t(n) + 1);
+  // scratch layout per query: acc | done | out_n | out
+  std::vector<uint64_t> off_acc(n), off_done(n), off_outn(n), off_out(n);
+  uint64_t scratch = 0;
+  size_t max_tables = 0;
+  const size_t table_budget =
+      t.ht_placement == DPF_HT_GLOBAL ? 0
+      : t.ht_placement == DPF_HT_SMEM ? size_t(std::max(0, c->smem_optin - int(kSmemAccSlots * 8) - 4096))
+                                      : size_t(64 * 1024);
+  for (int i = 0; i < n; ++i) {
+    DevQuery& Q = p->hq[i];
+    bool h = false;
+    std::vector<const HashTable*> probes;
+    dpf_status st = compile_plan(c, plans[i], Q, &h, probes);
+    if (st) return fail(st, "plan %d: %s", i, t_last_error.c_str());
+    host |= h;
+    // shared-memory placement of hash tables, in probe order, within budget
+    size_t used = 0;
+    uint32_t nt = 0;
+    for (uint32_t s = 0; s < Q.nsteps; ++s) {
+      DevStep& S = Q.steps[s];
+      if (S.kind != ST_PROBE || nt >= uint32_t(kMaxSmemTables)) continue;
+      const size_t bytes = size_t(S.ht_mask + 1) * 8;
+      if (used + bytes > table_budget) continue;
+      Q.tables[nt].src = S.ht;
+      Q.tables[nt].slots = S.ht_mask + 1;
+      Q.tables[nt].offset = uint32_t(used);
+      S.ht_smem = int32_t(nt);
+      used += bytes;
+      ++nt;
+    }
+    Q.ntables = nt;
+    Q.smem_table_bytes = uint32_t(used);
+    max_tables = std::max(max_tables, used);
+    Q.chunk_rows = t.chunk_rows;
+    Q.nchunks = (Q.nrows + t.chunk_rows - 1) / t.chunk_rows;
+    Q.chunk_begin = tickets;
+    qbegin[i] = tickets;
+    tickets += Q.nchunks;
+    const uint32_t S1 = 1 + Q.naggs;
+    Q.use_smem_acc = uint64_t(Q.domain) * S1 <= kSmemAccSlots ? 1u : 0u;
+    off_acc[i] = scratch; scratch += align16(uint64_t(Q.domain) * S1 * 8);
+    off_done[i] = scratch; scratch += 16;
+    off_outn[i] = scratch; scratch += 16;
+    off_out[i] = scratch; scratch += align16(uint64_t(std::max<uint32_t>(Q.domain, 1)) * sizeof(dpf_record));
+  }
+  qbegin[n] = tickets;
+  dpf_status st;
+  if ((st = dev_alloc(c, scratch, reinterpret_cast<void**>(&p->scratch)))) return st;
+  if ((st = dev_alloc_t(c, uint64_t(n), &p->dq)) || (st = dev_alloc_t(c, uint64_t(n) + 1, &p->dqbegin)) ||
+      (st = dev_alloc_t(c, 1, &p->sched))) {
+    release_prep(c, p.get());
+    return st;
+  }
+  for (int i = 0; i < n; ++i) {
+    DevQuery& Q = p->hq[i];
+    Q.acc = reinterpret_cast<unsigned long long*>(p->scratch + off_acc[i]);
+    Q.done = reinterpret_cast<unsigned int*>(p->scratch + off_done[i]);
+    Q.out_n = reinterpret_cast<unsigned int*>(p->scratch + off_outn[i]);
+    Q.out = p->scratch + off_out[i];
+  }
+  cudaError_t e = cudaMemsetAsync(p->scratch, 0, scratch, c->io);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->sched, 0, sizeof(Sched), c->io);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->dq, p->hq.data(), sizeof(DevQuery) * n, cudaMemcpyHostToDevice, c->io);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->dqbegin, qbegin.data(), 8 * (n + 1), cudaMemcpyHostToDevice, c->io);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->io);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    release_prep(c, p.get());
+    return fail(DPF_ECUDA, "prepare: %s", cudaGetErrorString(e));
+  }
+  int per_sm = fused_blocks_per_sm(int(t.threads), max_tables, host);
+  if (per_sm < 1) {
+    release_prep(c, p.get());
+    return fail(DPF_EINVAL, "fused kernel does not fit on an SM with %u threads and %zu table bytes", t.threads, max_tables);
+  }
+  if (t.ctas_per_sm == 0 || int(t.ctas_per_sm) > per_sm) t.ctas_per_sm = uint32_t(per_sm);
+  p->tuning = t;
+  p->L.queries = p->dq;
+  p->L.qbegin = p->dqbegin;
+  p->L.nq = n;
+  p->L.total_chunks = tickets;
+  p->L.sched = p->sched;
+  p->L.threads = int(t.threads);
+  p->L.grid = int(std::max<uint64_t>(1, std::min<uint64_t>(uint64_t(c->num_sms) * t.ctas_per_sm, tickets)));
+  p->L.smem_tables = max_tables;
+  p->L.host_data = host;
+  p->fetched.assign(size_t(n), 0);
+  p->id = c->next_prep++;
+  *out = p.get();
+  c->preps[p->id] = std::move(p);
+  return DPF_OK;
+}
+
+Prep* find_prep(dpf_ctx* c, dpf_prep_id id) {
+  auto it = c->preps.find(id);
+  return it == c->preps.end() ? nullptr : it->second.get();
+}
+
+dpf_status wait_event(cudaEvent_t ev, int32_t timeout_ms) {
+  if (timeout_ms < 0) {
+    CUDA_TRY(cudaEventSynchronize(ev));
+    return DPF_OK;
+  }
+  const auto until = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return DPF_OK;
+    if (e != cudaErrorNotReady) return fail(DPF_ECUDA, "cudaEventQuery: %s", cudaGetErrorString(e));
+    if (std::chrono::steady_clock::now() >= until) return fail(DPF_ETIMEOUT, "result not ready within %d ms", timeout_ms);
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+dpf_status read_result(dpf_ctx* c, Prep* p, int32_t i, dpf_record* buf, uint64_t cap, uint64_t* n_out,
+                       int32_t timeout_ms) {
+  if (i < 0 || i >= p->nq) return fail(DPF_EINVAL, "query index %d out of range", i);
+  if (!p->launched) return fail(DPF_EINVAL, "batch %d was never launched", p->id);
+  dpf_status st = wait_event(p->ev, timeout_ms);
+  if (st) return st;
+  uint32_t status = 0, n = 0;
+  CUDA_TRY(cudaMemcpyAsync(&status, &p->sched->status, 4, cudaMemcpyDeviceToHost, c->io));
+  CUDA_TRY(cudaMemcpyAsync(&n, p->hq[i].out_n, 4, cudaMemcpyDeviceToHost, c->io));
+  CUDA_TRY(cudaStreamSynchronize(c->io));
+  if (status) {
+    cudaMemsetAsync(&p->sched->status, 0, 4, c->io);
+    cudaStreamSynchronize(c->io);
+    if (status & S_CORRUPT) return fail(DPF_ECORRUPT, "device reported corrupt data (status %u)", status);
+    return fail(DPF_EINTERNAL, "device reported an internal error (status %u)", status);
+  }
+  if (n_out) *n_out = n;
+  if (cap < n) return fail(DPF_ETRUNC, "need %u records", n);
+  if (n) {
+    if (!buf) return fail(DPF_EINVAL, "buf is NULL");
+    CUDA_TRY(cudaMemcpyAsync(buf, p->hq[i].out, uint64_t(n) * sizeof(dpf_record), cudaMemcpyDeviceToHost, c->io));
+    CUDA_TRY(cudaStreamSynchronize(c->io));
+  }
+  return DPF_OK;
+}
+
+}  // namespace
+
+// ======================================================================
+// C ABI
+// ======================================================================
+extern "C" {
+
+const char* dpf_last_error(void) { return t_last_error.c_str(); }
+
+dpf_status dpf_create(dpf_ctx** out, int32_t device, uint64_t hbm_budget, const dpf_alloc_hooks* hooks) {
+  if (!out) return fail(DPF_EINVAL, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(DPF_ECUDA, "no CUDA device available");
+  }
+  if (device < 0 || device >= ndev) return fail(DPF_EINVAL, "device %d out of range (%d devices)", device, ndev);
+  if (hooks && (!hooks->alloc || !hooks->free)) return fail(DPF_EINVAL, "hooks need alloc and free");
+  DeviceGuard g(device);
+  auto c = std::make_unique<dpf_ctx>();
+  c->device = device;
+  c->budget = hbm_budget;
+  if (hooks) {
+    c->hooks = *hooks;
+    c->has_hooks = true;
+  }
+  CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+  CUDA_TRY(cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  CUDA_TRY(cudaStreamCreateWithFlags(&c->io, cudaStreamNonBlocking));
+  dpf_status st;
+  if ((st = dev_alloc_t(c.get(), 1, &c->bsched)) || (st = dev_alloc_t(c.get(), 1, &c->bcount))) return st;
+  CUDA_TRY(cudaMemsetAsync(c->bsched, 0, sizeof(Sched), c->io));
+  CUDA_TRY(cudaStreamSynchronize(c->io));
+  *out = c.release();
+  return DPF_OK;
+}
+
+dpf_status dpf_destroy(dpf_ctx* c) {
+  if (!c) return DPF_OK;
+  {
+    std::lock_guard<std::recursive_mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : c->preps) release_prep(c, kv.second.get());
+    c->preps.clear();
+    for (auto& kv : c->hts) dev_free(c, kv.second.slots);
+    for (auto& kv : c->cols) free_column(c, kv.second);
+    dev_free(c, c->bsched);
+    dev_free(c, c->bcount);
+    if (c->io) cudaStreamDestroy(c->io);
+  }
+  delete c;
+  return DPF_OK;
+}
+
+dpf_status dpf_memory_used(dpf_ctx* c, uint64_t* bytes) {
+  if (!c || !bytes) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  *bytes = c->used;
+  return DPF_OK;
+}
+
+dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t* pages, uint64_t size,
+                            const uint64_t* page_off, const uint64_t* row_prefix, uint64_t nrows,
+                            const int32_t* dict, uint64_t dict_n, dpf_col_id* out) {
+  if (!c || !d || !pages || !page_off || !row_prefix || !out) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  const uint32_t codec = uint32_t(d->codec);
+  const uint32_t P = d->page_rows ? d->page_rows : kDefaultPageRows;
+  if (codec < C_FOR || codec > C_STR) return fail(DPF_EINVAL, "unknown codec %u", codec);
+  if (nrows == 0 || P % kMB || P > kMaxPageRows) return fail(DPF_EINVAL, "bad nrows or page_rows");
+  if (d->placement != DPF_PLACE_DEVICE && d->placement != DPF_PLACE_HOST_PINNED) return fail(DPF_EINVAL, "bad placement");
+  if (codec == C_DICT && (!dict || dict_n == 0 || dict_n > 65536)) return fail(DPF_EINVAL, "DICT column needs 1..65536 dictionary values");
+  if (codec == C_DICT)
+    for (uint64_t i = 1; i < dict_n; ++i)
+      if (dict[i] <= dict[i - 1]) return fail(DPF_EINVAL, "dictionary must be strictly ascending");
+  const uint64_t npages = (nrows + P - 1) / P;
+  for (uint64_t p = 0; p < npages; ++p)
+    if (row_prefix[p] != std::min<uint64_t>(nrows, (p + 1) * uint64_t(P)))
+      return fail(DPF_ECORRUPT, "RID index entry %llu is inconsistent", (unsigned long long)p);
+  dpf_status st = validate_pages(codec, pages, size, page_off, npages, nrows, P, dict_n);
+  if (st) return st;
+  Column col;
+  col.codec = int32_t(codec);
+  col.placement = d->placement;
+  col.table = d->table;
+  col.page_rows = P;
+  col.nrows = nrows;
+  col.npages = npages;
+  col.bytes = size;
+  col.page_off.assign(page_off, page_off + npages + 1);
+  col.row_prefix.assign(row_prefix, row_prefix + npages);
+  if (codec == C_DICT) col.dict.assign(dict, dict + dict_n);
+  if (codec == C_STR) {
+    uint64_t sb = 0;
+    for (uint64_t p = 0; p < npages; ++p) {
+      const uint8_t* pg = pages + page_off[p];
+      sb += page_off[p + 1] - page_off[p] - rd32(pg + 12);
+    }
+    col.raw_bytes = sb + 8 * nrows;
+  } else {
+    col.raw_bytes = 4 * nrows;
+  }
+  if (col.placement == DPF_PLACE_HOST_PINNED) {
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&col.host_blob), size, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DPF_ENOMEM, "cudaHostAlloc(%llu): %s", (unsigned long long)size, cudaGetErrorString(e));
+    }
+    std::memcpy(col.host_blob, pages, size);
+    void* dp = nullptr;
+    e = cudaHostGetDevicePointer(&dp, col.host_blob, 0);
+    if (e != cudaSuccess) {
+      cudaFreeHost(col.host_blob);
+      return fail(DPF_ECUDA, "cudaHostGetDevicePointer: %s", cudaGetErrorString(e));
+    }
+    col.blob = static_cast<uint8_t*>(dp);
+  } else {
+    void* dp;
+    if ((st = dev_alloc(c, size, &dp))) return st;
+    col.blob = static_cast<uint8_t*>(dp);
+    if ((st = upload(c, col.blob, pages, size))) { free_column(c, col); return st; }
+  }
+  if ((st = dev_alloc_t(c, npages + 1, &col.d_page_off)) || (st = upload(c, col.d_page_off, page_off, 8 * (npages + 1)))) {
+    free_column(c, col);
+    return st;
+  }
+  if (codec == C_DICT) {
+    if ((st = dev_alloc_t(c, dict_n, &col.d_dict)) || (st = upload(c, col.d_dict, dict, 4 * dict_n))) {
+      free_column(c, col);
+      return st;
+    }
+  }
+  col.id = c->next_col++;
+  *out = col.id;
+  c->cols[col.id] = std::move(col);
+  return DPF_OK;
+}
+
+dpf_status dpf_load_column(dpf_ctx* c, const dpf_column_desc* d, const void* values, const uint64_t* str_offsets,
+                           uint64_t nrows, dpf_col_id* out) {
+  if (!c || !d || !out) return fail(DPF_EINVAL, "NULL argument");
+  const uint32_t P = d->page_rows ? d->page_rows : kDefaultPageRows;
+  if (nrows == 0 || P == 0) return fail(DPF_EINVAL, "nrows must be > 0");
+  const uint64_t npages = (nrows + P - 1) / P;
+  std::vector<uint64_t> page_off(npages + 1), row_prefix(npages);
+  uint64_t size = 0, dict_n = 0;
+  dpf_status st = dpf_encode_column(d, values, str_offsets, nrows, nullptr, 0, page_off.data(), row_prefix.data(),
+                                    nullptr, 0, &dict_n, &size);
+  if (st) return st;
+  std::vector<uint8_t> pages(size);
+  std::vector<int32_t> dict(std::max<uint64_t>(dict_n, 1));
+  st = dpf_encode_column(d, values, str_offsets, nrows, pages.data(), size, page_off.data(), row_prefix.data(),
+                         dict.data(), dict.size(), &dict_n, &size);
+  if (st) return st;
+  return dpf_load_encoded(c, d, pages.data(), size, page_off.data(), row_prefix.data(), nrows,
+                          d->codec == C_DICT ? dict.data() : nullptr, dict_n, out);
+}
+
+dpf_status dpf_column_info(dpf_ctx* c, dpf_col_id id, uint64_t* rows, uint64_t* enc, uint64_t* raw) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  auto it = c->cols.find(id);
+  if (it == c->cols.end()) return fail(DPF_EINVAL, "unknown column %d", id);
+  if (rows) *rows = it->second.nrows;
+  if (enc) *enc = it->second.bytes;
+  if (raw) *raw = it->second.raw_bytes;
+  return DPF_OK;
+}
+
+dpf_status dpf_column_read(dpf_ctx* c, dpf_col_id id, uint64_t offset, uint64_t bytes, uint8_t* host_out) {
+  if (!c || (!host_out && bytes)) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  auto it = c->cols.find(id);
+  if (it == c->cols.end()) return fail(DPF_EINVAL, "unknown column %d", id);
+  const Column& col = it->second;
+  if (offset > col.bytes || bytes > col.bytes - offset) return fail(DPF_EINVAL, "range beyond the column");
+  if (col.placement == DPF_PLACE_HOST_PINNED) {
+    std::memcpy(host_out, col.host_blob + offset, bytes);
+    return DPF_OK;
+  }
+  CUDA_TRY(cudaMemcpyAsync(host_out, col.blob + offset, bytes, cudaMemcpyDeviceToHost, c->io));
+  CUDA_TRY(cudaStreamSynchronize(c->io));
+  return DPF_OK;
+}
+
+dpf_status dpf_drop_column(dpf_ctx* c, dpf_col_id id) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  auto it = c->cols.find(id);
+  if (it == c->cols.end()) return fail(DPF_EINVAL, "unknown column %d", id);
+  cudaDeviceSynchronize();
+  free_column(c, it->second);
+  c->cols.erase(it);
+  return DPF_OK;
+}
+
+dpf_status dpf_build_hash(dpf_ctx* c, dpf_col_id key_col, const dpf_col_id* payload_cols, int32_t n_payload,
+                          const dpf_pred* preds, int32_t n_preds, void* stream, dpf_ht_id* out) {
+  if (!c || !out) return fail(DPF_EINVAL, "NULL argument");
+  if (n_payload < 0 || n_payload > 2 || (n_payload && !payload_cols)) return fail(DPF_EINVAL, "0..2 payload columns");
+  if (n_preds < 0 || n_preds > DPF_MAX_PREDS || (n_preds && !preds)) return fail(DPF_EINVAL, "bad predicates");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevQuery Q;
+  std::memset(&Q, 0, sizeof Q);
+  ColumnSet cs{c, Q};
+  int kidx;
+  dpf_status st = cs.add(key_col, &kidx);
+  if (st) return st;
+  const Column& kc = c->cols[key_col];
+  if (kc.codec != C_FOR && kc.codec != C_DELTA) return fail(DPF_EINVAL, "key column %d must be FOR or DELTA", key_col);
+  HashTable ht;
+  ht.npay = n_payload;
+  Q.build_key = kidx;
+  Q.build_npay = n_payload;
+  for (int f = 0; f < n_payload; ++f) {
+    int idx;
+    if ((st = cs.add(payload_cols[f], &idx))) return st;
+    const Column& pc = c->cols[payload_cols[f]];
+    if (pc.codec != C_DICT) return fail(DPF_EINVAL, "payload column %d must be DICT", payload_cols[f]);
+    Q.build_pay[f] = idx;
+    ht.pay_dom[f] = uint32_t(pc.dict.size());
+    ht.pay_dict[f] = pc.d_dict;
+  }
+  for (int i = 0; i < n_preds; ++i) {
+    int idx;
+    if ((st = cs.add(preds[i].col, &idx))) return st;
+    if ((st = compile_pred(c->cols[preds[i].col], preds[i], Q.steps[i], idx))) return st;
+  }
+  Q.nsteps = uint32_t(n_preds);
+  Q.nrows = cs.nrows;
+  Q.page_rows = cs.page_rows;
+  DevQuery* dq;
+  if ((st = dev_alloc_t(c, 1, &dq))) return st;
+  BuildLaunch L{};
+  L.q = dq;
+  L.count = c->bcount;
+  L.sched = c->bsched;
+  L.nrows = Q.nrows;
+  L.page_rows = Q.page_rows;
+  L.host_data = cs.host;
+  unsigned long long kept = 0;
+  uint32_t status = 0;
+  auto cleanup = [&](dpf_status r) {
+    dev_free(c, dq);
+    return r;
+  };
+  cudaError_t e = cudaMemcpyAsync(dq, &Q, sizeof Q, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->bcount, 0, 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->bsched, 0, sizeof(Sched), s);
+  if (e == cudaSuccess) e = launch_build_count(L, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&kept, c->bcount, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cleanup(fail(DPF_ECUDA, "hash build (count): %s", cudaGetErrorString(e)));
+  uint64_t cap = 16;
+  while (cap < 2 * kept) cap <<= 1;
+  if (cap > (1ull << 31)) return cleanup(fail(DPF_ENOMEM, "hash table of %llu entries is too large", kept));
+  if ((st = dev_alloc_t(c, cap, &ht.slots))) return cleanup(st);
+  ht.capacity = uint32_t(cap);
+  ht.entries = kept;
+  L.table = ht.slots;
+  L.mask = uint32_t(cap - 1);
+  e = launch_init_table(ht.slots, uint32_t(cap), s);
+  if (e == cudaSuccess) e = launch_build_insert(L, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, &c->bsched->status, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    dev_free(c, ht.slots);
+    return cleanup(fail(DPF_ECUDA, "hash build (insert): %s", cudaGetErrorString(e)));
+  }
+  if (status) {
+    dev_free(c, ht.slots);
+    if (status & S_DUPKEY) return cleanup(fail(DPF_EDUPKEY, "duplicate key in hash build of column %d", key_col));
+    if (status & S_CORRUPT) return cleanup(fail(DPF_EINVAL, "key column %d holds the reserved key INT32_MIN or corrupt data", key_col));
+    return cleanup(fail(DPF_EINTERNAL, "hash build status %u", status));
+  }
+  ht.table = kc.table;
+  ht.id = c->next_ht++;
+  c->hts[ht.id] = ht;
+  *out = ht.id;
+  return cleanup(DPF_OK);
+}
+
+dpf_status dpf_hash_info(dpf_ctx* c, dpf_ht_id id, uint64_t* entries, uint64_t* capacity) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  auto it = c->hts.find(id);
+  if (it == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", id);
+  if (entries) *entries = it->second.entries;
+  if (capacity) *capacity = it->second.capacity;
+  return DPF_OK;
+}
+
+dpf_status dpf_drop_hash(dpf_ctx* c, dpf_ht_id id) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  auto it = c->hts.find(id);
+  if (it == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", id);
+  cudaDeviceSynchronize();
+  dev_free(c, it->second.slots);
+  c->hts.erase(it);
+  return DPF_OK;
+}
+
+dpf_status dpf_prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tuning* tuning, dpf_prep_id* out) {
+  if (!c || !out) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  Prep* p;
+  dpf_status st = prepare(c, plans, n, tuning, &p);
+  if (st) return st;
+  *out = p->id;
+  return DPF_OK;
+}
+
+dpf_status dpf_launch(dpf_ctx* c, dpf_prep_id id, void* stream) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  Prep* p = find_prep(c, id);
+  if (!p) return fail(DPF_EINVAL, "unknown batch %d", id);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(launch_fused(p->L, s));
+  CUDA_TRY(cudaEventRecord(p->ev, s));
+  p->launched = true;
+  return DPF_OK;
+}
+
+dpf_status dpf_capture_graph(dpf_ctx* c, dpf_prep_id id, void* stream) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  Prep* p = find_prep(c, id);
+  if (!p) return fail(DPF_EINVAL, "unknown batch %d", id);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!s) return fail(DPF_EINVAL, "graph capture needs a non-default stream");
+  if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+  if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
+  // set the smem attribute before capture (not a stream operation)
+  fused_blocks_per_sm(p->L.threads, p->L.smem_tables, p->L.host_data);
+  CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = launch_fused(p->L, s);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(DPF_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  p->graph = graph;
+  CUDA_TRY(cudaGraphInstantiate(&p->gexec, graph, 0));
+  return DPF_OK;
+}
+
+dpf_status dpf_launch_graph(dpf_ctx* c, dpf_prep_id id, void* stream) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  Prep* p = find_prep(c, id);
+  if (!p || !p->gexec) return fail(DPF_EINVAL, "batch %d has no captured graph", id);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaGraphLaunch(p->gexec, s));
+  CUDA_TRY(cudaEventRecord(p->ev, s));
+  p->launched = true;
+  return DPF_OK;
+}
+
+dpf_status dpf_read_result(dpf_ctx* c, dpf_prep_id id, int32_t i, dpf_record* buf, uint64_t cap, uint64_t* n_out,
+                           int32_t timeout_ms) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  Prep* p = find_prep(c, id);
+  if (!p) return fail(DPF_EINVAL, "unknown batch %d", id);
+  return read_result(c, p, i, buf, cap, n_out, timeout_ms);
+}
+
+dpf_status dpf_prep_tuning(dpf_ctx* c, dpf_prep_id id, dpf_tuning* out) {
+  if (!c || !out) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  Prep* p = find_prep(c, id);
+  if (!p) return fail(DPF_EINVAL, "unknown batch %d", id);
+  *out = p->tuning;
+  return DPF_OK;
+}
+
+dpf_status dpf_release(dpf_ctx* c, dpf_prep_id id) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  auto it = c->preps.find(id);
+  if (it == c->preps.end()) return fail(DPF_EINVAL, "unknown batch %d", id);
+  release_prep(c, it->second.get());
+  c->preps.erase(it);
+  return DPF_OK;
+}
+
+dpf_status dpf_execute_plan(dpf_ctx* c, const dpf_plan* plans, int32_t n, void* stream, dpf_query_id* out_ids) {
+  if (!c || !out_ids) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  Prep* p;
+  dpf_status st = prepare(c, plans, n, nullptr, &p);
+  if (st) return st;
+  p->oneshot = true;
+  st = dpf_launch(c, p->id, stream);
+  if (st) {
+    const std::string msg = t_last_error;
+    dpf_release(c, p->id);
+    return fail(st, "%s", msg.c_str());
+  }
+  for (int i = 0; i < n; ++i) out_ids[i] = (dpf_query_id(p->id) << 20) | i;
+  return DPF_OK;
+}
+
+dpf_status dpf_fetch_result(dpf_ctx* c, dpf_query_id id, dpf_record* buf, uint64_t cap, uint64_t* n_out,
+                            int32_t timeout_ms) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  Prep* p = find_prep(c, dpf_prep_id(id >> 20));
+  const int32_t i = int32_t(id & 0xfffff);
+  if (!p || !p->oneshot || i >= p->nq || p->fetched[i]) return fail(DPF_ENOTFOUND, "unknown or fetched query id %lld", (long long)id);
+  dpf_status st = read_result(c, p, i, buf, cap, n_out, timeout_ms);
+  if (st) return st;
+  p->fetched[i] = 1;
+  if (std::all_of(p->fetched.begin(), p->fetched.end(), [](char f) { return f != 0; })) {
+    const int32_t pid = p->id;
+    release_prep(c, p);
+    c->preps.erase(pid);
+  }
+  return DPF_OK;
+}
+
+}  // extern "C"

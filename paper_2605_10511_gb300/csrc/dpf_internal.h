@@ -1,0 +1,123 @@
+// Internal structures shared by the host side and the kernels of the library.
+//
+// The storage format (Sec. 3.4.1 fixed-length pages of mini blocks with a FOR
+// base, a bit width and an offset; Sec. 3.4.2 variable-length pages and the
+// RID index; Sec. 4.1 GPU-FOR; Sec. 4.2 page metadata) and the compiled
+// device plan of one query pipeline (Sec. 3.1 Kernels #1-#3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dpf {
+
+// ------------------------------------------------------------------ format
+constexpr uint32_t kMB = 128;                 // values per mini block
+constexpr uint32_t kPageHdr = 16;             // page header bytes
+constexpr uint32_t kMagic = 0x00465044u;      // 'D' 'P' 'F', codec in the top byte
+constexpr uint32_t kMaxPageRows = 1u << 20;
+constexpr uint32_t kDefaultPageRows = 65536;
+
+enum Codec : uint32_t { C_FOR = 1, C_DELTA = 2, C_DICT = 3, C_STR = 4 };
+
+// Bytes of one mini block header in the header array that follows the
+// page header (STR: the lengths' FOR header; the u32 starts come after all
+// headers).
+__host__ __device__ inline uint32_t mb_hdr_bytes(uint32_t codec) {
+  return codec == C_DELTA ? 16u : 8u;
+}
+__host__ __device__ inline uint32_t mb_meta_bytes(uint32_t codec) {
+  return codec == C_DELTA ? 16u : (codec == C_STR ? 12u : 8u);
+}
+__host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15u) & ~uint64_t(15); }
+// Byte offset of the packed payload inside a page of `rows` rows.
+__host__ __device__ inline uint32_t payload_offset(uint32_t codec, uint32_t rows) {
+  const uint32_t nmb = (rows + kMB - 1) / kMB;
+  return uint32_t(align16(kPageHdr + uint64_t(nmb) * mb_meta_bytes(codec)));
+}
+
+// ------------------------------------------------------------ device plan
+constexpr int kMaxCols = 8;        // distinct fact columns one query touches
+constexpr int kMaxSteps = 12;
+constexpr int kMaxIn = 8;
+constexpr int kMaxPrefix = 32;
+constexpr int kMaxAggCols = 4;
+constexpr int kMaxSmemTables = 4;
+constexpr int32_t kEmptyKey = int32_t(0x80000000);
+
+// Device status bits (OR-ed into a status word, read by the host).
+enum StatusBits : uint32_t { S_CORRUPT = 1u, S_INTERNAL = 2u, S_DUPKEY = 4u, S_TIMEOUT = 8u };
+
+struct DevColumn {
+  const uint8_t* blob;        // page images (device, or mapped pinned host)
+  const uint64_t* page_off;   // [npages + 1] byte offset of each page (device)
+  uint64_t nrows;
+  uint32_t codec;
+  uint32_t page_rows;
+};
+
+enum StepKind : uint8_t {
+  ST_RANGE = 1,     // lo <= x <= hi
+  ST_NOTRANGE = 2,  // !(lo <= x <= hi)
+  ST_IN = 3,        // x in in[0..nin)
+  ST_FALSE = 4,     // no row passes (e.g. an equality on a value absent from a dictionary)
+  ST_PREFIX = 5,    // STR column starts with pfx[0..plen)
+  ST_PROBE = 6,     // hash probe; a miss drops the row, a hit adds payload fields to gid
+  ST_KEY = 7,       // DICT column code added to gid
+};
+
+struct DevStep {
+  uint8_t kind, col, nin, plen;
+  int32_t lo, hi;
+  int32_t in[kMaxIn];
+  // ST_PROBE
+  const uint2* ht;        // global slots {key, payload}
+  uint32_t ht_mask;       // capacity - 1 (power of two)
+  int32_t ht_smem;        // index of the smem copy (-1: probe global memory)
+  uint32_t mul0, mul1;    // gid multipliers of payload fields 0 and 1 (0 = unused)
+  // ST_KEY
+  uint32_t key_mul;
+  uint8_t pfx[kMaxPrefix];
+};
+
+struct SmemTable {
+  const uint2* src;       // global slots
+  uint32_t slots;         // capacity
+  uint32_t offset;        // byte offset inside the CTA's table region
+};
+
+struct alignas(16) DevQuery {
+  DevColumn cols[kMaxCols];
+  DevStep steps[kMaxSteps];
+  SmemTable tables[kMaxSmemTables];
+  uint32_t ncols, nsteps, ntables, smem_table_bytes;
+  uint64_t nrows;
+  uint32_t page_rows;
+  uint32_t chunk_rows;
+  uint64_t chunk_begin;        // first global ticket of this query
+  uint64_t nchunks;
+  // aggregation: slot 0 = count, slot 1 + a = aggregate a
+  uint32_t domain;             // number of dense group ids
+  uint32_t naggs;
+  uint8_t agg_op[4], agg_a[4], agg_b[4];   // agg_a/agg_b: column indices
+  uint32_t use_smem_acc;
+  // group key reconstruction: code_k = (gid / key_div[k]) % key_dom[k]
+  uint32_t nkeys;
+  uint32_t key_div[2], key_dom[2];
+  const int32_t* key_dict[2];
+  // scratch and output (device)
+  unsigned long long* acc;     // [domain][1 + naggs], zero between launches
+  unsigned int* done;          // chunks flushed so far, zero between launches
+  void* out;                   // dpf_record[domain]
+  unsigned int* out_n;
+  // dimension scans (hash build): key column and payload columns
+  int32_t build_key, build_npay, build_pay[2];
+};
+
+struct Sched {
+  unsigned long long next;     // ticket counter
+  unsigned int exited;         // CTAs that left the persistent loop
+  unsigned int status;         // StatusBits
+};
+
+}  // namespace dpf

@@ -1,0 +1,48 @@
+// Host-callable launchers of the library's kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dpf_internal.h"
+
+namespace dpf {
+
+// Shared-memory accumulator capacity of one CTA (int64 slots).
+constexpr uint32_t kSmemAccSlots = 4096;
+constexpr uint32_t kMbPerWarpTile = 4;
+
+// Fused persistent kernel over a batch of compiled queries (Sec. 3.2).
+// qbegin[0..nq] = first ticket of each query (qbegin[nq] = total tickets).
+struct FusedLaunch {
+  const DevQuery* queries;
+  const uint64_t* qbegin;
+  int nq;
+  uint64_t total_chunks;
+  Sched* sched;
+  int grid, threads;
+  size_t smem_tables;   // bytes of the CTA's hash-table region
+  bool host_data;       // some column lives in mapped pinned host memory
+};
+cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s);
+// Occupancy of the fused kernel for (threads, dynamic smem).
+int fused_blocks_per_sm(int threads, size_t smem_tables, bool host_data);
+size_t fused_dynamic_smem(size_t smem_tables);
+
+// Hash build (Kernel #1 of Sec. 3.1).  `q` describes the dimension scan:
+// cols/steps as for the fused kernel, build_key/build_pay name columns.
+struct BuildLaunch {
+  const DevQuery* q;          // device copy
+  uint2* table;               // capacity slots, initialised by init_table
+  uint32_t mask;
+  unsigned long long* count;  // device counter (count mode)
+  Sched* sched;               // status word
+  int key_col, npay, pay_col0, pay_col1;
+  uint64_t nrows, page_rows;
+  bool host_data;
+};
+cudaError_t launch_build_count(const BuildLaunch& L, cudaStream_t s);
+cudaError_t launch_build_insert(const BuildLaunch& L, cudaStream_t s);
+cudaError_t launch_init_table(uint2* table, uint32_t slots, cudaStream_t s);
+
+}  // namespace dpf

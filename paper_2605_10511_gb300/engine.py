@@ -1,0 +1,108 @@
+"""Loads workload tables into a library context and turns query descriptions
+into plans (argument marshalling only; the work is done by the library).
+
+A query description has the form documented in ``synth.tables``: fact
+predicates, equi-joins against dimension tables (with dimension predicates
+and payload columns), up to two group keys and up to four aggregates.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+from . import AGG, Agg, Context, Join, Key, Plan, Pred, make_pred
+
+
+class PlanHandle:
+    """A ``dpf_plan`` plus the ctypes arrays it points into."""
+
+    def __init__(self, plan, keep):
+        self.plan = plan
+        self._keep = keep
+
+
+class Engine:
+    def __init__(self, device=0, hbm_budget=0, use_torch_allocator=False, ctx=None):
+        self.ctx = ctx or Context(device, hbm_budget, use_torch_allocator)
+        self.cols = {}       # (workload name, table, column) -> column id
+        self.tables = {}     # (workload name, table) -> table id
+        self.hts = {}        # join signature -> hash table id
+
+    def close(self):
+        self.ctx.close()
+
+    # ------------------------------------------------------------------ loading
+    def load_workload(self, w, placement="device", fact_placement=None):
+        """Loads every column of every table of workload ``w`` (once)."""
+        for tname, t in w["tables"].items():
+            key = (w["name"], tname)
+            if key in self.tables:
+                continue
+            tid = len(self.tables) + 1
+            self.tables[key] = tid
+            place = fact_placement if (fact_placement and tname == w["fact"]) else placement
+            for cname, c in t["cols"].items():
+                self.cols[(w["name"], tname, cname)] = self.ctx.load_column(
+                    c, table=tid, page_rows=t["page_rows"], placement=place)
+
+    def col(self, w, table, name):
+        return self.cols[(w["name"], table, name)]
+
+    def fact_bytes(self, w):
+        """Encoded bytes of every fact column the query reads (algorithmic
+        bytes of one scan) and the fact row count."""
+        q = w["query"]
+        names = {p["col"] for p in q["preds"]} | {j["fk"] for j in q["joins"]}
+        names |= {g["col"] for g in q["group"] if "col" in g}
+        for a in q["aggs"]:
+            names |= set(a.get("cols", []))
+        total = sum(self.ctx.column_info(self.col(w, w["fact"], n))["encoded_bytes"] for n in names)
+        return total, w["tables"][w["fact"]]["rows"]
+
+    # ------------------------------------------------------------------ planning
+    def build_joins(self, w, stream=None):
+        """Builds (or reuses) the hash table of every join of ``w``'s query."""
+        out = []
+        for j in w["query"]["joins"]:
+            sig = (w["name"], j["dim"], j["key"], repr(j["preds"]), tuple(j["payload"]))
+            if sig not in self.hts:
+                preds = [make_pred(self.col(w, j["dim"], p["col"]), p["op"], p["args"]) for p in j["preds"]]
+                pay = [self.col(w, j["dim"], c) for c in j["payload"]]
+                self.hts[sig] = self.ctx.build_hash(self.col(w, j["dim"], j["key"]), pay, preds, stream)
+            out.append(self.hts[sig])
+        return out
+
+    def plan(self, w, stream=None):
+        q = w["query"]
+        f = w["fact"]
+        hts = self.build_joins(w, stream)
+        preds = (Pred * max(len(q["preds"]), 1))(
+            *[make_pred(self.col(w, f, p["col"]), p["op"], p["args"]) for p in q["preds"]])
+        joins = (Join * max(len(q["joins"]), 1))(
+            *[Join(self.col(w, f, j["fk"]), h) for j, h in zip(q["joins"], hts)])
+        keys = (Key * max(len(q["group"]), 1))()
+        for i, g in enumerate(q["group"]):
+            if "col" in g:
+                keys[i] = Key(0, self.col(w, f, g["col"]), 0, 0)
+            else:
+                keys[i] = Key(1, 0, g["join"], g["field"])
+        aggs = (Agg * max(len(q["aggs"]), 1))()
+        for i, a in enumerate(q["aggs"]):
+            cols = [self.col(w, f, c) for c in a.get("cols", [])]
+            aggs[i] = Agg(AGG[a["op"]], cols[0] if cols else 0, cols[1] if len(cols) > 1 else 0)
+        plan = Plan(len(q["preds"]), C.cast(preds, C.POINTER(Pred)),
+                    len(q["joins"]), C.cast(joins, C.POINTER(Join)),
+                    len(q["group"]), C.cast(keys, C.POINTER(Key)),
+                    len(q["aggs"]), C.cast(aggs, C.POINTER(Agg)))
+        return PlanHandle(plan, (preds, joins, keys, aggs))
+
+    def run(self, w, stream=None, tuning=None):
+        """Loads (if needed), plans, launches and reads one query's records."""
+        self.load_workload(w)
+        h = self.plan(w, stream)
+        prep = self.ctx.prepare([h], tuning)
+        try:
+            self.ctx.launch(prep, stream)
+            return self.ctx.read_result(prep, 0)
+        finally:
+            self.ctx.release(prep)
