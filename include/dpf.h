@@ -224,6 +224,9 @@ typedef struct dpf_plan {
   int32_t n_joins;  const dpf_join* joins;  /* inner equi-joins, in order   */
   int32_t n_keys;   const dpf_key* keys;    /* group keys, <= 2             */
   int32_t n_aggs;   const dpf_agg* aggs;    /* <= 4                         */
+  dpf_col_id scan_col; /* any column of the scanned table; names the table
+                          when no predicate, join, key or aggregate does
+                          (e.g. a bare COUNT(*)); 0 = none              */
 } dpf_plan;
 
 /* Launch configuration; 0 in a field = chosen by the library (tuning cache,
@@ -267,6 +270,18 @@ dpf_status dpf_read_result(dpf_ctx* ctx, dpf_prep_id prep, int32_t i, dpf_record
 /* Tuning the batch will launch with (after defaults and cache lookup). */
 dpf_status dpf_prep_tuning(dpf_ctx* ctx, dpf_prep_id prep, dpf_tuning* out);
 dpf_status dpf_release(dpf_ctx* ctx, dpf_prep_id prep);
+
+/* The unfused baseline: the same single plan prepared as a chain of one
+ * kernel per operator that materialises every intermediate in device
+ * memory (decoded columns, predicate flags, row-id lists after each join),
+ * like the separate-kernel data path the paper compares with (Sec. 5.1).
+ * Launched, captured and read with the calls above.  Errors as
+ * dpf_prepare. */
+dpf_status dpf_prepare_unfused(dpf_ctx* ctx, const dpf_plan* plan, dpf_prep_id* out);
+/* Kernel launches per run and device bytes of intermediates written by the
+ * last completed run (0 for the fused kernel); waits for that run. */
+dpf_status dpf_prep_stats(dpf_ctx* ctx, dpf_prep_id prep, uint32_t* launches,
+                          uint64_t* intermediate_bytes);
 
 /* One-shot form (Sec. 3.1): prepare + launch on `stream`; out_ids[i]
  * names plan i's result.  n > 1 runs every plan in one persistent launch. */

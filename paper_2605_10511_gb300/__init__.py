@@ -69,7 +69,7 @@ class Plan(C.Structure):
     _fields_ = [("n_preds", C.c_int32), ("preds", C.POINTER(Pred)),
                 ("n_joins", C.c_int32), ("joins", C.POINTER(Join)),
                 ("n_keys", C.c_int32), ("keys", C.POINTER(Key)),
-                ("n_aggs", C.c_int32), ("aggs", C.POINTER(Agg))]
+                ("n_aggs", C.c_int32), ("aggs", C.POINTER(Agg)), ("scan_col", C.c_int32)]
 
 
 class Tuning(C.Structure):
@@ -111,6 +111,8 @@ _SIGS = {
                                     C.c_int32]),
     "dpf_prep_tuning": (C.c_int32, [_P, C.c_int32, C.POINTER(Tuning)]),
     "dpf_release": (C.c_int32, [_P, C.c_int32]),
+    "dpf_prepare_unfused": (C.c_int32, [_P, C.POINTER(Plan), C.POINTER(C.c_int32)]),
+    "dpf_prep_stats": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]),
     "dpf_execute_plan": (C.c_int32, [_P, C.POINTER(Plan), C.c_int32, _P, C.POINTER(C.c_int64)]),
     "dpf_fetch_result": (C.c_int32, [_P, C.c_int64, _P, C.c_uint64, C.POINTER(C.c_uint64), C.c_int32]),
 }
@@ -335,6 +337,16 @@ class Context:
         _check(lib().dpf_prep_tuning(self.h, prep, C.byref(t)))
         return {"chunk_rows": t.chunk_rows, "threads": t.threads, "ht_placement": t.ht_placement,
                 "ctas_per_sm": t.ctas_per_sm}
+
+    def prepare_unfused(self, plan):
+        out = C.c_int32()
+        _check(lib().dpf_prepare_unfused(self.h, C.byref(plan.plan), C.byref(out)))
+        return out.value
+
+    def prep_stats(self, prep):
+        n, b = C.c_uint32(), C.c_uint64()
+        _check(lib().dpf_prep_stats(self.h, prep, C.byref(n), C.byref(b)))
+        return {"launches": n.value, "intermediate_bytes": b.value}
 
     def release(self, prep):
         _check(lib().dpf_release(self.h, prep))

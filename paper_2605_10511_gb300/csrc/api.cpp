@@ -84,6 +84,12 @@ struct Prep {
   cudaGraphExec_t gexec = nullptr;
   bool oneshot = false;
   std::vector<char> fetched;
+  // unfused baseline chain
+  bool unfused = false;
+  UnfusedChain U{};
+  uint8_t* unf_scratch = nullptr;
+  uint32_t launches = 1;
+  uint64_t fixed_inter_bytes = 0;   // decoded columns + flags per run
 };
 
 struct dpf_ctx {
@@ -458,6 +464,11 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
       (i == 0 ? Q.agg_a : Q.agg_b)[a] = uint8_t(idx);
     }
   }
+  if (cs.ids.empty() && P.scan_col != 0) {
+    int idx;
+    dpf_status st = cs.add(P.scan_col, &idx);
+    if (st) return st;
+  }
   if (cs.ids.empty()) return fail(DPF_EINVAL, "plan names no column of the scanned table");
   if (steps.size() > size_t(kMaxSteps)) return fail(DPF_EINVAL, "plan compiles to more than %d steps", kMaxSteps);
   Q.nsteps = uint32_t(steps.size());
@@ -484,7 +495,19 @@ dpf_status release_prep(dpf_ctx* c, Prep* p) {
   dev_free(c, p->dqbegin);
   dev_free(c, p->sched);
   dev_free(c, p->scratch);
+  dev_free(c, p->unf_scratch);
   return DPF_OK;
+}
+
+// Launch of a prepared batch (fused kernel or unfused chain) on s.
+cudaError_t launch_prep(Prep* p, cudaStream_t s) {
+  if (p->unfused) {
+    uint32_t n = 0;
+    cudaError_t e = launch_unfused(p->U, s, &n);
+    p->launches = n;
+    return e;
+  }
+  return launch_fused(p->L, s);
 }
 
 dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tuning* tuning, Prep** out) {
@@ -968,7 +991,7 @@ dpf_status dpf_launch(dpf_ctx* c, dpf_prep_id id, void* stream) {
   Prep* p = find_prep(c, id);
   if (!p) return fail(DPF_EINVAL, "unknown batch %d", id);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  CUDA_TRY(launch_fused(p->L, s));
+  CUDA_TRY(launch_prep(p, s));
   CUDA_TRY(cudaEventRecord(p->ev, s));
   p->launched = true;
   return DPF_OK;
@@ -987,7 +1010,7 @@ dpf_status dpf_capture_graph(dpf_ctx* c, dpf_prep_id id, void* stream) {
   // set the smem attribute before capture (not a stream operation)
   fused_blocks_per_sm(p->L.threads, p->L.smem_tables, p->L.host_data);
   CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = launch_fused(p->L, s);
+  cudaError_t e = launch_prep(p, s);
   cudaGraph_t graph = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(s, &graph);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -1020,6 +1043,94 @@ dpf_status dpf_read_result(dpf_ctx* c, dpf_prep_id id, int32_t i, dpf_record* bu
   Prep* p = find_prep(c, id);
   if (!p) return fail(DPF_EINVAL, "unknown batch %d", id);
   return read_result(c, p, i, buf, cap, n_out, timeout_ms);
+}
+
+dpf_status dpf_prepare_unfused(dpf_ctx* c, const dpf_plan* plan, dpf_prep_id* out) {
+  if (!c || !plan || !out) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  dpf_tuning t{};
+  t.ht_placement = DPF_HT_GLOBAL;
+  Prep* p;
+  dpf_status st = prepare(c, plan, 1, &t, &p);
+  if (st) return st;
+  const DevQuery& Q = p->hq[0];
+  if (p->L.host_data) {
+    dpf_release(c, p->id);
+    return fail(DPF_EINVAL, "the unfused chain reads device-resident columns only");
+  }
+  const uint64_t n = Q.nrows;
+  // layout: per column decoded arrays, flags, two (rid, gid) lists, counts
+  uint64_t bytes = 0;
+  std::vector<uint64_t> off_v(Q.ncols), off_l(Q.ncols), off_o(Q.ncols);
+  uint64_t fixed = 0;
+  for (uint32_t i = 0; i < Q.ncols; ++i) {
+    if (Q.cols[i].codec == C_STR) {
+      off_l[i] = bytes; bytes += align16(4 * n);
+      off_o[i] = bytes; bytes += align16(8 * n);
+      fixed += 12 * n;
+    } else {
+      off_v[i] = bytes; bytes += align16(4 * n);
+      fixed += 4 * n;
+    }
+  }
+  const uint64_t off_flags = bytes; bytes += align16(n);
+  fixed += n;
+  uint64_t off_list[4];
+  for (int k = 0; k < 4; ++k) { off_list[k] = bytes; bytes += align16(4 * n); }
+  const uint64_t off_counts = bytes; bytes += 8 * kUnfusedCounts;
+  if ((st = dev_alloc(c, bytes, reinterpret_cast<void**>(&p->unf_scratch)))) {
+    dpf_release(c, p->id);
+    return st;
+  }
+  UnfusedChain& U = p->U;
+  U.q = Q;
+  U.dq = p->dq;
+  for (uint32_t i = 0; i < Q.ncols; ++i) {
+    if (Q.cols[i].codec == C_STR) {
+      U.lens[i] = reinterpret_cast<int32_t*>(p->unf_scratch + off_l[i]);
+      U.offs[i] = reinterpret_cast<uint64_t*>(p->unf_scratch + off_o[i]);
+    } else {
+      U.vals[i] = reinterpret_cast<int32_t*>(p->unf_scratch + off_v[i]);
+    }
+  }
+  U.flags = p->unf_scratch + off_flags;
+  U.rid[0] = reinterpret_cast<uint32_t*>(p->unf_scratch + off_list[0]);
+  U.gid[0] = reinterpret_cast<uint32_t*>(p->unf_scratch + off_list[1]);
+  U.rid[1] = reinterpret_cast<uint32_t*>(p->unf_scratch + off_list[2]);
+  U.gid[1] = reinterpret_cast<uint32_t*>(p->unf_scratch + off_list[3]);
+  U.counts = reinterpret_cast<unsigned long long*>(p->unf_scratch + off_counts);
+  U.sched = p->sched;
+  p->unfused = true;
+  p->fixed_inter_bytes = fixed;
+  *out = p->id;
+  return DPF_OK;
+}
+
+dpf_status dpf_prep_stats(dpf_ctx* c, dpf_prep_id id, uint32_t* launches, uint64_t* inter) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  Prep* p = find_prep(c, id);
+  if (!p) return fail(DPF_EINVAL, "unknown batch %d", id);
+  if (launches) *launches = p->launches;
+  if (inter) {
+    *inter = 0;
+    if (p->unfused) {
+      if (p->launched) {
+        CUDA_TRY(cudaEventSynchronize(p->ev));
+        unsigned long long counts[kUnfusedCounts];
+        CUDA_TRY(cudaMemcpyAsync(counts, p->U.counts, sizeof counts, cudaMemcpyDeviceToHost, c->io));
+        CUDA_TRY(cudaStreamSynchronize(c->io));
+        uint64_t lists = 0;
+        for (int k = 0; k < kUnfusedCounts; ++k) lists += counts[k] * 8;
+        *inter = p->fixed_inter_bytes + lists;
+      } else {
+        *inter = p->fixed_inter_bytes;
+      }
+    }
+  }
+  return DPF_OK;
 }
 
 dpf_status dpf_prep_tuning(dpf_ctx* c, dpf_prep_id id, dpf_tuning* out) {

@@ -45,4 +45,22 @@ cudaError_t launch_build_count(const BuildLaunch& L, cudaStream_t s);
 cudaError_t launch_build_insert(const BuildLaunch& L, cudaStream_t s);
 cudaError_t launch_init_table(uint2* table, uint32_t slots, cudaStream_t s);
 
+// Unfused per-operator chain (baseline).  Buffers for every intermediate:
+// decoded columns, predicate flags, two ping-pong (row id, group id) lists
+// and the device-side list lengths.
+struct UnfusedChain {
+  DevQuery q;                 // host copy of the compiled plan
+  const DevQuery* dq;         // device copy (read by the assembly kernel)
+  int32_t* vals[kMaxCols];    // decoded int columns
+  int32_t* lens[kMaxCols];    // decoded string lengths
+  uint64_t* offs[kMaxCols];   // absolute string byte offsets in the column blob
+  uint8_t* flags;
+  uint32_t* rid[2];
+  uint32_t* gid[2];
+  unsigned long long* counts; // [2 + kMaxSteps] list lengths
+  Sched* sched;
+};
+constexpr int kUnfusedCounts = 2 + kMaxSteps;
+cudaError_t launch_unfused(const UnfusedChain& U, cudaStream_t s, uint32_t* launches);
+
 }  // namespace dpf

@@ -93,7 +93,8 @@ class Engine:
         plan = Plan(len(q["preds"]), C.cast(preds, C.POINTER(Pred)),
                     len(q["joins"]), C.cast(joins, C.POINTER(Join)),
                     len(q["group"]), C.cast(keys, C.POINTER(Key)),
-                    len(q["aggs"]), C.cast(aggs, C.POINTER(Agg)))
+                    len(q["aggs"]), C.cast(aggs, C.POINTER(Agg)),
+                    self.col(w, f, next(iter(w["tables"][f]["cols"]))))
         return PlanHandle(plan, (preds, joins, keys, aggs))
 
     def run(self, w, stream=None, tuning=None):
@@ -101,6 +102,17 @@ class Engine:
         self.load_workload(w)
         h = self.plan(w, stream)
         prep = self.ctx.prepare([h], tuning)
+        try:
+            self.ctx.launch(prep, stream)
+            return self.ctx.read_result(prep, 0)
+        finally:
+            self.ctx.release(prep)
+
+    def run_unfused(self, w, stream=None):
+        """The same query through the unfused per-operator chain."""
+        self.load_workload(w)
+        h = self.plan(w, stream)
+        prep = self.ctx.prepare_unfused(h)
         try:
             self.ctx.launch(prep, stream)
             return self.ctx.read_result(prep, 0)

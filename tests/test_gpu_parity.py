@@ -67,6 +67,27 @@ def test_workload_shapes(eng, shapes, name):
     assert_same(eng.run(w), expect(w), name)
 
 
+@pytest.mark.parametrize("seed", range(0, 40, 3))
+def test_unfused_chain_random_small(eng, seed):
+    w = synth.tiny_random_workload(seed)
+    assert_same(eng.run_unfused(w), expect(w), w["name"])
+
+
+@pytest.mark.parametrize("name", ["scan", "star", "strings"])
+def test_unfused_chain_shapes(eng, shapes, name):
+    w = shapes[name]
+    assert_same(eng.run_unfused(w), expect(w), name)
+    h = eng.plan(w)
+    prep = eng.ctx.prepare_unfused(h)
+    try:
+        eng.ctx.launch(prep)
+        eng.ctx.read_result(prep, 0)
+        st = eng.ctx.prep_stats(prep)
+        assert st["launches"] >= 4 and st["intermediate_bytes"] > 4 * w["tables"][w["fact"]]["rows"]
+    finally:
+        eng.ctx.release(prep)
+
+
 def test_clustered_and_unsorted_star_agree(eng, shapes):
     assert_same(eng.run(shapes["star"]), eng.run(shapes["star_unsorted"]))
 
