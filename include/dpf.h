@@ -283,6 +283,30 @@ dpf_status dpf_prepare_unfused(dpf_ctx* ctx, const dpf_plan* plan, dpf_prep_id* 
 dpf_status dpf_prep_stats(dpf_ctx* ctx, dpf_prep_id prep, uint32_t* launches,
                           uint64_t* intermediate_bytes);
 
+/* For callers that cannot allocate device memory while they run a query
+ * (a framework that has reserved all device memory in its own pool, a
+ * serving loop whose policy forbids allocation, code running inside another
+ * allocator).  The paper has no counterpart; this is a library convenience.
+ * Runs ONE plan through the fused kernel on `stream` and allocates nothing:
+ * the kernel's scratch (scheduler counters, the compiled plan, the per-group
+ * int64 accumulators) lives in a fixed 1 MiB region of device memory that is
+ * part of the library image (every GPU that loads the library holds it until
+ * the process exits).  The caller passes the outputs:
+ *   out: device dpf_record[cap], cap >= the plan's group domain (1 when
+ *        ungrouped); records are written ascending by key tuple
+ *   out_count: device uint32, receives the number of records
+ * Asynchronous; read the outputs after synchronising `stream`.  The first
+ * call on a device looks up the region's device address (a one-time set-up
+ * per device); make that first call before any stream capture.  Every call
+ * shares the one region per device and clears it before use, so calls whose
+ * kernels overlap on the GPU (different streams, or different threads) race
+ * and give wrong results: serialise them.  Device-side data checks are not
+ * reported by this call.  Errors: DPF_EINVAL (a plan needing more than 1 MiB
+ * of scratch: 2816 bytes + 8 x domain x (1 + aggregates); cap below the
+ * domain; the dpf_prepare plan errors), DPF_ECUDA. */
+dpf_status dpf_execute_noalloc(dpf_ctx* ctx, const dpf_plan* plan, void* stream, dpf_record* out,
+                               uint64_t cap, uint32_t* out_count);
+
 /* One-shot form (Sec. 3.1): prepare + launch on `stream`; out_ids[i]
  * names plan i's result.  n > 1 runs every plan in one persistent launch. */
 dpf_status dpf_execute_plan(dpf_ctx* ctx, const dpf_plan* plans, int32_t n, void* stream,

@@ -113,6 +113,7 @@ _SIGS = {
     "dpf_release": (C.c_int32, [_P, C.c_int32]),
     "dpf_prepare_unfused": (C.c_int32, [_P, C.POINTER(Plan), C.POINTER(C.c_int32)]),
     "dpf_prep_stats": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]),
+    "dpf_execute_noalloc": (C.c_int32, [_P, C.POINTER(Plan), _P, _P, C.c_uint64, _P]),
     "dpf_execute_plan": (C.c_int32, [_P, C.POINTER(Plan), C.c_int32, _P, C.POINTER(C.c_int64)]),
     "dpf_fetch_result": (C.c_int32, [_P, C.c_int64, _P, C.c_uint64, C.POINTER(C.c_uint64), C.c_int32]),
 }
@@ -350,6 +351,13 @@ class Context:
 
     def release(self, prep):
         _check(lib().dpf_release(self.h, prep))
+
+    def execute_noalloc(self, plan, out_ptr, cap, count_ptr, stream=None):
+        """One plan through the fused kernel with no device allocation by
+        the library; ``out_ptr`` / ``count_ptr`` are caller-owned device
+        buffers (dpf_record[cap], uint32)."""
+        _check(lib().dpf_execute_noalloc(self.h, C.byref(plan.plan), _stream_ptr(stream),
+                                         C.c_void_p(out_ptr), int(cap), C.c_void_p(count_ptr)))
 
     def execute(self, plans, stream=None):
         arr = (Plan * len(plans))(*[p.plan for p in plans])

@@ -664,6 +664,42 @@ dpf_status read_result(dpf_ctx* c, Prep* p, int32_t i, dpf_record* buf, uint64_t
 
 }  // namespace
 
+namespace dpf {
+
+// Compiles one plan for dpf_execute_noalloc (no device allocation): the
+// device plan with hash tables placed in shared memory as dpf_prepare's
+// automatic placement would, the table bytes and the launch geometry.
+dpf_status noalloc_compile(dpf_ctx* c, const dpf_plan* plan, DevQuery* Q, size_t* smem_tables, bool* host,
+                           int* device, int* num_sms) {
+  std::vector<const HashTable*> probes;
+  dpf_status st = compile_plan(c, *plan, *Q, host, probes);
+  if (st) return st;
+  size_t used = 0;
+  uint32_t nt = 0;
+  for (uint32_t s = 0; s < Q->nsteps; ++s) {
+    DevStep& S = Q->steps[s];
+    if (S.kind != ST_PROBE || nt >= uint32_t(kMaxSmemTables)) continue;
+    const size_t bytes = size_t(S.ht_mask + 1) * 8;
+    if (used + bytes > size_t(64 * 1024)) continue;
+    Q->tables[nt].src = S.ht;
+    Q->tables[nt].slots = S.ht_mask + 1;
+    Q->tables[nt].offset = uint32_t(used);
+    S.ht_smem = int32_t(nt);
+    used += bytes;
+    ++nt;
+  }
+  Q->ntables = nt;
+  Q->smem_table_bytes = uint32_t(used);
+  *smem_tables = used;
+  *device = c->device;
+  *num_sms = c->num_sms;
+  return DPF_OK;
+}
+
+std::recursive_mutex& ctx_mutex(dpf_ctx* c) { return c->mu; }
+
+}  // namespace dpf
+
 // ======================================================================
 // C ABI
 // ======================================================================

@@ -1,6 +1,7 @@
 // Host-side helpers shared by the library's C++ translation units.
 #pragma once
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdint>
 #include <string>
