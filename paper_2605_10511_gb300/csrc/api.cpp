@@ -61,8 +61,11 @@ struct Column {
 
 struct HashTable {
   int32_t id = 0, table = 0, npay = 0;
-  uint2* slots = nullptr;
-  uint32_t capacity = 0;
+  int kind = HT_OPEN;
+  uint2* slots = nullptr;         // HT_OPEN
+  uint32_t capacity = 0;          // HT_OPEN slots, HT_DIRECT entries
+  uint32_t* direct = nullptr;     // HT_DIRECT
+  int32_t kmin = 0;
   uint64_t entries = 0;
   uint32_t pay_dom[2] = {0, 0};
   const int32_t* pay_dict[2] = {nullptr, nullptr};
@@ -106,6 +109,7 @@ struct dpf_ctx {
   cudaStream_t io = nullptr;      // private non-blocking stream for copies
   Sched* bsched = nullptr;        // status word of hash builds
   unsigned long long* bcount = nullptr;
+  int32_t* bkminmax = nullptr;
   int num_sms = 0;
   int smem_optin = 0;
 };
@@ -254,7 +258,6 @@ dpf_status validate_pages(uint32_t codec, const uint8_t* pages, uint64_t size, c
 dpf_status compile_pred(const Column& c, const dpf_pred& p, DevStep& S, int col_index) {
   std::memset(&S, 0, sizeof S);
   S.col = uint8_t(col_index);
-  S.ht_smem = -1;
   if (p.op == DPF_OP_PREFIX) {
     if (c.codec != C_STR) return fail(DPF_EINVAL, "PREFIX needs a STR column (column %d)", c.id);
     if (p.prefix_len < 0 || p.prefix_len > DPF_MAX_PREFIX) return fail(DPF_EINVAL, "prefix_len %d out of range", p.prefix_len);
@@ -393,9 +396,16 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
     std::memset(&S, 0, sizeof S);
     S.kind = ST_PROBE;
     S.col = uint8_t(idx);
-    S.ht = ht->second.slots;
-    S.ht_mask = ht->second.capacity - 1;
-    S.ht_smem = -1;
+    const HashTable& H = ht->second;
+    S.ht_kind = uint8_t(H.kind);
+    if (H.kind == HT_DIRECT) {
+      S.ht = H.direct;
+      S.kmin = H.kmin;
+      S.krange = H.capacity;
+    } else {
+      S.ht = H.slots;
+      S.ht_mask = H.capacity - 1;
+    }
     probe_step.push_back(steps.size());
     steps.push_back(S);
     probes.push_back(&ht->second);
@@ -442,8 +452,7 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
       S.kind = ST_KEY;
       S.col = uint8_t(idx);
       S.key_mul = Q.key_div[k];
-      S.ht_smem = -1;
-      steps.push_back(S);
+          steps.push_back(S);
     }
   }
   Q.naggs = uint32_t(P.n_aggs);
@@ -477,6 +486,29 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
   Q.page_rows = cs.page_rows;
   *host = cs.host;
   return DPF_OK;
+}
+
+// Places join tables in the CTA's shared-memory region, in probe order,
+// while they fit the budget: open-addressing tables as 8-byte slots, direct
+// tables as 1/2/4-byte group-id contributions.  Returns the bytes used.
+size_t place_tables(DevQuery& Q, size_t budget) {
+  const uint32_t width = Q.domain <= 255 ? 1u : (Q.domain <= 65535 ? 2u : 4u);
+  size_t used = 0;
+  for (uint32_t s = 0; s < Q.nsteps; ++s) {
+    DevStep& S = Q.steps[s];
+    if (S.kind != ST_PROBE) continue;
+    S.smem_width = 0;
+    const uint32_t w = S.ht_kind == HT_DIRECT ? width : 8u;
+    const size_t bytes = S.ht_kind == HT_DIRECT ? size_t(S.krange) * w : size_t(S.ht_mask + 1) * 8;
+    const size_t at = (used + 15) & ~size_t(15);
+    if (at + bytes > budget) continue;
+    S.smem_width = uint8_t(w);
+    S.smem_off = uint32_t(at);
+    used = at + bytes;
+  }
+  used = (used + 15) & ~size_t(15);
+  Q.smem_table_bytes = uint32_t(used);
+  return used;
 }
 
 void fill_tuning_defaults(dpf_ctx* c, dpf_tuning& t) {
@@ -519,7 +551,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   if (tuning) t = *tuning;
   fill_tuning_defaults(c, t);
   if (t.chunk_rows % 2048 != 0 || t.chunk_rows > (1u << 24)) return fail(DPF_EINVAL, "chunk_rows %u must be a multiple of 2048", t.chunk_rows);
-  if (t.threads != 128 && t.threads != 256 && t.threads != 512) return fail(DPF_EINVAL, "threads must be 128, 256 or 512");
+  if (t.threads != 128 && t.threads != 256) return fail(DPF_EINVAL, "threads must be 128 or 256");
   bool host = false;
   uint64_t tickets = 0;
   std::vector<uint64_t> qbegin(size_t(n) + 1);
@@ -527,10 +559,11 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   std::vector<uint64_t> off_acc(n), off_done(n), off_outn(n), off_out(n);
   uint64_t scratch = 0;
   size_t max_tables = 0;
+  uint32_t acc_slots = 0;
   const size_t table_budget =
       t.ht_placement == DPF_HT_GLOBAL ? 0
       : t.ht_placement == DPF_HT_SMEM ? size_t(std::max(0, c->smem_optin - int(kSmemAccSlots * 8) - 4096))
-                                      : size_t(64 * 1024);
+                                      : size_t(48 * 1024);
   for (int i = 0; i < n; ++i) {
     DevQuery& Q = p->hq[i];
     bool h = false;
@@ -538,23 +571,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
     dpf_status st = compile_plan(c, plans[i], Q, &h, probes);
     if (st) return fail(st, "plan %d: %s", i, t_last_error.c_str());
     host |= h;
-    // shared-memory placement of hash tables, in probe order, within budget
-    size_t used = 0;
-    uint32_t nt = 0;
-    for (uint32_t s = 0; s < Q.nsteps; ++s) {
-      DevStep& S = Q.steps[s];
-      if (S.kind != ST_PROBE || nt >= uint32_t(kMaxSmemTables)) continue;
-      const size_t bytes = size_t(S.ht_mask + 1) * 8;
-      if (used + bytes > table_budget) continue;
-      Q.tables[nt].src = S.ht;
-      Q.tables[nt].slots = S.ht_mask + 1;
-      Q.tables[nt].offset = uint32_t(used);
-      S.ht_smem = int32_t(nt);
-      used += bytes;
-      ++nt;
-    }
-    Q.ntables = nt;
-    Q.smem_table_bytes = uint32_t(used);
+    const size_t used = place_tables(Q, table_budget);
     max_tables = std::max(max_tables, used);
     Q.chunk_rows = t.chunk_rows;
     Q.nchunks = (Q.nrows + t.chunk_rows - 1) / t.chunk_rows;
@@ -563,6 +580,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
     tickets += Q.nchunks;
     const uint32_t S1 = 1 + Q.naggs;
     Q.use_smem_acc = uint64_t(Q.domain) * S1 <= kSmemAccSlots ? 1u : 0u;
+    if (Q.use_smem_acc) acc_slots = std::max<uint32_t>(acc_slots, Q.domain * S1);
     off_acc[i] = scratch; scratch += align16(uint64_t(Q.domain) * S1 * 8);
     off_done[i] = scratch; scratch += 16;
     off_outn[i] = scratch; scratch += 16;
@@ -593,7 +611,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
     release_prep(c, p.get());
     return fail(DPF_ECUDA, "prepare: %s", cudaGetErrorString(e));
   }
-  int per_sm = fused_blocks_per_sm(int(t.threads), max_tables, host);
+  int per_sm = fused_blocks_per_sm(int(t.threads), acc_slots, max_tables, host);
   if (per_sm < 1) {
     release_prep(c, p.get());
     return fail(DPF_EINVAL, "fused kernel does not fit on an SM with %u threads and %zu table bytes", t.threads, max_tables);
@@ -608,6 +626,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   p->L.threads = int(t.threads);
   p->L.grid = int(std::max<uint64_t>(1, std::min<uint64_t>(uint64_t(c->num_sms) * t.ctas_per_sm, tickets)));
   p->L.smem_tables = max_tables;
+  p->L.acc_slots = acc_slots;
   p->L.host_data = host;
   p->fetched.assign(size_t(n), 0);
   p->id = c->next_prep++;
@@ -674,22 +693,7 @@ dpf_status noalloc_compile(dpf_ctx* c, const dpf_plan* plan, DevQuery* Q, size_t
   std::vector<const HashTable*> probes;
   dpf_status st = compile_plan(c, *plan, *Q, host, probes);
   if (st) return st;
-  size_t used = 0;
-  uint32_t nt = 0;
-  for (uint32_t s = 0; s < Q->nsteps; ++s) {
-    DevStep& S = Q->steps[s];
-    if (S.kind != ST_PROBE || nt >= uint32_t(kMaxSmemTables)) continue;
-    const size_t bytes = size_t(S.ht_mask + 1) * 8;
-    if (used + bytes > size_t(64 * 1024)) continue;
-    Q->tables[nt].src = S.ht;
-    Q->tables[nt].slots = S.ht_mask + 1;
-    Q->tables[nt].offset = uint32_t(used);
-    S.ht_smem = int32_t(nt);
-    used += bytes;
-    ++nt;
-  }
-  Q->ntables = nt;
-  Q->smem_table_bytes = uint32_t(used);
+  const size_t used = place_tables(*Q, size_t(48 * 1024));
   *smem_tables = used;
   *device = c->device;
   *num_sms = c->num_sms;
@@ -729,7 +733,9 @@ dpf_status dpf_create(dpf_ctx** out, int32_t device, uint64_t hbm_budget, const 
   CUDA_TRY(cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
   CUDA_TRY(cudaStreamCreateWithFlags(&c->io, cudaStreamNonBlocking));
   dpf_status st;
-  if ((st = dev_alloc_t(c.get(), 1, &c->bsched)) || (st = dev_alloc_t(c.get(), 1, &c->bcount))) return st;
+  if ((st = dev_alloc_t(c.get(), 1, &c->bsched)) || (st = dev_alloc_t(c.get(), 1, &c->bcount)) ||
+      (st = dev_alloc_t(c.get(), 2, &c->bkminmax)))
+    return st;
   CUDA_TRY(cudaMemsetAsync(c->bsched, 0, sizeof(Sched), c->io));
   CUDA_TRY(cudaStreamSynchronize(c->io));
   *out = c.release();
@@ -744,10 +750,14 @@ dpf_status dpf_destroy(dpf_ctx* c) {
     cudaDeviceSynchronize();
     for (auto& kv : c->preps) release_prep(c, kv.second.get());
     c->preps.clear();
-    for (auto& kv : c->hts) dev_free(c, kv.second.slots);
+    for (auto& kv : c->hts) {
+      dev_free(c, kv.second.slots);
+      dev_free(c, kv.second.direct);
+    }
     for (auto& kv : c->cols) free_column(c, kv.second);
     dev_free(c, c->bsched);
     dev_free(c, c->bcount);
+    dev_free(c, c->bkminmax);
     if (c->io) cudaStreamDestroy(c->io);
   }
   delete c;
@@ -945,7 +955,9 @@ dpf_status dpf_build_hash(dpf_ctx* c, dpf_col_id key_col, const dpf_col_id* payl
   L.nrows = Q.nrows;
   L.page_rows = Q.page_rows;
   L.host_data = cs.host;
+  L.kminmax = c->bkminmax;
   unsigned long long kept = 0;
+  int32_t minmax[2] = {INT32_MAX, INT32_MIN};
   uint32_t status = 0;
   auto cleanup = [&](dpf_status r) {
     dev_free(c, dq);
@@ -954,28 +966,44 @@ dpf_status dpf_build_hash(dpf_ctx* c, dpf_col_id key_col, const dpf_col_id* payl
   cudaError_t e = cudaMemcpyAsync(dq, &Q, sizeof Q, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->bcount, 0, 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->bsched, 0, sizeof(Sched), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->bkminmax, minmax, 8, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = launch_build_count(L, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&kept, c->bcount, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(minmax, c->bkminmax, 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cleanup(fail(DPF_ECUDA, "hash build (count): %s", cudaGetErrorString(e)));
-  uint64_t cap = 16;
-  while (cap < 2 * kept) cap <<= 1;
-  if (cap > (1ull << 31)) return cleanup(fail(DPF_ENOMEM, "hash table of %llu entries is too large", kept));
-  if ((st = dev_alloc_t(c, cap, &ht.slots))) return cleanup(st);
-  ht.capacity = uint32_t(cap);
+  // dense key ranges get a direct table (one load per probe); others open
+  // addressing with capacity a power of two >= 2 x entries
+  const uint64_t range = kept ? uint64_t(int64_t(minmax[1]) - int64_t(minmax[0]) + 1) : 0;
+  const bool wide_payload = n_payload == 2 && ht.pay_dom[0] == 65536 && ht.pay_dom[1] == 65536;
+  if (!wide_payload && range <= std::max<uint64_t>(64 * kept, 1u << 20) && range <= (1u << 26)) {
+    ht.kind = HT_DIRECT;
+    ht.kmin = kept ? minmax[0] : 0;
+    ht.capacity = uint32_t(range);
+    if ((st = dev_alloc_t(c, std::max<uint64_t>(range, 1), &ht.direct))) return cleanup(st);
+    L.direct = ht.direct;
+    L.kmin = ht.kmin;
+    L.krange = ht.capacity;
+    e = launch_init_direct(ht.direct, uint32_t(std::max<uint64_t>(range, 1)), s);
+  } else {
+    uint64_t cap = 16;
+    while (cap < 2 * kept) cap <<= 1;
+    if (cap > (1ull << 31)) return cleanup(fail(DPF_ENOMEM, "hash table of %llu entries is too large", kept));
+    if ((st = dev_alloc_t(c, cap, &ht.slots))) return cleanup(st);
+    ht.kind = HT_OPEN;
+    ht.capacity = uint32_t(cap);
+    L.table = ht.slots;
+    L.mask = uint32_t(cap - 1);
+    e = launch_init_table(ht.slots, uint32_t(cap), s);
+  }
   ht.entries = kept;
-  L.table = ht.slots;
-  L.mask = uint32_t(cap - 1);
-  e = launch_init_table(ht.slots, uint32_t(cap), s);
   if (e == cudaSuccess) e = launch_build_insert(L, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&status, &c->bsched->status, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
+  if (e != cudaSuccess || status) {
     dev_free(c, ht.slots);
-    return cleanup(fail(DPF_ECUDA, "hash build (insert): %s", cudaGetErrorString(e)));
-  }
-  if (status) {
-    dev_free(c, ht.slots);
+    dev_free(c, ht.direct);
+    if (e != cudaSuccess) return cleanup(fail(DPF_ECUDA, "hash build (insert): %s", cudaGetErrorString(e)));
     if (status & S_DUPKEY) return cleanup(fail(DPF_EDUPKEY, "duplicate key in hash build of column %d", key_col));
     if (status & S_CORRUPT) return cleanup(fail(DPF_EINVAL, "key column %d holds the reserved key INT32_MIN or corrupt data", key_col));
     return cleanup(fail(DPF_EINTERNAL, "hash build status %u", status));
@@ -1005,6 +1033,7 @@ dpf_status dpf_drop_hash(dpf_ctx* c, dpf_ht_id id) {
   if (it == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", id);
   cudaDeviceSynchronize();
   dev_free(c, it->second.slots);
+  dev_free(c, it->second.direct);
   c->hts.erase(it);
   return DPF_OK;
 }
@@ -1044,7 +1073,7 @@ dpf_status dpf_capture_graph(dpf_ctx* c, dpf_prep_id id, void* stream) {
   if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
   if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
   // set the smem attribute before capture (not a stream operation)
-  fused_blocks_per_sm(p->L.threads, p->L.smem_tables, p->L.host_data);
+  fused_blocks_per_sm(p->L.threads, p->L.acc_slots, p->L.smem_tables, p->L.host_data);
   CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = launch_prep(p, s);
   cudaGraph_t graph = nullptr;

@@ -13,11 +13,13 @@ namespace {
 
 constexpr unsigned long long kEmptySlot = 0x0000000080000000ull;  // {INT32_MIN, 0}
 
-template <bool kHost, bool kInsert>
-__global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__ qdev, uint2* table,
-                                                    uint32_t mask, unsigned long long* count,
+// kMode 0: count kept rows and their key range; 1: insert into an
+// open-addressing table; 2: insert into a direct table.
+template <bool kHost, int kMode>
+__global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__ qdev, BuildLaunch L,
                                                     unsigned int* status) {
   __shared__ __align__(16) DevQuery Q;
+  __shared__ uint32_t lists[8 * kTileRows];
   {
     const uint4* src = reinterpret_cast<const uint4*>(qdev);
     uint4* dst = reinterpret_cast<uint4*>(&Q);
@@ -25,65 +27,85 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  uint32_t* list = lists + (threadIdx.x >> 5) * kTileRows;
   const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  const uint64_t P = Q.page_rows;
-  const uint64_t npages = (Q.nrows + P - 1) / P;
-  const uint64_t tiles_per_page = (P / kMB + TB - 1) / TB;
+  const uint64_t PR = Q.page_rows;
+  const uint64_t npages = (Q.nrows + PR - 1) / PR;
+  const uint64_t tiles_per_page = (PR / kMB + TB - 1) / TB;
   unsigned long long kept = 0;
+  int32_t kmin = INT32_MAX, kmax = INT32_MIN;
   for (uint64_t w = warp; w < npages * tiles_per_page; w += nwarps) {
     const uint64_t p = w / tiles_per_page;
     const uint32_t i0 = uint32_t(w % tiles_per_page) * TB;
-    const uint32_t prow = uint32_t(tmin<uint64_t>(P, Q.nrows - p * P));
-    const uint32_t nmb_page = (prow + kMB - 1) / kMB;
-    if (i0 >= nmb_page) continue;
+    PageState P;
+    page_begin<kHost>(Q, p, lane, P);
+    if (i0 >= P.nmb_page) continue;
+    const uint32_t nmb = tmin<uint32_t>(TB, P.nmb_page - i0);
+    const TileHdr H = load_headers<kHost>(Q, P, i0, nmb, lane);
     TileState T;
-    tile_begin<kHost>(Q, p, i0, tmin<uint32_t>(TB, nmb_page - i0), lane, T);
-    if (!tile_steps<kHost>(Q, T, nullptr, lane, status)) continue;
-    if (!kInsert) {
-      kept += __popc(T.alive);
-      continue;
-    }
-    uint32_t key[TB][4], p0[TB][4], p1[TB][4], anym;
-    MbHdr H[TB];
-    tile_decode<kHost>(Q, Q.build_key, T, lane, key, anym, H, status);
-    if (Q.build_npay > 0) tile_decode<kHost>(Q, Q.build_pay[0], T, lane, p0, anym, H, status);
-    if (Q.build_npay > 1) tile_decode<kHost>(Q, Q.build_pay[1], T, lane, p1, anym, H, status);
-#pragma unroll
-    for (int t = 0; t < TB; ++t)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (!((T.alive >> (4 * t + k)) & 1u)) continue;
-        const int32_t kv = int32_t(key[t][k]);
-        if (kv == kEmptyKey) {
-          atomicOr(status, S_CORRUPT);
+    tile_init(P, i0, nmb, lane, T);
+    tile_first_step<kHost>(Q, P, H, T, nullptr, lane, status);
+    uint32_t n = tile_compact(T, list, lane);
+    n = list_steps<kHost>(Q, P, H, list, n, nullptr, lane, status);
+    for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+      const bool valid = j0 + lane < n;
+      const uint32_t r = valid ? (list[j0 + lane] & ((1u << kRowBits) - 1u)) : 0u;
+      const int32_t kv = int32_t(row_value<kHost>(Q, Q.build_key, P, H, r, valid, lane, status));
+      const uint32_t c0 = Q.build_npay > 0 ? row_value<kHost>(Q, Q.build_pay[0], P, H, r, valid, lane, status) : 0u;
+      const uint32_t c1 = Q.build_npay > 1 ? row_value<kHost>(Q, Q.build_pay[1], P, H, r, valid, lane, status) : 0u;
+      if (!valid) continue;
+      if (kMode == 0) {
+        ++kept;
+        kmin = min(kmin, kv);
+        kmax = max(kmax, kv);
+        continue;
+      }
+      if (kv == kEmptyKey) {
+        atomicOr(status, S_CORRUPT);
+        continue;
+      }
+      const uint32_t pay = (c0 & 0xffffu) | ((c1 & 0xffffu) << 16);
+      if (kMode == 2) {
+        const uint32_t off = uint32_t(kv) - uint32_t(L.kmin);
+        if (off >= L.krange) {
+          atomicOr(status, S_INTERNAL);
           continue;
         }
-        uint32_t pay = 0;
-        if (Q.build_npay > 0) pay |= p0[t][k] & 0xffffu;
-        if (Q.build_npay > 1) pay |= (p1[t][k] & 0xffffu) << 16;
-        const unsigned long long slot = (unsigned long long)uint32_t(kv) | ((unsigned long long)pay << 32);
-        uint32_t h = fmix32(uint32_t(kv)) & mask;
-        bool done = false;
-        for (uint32_t n = 0; n <= mask && !done; ++n) {
-          unsigned long long* addr = reinterpret_cast<unsigned long long*>(table + h);
-          const unsigned long long old = atomicCAS(addr, kEmptySlot, slot);
-          if (old == kEmptySlot) {
-            done = true;
-          } else if (int32_t(uint32_t(old)) == kv) {
-            atomicOr(status, S_DUPKEY);
-            done = true;
-          } else {
-            h = (h + 1) & mask;
-          }
-        }
-        if (!done) atomicOr(status, S_INTERNAL);
+        if (atomicCAS(L.direct + off, kAbsent, pay) != kAbsent) atomicOr(status, S_DUPKEY);
+        continue;
       }
+      const unsigned long long slot = (unsigned long long)uint32_t(kv) | ((unsigned long long)pay << 32);
+      uint32_t h = fmix32(uint32_t(kv)) & L.mask;
+      bool done = false;
+      for (uint32_t q = 0; q <= L.mask && !done; ++q) {
+        unsigned long long* addr = reinterpret_cast<unsigned long long*>(L.table + h);
+        const unsigned long long old = atomicCAS(addr, kEmptySlot, slot);
+        if (old == kEmptySlot) {
+          done = true;
+        } else if (int32_t(uint32_t(old)) == kv) {
+          atomicOr(status, S_DUPKEY);
+          done = true;
+        } else {
+          h = (h + 1) & L.mask;
+        }
+      }
+      if (!done) atomicOr(status, S_INTERNAL);
+    }
+    __syncwarp();
   }
-  if (!kInsert) {
+  if (kMode == 0) {
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) kept += __shfl_down_sync(kFull, kept, d);
-    if (lane == 0 && kept) atomicAdd(count, kept);
+    for (int d = 16; d > 0; d >>= 1) {
+      kept += __shfl_down_sync(kFull, kept, d);
+      kmin = min(kmin, __shfl_down_sync(kFull, kmin, d));
+      kmax = max(kmax, __shfl_down_sync(kFull, kmax, d));
+    }
+    if (lane == 0 && kept) {
+      atomicAdd(L.count, kept);
+      atomicMin(L.kminmax, kmin);
+      atomicMax(L.kminmax + 1, kmax);
+    }
   }
 }
 
@@ -101,24 +123,28 @@ int build_grid(uint64_t nrows, uint64_t page_rows) {
 
 }  // namespace
 
-cudaError_t launch_build_count(const BuildLaunch& L, cudaStream_t s) {
+template <int kMode>
+cudaError_t launch_build_mode(const BuildLaunch& L, cudaStream_t s) {
   const int g = build_grid(L.nrows, L.page_rows);
-  if (L.host_data) build_kernel<true, false><<<g, 256, 0, s>>>(L.q, nullptr, 0, L.count, &L.sched->status);
-  else build_kernel<false, false><<<g, 256, 0, s>>>(L.q, nullptr, 0, L.count, &L.sched->status);
+  if (L.host_data) build_kernel<true, kMode><<<g, 256, 0, s>>>(L.q, L, &L.sched->status);
+  else build_kernel<false, kMode><<<g, 256, 0, s>>>(L.q, L, &L.sched->status);
   return cudaGetLastError();
 }
 
+cudaError_t launch_build_count(const BuildLaunch& L, cudaStream_t s) { return launch_build_mode<0>(L, s); }
+
 cudaError_t launch_build_insert(const BuildLaunch& L, cudaStream_t s) {
-  const int g = build_grid(L.nrows, L.page_rows);
-  if (L.host_data) build_kernel<true, true><<<g, 256, 0, s>>>(L.q, L.table, L.mask, nullptr, &L.sched->status);
-  else build_kernel<false, true><<<g, 256, 0, s>>>(L.q, L.table, L.mask, nullptr, &L.sched->status);
-  return cudaGetLastError();
+  return L.direct ? launch_build_mode<2>(L, s) : launch_build_mode<1>(L, s);
 }
 
 cudaError_t launch_init_table(uint2* table, uint32_t slots, cudaStream_t s) {
   const int g = int(tmin<uint32_t>((slots + 255) / 256, 2048u));
   init_table_kernel<<<g, 256, 0, s>>>(table, slots);
   return cudaGetLastError();
+}
+
+cudaError_t launch_init_direct(uint32_t* table, uint32_t n, cudaStream_t s) {
+  return cudaMemsetAsync(table, 0xff, size_t(n) * 4, s);
 }
 
 }  // namespace dpf

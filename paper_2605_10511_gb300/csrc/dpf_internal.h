@@ -42,7 +42,6 @@ constexpr int kMaxSteps = 12;
 constexpr int kMaxIn = 8;
 constexpr int kMaxPrefix = 32;
 constexpr int kMaxAggCols = 4;
-constexpr int kMaxSmemTables = 4;
 constexpr int32_t kEmptyKey = int32_t(0x80000000);
 
 // Device status bits (OR-ed into a status word, read by the host).
@@ -66,31 +65,38 @@ enum StepKind : uint8_t {
   ST_KEY = 7,       // DICT column code added to gid
 };
 
+// Join tables (Sec. 3.1 hash tables; representation chosen at build):
+//  HT_OPEN   open addressing, slots {key, payload}, linear probing;
+//  HT_DIRECT dense key range: entry[key - kmin] = payload or kAbsent.
+// payload = code0 | code1 << 16 (dictionary codes of the payload columns).
+enum HtKind : uint8_t { HT_OPEN = 0, HT_DIRECT = 1 };
+constexpr uint32_t kAbsent = 0xffffffffu;
+
 struct DevStep {
   uint8_t kind, col, nin, plen;
   int32_t lo, hi;
   int32_t in[kMaxIn];
   // ST_PROBE
-  const uint2* ht;        // global slots {key, payload}
-  uint32_t ht_mask;       // capacity - 1 (power of two)
-  int32_t ht_smem;        // index of the smem copy (-1: probe global memory)
+  const void* ht;         // OPEN: uint2 slots; DIRECT: uint32 entries (global)
+  uint32_t ht_mask;       // OPEN: capacity - 1 (power of two)
+  int32_t kmin;           // DIRECT: smallest key
+  uint32_t krange;        // DIRECT: number of entries
+  uint8_t ht_kind;
+  uint8_t smem_width;     // 0: probe global memory; OPEN: 8 (slots copied);
+                          // DIRECT: 1/2/4-byte entries holding this join's
+                          // group-id contribution (all ones = absent)
+  uint16_t pad_;
+  uint32_t smem_off;      // byte offset of the copy in the CTA's table region
   uint32_t mul0, mul1;    // gid multipliers of payload fields 0 and 1 (0 = unused)
   // ST_KEY
   uint32_t key_mul;
   uint8_t pfx[kMaxPrefix];
 };
 
-struct SmemTable {
-  const uint2* src;       // global slots
-  uint32_t slots;         // capacity
-  uint32_t offset;        // byte offset inside the CTA's table region
-};
-
 struct alignas(16) DevQuery {
   DevColumn cols[kMaxCols];
   DevStep steps[kMaxSteps];
-  SmemTable tables[kMaxSmemTables];
-  uint32_t ncols, nsteps, ntables, smem_table_bytes;
+  uint32_t ncols, nsteps, smem_table_bytes, pad0_;
   uint64_t nrows;
   uint32_t page_rows;
   uint32_t chunk_rows;

@@ -113,90 +113,53 @@ __device__ void finish_query(const DevQuery& Q, unsigned long long* sacc, uint32
   __syncthreads();
 }
 
-// Aggregation of a tile's live rows (Kernel #3 hash aggregation; int64 as
-// in Sec. 4.3).  domain == 1: per-lane registers; otherwise int64 atomics
-// into the CTA's shared accumulators (or global ones for large domains).
+// Aggregation over a warp's survivor list (Kernel #3 hash aggregation;
+// int64 as in Sec. 4.3).  domain == 1: per-lane int64 sums reduced across
+// the warp; otherwise int64 atomics into the CTA's shared accumulators (or
+// the query's global ones for large domains), indexed by the dense group id.
 template <bool kHost>
-__device__ __forceinline__ void tile_aggregate(const DevQuery& Q, TileState& T, int lane,
-                                               unsigned long long* acc, long long (&racc)[5],
-                                               unsigned int* status) {
+__device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageState& P, const TileHdr& Hd,
+                                               const uint32_t* list, uint32_t n, int lane,
+                                               unsigned long long* acc, unsigned int* status) {
   const uint32_t S1 = 1 + Q.naggs;
   const bool single = Q.domain == 1;
-  if (!single) {
-    // a corrupt dictionary code could push a group id out of the domain
+  long long sum[5] = {0, 0, 0, 0, 0};
+  for (uint32_t i0 = 0; i0 < n; i0 += 32) {
+    bool valid = i0 + lane < n;
+    const uint32_t e = valid ? list[i0 + lane] : 0u;
+    const uint32_t r = e & ((1u << kRowBits) - 1u);
+    const uint32_t gid = e >> kRowBits;
+    if (!single && valid && gid >= Q.domain) {  // a corrupt dictionary code
+      atomicOr(status, S_CORRUPT);
+      valid = false;
+    }
+    if (single) sum[0] += valid ? 1 : 0;
+    else if (valid) atomicAdd(acc + uint64_t(gid) * S1, 1ull);
 #pragma unroll
-    for (int t = 0; t < TB; ++t)
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (((T.alive >> (4 * t + k)) & 1u) && T.gid[t][k] >= Q.domain) {
-          T.alive &= ~(1u << (4 * t + k));
-          atomicOr(status, S_CORRUPT);
+    for (uint32_t a = 0; a < 4; ++a) {
+      if (a >= Q.naggs) break;
+      const uint32_t op = Q.agg_op[a];
+      long long x = 1;
+      if (op != DPF_AGG_COUNT) {
+        const int32_t va = int32_t(row_value<kHost>(Q, Q.agg_a[a], P, Hd, r, valid, lane, status));
+        if (op == DPF_AGG_SUM) {
+          x = va;
+        } else {
+          const int32_t vb = int32_t(row_value<kHost>(Q, Q.agg_b[a], P, Hd, r, valid, lane, status));
+          x = op == DPF_AGG_SUM_MUL
+                  ? (long long)((unsigned long long)(long long)va * (unsigned long long)(long long)vb)
+                  : (long long)va - (long long)vb;
         }
+      }
+      if (single) sum[1 + a] += valid ? x : 0;
+      else if (valid) atomicAdd(acc + uint64_t(gid) * S1 + 1 + a, (unsigned long long)x);
+    }
   }
   if (single) {
-    racc[0] += __popc(T.alive);
-  } else {
 #pragma unroll
-    for (int t = 0; t < TB; ++t)
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if ((T.alive >> (4 * t + k)) & 1u) atomicAdd(acc + uint64_t(T.gid[t][k]) * S1, 1ull);
-  }
-  for (uint32_t a = 0; a < Q.naggs; ++a) {
-    const uint32_t op = Q.agg_op[a];
-    uint32_t va[TB][4], vb[TB][4], anym;
-    MbHdr H[TB];
-    if (op != DPF_AGG_COUNT) tile_decode<kHost>(Q, Q.agg_a[a], T, lane, va, anym, H, status);
-    if (op == DPF_AGG_SUM_MUL || op == DPF_AGG_SUM_SUB)
-      tile_decode<kHost>(Q, Q.agg_b[a], T, lane, vb, anym, H, status);
-#pragma unroll
-    for (int t = 0; t < TB; ++t)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (!((T.alive >> (4 * t + k)) & 1u)) continue;
-        long long x;
-        if (op == DPF_AGG_COUNT) x = 1;
-        else if (op == DPF_AGG_SUM) x = (long long)int32_t(va[t][k]);
-        else if (op == DPF_AGG_SUM_MUL)
-          x = (long long)((unsigned long long)(long long)int32_t(va[t][k]) *
-                          (unsigned long long)(long long)int32_t(vb[t][k]));
-        else x = (long long)int32_t(va[t][k]) - (long long)int32_t(vb[t][k]);
-        if (single) racc[1 + a] += x;
-        else atomicAdd(acc + uint64_t(T.gid[t][k]) * S1 + 1 + a, (unsigned long long)x);
-      }
-  }
-}
-
-// One ticket: the rows [chunk*chunk_rows, +chunk_rows) of Q's fact table,
-// cut at page boundaries into warp tiles that the CTA's warps share.
-template <bool kHost>
-__device__ void process_chunk(const DevQuery& Q, uint64_t chunk, unsigned long long* acc,
-                              const uint8_t* stab, unsigned int* status) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint64_t P = Q.page_rows;
-  const uint64_t r0 = chunk * Q.chunk_rows;
-  const uint64_t r1 = min(Q.nrows, r0 + Q.chunk_rows);
-  long long racc[5] = {0, 0, 0, 0, 0};
-  uint64_t tile_base = 0;
-  for (uint64_t p = r0 / P; p <= (r1 - 1) / P; ++p) {
-    const uint64_t pr0 = max(r0, p * P), pr1 = min(r1, (p + 1) * P);
-    const uint32_t mb0 = uint32_t((pr0 - p * P) / kMB);
-    const uint32_t mb1 = uint32_t((pr1 - p * P + kMB - 1) / kMB);
-    const uint32_t ntiles = (mb1 - mb0 + TB - 1) / TB;
-    uint32_t j = uint32_t((warp + nw - int(tile_base % nw)) % nw);
-    for (; j < ntiles; j += nw) {
-      const uint32_t i0 = mb0 + j * TB;
-      TileState T;
-      tile_begin<kHost>(Q, p, i0, tmin<uint32_t>(TB, mb1 - i0), lane, T);
-      if (tile_steps<kHost>(Q, T, stab, lane, status))
-        tile_aggregate<kHost>(Q, T, lane, acc, racc, status);
-    }
-    tile_base += ntiles;
-  }
-  if (Q.domain == 1) {
-    const uint32_t S1 = 1 + Q.naggs;
-    for (uint32_t s = 0; s < S1; ++s) {
-      long long x = racc[s];
+    for (uint32_t s = 0; s < 5; ++s) {
+      if (s >= S1) break;
+      long long x = sum[s];
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) x += __shfl_down_sync(kFull, x, d);
       if (lane == 0 && x != 0) atomicAdd(acc + s, (unsigned long long)x);
@@ -204,14 +167,81 @@ __device__ void process_chunk(const DevQuery& Q, uint64_t chunk, unsigned long l
   }
 }
 
+// One ticket: the rows [chunk*chunk_rows, +chunk_rows) of Q's fact table,
+// cut at page boundaries into warp tiles that the CTA's warps share.  Each
+// warp loads the headers of its next tile before working on the current one.
 template <bool kHost>
-__global__ void __launch_bounds__(512) fused_kernel(const DevQuery* __restrict__ queries,
-                                                     const uint64_t* __restrict__ qbegin, int nq,
-                                                     uint64_t total, Sched* sched) {
+__device__ void process_chunk(const DevQuery& Q, uint64_t chunk, unsigned long long* acc,
+                              const uint8_t* stab, uint32_t* lists, unsigned int* status) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint64_t PR = Q.page_rows;
+  const uint64_t r0 = chunk * Q.chunk_rows;
+  const uint64_t r1 = tmin<uint64_t>(Q.nrows, r0 + Q.chunk_rows);
+  uint64_t tile_base = 0;
+  for (uint64_t p = r0 / PR; p <= (r1 - 1) / PR; ++p) {
+    const uint64_t pr0 = tmax<uint64_t>(r0, p * PR), pr1 = tmin<uint64_t>(r1, (p + 1) * PR);
+    const uint32_t mb0 = uint32_t((pr0 - p * PR) / kMB);
+    const uint32_t mb1 = uint32_t((pr1 - p * PR + kMB - 1) / kMB);
+    const uint32_t ntiles = (mb1 - mb0 + TB - 1) / TB;
+    uint32_t j = uint32_t((warp + nw - int(tile_base % nw)) % nw);
+    tile_base += ntiles;
+    if (j >= ntiles) continue;
+    PageState P;
+    page_begin<kHost>(Q, p, lane, P);
+    TileHdr H = load_headers<kHost>(Q, P, mb0 + j * TB, tmin<uint32_t>(TB, mb1 - (mb0 + j * TB)), lane);
+    for (; j < ntiles; j += nw) {
+      const uint32_t i0 = mb0 + j * TB;
+      const uint32_t nmb = tmin<uint32_t>(TB, mb1 - i0);
+      const uint32_t jn = j + nw;
+      TileHdr Hn{0, 0, 0, 0};
+      if (jn < ntiles) Hn = load_headers<kHost>(Q, P, mb0 + jn * TB, tmin<uint32_t>(TB, mb1 - (mb0 + jn * TB)), lane);
+      TileState T;
+      tile_init(P, i0, nmb, lane, T);
+      tile_first_step<kHost>(Q, P, H, T, stab, lane, status);
+      uint32_t* list = lists + uint32_t(warp) * kTileRows;
+      uint32_t n = tile_compact(T, list, lane);
+      n = list_steps<kHost>(Q, P, H, list, n, stab, lane, status);
+      if (n) list_aggregate<kHost>(Q, P, H, list, n, lane, acc, status);
+      H = Hn;
+    }
+  }
+}
+
+// Copies a query's shared-memory join tables into the CTA's table region:
+// open-addressing slots as they are, direct tables as 1/2/4-byte group-id
+// contributions (all ones = absent).
+__device__ void load_smem_tables(const DevQuery& Q, uint8_t* stab) {
+  for (uint32_t s = 0; s < Q.nsteps; ++s) {
+    const DevStep& S = Q.steps[s];
+    if (S.kind != ST_PROBE || S.smem_width == 0) continue;
+    if (S.ht_kind == HT_OPEN) {
+      const uint2* src = static_cast<const uint2*>(S.ht);
+      uint2* dst = reinterpret_cast<uint2*>(stab + S.smem_off);
+      for (uint32_t i = threadIdx.x; i <= S.ht_mask; i += blockDim.x) dst[i] = __ldg(src + i);
+      continue;
+    }
+    const uint32_t* src = static_cast<const uint32_t*>(S.ht);
+    for (uint32_t i = threadIdx.x; i < S.krange; i += blockDim.x) {
+      const uint32_t e = __ldg(src + i);
+      const uint32_t c = (e & 0xffffu) * S.mul0 + (e >> 16) * S.mul1;
+      if (S.smem_width == 1) stab[S.smem_off + i] = e == kAbsent ? 0xffu : uint8_t(c);
+      else if (S.smem_width == 2)
+        reinterpret_cast<uint16_t*>(stab + S.smem_off)[i] = e == kAbsent ? 0xffffu : uint16_t(c);
+      else reinterpret_cast<uint32_t*>(stab + S.smem_off)[i] = e == kAbsent ? kAbsent : c;
+    }
+  }
+}
+
+template <bool kHost>
+__global__ void __launch_bounds__(256, 2) fused_kernel(const DevQuery* __restrict__ queries,
+                                                       const uint64_t* __restrict__ qbegin, int nq,
+                                                       uint64_t total, Sched* sched, uint32_t acc_slots,
+                                                     uint32_t tables_bytes) {
   extern __shared__ __align__(16) uint8_t dyn[];
   __shared__ CtaState cs;
   unsigned long long* sacc = reinterpret_cast<unsigned long long*>(dyn);
-  uint8_t* stab = dyn + kSmemAccSlots * sizeof(unsigned long long);
+  uint8_t* stab = dyn + ((acc_slots * sizeof(unsigned long long) + 15) & ~size_t(15));
+  uint32_t* lists = reinterpret_cast<uint32_t*>(stab + tables_bytes);
   int cur = -1;
   uint32_t mine = 0;
   for (;;) {
@@ -246,17 +276,13 @@ __global__ void __launch_bounds__(512) fused_kernel(const DevQuery* __restrict__
         const uint32_t n = Q.domain * (1 + Q.naggs);
         for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sacc[i] = 0ull;
       }
-      for (uint32_t ti = 0; ti < Q.ntables; ++ti) {
-        const SmemTable& st = Q.tables[ti];
-        uint2* dst = reinterpret_cast<uint2*>(stab + st.offset);
-        for (uint32_t i = threadIdx.x; i < st.slots; i += blockDim.x) dst[i] = __ldg(st.src + i);
-      }
+      load_smem_tables(Q, stab);
       __syncthreads();
       cur = qi;
       mine = 0;
     }
     const DevQuery& Q = cs.q;
-    process_chunk<kHost>(Q, t - Q.chunk_begin, Q.use_smem_acc ? sacc : Q.acc, stab, &sched->status);
+    process_chunk<kHost>(Q, t - Q.chunk_begin, Q.use_smem_acc ? sacc : Q.acc, stab, lists, &sched->status);
     ++mine;
     __syncthreads();
   }
@@ -273,12 +299,13 @@ __global__ void __launch_bounds__(512) fused_kernel(const DevQuery* __restrict__
 
 }  // namespace
 
-size_t fused_dynamic_smem(size_t smem_tables) {
-  return kSmemAccSlots * sizeof(unsigned long long) + smem_tables;
+size_t fused_dynamic_smem(uint32_t acc_slots, size_t smem_tables, int threads) {
+  return ((acc_slots * sizeof(unsigned long long) + 15) & ~size_t(15)) + ((smem_tables + 15) & ~size_t(15)) +
+         size_t(threads / 32) * kTileRows * sizeof(uint32_t);
 }
 
-int fused_blocks_per_sm(int threads, size_t smem_tables, bool host_data) {
-  const size_t smem = fused_dynamic_smem(smem_tables);
+int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, bool host_data) {
+  const size_t smem = fused_dynamic_smem(acc_slots, smem_tables, threads);
   int n = 0;
   if (host_data) {
     cudaFuncSetAttribute(fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -291,15 +318,18 @@ int fused_blocks_per_sm(int threads, size_t smem_tables, bool host_data) {
 }
 
 cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s) {
-  const size_t smem = fused_dynamic_smem(L.smem_tables);
+  const size_t smem = fused_dynamic_smem(L.acc_slots, L.smem_tables, L.threads);
+  const uint32_t tb = uint32_t((L.smem_tables + 15) & ~size_t(15));
   if (L.host_data) {
     cudaError_t e = cudaFuncSetAttribute(fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    fused_kernel<true><<<L.grid, L.threads, smem, s>>>(L.queries, L.qbegin, L.nq, L.total_chunks, L.sched);
+    fused_kernel<true><<<L.grid, L.threads, smem, s>>>(L.queries, L.qbegin, L.nq, L.total_chunks, L.sched,
+                                                       L.acc_slots, tb);
   } else {
     cudaError_t e = cudaFuncSetAttribute(fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    fused_kernel<false><<<L.grid, L.threads, smem, s>>>(L.queries, L.qbegin, L.nq, L.total_chunks, L.sched);
+    fused_kernel<false><<<L.grid, L.threads, smem, s>>>(L.queries, L.qbegin, L.nq, L.total_chunks, L.sched,
+                                                        L.acc_slots, tb);
   }
   return cudaGetLastError();
 }

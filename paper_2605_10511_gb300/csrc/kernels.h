@@ -21,29 +21,35 @@ struct FusedLaunch {
   uint64_t total_chunks;
   Sched* sched;
   int grid, threads;
-  size_t smem_tables;   // bytes of the CTA's hash-table region
+  uint32_t acc_slots;   // int64 shared accumulators per CTA (max over the batch)
+  size_t smem_tables;   // bytes of the CTA's join-table region
   bool host_data;       // some column lives in mapped pinned host memory
 };
 cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s);
-// Occupancy of the fused kernel for (threads, dynamic smem).
-int fused_blocks_per_sm(int threads, size_t smem_tables, bool host_data);
-size_t fused_dynamic_smem(size_t smem_tables);
+// Occupancy of the fused kernel for (threads, dynamic smem); also sets the
+// kernel's dynamic shared-memory limit.
+int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, bool host_data);
+size_t fused_dynamic_smem(uint32_t acc_slots, size_t smem_tables, int threads);
 
 // Hash build (Kernel #1 of Sec. 3.1).  `q` describes the dimension scan:
 // cols/steps as for the fused kernel, build_key/build_pay name columns.
 struct BuildLaunch {
   const DevQuery* q;          // device copy
-  uint2* table;               // capacity slots, initialised by init_table
+  uint2* table;               // open addressing: capacity slots (mask + 1)
   uint32_t mask;
-  unsigned long long* count;  // device counter (count mode)
+  uint32_t* direct;           // direct table: krange entries (or nullptr)
+  int32_t kmin;
+  uint32_t krange;
+  unsigned long long* count;  // device counter (count pass)
+  int32_t* kminmax;           // device {min, max} of kept keys (count pass)
   Sched* sched;               // status word
-  int key_col, npay, pay_col0, pay_col1;
   uint64_t nrows, page_rows;
   bool host_data;
 };
 cudaError_t launch_build_count(const BuildLaunch& L, cudaStream_t s);
 cudaError_t launch_build_insert(const BuildLaunch& L, cudaStream_t s);
 cudaError_t launch_init_table(uint2* table, uint32_t slots, cudaStream_t s);
+cudaError_t launch_init_direct(uint32_t* table, uint32_t n, cudaStream_t s);
 
 // Unfused per-operator chain (baseline).  Buffers for every intermediate:
 // decoded columns, predicate flags, two ping-pong (row id, group id) lists

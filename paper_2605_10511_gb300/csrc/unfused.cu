@@ -137,9 +137,8 @@ __global__ void compact_kernel(const uint8_t* flags, uint64_t n, uint32_t* rid, 
 }
 
 __global__ void probe_kernel(const uint32_t* rid_in, const uint32_t* gid_in, const unsigned long long* n_in,
-                             const int32_t* fk, const uint2* ht, uint32_t mask, uint32_t mul0, uint32_t mul1,
-                             uint32_t* rid_out, uint32_t* gid_out, unsigned long long* n_out,
-                             unsigned int* status) {
+                             const int32_t* fk, DevStep S, uint32_t* rid_out, uint32_t* gid_out,
+                             unsigned long long* n_out, unsigned int* status) {
   const uint64_t n = *n_in;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   const uint64_t n_pad = (n + 31) & ~uint64_t(31);
@@ -150,9 +149,17 @@ __global__ void probe_kernel(const uint32_t* rid_in, const uint32_t* gid_in, con
       r = rid_in[i];
       g = gid_in[i];
       const int32_t key = fk[r];
-      if (key != kEmptyKey) hit = ht_probe(ht, mask, key, &pay, status);
+      if (S.ht_kind == HT_DIRECT) {
+        const uint32_t off = uint32_t(key) - uint32_t(S.kmin);
+        if (off < S.krange) {
+          pay = __ldg(static_cast<const uint32_t*>(S.ht) + off);
+          hit = pay != kAbsent;
+        }
+      } else if (key != kEmptyKey) {
+        hit = ht_probe(static_cast<const uint2*>(S.ht), S.ht_mask, key, &pay, status);
+      }
     }
-    append(hit, r, g + (pay & 0xffffu) * mul0 + (pay >> 16) * mul1, rid_out, gid_out, n_out);
+    append(hit, r, g + (pay & 0xffffu) * S.mul0 + (pay >> 16) * S.mul1, rid_out, gid_out, n_out);
   }
 }
 
@@ -297,9 +304,9 @@ cudaError_t launch_unfused(const UnfusedChain& U, cudaStream_t s, uint32_t* laun
   for (uint32_t i = 0; i < Q.nsteps; ++i) {
     const DevStep& S = Q.steps[i];
     if (S.kind != ST_PROBE) continue;
-    probe_kernel<<<grid_for(n, 256), 256, 0, s>>>(U.rid[cur], U.gid[cur], U.counts + slot - 1, U.vals[S.col], S.ht,
-                                                 S.ht_mask, S.mul0, S.mul1, U.rid[cur ^ 1], U.gid[cur ^ 1],
-                                                 U.counts + slot, &U.sched->status);
+    probe_kernel<<<grid_for(n, 256), 256, 0, s>>>(U.rid[cur], U.gid[cur], U.counts + slot - 1, U.vals[S.col], S,
+                                                 U.rid[cur ^ 1], U.gid[cur ^ 1], U.counts + slot,
+                                                 &U.sched->status);
     cur ^= 1;
     ++slot;
     ++L;

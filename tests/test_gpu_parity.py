@@ -93,7 +93,7 @@ def test_clustered_and_unsorted_star_agree(eng, shapes):
 
 
 @pytest.mark.parametrize("chunk_rows", [2048, 16384, 262144])
-@pytest.mark.parametrize("threads", [128, 256, 512])
+@pytest.mark.parametrize("threads", [128, 256])
 @pytest.mark.parametrize("place", ["smem", "global"])
 def test_launch_knobs_do_not_change_results(eng, shapes, chunk_rows, threads, place):
     for name in ("star", "strings"):
