@@ -233,7 +233,8 @@ typedef struct dpf_plan {
  * then defaults). */
 enum dpf_ht_place { DPF_HT_AUTO = 0, DPF_HT_SMEM = 1, DPF_HT_GLOBAL = 2 };
 typedef struct dpf_tuning {
-  uint32_t chunk_rows;   /* rows per scheduling chunk: multiple of 2048          */
+  uint32_t chunk_rows;   /* rows per scheduling ticket (one warp's unit of work):
+                            multiple of 512, at most 2^24; default 2048        */
   uint32_t threads;      /* threads per CTA: 128 or 256                          */
   int32_t ht_placement;  /* enum dpf_ht_place                                     */
   uint32_t ctas_per_sm;  /* persistent CTAs per SM                                */

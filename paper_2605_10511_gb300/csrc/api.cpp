@@ -513,7 +513,7 @@ size_t place_tables(DevQuery& Q, size_t budget) {
 
 void fill_tuning_defaults(dpf_ctx* c, dpf_tuning& t) {
   (void)c;
-  if (t.chunk_rows == 0) t.chunk_rows = 16384;
+  if (t.chunk_rows == 0) t.chunk_rows = kDefaultChunkRows;
   if (t.threads == 0) t.threads = 256;
   if (t.ht_placement == 0) t.ht_placement = DPF_HT_AUTO;
 }
@@ -550,7 +550,8 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   dpf_tuning t{};
   if (tuning) t = *tuning;
   fill_tuning_defaults(c, t);
-  if (t.chunk_rows % 2048 != 0 || t.chunk_rows > (1u << 24)) return fail(DPF_EINVAL, "chunk_rows %u must be a multiple of 2048", t.chunk_rows);
+  if (t.chunk_rows % (kMbPerWarpTile * kMB) != 0 || t.chunk_rows > (1u << 24))
+    return fail(DPF_EINVAL, "chunk_rows %u must be a multiple of %u and at most 2^24", t.chunk_rows, kMbPerWarpTile * kMB);
   if (t.threads != 128 && t.threads != 256) return fail(DPF_EINVAL, "threads must be 128 or 256");
   bool host = false;
   uint64_t tickets = 0;

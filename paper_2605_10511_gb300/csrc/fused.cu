@@ -10,6 +10,8 @@
 // The CTA that flushes a query's last chunk turns its accumulators into
 // records ordered by key tuple (the record format of Kernel #3, Sec. 3.1) and
 // zeroes the scratch state, so the kernel can be replayed from a CUDA graph.
+#include <climits>
+
 #include "../../include/dpf.h"
 #include "tile.cuh"
 
@@ -18,8 +20,8 @@ namespace {
 
 struct alignas(16) CtaState {
   DevQuery q;
-  unsigned long long ticket;
-  int qi;
+  int wq[32];          // query of the ticket each warp holds (INT_MAX: none left)
+  unsigned int mine;   // tickets of the current query this CTA processed
   int last;
   unsigned int warp_sum[32];
 };
@@ -113,96 +115,140 @@ __device__ void finish_query(const DevQuery& Q, unsigned long long* sacc, uint32
   __syncthreads();
 }
 
+// One aggregate over a warp's list, specialised on its operation (dpf_agg_op)
+// and on how its operands are read: kPoint = FOR/DICT columns, one bit field
+// per row; otherwise any codec through row_value (DELTA decodes densely).
+template <bool kHost, int kOp, bool kPoint>
+__device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, const TileHdr& Hd,
+                                         const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
+                                         uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
+  constexpr int U = kPoint ? kListUnroll : 1;  // rounds whose loads are issued together
+  const uint32_t S1 = 1 + Q.naggs;
+  long long sum = 0;
+  for (uint32_t i0 = 0; i0 < n; i0 += 32 * U) {
+    uint32_t r[U], gid[U];
+    bool valid[U];
+    int32_t va[U], vb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      valid[u] = i0 + 32u * u + lane < n;
+      const uint32_t e = valid[u] ? list[i0 + 32u * u + lane] : 0u;
+      r[u] = e & ((1u << kRowBits) - 1u);
+      gid[u] = e >> kRowBits;
+      if (!single && gid[u] >= Q.domain) valid[u] = false;  // reported by list_aggregate
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      va[u] = vb[u] = 0;
+      if (kOp != DPF_AGG_COUNT)
+        va[u] = int32_t(kPoint ? point_value<kHost>(Q, ca, P, Hd, r[u], valid[u])
+                               : row_value<kHost>(Q, ca, P, Hd, r[u], valid[u], lane, status));
+      if (kOp == DPF_AGG_SUM_MUL || kOp == DPF_AGG_SUM_SUB)
+        vb[u] = int32_t(kPoint ? point_value<kHost>(Q, cb, P, Hd, r[u], valid[u])
+                               : row_value<kHost>(Q, cb, P, Hd, r[u], valid[u], lane, status));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      long long x = 1;
+      if (kOp == DPF_AGG_SUM) x = va[u];
+      else if (kOp == DPF_AGG_SUM_MUL)
+        x = (long long)((unsigned long long)(long long)va[u] * (unsigned long long)(long long)vb[u]);
+      else if (kOp == DPF_AGG_SUM_SUB)
+        x = (long long)va[u] - (long long)vb[u];
+      if (single) sum += valid[u] ? x : 0;
+      else if (valid[u]) atomicAdd(acc + uint64_t(gid[u]) * S1 + slot, (unsigned long long)x);
+    }
+  }
+  if (single) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) sum += __shfl_down_sync(kFull, sum, d);
+    if (lane == 0 && sum != 0) atomicAdd(acc + slot, (unsigned long long)sum);
+  }
+}
+
+template <bool kHost, int kOp>
+__device__ __forceinline__ void agg_dispatch(const DevQuery& Q, const PageState& P, const TileHdr& Hd,
+                                             const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
+                                             uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
+  const bool point = Q.cols[ca].codec != C_DELTA && (kOp == DPF_AGG_SUM || Q.cols[cb].codec != C_DELTA);
+  if (point) agg_pass<kHost, kOp, true>(Q, P, Hd, list, n, lane, acc, slot, ca, cb, single, status);
+  else agg_pass<kHost, kOp, false>(Q, P, Hd, list, n, lane, acc, slot, ca, cb, single, status);
+}
+
 // Aggregation over a warp's survivor list (Kernel #3 hash aggregation;
-// int64 as in Sec. 4.3).  domain == 1: per-lane int64 sums reduced across
-// the warp; otherwise int64 atomics into the CTA's shared accumulators (or
-// the query's global ones for large domains), indexed by the dense group id.
+// int64 as in Sec. 4.3): slot 0 counts rows, slot 1 + a holds aggregate a.
+// domain == 1: per-lane int64 sums reduced across the warp; otherwise int64
+// atomics into the CTA's shared accumulators (or the query's global ones for
+// large domains), indexed by the dense group id.
 template <bool kHost>
 __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageState& P, const TileHdr& Hd,
                                                const uint32_t* list, uint32_t n, int lane,
                                                unsigned long long* acc, unsigned int* status) {
   const uint32_t S1 = 1 + Q.naggs;
   const bool single = Q.domain == 1;
-  long long sum[5] = {0, 0, 0, 0, 0};
-  for (uint32_t i0 = 0; i0 < n; i0 += 32) {
-    bool valid = i0 + lane < n;
-    const uint32_t e = valid ? list[i0 + lane] : 0u;
-    const uint32_t r = e & ((1u << kRowBits) - 1u);
-    const uint32_t gid = e >> kRowBits;
-    if (!single && valid && gid >= Q.domain) {  // a corrupt dictionary code
-      atomicOr(status, S_CORRUPT);
-      valid = false;
-    }
-    if (single) sum[0] += valid ? 1 : 0;
-    else if (valid) atomicAdd(acc + uint64_t(gid) * S1, 1ull);
-#pragma unroll
-    for (uint32_t a = 0; a < 4; ++a) {
-      if (a >= Q.naggs) break;
-      const uint32_t op = Q.agg_op[a];
-      long long x = 1;
-      if (op != DPF_AGG_COUNT) {
-        const int32_t va = int32_t(row_value<kHost>(Q, Q.agg_a[a], P, Hd, r, valid, lane, status));
-        if (op == DPF_AGG_SUM) {
-          x = va;
-        } else {
-          const int32_t vb = int32_t(row_value<kHost>(Q, Q.agg_b[a], P, Hd, r, valid, lane, status));
-          x = op == DPF_AGG_SUM_MUL
-                  ? (long long)((unsigned long long)(long long)va * (unsigned long long)(long long)vb)
-                  : (long long)va - (long long)vb;
-        }
-      }
-      if (single) sum[1 + a] += valid ? x : 0;
-      else if (valid) atomicAdd(acc + uint64_t(gid) * S1 + 1 + a, (unsigned long long)x);
+  if (single) {
+    if (lane == 0) atomicAdd(acc, (unsigned long long)n);
+  } else {
+    for (uint32_t i = lane; i < n; i += 32) {
+      const uint32_t gid = list[i] >> kRowBits;
+      if (gid < Q.domain) atomicAdd(acc + uint64_t(gid) * S1, 1ull);
+      else atomicOr(status, S_CORRUPT);  // a corrupt dictionary code
     }
   }
-  if (single) {
-#pragma unroll
-    for (uint32_t s = 0; s < 5; ++s) {
-      if (s >= S1) break;
-      long long x = sum[s];
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) x += __shfl_down_sync(kFull, x, d);
-      if (lane == 0 && x != 0) atomicAdd(acc + s, (unsigned long long)x);
+  for (uint32_t a = 0; a < Q.naggs; ++a) {
+    const int ca = Q.agg_a[a], cb = Q.agg_b[a];
+    switch (Q.agg_op[a]) {
+      case DPF_AGG_COUNT:
+        agg_pass<kHost, DPF_AGG_COUNT, true>(Q, P, Hd, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        break;
+      case DPF_AGG_SUM:
+        agg_dispatch<kHost, DPF_AGG_SUM>(Q, P, Hd, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        break;
+      case DPF_AGG_SUM_MUL:
+        agg_dispatch<kHost, DPF_AGG_SUM_MUL>(Q, P, Hd, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        break;
+      default:
+        agg_dispatch<kHost, DPF_AGG_SUM_SUB>(Q, P, Hd, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        break;
     }
   }
 }
 
 // One ticket: the rows [chunk*chunk_rows, +chunk_rows) of Q's fact table,
-// cut at page boundaries into warp tiles that the CTA's warps share.  Each
-// warp loads the headers of its next tile before working on the current one.
+// processed by one warp, cut at page boundaries into tiles.  Tile headers
+// are loaded two tiles ahead and payloads prefetched into L2 one tile ahead.
 template <bool kHost>
-__device__ void process_chunk(const DevQuery& Q, uint64_t chunk, unsigned long long* acc,
-                              const uint8_t* stab, uint32_t* lists, unsigned int* status) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+__device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long long* acc, const uint8_t* stab,
+                               uint32_t* list, int lane, unsigned int* status) {
   const uint64_t PR = Q.page_rows;
   const uint64_t r0 = chunk * Q.chunk_rows;
   const uint64_t r1 = tmin<uint64_t>(Q.nrows, r0 + Q.chunk_rows);
-  uint64_t tile_base = 0;
   for (uint64_t p = r0 / PR; p <= (r1 - 1) / PR; ++p) {
     const uint64_t pr0 = tmax<uint64_t>(r0, p * PR), pr1 = tmin<uint64_t>(r1, (p + 1) * PR);
     const uint32_t mb0 = uint32_t((pr0 - p * PR) / kMB);
     const uint32_t mb1 = uint32_t((pr1 - p * PR + kMB - 1) / kMB);
     const uint32_t ntiles = (mb1 - mb0 + TB - 1) / TB;
-    uint32_t j = uint32_t((warp + nw - int(tile_base % nw)) % nw);
-    tile_base += ntiles;
-    if (j >= ntiles) continue;
     PageState P;
     page_begin<kHost>(Q, p, lane, P);
-    TileHdr H = load_headers<kHost>(Q, P, mb0 + j * TB, tmin<uint32_t>(TB, mb1 - (mb0 + j * TB)), lane);
-    for (; j < ntiles; j += nw) {
+    auto nmb_of = [&](uint32_t jj) { return tmin<uint32_t>(TB, mb1 - (mb0 + jj * TB)); };
+    TileHdr H = load_headers<kHost>(Q, P, mb0, nmb_of(0), lane);
+    TileHdr Hn{0, 0, 0, 0};
+    if (1 < ntiles) Hn = load_headers<kHost>(Q, P, mb0 + TB, nmb_of(1), lane);
+    if (!kHost) prefetch_payloads(Q, P, H, nmb_of(0), lane);
+    for (uint32_t j = 0; j < ntiles; ++j) {
       const uint32_t i0 = mb0 + j * TB;
-      const uint32_t nmb = tmin<uint32_t>(TB, mb1 - i0);
-      const uint32_t jn = j + nw;
-      TileHdr Hn{0, 0, 0, 0};
-      if (jn < ntiles) Hn = load_headers<kHost>(Q, P, mb0 + jn * TB, tmin<uint32_t>(TB, mb1 - (mb0 + jn * TB)), lane);
+      const uint32_t nmb = nmb_of(j);
+      TileHdr Hnn{0, 0, 0, 0};
+      if (j + 2 < ntiles) Hnn = load_headers<kHost>(Q, P, mb0 + (j + 2) * TB, nmb_of(j + 2), lane);
+      if (!kHost && j + 1 < ntiles) prefetch_payloads(Q, P, Hn, nmb_of(j + 1), lane);
       TileState T;
       tile_init(P, i0, nmb, lane, T);
       tile_first_step<kHost>(Q, P, H, T, stab, lane, status);
-      uint32_t* list = lists + uint32_t(warp) * kTileRows;
       uint32_t n = tile_compact(T, list, lane);
       n = list_steps<kHost>(Q, P, H, list, n, stab, lane, status);
       if (n) list_aggregate<kHost>(Q, P, H, list, n, lane, acc, status);
       H = Hn;
+      Hn = Hnn;
     }
   }
 }
@@ -242,49 +288,59 @@ __global__ void __launch_bounds__(256, 2) fused_kernel(const DevQuery* __restric
   unsigned long long* sacc = reinterpret_cast<unsigned long long*>(dyn);
   uint8_t* stab = dyn + ((acc_slots * sizeof(unsigned long long) + 15) & ~size_t(15));
   uint32_t* lists = reinterpret_cast<uint32_t*>(stab + tables_bytes);
+  // Warps draw tickets on their own (one ticket = chunk_rows rows of one
+  // query, processed by one warp), so no CTA barrier separates tickets.  The
+  // CTA meets only when its warps' tickets leave the current query: it then
+  // moves to the smallest query any warp holds (tickets are handed out in
+  // query order, so every warp reaches that meeting point), flushing the
+  // finished query's accumulators first.
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t* list = lists + uint32_t(warp) * kTileRows;
+  auto draw = [&](unsigned long long& t) -> int {
+    unsigned long long x = 0;
+    if (lane == 0) x = atomicAdd(&sched->next, 1ull);
+    t = __shfl_sync(kFull, x, 0);
+    if (t >= total) return INT_MAX;
+    int lo = 0, hi = nq - 1;  // last query with qbegin <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (__ldg(qbegin + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  unsigned long long held;
+  int hq = draw(held);
   int cur = -1;
-  uint32_t mine = 0;
   for (;;) {
-    if (threadIdx.x == 0) {
-      const unsigned long long t = atomicAdd(&sched->next, 1ull);
-      int qi = -1;
-      if (t < total) {
-        int lo = 0, hi = nq - 1;  // last query with qbegin <= t
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) / 2;
-          if (__ldg(qbegin + mid) <= t) lo = mid; else hi = mid - 1;
-        }
-        qi = lo;
-      }
-      cs.ticket = t;
-      cs.qi = qi;
-    }
+    if (lane == 0) cs.wq[warp] = hq;
     __syncthreads();
-    const unsigned long long t = cs.ticket;
-    const int qi = cs.qi;
-    if (qi != cur) {
-      if (cur >= 0) finish_query(cs.q, sacc, mine, cs);
-      if (qi < 0) break;
-      {  // bring the query's plan into shared memory
-        const uint4* src = reinterpret_cast<const uint4*>(queries + qi);
-        uint4* dst = reinterpret_cast<uint4*>(&cs.q);
-        for (uint32_t i = threadIdx.x; i < sizeof(DevQuery) / 16; i += blockDim.x) dst[i] = __ldg(src + i);
-      }
-      __syncthreads();
-      const DevQuery& Q = cs.q;
-      if (Q.use_smem_acc) {
-        const uint32_t n = Q.domain * (1 + Q.naggs);
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sacc[i] = 0ull;
-      }
-      load_smem_tables(Q, stab);
-      __syncthreads();
-      cur = qi;
-      mine = 0;
+    int next = INT_MAX;
+    for (int w = 0; w < nw; ++w) next = min(next, cs.wq[w]);
+    if (cur >= 0) finish_query(cs.q, sacc, cs.mine, cs);
+    if (next == INT_MAX) break;
+    {  // bring the query's plan into shared memory
+      const uint4* src = reinterpret_cast<const uint4*>(queries + next);
+      uint4* dst = reinterpret_cast<uint4*>(&cs.q);
+      for (uint32_t i = threadIdx.x; i < sizeof(DevQuery) / 16; i += blockDim.x) dst[i] = __ldg(src + i);
     }
+    if (threadIdx.x == 0) cs.mine = 0;
+    __syncthreads();
     const DevQuery& Q = cs.q;
-    process_chunk<kHost>(Q, t - Q.chunk_begin, Q.use_smem_acc ? sacc : Q.acc, stab, lists, &sched->status);
-    ++mine;
+    if (Q.use_smem_acc) {
+      const uint32_t n = Q.domain * (1 + Q.naggs);
+      for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) sacc[i] = 0ull;
+    }
+    load_smem_tables(Q, stab);
     __syncthreads();
+    cur = next;
+    unsigned long long* acc = Q.use_smem_acc ? sacc : Q.acc;
+    uint32_t done_here = 0;
+    while (hq == cur) {
+      process_ticket<kHost>(Q, held - Q.chunk_begin, acc, stab, list, lane, &sched->status);
+      ++done_here;
+      hq = draw(held);
+    }
+    if (lane == 0 && done_here) atomicAdd(&cs.mine, done_here);
   }
   if (threadIdx.x == 0) {
     __threadfence();

@@ -11,6 +11,8 @@ namespace dpf {
 // Shared-memory accumulator capacity of one CTA (int64 slots).
 constexpr uint32_t kSmemAccSlots = 4096;
 constexpr uint32_t kMbPerWarpTile = 4;
+// Rows of one scheduling ticket (one warp's unit of work) unless tuned.
+constexpr uint32_t kDefaultChunkRows = 2048;
 
 // Fused persistent kernel over a batch of compiled queries (Sec. 3.2).
 // qbegin[0..nq] = first ticket of each query (qbegin[nq] = total tickets).

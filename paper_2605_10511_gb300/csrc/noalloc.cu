@@ -98,7 +98,7 @@ extern "C" dpf_status dpf_execute_noalloc(dpf_ctx* ctx, const dpf_plan* plan, vo
   uint8_t* base = nullptr;
   if ((st = scratch_address(device, &base))) return st;
 
-  const uint32_t chunk_rows = 16384;
+  const uint32_t chunk_rows = kDefaultChunkRows;
   Q.chunk_rows = chunk_rows;
   Q.nchunks = (Q.nrows + chunk_rows - 1) / chunk_rows;
   Q.chunk_begin = 0;

@@ -71,6 +71,28 @@ __device__ __forceinline__ TileHdr load_headers(const DevQuery& Q, const PageSta
   return h;
 }
 
+// Asks L2 to fetch [p, p + bytes) (p 16-byte aligned, bytes a multiple of
+// 16): a bulk prefetch that returns at once and needs no completion.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Prefetches the packed payload of every (column, mini block) header a lane
+// holds (see load_headers) into L2, so the tile's later loads, dense or
+// per survivor, find their lines there instead of waiting on HBM.
+__device__ __forceinline__ void prefetch_payloads(const DevQuery& Q, const PageState& P, const TileHdr& H,
+                                                  uint32_t nmb, int lane) {
+  const int hc = lane / TB, ht = lane % TB;
+  const uint64_t hpg = __shfl_sync(kFull, P.pg, hc < int(Q.ncols) ? hc : 0);
+  if (hc >= int(Q.ncols) || ht >= int(nmb)) return;
+  const uint32_t codec = Q.cols[hc].codec;
+  const uint32_t wob = codec == C_DELTA ? H.z : H.y;
+  const uint32_t bw = wob & 0xffu;
+  if (bw == 0 || bw > 32) return;
+  const uint8_t* pay = reinterpret_cast<const uint8_t*>(hpg) + payload_offset(codec, P.prow) + uint64_t(wob >> 8) * 4;
+  prefetch_l2(pay, 16u * bw);
+}
+
 struct TileState {
   uint32_t alive;         // bit 4t+k: row 32k+lane of mini block t is live
   uint32_t gid[TB][4];    // dense group id of each row
@@ -78,6 +100,14 @@ struct TileState {
 
 __device__ __forceinline__ void tile_init(const PageState& P, uint32_t i0, uint32_t nmb, int lane,
                                           TileState& T) {
+#pragma unroll
+  for (int t = 0; t < TB; ++t)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) T.gid[t][k] = 0;
+  if (nmb == uint32_t(TB) && (i0 + TB) * kMB <= P.prow) {  // a full tile
+    T.alive = (TB == 8) ? 0xffffffffu : ((1u << (4 * TB)) - 1u);
+    return;
+  }
   T.alive = 0;
 #pragma unroll
   for (int t = 0; t < TB; ++t)
@@ -85,27 +115,27 @@ __device__ __forceinline__ void tile_init(const PageState& P, uint32_t i0, uint3
     for (int k = 0; k < 4; ++k) {
       const uint32_t r = (i0 + t) * kMB + k * 32 + lane;
       if (t < int(nmb) && r < P.prow) T.alive |= 1u << (4 * t + k);
-      T.gid[t][k] = 0;
     }
 }
 
 // Loads and decodes column c for the mini blocks with live rows: v[t][k]
 // = value of row 32k + lane of mini block t (the payload words are loaded
 // into v and decoded in place).  anym bit t = mini block t was decoded.
-template <bool kHost>
-__device__ __forceinline__ void tile_decode(const DevQuery& Q, int c, const PageState& P, const TileHdr& Hd,
-                                            uint32_t alive, int lane, uint32_t (&v)[TB][4], uint32_t& anym,
-                                            unsigned int* status) {
-  const uint32_t codec = Q.cols[c].codec;
+// Specialised on the codec (FOR/DICT/STR lengths vs DELTA) so the unrolled
+// loops carry no per-value branch on it.
+template <bool kHost, bool kDelta>
+__device__ __forceinline__ void decode_t(const DevQuery& Q, int c, const PageState& P, const TileHdr& Hd,
+                                         uint32_t alive, int lane, uint32_t (&v)[TB][4], uint32_t& anym,
+                                         unsigned int* status) {
   const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, c));
-  const uint32_t* pay = reinterpret_cast<const uint32_t*>(pg + payload_offset(codec, P.prow));
+  const uint32_t* pay = reinterpret_cast<const uint32_t*>(pg + payload_offset(Q.cols[c].codec, P.prow));
   uint32_t hx[TB], hy[TB];
   anym = 0;
 #pragma unroll
   for (int t = 0; t < TB; ++t) {
     bool any = __any_sync(kFull, (alive >> (4 * t)) & 15u) != 0;
     hx[t] = __shfl_sync(kFull, Hd.x, c * TB + t);
-    hy[t] = __shfl_sync(kFull, codec == C_DELTA ? Hd.z : Hd.y, c * TB + t);
+    hy[t] = __shfl_sync(kFull, kDelta ? Hd.z : Hd.y, c * TB + t);
     const uint32_t bw = hy[t] & 0xffu;
     if (any && bw > 32) {
       if (lane == 0) atomicOr(status, S_CORRUPT);
@@ -121,19 +151,31 @@ __device__ __forceinline__ void tile_decode(const DevQuery& Q, int c, const Page
   for (int t = 0; t < TB; ++t) {
     if (!((anym >> t) & 1u)) continue;
     const uint32_t bw = hy[t] & 0xffu;
-    if (codec == C_DELTA) {
-      MbHdr h;
-      h.first = int32_t(hx[t]);
-      h.base = int32_t(__shfl_sync(kFull, Hd.y, c * TB + t));
-      h.bw = bw;
-      h.woff = 0;
-      uint32_t w[4] = {v[t][0], v[t][1], v[t][2], v[t][3]};
-      decode_mb(w, h, C_DELTA, lane, v[t]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[t][k] = unpack_lane(v[t][k], bw, lane);
+    if (kDelta) {
+      // x_j = first + sum_{i<=j} (dmin + p_i), modulo 2^32
+      const uint32_t dmin = __shfl_sync(kFull, Hd.y, c * TB + t);
+      uint32_t carry = hx[t];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t s = warp_incl_scan(v[t][k] + dmin, lane);
+        v[t][k] = carry + s;
+        carry += __shfl_sync(kFull, s, 31);
+      }
     } else {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) v[t][k] = unpack_lane(v[t][k], bw, lane) + hx[t];
+      for (int k = 0; k < 4; ++k) v[t][k] += hx[t];
     }
   }
+}
+
+template <bool kHost>
+__device__ __forceinline__ void tile_decode(const DevQuery& Q, int c, const PageState& P, const TileHdr& Hd,
+                                            uint32_t alive, int lane, uint32_t (&v)[TB][4], uint32_t& anym,
+                                            unsigned int* status) {
+  if (Q.cols[c].codec == C_DELTA) decode_t<kHost, true>(Q, c, P, Hd, alive, lane, v, anym, status);
+  else decode_t<kHost, false>(Q, c, P, Hd, alive, lane, v, anym, status);
 }
 
 // PREFIX step over a STR column: lengths are decoded, their exclusive scan
@@ -171,49 +213,55 @@ __device__ __forceinline__ void tile_prefix(const DevQuery& Q, const DevStep& S,
   }
 }
 
-// Join probe step: live rows that miss are dropped; hits add this join's
-// group-id contribution.
-template <bool kHost>
-__device__ __forceinline__ void tile_probe(const DevQuery& Q, const DevStep& S, const PageState& P,
-                                           const TileHdr& Hd, TileState& T, const uint8_t* stab, int lane,
-                                           unsigned int* status) {
-  uint32_t v[TB][4];
-  uint32_t anym;
-  tile_decode<kHost>(Q, S.col, P, Hd, T.alive, lane, v, anym, status);
-  if (S.ht_kind == HT_DIRECT) {
-    const uint32_t width = S.smem_width;
-    const uint8_t* sm = stab + S.smem_off;
-    const uint32_t* gt = static_cast<const uint32_t*>(S.ht);
+// Probe modes: direct table copied into shared memory as 1/2/4-byte group-id
+// contributions, direct table in global memory, open addressing (shared or
+// global slots).
+enum ProbeMode : int { PM_S1 = 0, PM_S2 = 1, PM_S4 = 2, PM_GDIRECT = 3, PM_OPEN = 4 };
+__device__ __forceinline__ int probe_mode(const DevStep& S) {
+  if (S.ht_kind == HT_OPEN) return PM_OPEN;
+  return S.smem_width == 1 ? PM_S1 : S.smem_width == 2 ? PM_S2 : S.smem_width == 4 ? PM_S4 : PM_GDIRECT;
+}
+
+// Direct-table probe of one key: true on a hit, which adds the join's
+// group-id contribution to gid.
+template <int kMode>
+__device__ __forceinline__ bool probe_direct(const DevStep& S, const uint8_t* stab, uint32_t key, bool valid,
+                                             uint32_t& gid) {
+  const uint32_t off = key - uint32_t(S.kmin);
+  const bool look = valid && off < S.krange;
+  uint32_t e;
+  bool hit;
+  if (kMode == PM_S1) {
+    e = look ? uint32_t(stab[S.smem_off + off]) : 0xffu;
+    hit = e != 0xffu;
+  } else if (kMode == PM_S2) {
+    e = look ? uint32_t(reinterpret_cast<const uint16_t*>(stab + S.smem_off)[off]) : 0xffffu;
+    hit = e != 0xffffu;
+  } else if (kMode == PM_S4) {
+    e = look ? reinterpret_cast<const uint32_t*>(stab + S.smem_off)[off] : kAbsent;
+    hit = e != kAbsent;
+  } else {
+    e = look ? __ldg(static_cast<const uint32_t*>(S.ht) + off) : kAbsent;
+    hit = e != kAbsent;
+    e = (e & 0xffffu) * S.mul0 + (e >> 16) * S.mul1;
+  }
+  gid += hit ? e : 0u;
+  return hit;
+}
+
+// Join probe step over a decoded tile: live rows that miss are dropped;
+// hits add this join's group-id contribution.
+template <int kMode>
+__device__ __forceinline__ void dense_probe(const DevStep& S, const uint8_t* stab, const uint32_t (&v)[TB][4],
+                                            uint32_t anym, TileState& T, unsigned int* status) {
+  if (kMode != PM_OPEN) {
 #pragma unroll
     for (int t = 0; t < TB; ++t) {
       if (!((anym >> t) & 1u)) continue;
       uint32_t keep = 0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const uint32_t off = v[t][k] - uint32_t(S.kmin);
-        const bool look = ((T.alive >> (4 * t + k)) & 1u) && off < S.krange;
-        uint32_t contrib = 0;
-        bool hit = false;
-        if (width == 1) {
-          const uint32_t e = look ? uint32_t(sm[off]) : 0xffu;
-          hit = e != 0xffu;
-          contrib = e;
-        } else if (width == 2) {
-          const uint32_t e = look ? uint32_t(reinterpret_cast<const uint16_t*>(sm)[off]) : 0xffffu;
-          hit = e != 0xffffu;
-          contrib = e;
-        } else if (width == 4) {
-          const uint32_t e = look ? reinterpret_cast<const uint32_t*>(sm)[off] : kAbsent;
-          hit = e != kAbsent;
-          contrib = e;
-        } else {
-          const uint32_t e = look ? __ldg(gt + off) : kAbsent;
-          hit = e != kAbsent;
-          contrib = (e & 0xffffu) * S.mul0 + (e >> 16) * S.mul1;
-        }
-        T.gid[t][k] += hit ? contrib : 0u;
-        keep |= uint32_t(hit) << k;
-      }
+      for (int k = 0; k < 4; ++k)
+        keep |= uint32_t(probe_direct<kMode>(S, stab, v[t][k], (T.alive >> (4 * t + k)) & 1u, T.gid[t][k])) << k;
       T.alive &= ~((~keep & 15u) << (4 * t));
     }
     return;
@@ -257,41 +305,58 @@ __device__ __forceinline__ void tile_probe(const DevQuery& Q, const DevStep& S, 
   }
 }
 
-// Predicate (RANGE / NOTRANGE / IN / FALSE) or group-key step.
-template <bool kHost>
-__device__ __forceinline__ void tile_filter_or_key(const DevQuery& Q, const DevStep& S, const PageState& P,
-                                                   const TileHdr& Hd, TileState& T, int lane,
-                                                   unsigned int* status) {
+// Dense step over one tile, specialised on the column's codec: a probe, a
+// group key or a predicate (RANGE / NOTRANGE / IN / FALSE).
+template <bool kHost, bool kDelta>
+__device__ __forceinline__ void dense_step_t(const DevQuery& Q, const DevStep& S, const PageState& P,
+                                             const TileHdr& Hd, TileState& T, const uint8_t* stab, int lane,
+                                             unsigned int* status) {
   uint32_t v[TB][4];
   uint32_t anym;
-  tile_decode<kHost>(Q, S.col, P, Hd, T.alive, lane, v, anym, status);
-  if (S.kind == ST_KEY) {
-#pragma unroll
-    for (int t = 0; t < TB; ++t)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) T.gid[t][k] += v[t][k] * S.key_mul;
-    return;
-  }
-  uint32_t keep = 0;
-  if (S.kind == ST_RANGE || S.kind == ST_NOTRANGE) {
-    const bool neg = S.kind == ST_NOTRANGE;
-    // lo <= x <= hi  <=>  (x - lo) <= (hi - lo) as unsigned
-    const uint32_t lo = uint32_t(S.lo), span = uint32_t(S.hi) - uint32_t(S.lo);
-#pragma unroll
-    for (int t = 0; t < TB; ++t)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) keep |= uint32_t(((v[t][k] - lo) <= span) != neg) << (4 * t + k);
-  } else if (S.kind == ST_IN) {
-#pragma unroll
-    for (int t = 0; t < TB; ++t)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        bool hit = false;
-        for (int i = 0; i < S.nin; ++i) hit |= (int32_t(v[t][k]) == S.in[i]);
-        keep |= uint32_t(hit) << (4 * t + k);
+  decode_t<kHost, kDelta>(Q, S.col, P, Hd, T.alive, lane, v, anym, status);
+  switch (S.kind) {
+    case ST_PROBE:
+      switch (probe_mode(S)) {
+        case PM_S1: dense_probe<PM_S1>(S, stab, v, anym, T, status); break;
+        case PM_S2: dense_probe<PM_S2>(S, stab, v, anym, T, status); break;
+        case PM_S4: dense_probe<PM_S4>(S, stab, v, anym, T, status); break;
+        case PM_GDIRECT: dense_probe<PM_GDIRECT>(S, stab, v, anym, T, status); break;
+        default: dense_probe<PM_OPEN>(S, stab, v, anym, T, status); break;
       }
+      return;
+    case ST_KEY:
+#pragma unroll
+      for (int t = 0; t < TB; ++t)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) T.gid[t][k] += v[t][k] * S.key_mul;
+      return;
+    case ST_RANGE:
+    case ST_NOTRANGE: {
+      const bool neg = S.kind == ST_NOTRANGE;
+      // lo <= x <= hi  <=>  (x - lo) <= (hi - lo) as unsigned
+      const uint32_t lo = uint32_t(S.lo), span = uint32_t(S.hi) - uint32_t(S.lo);
+      uint32_t keep = 0;
+#pragma unroll
+      for (int t = 0; t < TB; ++t)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) keep |= uint32_t(((v[t][k] - lo) <= span) != neg) << (4 * t + k);
+      T.alive &= keep;
+      return;
+    }
+    default: {  // IN (FALSE compiles to IN with an empty list)
+      uint32_t keep = 0;
+#pragma unroll
+      for (int t = 0; t < TB; ++t)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          bool hit = false;
+          for (int i = 0; i < S.nin; ++i) hit |= (int32_t(v[t][k]) == S.in[i]);
+          keep |= uint32_t(hit) << (4 * t + k);
+        }
+      T.alive &= S.kind == ST_IN ? keep : 0u;
+      return;
+    }
   }
-  T.alive &= keep;
 }
 
 // ---------------------------------------------------------------------------
@@ -303,17 +368,19 @@ __device__ __forceinline__ void tile_filter_or_key(const DevQuery& Q, const DevS
 // ---------------------------------------------------------------------------
 constexpr uint32_t kTileRows = kMB * TB;
 constexpr uint32_t kRowBits = 9;
+constexpr int kListUnroll = 1;  // survivor rounds whose loads are issued together (measured best at 1)
 static_assert(kTileRows <= (1u << kRowBits), "row index field too narrow");
 
 // Dense first step of a tile (or none): live bits and group-id contributions.
+// The step's kind, table and codec are resolved here, once per tile.
 template <bool kHost>
 __device__ __forceinline__ void tile_first_step(const DevQuery& Q, const PageState& P, const TileHdr& Hd,
                                                 TileState& T, const uint8_t* stab, int lane, unsigned int* status) {
   if (Q.nsteps == 0) return;
   const DevStep& S = Q.steps[0];
   if (S.kind == ST_PREFIX) tile_prefix<kHost>(Q, S, P, Hd, T, lane, status);
-  else if (S.kind == ST_PROBE) tile_probe<kHost>(Q, S, P, Hd, T, stab, lane, status);
-  else tile_filter_or_key<kHost>(Q, S, P, Hd, T, lane, status);
+  else if (Q.cols[S.col].codec == C_DELTA) dense_step_t<kHost, true>(Q, S, P, Hd, T, stab, lane, status);
+  else dense_step_t<kHost, false>(Q, S, P, Hd, T, stab, lane, status);
 }
 
 // Appends the tile's live rows to the warp's list; returns the list length.
@@ -426,25 +493,11 @@ __device__ __forceinline__ bool row_prefix(const DevQuery& Q, const DevStep& S, 
 }
 
 // Join probe of one key; on a hit adds the join's group-id contribution.
+template <int kMode>
 __device__ __forceinline__ bool row_probe(const DevStep& S, const uint8_t* stab, uint32_t key, bool valid,
                                           uint32_t& gid, unsigned int* status) {
-  if (!valid) return false;
-  if (S.ht_kind == HT_DIRECT) {
-    const uint32_t off = key - uint32_t(S.kmin);
-    if (off >= S.krange) return false;
-    uint32_t e;
-    switch (S.smem_width) {
-      case 1: e = stab[S.smem_off + off]; if (e == 0xffu) return false; gid += e; return true;
-      case 2: e = reinterpret_cast<const uint16_t*>(stab + S.smem_off)[off]; if (e == 0xffffu) return false; gid += e; return true;
-      case 4: e = reinterpret_cast<const uint32_t*>(stab + S.smem_off)[off]; if (e == kAbsent) return false; gid += e; return true;
-      default:
-        e = __ldg(static_cast<const uint32_t*>(S.ht) + off);
-        if (e == kAbsent) return false;
-        gid += (e & 0xffffu) * S.mul0 + (e >> 16) * S.mul1;
-        return true;
-    }
-  }
-  if (int32_t(key) == kEmptyKey) return false;
+  if (kMode != PM_OPEN) return probe_direct<kMode>(S, stab, key, valid, gid);
+  if (!valid || int32_t(key) == kEmptyKey) return false;
   const uint2* tab = S.smem_width ? reinterpret_cast<const uint2*>(stab + S.smem_off) : static_cast<const uint2*>(S.ht);
   uint32_t pay;
   if (!ht_probe(tab, S.ht_mask, int32_t(key), &pay, status)) return false;
@@ -452,41 +505,123 @@ __device__ __forceinline__ bool row_probe(const DevStep& S, const uint8_t* stab,
   return true;
 }
 
-// Steps 1.. of the query over the warp's list; returns the list length.
+// One later step over a warp's list for a FOR/DICT column, specialised on the
+// operation: kOp 0..4 = probe modes, 5 = group key, 6 = RANGE, 7 = NOTRANGE,
+// 8 = IN / FALSE.  Returns the new list length.
+template <bool kHost, int kOp>
+__device__ __forceinline__ uint32_t list_step_t(const DevQuery& Q, const DevStep& S, const PageState& P,
+                                                const TileHdr& Hd, uint32_t* list, uint32_t n, const uint8_t* stab,
+                                                int lane, unsigned int* status) {
+  // Rounds of 32 survivors are taken kListUnroll at a time: their entries
+  // and packed values are all loaded before any is used, so the warp keeps
+  // that many independent loads in flight.  Compacted entries are written
+  // only after the group's entries were read, never ahead of them.
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t out = 0;
+  for (uint32_t i0 = 0; i0 < n; i0 += 32 * kListUnroll) {
+    uint32_t r[kListUnroll], gid[kListUnroll], v[kListUnroll];
+    bool valid[kListUnroll];
+#pragma unroll
+    for (int u = 0; u < kListUnroll; ++u) {
+      valid[u] = i0 + 32u * u + lane < n;
+      const uint32_t e = valid[u] ? list[i0 + 32u * u + lane] : 0u;
+      r[u] = e & ((1u << kRowBits) - 1u);
+      gid[u] = e >> kRowBits;
+    }
+#pragma unroll
+    for (int u = 0; u < kListUnroll; ++u) v[u] = point_value<kHost>(Q, S.col, P, Hd, r[u], valid[u]);
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < kListUnroll; ++u) {
+      bool keep;
+      if (kOp <= PM_OPEN) {
+        keep = row_probe<kOp>(S, stab, v[u], valid[u], gid[u], status);
+      } else if (kOp == 5) {
+        gid[u] += v[u] * S.key_mul;
+        keep = valid[u];
+      } else if (kOp == 6 || kOp == 7) {
+        keep = valid[u] && (((v[u] - uint32_t(S.lo)) <= uint32_t(S.hi) - uint32_t(S.lo)) != (kOp == 7));
+      } else {
+        keep = valid[u] && step_pred(S, int32_t(v[u]));
+      }
+      const uint32_t m = __ballot_sync(kFull, keep);
+      if (keep) list[out + __popc(m & lt)] = r[u] | (gid[u] << kRowBits);
+      out += __popc(m);
+    }
+  }
+  __syncwarp();
+  return out;
+}
+
+// A later step on a DELTA column or a PREFIX step (dense decode of the
+// round's mini blocks); kept out of line.
+template <bool kHost>
+__device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevStep& S, const PageState& P,
+                                                   const TileHdr& Hd, uint32_t* list, uint32_t n,
+                                                   const uint8_t* stab, int lane, unsigned int* status) {
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t out = 0;
+  for (uint32_t i0 = 0; i0 < n; i0 += 32) {
+    const bool valid = i0 + lane < n;
+    const uint32_t e = valid ? list[i0 + lane] : 0u;
+    const uint32_t r = e & ((1u << kRowBits) - 1u);
+    uint32_t gid = e >> kRowBits;
+    bool keep;
+    if (S.kind == ST_PREFIX) {
+      keep = row_prefix<kHost>(Q, S, P, Hd, r, valid, lane, status);
+    } else {
+      const uint32_t v = row_value<kHost>(Q, S.col, P, Hd, r, valid, lane, status);
+      if (S.kind == ST_PROBE) {
+        switch (probe_mode(S)) {
+          case PM_S1: keep = row_probe<PM_S1>(S, stab, v, valid, gid, status); break;
+          case PM_S2: keep = row_probe<PM_S2>(S, stab, v, valid, gid, status); break;
+          case PM_S4: keep = row_probe<PM_S4>(S, stab, v, valid, gid, status); break;
+          case PM_GDIRECT: keep = row_probe<PM_GDIRECT>(S, stab, v, valid, gid, status); break;
+          default: keep = row_probe<PM_OPEN>(S, stab, v, valid, gid, status); break;
+        }
+      } else if (S.kind == ST_KEY) {
+        gid += v * S.key_mul;
+        keep = valid;
+      } else {
+        keep = valid && step_pred(S, int32_t(v));
+      }
+    }
+    const uint32_t m = __ballot_sync(kFull, keep);
+    __syncwarp();
+    if (keep) list[out + __popc(m & lt)] = r | (gid << kRowBits);
+    out += __popc(m);
+  }
+  __syncwarp();
+  return out;
+}
+
+// Steps 1.. of the query over the warp's list; returns the list length.  Each
+// step is resolved to its specialised loop once, outside the loop.
 template <bool kHost>
 __device__ __forceinline__ uint32_t list_steps(const DevQuery& Q, const PageState& P, const TileHdr& Hd,
                                                uint32_t* list, uint32_t n, const uint8_t* stab, int lane,
                                                unsigned int* status) {
-  const uint32_t lt = (1u << lane) - 1u;
   for (uint32_t s = 1; s < Q.nsteps && n != 0; ++s) {
     const DevStep& S = Q.steps[s];
-    uint32_t out = 0;
-    for (uint32_t i0 = 0; i0 < n; i0 += 32) {
-      const bool valid = i0 + lane < n;
-      const uint32_t e = valid ? list[i0 + lane] : 0u;
-      const uint32_t r = e & ((1u << kRowBits) - 1u);
-      uint32_t gid = e >> kRowBits;
-      bool keep;
-      if (S.kind == ST_PREFIX) {
-        keep = row_prefix<kHost>(Q, S, P, Hd, r, valid, lane, status);
-      } else {
-        const uint32_t v = row_value<kHost>(Q, S.col, P, Hd, r, valid, lane, status);
-        if (S.kind == ST_PROBE) {
-          keep = row_probe(S, stab, v, valid, gid, status);
-        } else if (S.kind == ST_KEY) {
-          gid += v * S.key_mul;
-          keep = valid;
-        } else {
-          keep = valid && step_pred(S, int32_t(v));
-        }
-      }
-      const uint32_t m = __ballot_sync(kFull, keep);
-      __syncwarp();
-      if (keep) list[out + __popc(m & lt)] = r | (gid << kRowBits);
-      out += __popc(m);
+    if (S.kind == ST_PREFIX || Q.cols[S.col].codec == C_DELTA) {
+      n = list_step_generic<kHost>(Q, S, P, Hd, list, n, stab, lane, status);
+      continue;
     }
-    __syncwarp();
-    n = out;
+    switch (S.kind) {
+      case ST_PROBE:
+        switch (probe_mode(S)) {
+          case PM_S1: n = list_step_t<kHost, PM_S1>(Q, S, P, Hd, list, n, stab, lane, status); break;
+          case PM_S2: n = list_step_t<kHost, PM_S2>(Q, S, P, Hd, list, n, stab, lane, status); break;
+          case PM_S4: n = list_step_t<kHost, PM_S4>(Q, S, P, Hd, list, n, stab, lane, status); break;
+          case PM_GDIRECT: n = list_step_t<kHost, PM_GDIRECT>(Q, S, P, Hd, list, n, stab, lane, status); break;
+          default: n = list_step_t<kHost, PM_OPEN>(Q, S, P, Hd, list, n, stab, lane, status); break;
+        }
+        break;
+      case ST_KEY: n = list_step_t<kHost, 5>(Q, S, P, Hd, list, n, stab, lane, status); break;
+      case ST_RANGE: n = list_step_t<kHost, 6>(Q, S, P, Hd, list, n, stab, lane, status); break;
+      case ST_NOTRANGE: n = list_step_t<kHost, 7>(Q, S, P, Hd, list, n, stab, lane, status); break;
+      default: n = list_step_t<kHost, 8>(Q, S, P, Hd, list, n, stab, lane, status); break;
+    }
   }
   return n;
 }

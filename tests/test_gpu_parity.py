@@ -92,7 +92,7 @@ def test_clustered_and_unsorted_star_agree(eng, shapes):
     assert_same(eng.run(shapes["star"]), eng.run(shapes["star_unsorted"]))
 
 
-@pytest.mark.parametrize("chunk_rows", [2048, 16384, 262144])
+@pytest.mark.parametrize("chunk_rows", [512, 2048, 262144])
 @pytest.mark.parametrize("threads", [128, 256])
 @pytest.mark.parametrize("place", ["smem", "global"])
 def test_launch_knobs_do_not_change_results(eng, shapes, chunk_rows, threads, place):
