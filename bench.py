@@ -39,6 +39,40 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_hash():
+    """Hash of the CUDA/C++ sources of the library: ties stored ncu counters
+    to the kernel build they were taken on."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2605_10511_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(workload, fact_rows):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary of this workload (scaled by rows when it was captured on a
+    smaller case), or None when absent or taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"fused_kernel_{workload}.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith(" "):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_hash") != kernel_source_hash():
+            return None, "stale (kernel changed since capture)"
+        b = float(kv["dram_bytes_per_launch"])
+        rows = float(kv["captured_rows"])
+        return b * fact_rows / rows, f"ncu capture at {int(rows)} rows, scaled by rows"
+    except Exception:  # noqa: BLE001
+        return None, "no capture"
+
+
 def _workload(name, rows):
     import synth
     if name == "star":
@@ -184,7 +218,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dpf", choices=["dpf", "reference"])
     ap.add_argument("--workload", default="star", choices=["star", "star_unsorted", "scan", "strings"])
@@ -194,6 +228,7 @@ def main():
     ap.add_argument("--ht", default="auto", choices=["auto", "smem", "global"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--ref-budget-s", type=float, default=20.0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -267,8 +302,12 @@ def main():
     check = eng.ctx.read_result(prep, 0)
     assert np.array_equal(check, records), "result changed across replays"
 
+    unfused = time_unfused(eng, plan, stream, records, reps=max(3, min(args.steps, 10)),
+                           fused_ms=ms_step) if not args.no_unfused else None
+
     peak, peak_kind = _peaks()
     avg_launch_ms = statistics.mean(per)
+    traffic, traffic_src = stored_traffic(args.workload, fact_rows)
     achieved = alg_bytes / (avg_launch_ms * 1e-3) / 1e9
     value = world * fact_rows / (ms_step * 1e-3)
     per_sorted = sorted(per)
@@ -289,7 +328,9 @@ def main():
         "latency_ms": {"p50": pct(50), "p99": pct(99)},
         "build_ms": build_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind},
+                     "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                     "peak_kind": f"{peak_kind} copy bandwidth (burst)"},
+        "unfused": unfused,
         "gpu_launches": args.steps,
         "clocks": clocks,
         "wall_s": wall,
@@ -307,6 +348,34 @@ def main():
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def time_unfused(eng, plan, stream, fused_records, reps, fused_ms):
+    """The same plan through the unfused per-operator chain (one kernel per
+    operator, intermediates in HBM): time per query, kernel launches and
+    intermediate bytes, checked against the fused result."""
+    import numpy as np
+    import torch
+    prep = eng.ctx.prepare_unfused(plan)
+    try:
+        for _ in range(2):
+            eng.ctx.launch(prep, stream)
+        got = eng.ctx.read_result(prep, 0)
+        assert np.array_equal(got, fused_records), "unfused chain disagrees with the fused kernel"
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record(stream)
+        for _ in range(reps):
+            eng.ctx.launch(prep, stream)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / reps
+        st = eng.ctx.prep_stats(prep)
+        return {"ms_per_query": ms, "launches_per_query": st["launches"],
+                "intermediate_bytes": st["intermediate_bytes"], "fused_speedup": ms / fused_ms}
+    finally:
+        eng.ctx.release(prep)
 
 
 def e2e_host_resident(dpf, w, args, device, tuning):
