@@ -279,7 +279,7 @@ __device__ void load_smem_tables(const DevQuery& Q, uint8_t* stab) {
 }
 
 template <bool kHost>
-__global__ void __launch_bounds__(256, 2) fused_kernel(const DevQuery* __restrict__ queries,
+__global__ void __launch_bounds__(256, kFusedMinBlocks) fused_kernel(const DevQuery* __restrict__ queries,
                                                        const uint64_t* __restrict__ qbegin, int nq,
                                                        uint64_t total, Sched* sched, uint32_t acc_slots,
                                                      uint32_t tables_bytes) {

@@ -11,6 +11,10 @@ namespace dpf {
 // Shared-memory accumulator capacity of one CTA (int64 slots).
 constexpr uint32_t kSmemAccSlots = 4096;
 constexpr uint32_t kMbPerWarpTile = 4;
+// Resident 256-thread CTAs per SM the fused kernel is compiled for (register
+// budget 65536 / (256 x this)): occupancy, more than issue, bounds the kernel,
+// and 3 (24 warps, 80 registers) measured fastest.
+constexpr int kFusedMinBlocks = 3;
 // Rows of one scheduling ticket (one warp's unit of work) unless tuned.
 constexpr uint32_t kDefaultChunkRows = 2048;
 
