@@ -172,6 +172,163 @@ def oracle_rows_per_s(w, budget_s=15.0, max_rows=None):
         _ = np
 
 
+def run_batched(args, dpf, torch, np, local):
+    """64 queries of the three shapes over fact tables of log-uniform size
+    (2^16..2^26 rows) in ONE persistent launch replayed from a CUDA graph,
+    under the launch configuration the library's autotuner picks."""
+    import synth
+    ws = synth.batched_workloads(n_queries=args.batch_queries, seed=4)
+    eng = dpf.Engine(device=local)
+    for w in ws:
+        eng.load_workload(w)
+    stream = torch.cuda.Stream()
+    plans = [eng.plan(w, stream) for w in ws]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    best, tune_ms = eng.ctx.autotune(plans, stream, reps=2)
+    tune_s = time.perf_counter() - t0
+    prep = eng.ctx.prepare(plans)
+    eng.ctx.capture_graph(prep, stream)
+    for _ in range(args.warmup):
+        eng.ctx.launch_graph(prep, stream)
+    first = [eng.ctx.read_result(prep, i) for i in range(len(ws))]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        starts[i].record(stream)
+        eng.ctx.launch_graph(prep, stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    per = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms_step = starts[0].elapsed_time(ends[-1]) / args.steps
+    for i in range(len(ws)):
+        assert np.array_equal(eng.ctx.read_result(prep, i), first[i]), "result changed across replays"
+    rows = sum(w["tables"][w["fact"]]["rows"] for w in ws)
+    alg = sum(eng.fact_bytes(w)[0] for w in ws)
+    tuned = eng.ctx.prep_tuning(prep)
+    eng.ctx.release(prep)
+    # the same 64 queries through the unfused chain, one query at a time
+    unf_ms, unf_launches, unf_bytes = 0.0, 0, 0
+    if not args.no_unfused:
+        for i, w in enumerate(ws):
+            r = time_unfused(eng, plans[i], stream, first[i], reps=2, fused_ms=1.0)
+            unf_ms += r["ms_per_query"]
+            unf_launches += r["launches_per_query"]
+            unf_bytes += r["intermediate_bytes"]
+    peak, peak_kind = _peaks()
+    achieved = alg / (statistics.mean(per) * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": rows / (ms_step * 1e-3), "unit": "rows/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded; 64 queries of the scan / star / strings shapes)",
+        "config": {"workload": f"batched_{len(ws)}_queries", "fact_rows_total": rows,
+                   "queries": len(ws), "l2": "inputs larger than L2", "tuning": tuned},
+        "autotune": {"best": best, "best_ms": tune_ms, "search_s": tune_s},
+        "compressed_gbs": achieved, "compressed_bytes": alg,
+        "latency_ms": {"p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(0.99 * (len(per) - 1) + 0.5))]},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "traffic_source": "no capture for the batch",
+                     "peak_kind": f"{peak_kind} copy bandwidth (burst)"},
+        "unfused": None if args.no_unfused else {
+            "ms_per_batch": unf_ms, "launches_per_batch": unf_launches, "intermediate_bytes": unf_bytes,
+            "fused_speedup": unf_ms / ms_step},
+        "gpu_launches": args.steps, "clocks": clocks,
+    }
+    eng.close()
+    print(json.dumps(out), flush=True)
+
+
+def serve_variants(w, n_star, n_scan, seed):
+    """Queries over one resident star schema: star joins with the dimension
+    predicate constants re-drawn from the dimensions' own values, and
+    scan-filter-aggregates over the fact's measures."""
+    import copy
+
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_star):
+        v = copy.deepcopy(w)
+        v["tables"] = w["tables"]
+        for j in v["query"]["joins"]:
+            for p in j["preds"]:
+                vals = np.unique(w["tables"][j["dim"]]["cols"][p["col"]]["values"])
+                p["args"] = [int(x) for x in rng.choice(vals, len(p["args"]), replace=False)]
+        out.append(v)
+    for i in range(n_scan):
+        v = {k: w[k] for k in ("name", "tables", "fact")}
+        lo = int(rng.integers(1, 5_000_000))
+        v["query"] = {"preds": [{"col": "m2", "op": "lt", "args": [int(rng.integers(1000, 100_000))]},
+                                {"col": "m1", "op": "between", "args": [lo, lo + int(rng.integers(1, 5_000_000))]}],
+                      "joins": [], "group": [], "aggs": [{"op": "sum", "cols": ["m1"]}, {"op": "count"}]}
+        out.append(v)
+    return out
+
+
+def run_serve(args, dpf, torch, np, local):
+    """Poisson streams of queries at several rates through the
+    continuous-batching server over a resident star schema; p50/p99 latency
+    (submit to result on the host) and throughput per rate."""
+    import synth
+    rows = args.rows or (1 << 28)
+    w = synth.star_join(rows=rows, clustered=args.serve_placement == "device")
+    eng = dpf.Engine(device=local)
+    t0 = time.perf_counter()
+    eng.load_workload(w, fact_placement=args.serve_placement)
+    load_s = time.perf_counter() - t0
+    qs = serve_variants(w, 12, 4, seed=5)
+    plans = [eng.plan(v) for v in qs]
+    ref = [eng.run(v) for v in qs]  # each query alone
+    alg = [eng.fact_bytes(v)[0] for v in qs]
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    rng = np.random.default_rng(7)
+    lines = []
+    for lam in rates:
+        n = int(min(args.serve_queries, max(20, lam * args.serve_seconds)))
+        gaps = rng.exponential(1.0 / lam, n)
+        pick = rng.integers(0, len(qs), n)
+        with dpf.Server(eng.ctx, max_batch=64, max_inflight=2) as srv:
+            tickets = []
+            t_start = time.perf_counter()
+            due = t_start
+            for k in range(n):
+                due += gaps[k]
+                while True:
+                    d = due - time.perf_counter()
+                    if d <= 0:
+                        break
+                    time.sleep(min(d, 0.002) if d > 0.0005 else 0)
+                tickets.append(srv.submit(plans[pick[k]]))
+            lat, batch, mismatch, done_last = [], [], 0, 0.0
+            for k, tk in enumerate(tickets):
+                got, tm = srv.wait(tk)
+                mismatch += int(not np.array_equal(got, ref[pick[k]]))
+                lat.append((tm["done_us"] - tm["submit_us"]) / 1e3)
+                batch.append(tm["batch_size"])
+                done_last = max(done_last, tm["done_us"])
+            wall = time.perf_counter() - t_start
+        lat_sorted = sorted(lat)
+        q_rows = sum(w["tables"]["fact"]["rows"] for _ in range(n))
+        lines.append({"offered_qps": lam, "queries": n, "achieved_qps": n / wall,
+                      "p50_ms": lat_sorted[len(lat) // 2],
+                      "p99_ms": lat_sorted[min(n - 1, int(0.99 * (n - 1) + 0.5))],
+                      "rows_per_s": q_rows / wall,
+                      "compressed_gbs": sum(alg[i] for i in pick) / wall / 1e9,
+                      "mean_batch": float(np.mean(batch)), "mismatches_vs_alone": mismatch})
+    out = {"metric": METRIC, "mode": "serve", "unit": "ms", "n_gpus": 1, "higher_is_better": False,
+           "dtype": "int64", "data": "synthetic (seeded star schema; Poisson arrivals)",
+           "config": {"workload": w["name"], "fact_rows": rows, "fact_placement": args.serve_placement,
+                      "query_variants": len(qs), "load_s": load_s},
+           "rates": lines}
+    eng.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     """The CPU oracle as the reference arm: each step evaluates a bounded
     sample of the same workload on the host."""
@@ -221,7 +378,14 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dpf", choices=["dpf", "reference"])
-    ap.add_argument("--workload", default="star", choices=["star", "star_unsorted", "scan", "strings"])
+    ap.add_argument("--workload", default="star",
+                    choices=["star", "star_unsorted", "scan", "strings", "batched"])
+    ap.add_argument("--batch-queries", type=int, default=64)
+    ap.add_argument("--serve", action="store_true", help="Poisson serving run instead of the step benchmark")
+    ap.add_argument("--serve-rates", default="10,100,500,1000,2000")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-queries", type=int, default=2000)
+    ap.add_argument("--serve-placement", default="device", choices=["device", "host"])
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--chunk-rows", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
@@ -249,6 +413,14 @@ def main():
     import paper_2605_10511_gb300 as dpf
 
     torch.cuda.set_device(local)
+    if args.serve:
+        if rank == 0:
+            run_serve(args, dpf, torch, np, local)
+        return
+    if args.workload == "batched":
+        if rank == 0:
+            run_batched(args, dpf, torch, np, local)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

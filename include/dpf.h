@@ -71,6 +71,8 @@ dpf_status dpf_create(dpf_ctx** out, int32_t device, uint64_t hbm_budget,
 dpf_status dpf_destroy(dpf_ctx* ctx);
 /* Device bytes currently held by the context. */
 dpf_status dpf_memory_used(dpf_ctx* ctx, uint64_t* bytes);
+/* CUDA device the context is bound to. */
+dpf_status dpf_context_device(dpf_ctx* ctx, int32_t* device);
 
 /* ----------------------------------------------------------- columns */
 /* Storage encodings (Sec. 3.4, Sec. 4.1).  Every encoding splits a column
@@ -272,6 +274,27 @@ dpf_status dpf_read_result(dpf_ctx* ctx, dpf_prep_id prep, int32_t i, dpf_record
 dpf_status dpf_prep_tuning(dpf_ctx* ctx, dpf_prep_id prep, dpf_tuning* out);
 dpf_status dpf_release(dpf_ctx* ctx, dpf_prep_id prep);
 
+/* Autotuner for batched launches.  Sec. 3.2 splits a table into chunks that
+ * thread blocks process in a loop; the chunk size, the threads per block and
+ * where the join tables live (shared memory vs device memory, Sec. 4.3) are
+ * the launch configuration.  dpf_autotune prepares the n plans under each
+ * configuration of a fixed grid (chunk_rows 1K..256K, threads 128/256,
+ * tables AUTO/GLOBAL), times `reps` launches of each on `stream` with CUDA
+ * events after one warm-up launch (reps 0 = 3), and keeps the fastest in the
+ * context's tuning cache under the plans' signature (the rows and encodings
+ * of the columns they read, their steps, tables, groups and aggregates; not
+ * predicate constants).  Later dpf_prepare calls on plans with the same
+ * signature take the cached values for tuning fields left 0.  `best` and
+ * `best_ms` (mean time per launch) may be NULL.  Runs the device work
+ * synchronously.  Errors: as dpf_prepare; DPF_ECORRUPT / DPF_EINTERNAL from
+ * the device status word. */
+dpf_status dpf_autotune(dpf_ctx* ctx, const dpf_plan* plans, int32_t n, void* stream, uint32_t reps,
+                        dpf_tuning* best, float* best_ms);
+/* Device bytes one plan occupies while it runs (int64 accumulators of its
+ * group domain, result records, device plan), for admission by memory
+ * footprint.  Errors: as dpf_prepare. */
+dpf_status dpf_plan_footprint(dpf_ctx* ctx, const dpf_plan* plan, uint64_t* bytes);
+
 /* The unfused baseline: the same single plan prepared as a chain of one
  * kernel per operator that materialises every intermediate in device
  * memory (decoded columns, predicate flags, row-id lists after each join),
@@ -317,6 +340,53 @@ dpf_status dpf_execute_plan(dpf_ctx* ctx, const dpf_plan* plans, int32_t n, void
  * DPF_ETRUNC nothing is consumed; on success the id is freed. */
 dpf_status dpf_fetch_result(dpf_ctx* ctx, dpf_query_id id, dpf_record* buf, uint64_t cap,
                             uint64_t* n_out, int32_t timeout_ms);
+
+/* ---------------------------------------------------------------- serving
+ * A request loop over one context (not in the paper; the serving pattern
+ * built on its batched fused launch).  Join tables and compressed columns
+ * stay resident in the context; queries are submitted as plans over them.
+ * A dispatcher thread owned by the server keeps up to max_inflight batches
+ * on the device, each on its own stream, and launches the queued queries
+ * (FIFO, up to max_batch per launch) as soon as a slot is free and their
+ * device footprint (dpf_plan_footprint) fits mem_budget next to the
+ * queries already running: continuous batching.  A query's records do not
+ * depend on the batch it ran in. */
+typedef struct dpf_server dpf_server;
+typedef struct dpf_server_config {
+  uint32_t max_batch;    /* plans per launch; 0 = 64, at most 4096                */
+  uint32_t max_inflight; /* batches on the device at once; 0 = 2, at most 64      */
+  uint64_t mem_budget;   /* device bytes of admitted queries at once; 0 = no cap  */
+  dpf_tuning tuning;     /* launch configuration; 0 fields = cache / defaults     */
+} dpf_server_config;
+/* Host steady-clock times in microseconds since dpf_server_create. */
+typedef struct dpf_query_times {
+  double submit_us;    /* dpf_server_submit accepted the query              */
+  double launch_us;    /* its batch was handed to the GPU                   */
+  double done_us;      /* the dispatcher saw the batch complete             */
+  uint32_t batch_size; /* queries in that launch                            */
+} dpf_query_times;
+typedef struct dpf_server_stats {
+  uint64_t submitted, completed, failed, batches, launched_batches;
+  uint64_t queued;       /* waiting for a slot or memory                    */
+  uint64_t in_use_bytes; /* footprint of the queries on the device          */
+} dpf_server_stats;
+/* Starts the dispatcher thread.  cfg may be NULL (all defaults).  Errors:
+ * DPF_EINVAL, DPF_ECUDA. */
+dpf_status dpf_server_create(dpf_ctx* ctx, const dpf_server_config* cfg, dpf_server** out);
+/* Queues one plan (copied at call time; validated with dpf_plan_footprint)
+ * and returns its ticket.  DPF_EBUSY: its footprint alone exceeds
+ * mem_budget, or the server is stopping. */
+dpf_status dpf_server_submit(dpf_server* srv, const dpf_plan* plan, uint64_t* ticket);
+/* Waits up to timeout_ms (< 0 = forever) for a ticket and copies its
+ * records to host `buf`.  DPF_ETRUNC if cap < needed (*n_out = needed;
+ * nothing consumed).  On success, and on a query error (returned as its
+ * status), the ticket is collected.  `times` may be NULL. */
+dpf_status dpf_server_wait(dpf_server* srv, uint64_t ticket, dpf_record* buf, uint64_t cap,
+                           uint64_t* n_out, int32_t timeout_ms, dpf_query_times* times);
+dpf_status dpf_server_stats_get(dpf_server* srv, dpf_server_stats* out);
+/* Runs the queued and in-flight queries to completion, stops the
+ * dispatcher and frees the server (results not collected are dropped). */
+dpf_status dpf_server_destroy(dpf_server* srv);
 
 #ifdef __cplusplus
 }

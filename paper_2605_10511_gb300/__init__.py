@@ -77,6 +77,22 @@ class Tuning(C.Structure):
                 ("ctas_per_sm", C.c_uint32)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("max_batch", C.c_uint32), ("max_inflight", C.c_uint32), ("mem_budget", C.c_uint64),
+                ("tuning", Tuning)]
+
+
+class QueryTimes(C.Structure):
+    _fields_ = [("submit_us", C.c_double), ("launch_us", C.c_double), ("done_us", C.c_double),
+                ("batch_size", C.c_uint32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("batches", C.c_uint64), ("launched_batches", C.c_uint64), ("queued", C.c_uint64),
+                ("in_use_bytes", C.c_uint64)]
+
+
 class AllocHooks(C.Structure):
     _fields_ = [("alloc", C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_void_p)),
                 ("free", C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)),
@@ -90,6 +106,7 @@ _SIGS = {
     "dpf_create": (C.c_int32, [C.POINTER(_P), C.c_int32, C.c_uint64, C.POINTER(AllocHooks)]),
     "dpf_destroy": (C.c_int32, [_P]),
     "dpf_memory_used": (C.c_int32, [_P, C.POINTER(C.c_uint64)]),
+    "dpf_context_device": (C.c_int32, [_P, C.POINTER(C.c_int32)]),
     "dpf_encode_column": (C.c_int32, [C.POINTER(ColumnDesc), _P, _P, C.c_uint64, _P, C.c_uint64, _P, _P,
                                       _P, C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "dpf_load_encoded": (C.c_int32, [_P, C.POINTER(ColumnDesc), _P, C.c_uint64, _P, _P, C.c_uint64, _P,
@@ -111,11 +128,20 @@ _SIGS = {
                                     C.c_int32]),
     "dpf_prep_tuning": (C.c_int32, [_P, C.c_int32, C.POINTER(Tuning)]),
     "dpf_release": (C.c_int32, [_P, C.c_int32]),
+    "dpf_autotune": (C.c_int32, [_P, C.POINTER(Plan), C.c_int32, _P, C.c_uint32, C.POINTER(Tuning),
+                                 C.POINTER(C.c_float)]),
+    "dpf_plan_footprint": (C.c_int32, [_P, C.POINTER(Plan), C.POINTER(C.c_uint64)]),
     "dpf_prepare_unfused": (C.c_int32, [_P, C.POINTER(Plan), C.POINTER(C.c_int32)]),
     "dpf_prep_stats": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]),
     "dpf_execute_noalloc": (C.c_int32, [_P, C.POINTER(Plan), _P, _P, C.c_uint64, _P]),
     "dpf_execute_plan": (C.c_int32, [_P, C.POINTER(Plan), C.c_int32, _P, C.POINTER(C.c_int64)]),
     "dpf_fetch_result": (C.c_int32, [_P, C.c_int64, _P, C.c_uint64, C.POINTER(C.c_uint64), C.c_int32]),
+    "dpf_server_create": (C.c_int32, [_P, C.POINTER(ServerConfig), C.POINTER(_P)]),
+    "dpf_server_submit": (C.c_int32, [_P, C.POINTER(Plan), C.POINTER(C.c_uint64)]),
+    "dpf_server_wait": (C.c_int32, [_P, C.c_uint64, _P, C.c_uint64, C.POINTER(C.c_uint64), C.c_int32,
+                                    C.POINTER(QueryTimes)]),
+    "dpf_server_stats_get": (C.c_int32, [_P, C.POINTER(ServerStats)]),
+    "dpf_server_destroy": (C.c_int32, [_P]),
 }
 
 _lock = threading.Lock()
@@ -339,6 +365,25 @@ class Context:
         return {"chunk_rows": t.chunk_rows, "threads": t.threads, "ht_placement": t.ht_placement,
                 "ctas_per_sm": t.ctas_per_sm}
 
+    def autotune(self, plans, stream=None, reps=3):
+        """Times the plans under the library's grid of launch configurations
+        and caches the fastest for them; returns (tuning dict, ms/launch)."""
+        arr = (Plan * len(plans))(*[p.plan for p in plans])
+        t, ms = Tuning(), C.c_float()
+        _check(lib().dpf_autotune(self.h, arr, len(plans), _stream_ptr(stream), reps, C.byref(t), C.byref(ms)))
+        return ({"chunk_rows": t.chunk_rows, "threads": t.threads, "ht_placement": t.ht_placement,
+                 "ctas_per_sm": t.ctas_per_sm}, ms.value)
+
+    def plan_footprint(self, plan):
+        b = C.c_uint64()
+        _check(lib().dpf_plan_footprint(self.h, C.byref(plan.plan), C.byref(b)))
+        return b.value
+
+    def device(self):
+        d = C.c_int32()
+        _check(lib().dpf_context_device(self.h, C.byref(d)))
+        return d.value
+
     def prepare_unfused(self, plan):
         out = C.c_int32()
         _check(lib().dpf_prepare_unfused(self.h, C.byref(plan.plan), C.byref(out)))
@@ -376,6 +421,54 @@ class Context:
                 continue
             _check(st)
             return buf[: n.value].copy()
+
+
+class Server:
+    """Continuous-batching request loop over a context (``dpf_server_*``):
+    ``submit`` queues a plan and returns a ticket, ``wait`` returns its
+    records and host times (microseconds since the server started)."""
+
+    def __init__(self, ctx, max_batch=0, max_inflight=0, mem_budget=0, tuning=None):
+        cfg = ServerConfig(max_batch, max_inflight, mem_budget, tuning or Tuning())
+        h = C.c_void_p()
+        _check(lib().dpf_server_create(ctx.h, C.byref(cfg), C.byref(h)))
+        self.h = h
+        self.ctx = ctx
+
+    def submit(self, plan):
+        t = C.c_uint64()
+        _check(lib().dpf_server_submit(self.h, C.byref(plan.plan), C.byref(t)))
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        n = C.c_uint64()
+        times = QueryTimes()
+        cap = 1024
+        while True:
+            buf = np.zeros(cap, RECORD_DTYPE)
+            st = lib().dpf_server_wait(self.h, ticket, _ptr(buf), cap, C.byref(n), timeout_ms, C.byref(times))
+            if st == -7:
+                cap = int(n.value)
+                continue
+            _check(st)
+            return buf[: n.value].copy(), {"submit_us": times.submit_us, "launch_us": times.launch_us,
+                                           "done_us": times.done_us, "batch_size": times.batch_size}
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().dpf_server_stats_get(self.h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            _check(lib().dpf_server_destroy(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def encode_column(col, page_rows=0):

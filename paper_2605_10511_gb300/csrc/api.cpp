@@ -112,6 +112,7 @@ struct dpf_ctx {
   int32_t* bkminmax = nullptr;
   int num_sms = 0;
   int smem_optin = 0;
+  std::map<uint64_t, dpf_tuning> tune_cache;  // plan-set signature -> tuning chosen by dpf_autotune
 };
 
 namespace {
@@ -511,8 +512,60 @@ size_t place_tables(DevQuery& Q, size_t budget) {
   return used;
 }
 
-void fill_tuning_defaults(dpf_ctx* c, dpf_tuning& t) {
-  (void)c;
+// Signature of a set of plans for the tuning cache: what the launch
+// configuration's speed depends on (rows and encoding of every column a plan
+// reads, its steps, join tables, groups and aggregates), not the predicate
+// constants.  FNV-1a over those fields.
+uint64_t plans_signature(dpf_ctx* c, const dpf_plan* plans, int32_t n) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t x) {
+    for (int i = 0; i < 8; ++i) {
+      h ^= (x >> (8 * i)) & 0xffu;
+      h *= 1099511628211ull;
+    }
+  };
+  auto col = [&](dpf_col_id id) {
+    auto it = c->cols.find(id);
+    if (it == c->cols.end()) return mix(~0ull);
+    mix(it->second.nrows);
+    mix(uint64_t(it->second.codec) << 32 | it->second.page_rows);
+    mix(it->second.bytes);
+  };
+  mix(uint64_t(n));
+  for (int32_t i = 0; i < n; ++i) {
+    const dpf_plan& P = plans[i];
+    mix(uint64_t(P.n_preds) | uint64_t(P.n_joins) << 16 | uint64_t(P.n_keys) << 32 | uint64_t(P.n_aggs) << 48);
+    col(P.scan_col);
+    for (int k = 0; k < P.n_preds && P.preds; ++k) {
+      col(P.preds[k].col);
+      mix(uint64_t(P.preds[k].op));
+    }
+    for (int k = 0; k < P.n_joins && P.joins; ++k) {
+      col(P.joins[k].fk_col);
+      auto it = c->hts.find(P.joins[k].ht);
+      mix(it == c->hts.end() ? ~0ull : (uint64_t(it->second.kind) << 32 | it->second.capacity));
+    }
+    for (int k = 0; k < P.n_keys && P.keys; ++k) mix(uint64_t(P.keys[k].kind) << 32 | uint32_t(P.keys[k].col));
+    for (int k = 0; k < P.n_aggs && P.aggs; ++k) {
+      mix(uint64_t(P.aggs[k].op));
+      col(P.aggs[k].a);
+      if (P.aggs[k].op >= DPF_AGG_SUM_MUL) col(P.aggs[k].b);
+    }
+  }
+  return h;
+}
+
+// Fields left 0 take the tuning dpf_autotune stored for these plans, else the
+// defaults.
+void fill_tuning_defaults(dpf_ctx* c, dpf_tuning& t, const dpf_plan* plans, int32_t n) {
+  if (t.chunk_rows == 0 || t.threads == 0 || t.ht_placement == 0) {
+    auto it = c->tune_cache.find(plans_signature(c, plans, n));
+    if (it != c->tune_cache.end()) {
+      if (t.chunk_rows == 0) t.chunk_rows = it->second.chunk_rows;
+      if (t.threads == 0) t.threads = it->second.threads;
+      if (t.ht_placement == 0) t.ht_placement = it->second.ht_placement;
+    }
+  }
   if (t.chunk_rows == 0) t.chunk_rows = kDefaultChunkRows;
   if (t.threads == 0) t.threads = 256;
   if (t.ht_placement == 0) t.ht_placement = DPF_HT_AUTO;
@@ -549,7 +602,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   p->hq.resize(size_t(n));
   dpf_tuning t{};
   if (tuning) t = *tuning;
-  fill_tuning_defaults(c, t);
+  fill_tuning_defaults(c, t, plans, n);
   if (t.chunk_rows % (kMbPerWarpTile * kMB) != 0 || t.chunk_rows > (1u << 24))
     return fail(DPF_EINVAL, "chunk_rows %u must be a multiple of %u and at most 2^24", t.chunk_rows, kMbPerWarpTile * kMB);
   if (t.threads != 128 && t.threads != 256) return fail(DPF_EINVAL, "threads must be 128 or 256");
@@ -1047,6 +1100,97 @@ dpf_status dpf_prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_t
   dpf_status st = prepare(c, plans, n, tuning, &p);
   if (st) return st;
   *out = p->id;
+  return DPF_OK;
+}
+
+dpf_status dpf_context_device(dpf_ctx* c, int32_t* device) {
+  if (!c || !device) return fail(DPF_EINVAL, "NULL argument");
+  *device = c->device;
+  return DPF_OK;
+}
+
+dpf_status dpf_autotune(dpf_ctx* c, const dpf_plan* plans, int32_t n, void* stream, uint32_t reps, dpf_tuning* best,
+                        float* best_ms) {
+  if (!c || !plans) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  if (reps == 0) reps = 3;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  static const uint32_t kChunk[] = {1024, 2048, 4096, 16384, 65536, 262144};
+  static const uint32_t kThreads[] = {128, 256};
+  static const int32_t kPlace[] = {DPF_HT_AUTO, DPF_HT_GLOBAL};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(DPF_ECUDA, "cudaEventCreate failed");
+  }
+  dpf_tuning top{};
+  float top_ms = -1.f;
+  dpf_status last = DPF_OK;
+  for (uint32_t cr : kChunk)
+    for (uint32_t th : kThreads)
+      for (int32_t pl : kPlace) {
+        dpf_tuning t{};
+        t.chunk_rows = cr;
+        t.threads = th;
+        t.ht_placement = pl;
+        Prep* p = nullptr;
+        dpf_status st = prepare(c, plans, n, &t, &p);
+        if (st) {  // e.g. the tables do not fit this configuration
+          last = st;
+          continue;
+        }
+        const int32_t id = p->id;
+        cudaError_t e = launch_prep(p, s);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (uint32_t r = 0; r < reps && e == cudaSuccess; ++r) e = launch_prep(p, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        uint32_t status = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&status, &p->sched->status, 4, cudaMemcpyDeviceToHost);
+        const dpf_tuning used = p->tuning;
+        release_prep(c, p);
+        c->preps.erase(id);
+        if (e != cudaSuccess) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return fail(DPF_ECUDA, "autotune: %s", cudaGetErrorString(e));
+        }
+        if (status) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return fail(status & S_CORRUPT ? DPF_ECORRUPT : DPF_EINTERNAL, "autotune: device status %u", status);
+        }
+        ms /= float(reps);
+        if (top_ms < 0.f || ms < top_ms) {
+          top_ms = ms;
+          top = used;
+          top.ctas_per_sm = 0;  // recomputed per prepare
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (top_ms < 0.f) return fail(last ? last : DPF_EINVAL, "autotune: no configuration could be prepared");
+  c->tune_cache[plans_signature(c, plans, n)] = top;
+  if (best) *best = top;
+  if (best_ms) *best_ms = top_ms;
+  return DPF_OK;
+}
+
+dpf_status dpf_plan_footprint(dpf_ctx* c, const dpf_plan* plan, uint64_t* bytes) {
+  if (!c || !plan || !bytes) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DevQuery Q;
+  bool host = false;
+  std::vector<const HashTable*> probes;
+  dpf_status st = compile_plan(c, *plan, Q, &host, probes);
+  if (st) return st;
+  const uint64_t S1 = 1 + Q.naggs;
+  *bytes = align16(uint64_t(Q.domain) * S1 * 8) + 32 + align16(uint64_t(std::max<uint32_t>(Q.domain, 1)) * sizeof(dpf_record)) +
+           sizeof(DevQuery) + 8;
   return DPF_OK;
 }
 
