@@ -39,16 +39,18 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("fused.cu", "tile.cuh", "dpf_device.cuh", "dpf_internal.h", "kernels.h")
+
+
 def kernel_source_hash():
-    """Hash of the CUDA/C++ sources of the library: ties stored ncu counters
-    to the kernel build they were taken on."""
+    """Hash of the sources that define the fused kernel: ties stored ncu
+    counters to the kernel build they were taken on."""
     import hashlib
     d = os.path.join(ROOT, "paper_2605_10511_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 
