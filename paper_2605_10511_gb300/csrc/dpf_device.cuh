@@ -52,40 +52,25 @@ __device__ __forceinline__ MbHdr parse_hdr(uint4 h, uint32_t codec) {
   return m;
 }
 
-// Loads of compressed bytes.  Device-resident columns use the read-only
-// path; host-resident (mapped pinned) columns use plain global loads.
+// Loads of compressed bytes.  Both device-resident and host-resident
+// (mapped pinned) columns are immutable while a kernel runs, so both use
+// the read-only path: full-width vector loads that the host link serves in
+// whole lines.  (kHost only switches off the L2 bulk prefetch, which is
+// issued for device memory alone.)
 template <bool kHost>
 __device__ __forceinline__ uint32_t ld_u32(const uint32_t* p) {
-  if (kHost) return *reinterpret_cast<const volatile uint32_t*>(p);
   return __ldg(p);
 }
 template <bool kHost>
 __device__ __forceinline__ uint2 ld_u2(const uint2* p) {
-  if (kHost) {
-    const volatile uint2* q = reinterpret_cast<const volatile uint2*>(p);
-    uint2 r;
-    r.x = q->x;
-    r.y = q->y;
-    return r;
-  }
   return __ldg(p);
 }
 template <bool kHost>
 __device__ __forceinline__ uint4 ld_u4(const uint4* p) {
-  if (kHost) {
-    const volatile uint4* q = reinterpret_cast<const volatile uint4*>(p);
-    uint4 r;
-    r.x = q->x;
-    r.y = q->y;
-    r.z = q->z;
-    r.w = q->w;
-    return r;
-  }
   return __ldg(p);
 }
 template <bool kHost>
 __device__ __forceinline__ uint8_t ld_u8(const uint8_t* p) {
-  if (kHost) return *reinterpret_cast<const volatile uint8_t*>(p);
   return __ldg(p);
 }
 

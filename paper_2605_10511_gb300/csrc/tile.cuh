@@ -384,20 +384,30 @@ __device__ __forceinline__ void tile_first_step(const DevQuery& Q, const PageSta
 }
 
 // Appends the tile's live rows to the warp's list; returns the list length.
+// Each lane counts its live rows, a warp exclusive scan of the counts gives
+// the lane's first slot, and the lane writes its rows there in (t, k) order
+// (the list's order is free: later steps and the aggregation visit every
+// entry once, whatever its position).
 __device__ __forceinline__ uint32_t tile_compact(const TileState& T, uint32_t* list, int lane) {
-  uint32_t n = 0;
-  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t cnt = __popc(T.alive);
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += y;
+  }
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  uint32_t pos = incl - cnt;
 #pragma unroll
   for (int t = 0; t < TB; ++t)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const bool live = (T.alive >> (4 * t + k)) & 1u;
-      const uint32_t m = __ballot_sync(kFull, live);
-      if (live) list[n + __popc(m & lt)] = uint32_t(t * kMB + k * 32 + lane) | (T.gid[t][k] << kRowBits);
-      n += __popc(m);
-    }
+    for (int k = 0; k < 4; ++k)
+      if ((T.alive >> (4 * t + k)) & 1u) {
+        list[pos] = uint32_t(t * kMB + k * 32 + lane) | (T.gid[t][k] << kRowBits);
+        ++pos;
+      }
   __syncwarp();
-  return n;
+  return total;
 }
 
 // Value of FOR/DICT column c at tile row r: one bit-field read from the
