@@ -395,6 +395,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--ref-budget-s", type=float, default=20.0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -439,6 +440,12 @@ def main():
         plan = eng.plan(w, stream)
     torch.cuda.synchronize()
     build_ms = 1e3 * (time.perf_counter() - t0)
+    autotuned = None
+    if not (args.chunk_rows or args.threads or args.ht != "auto" or args.no_autotune):
+        # the library's autotuner picks the launch configuration (cached
+        # for this plan's signature; untimed)
+        best, best_ms = eng.ctx.autotune([plan], stream, reps=3)
+        autotuned = {"best": best, "best_ms": best_ms}
     tuning = dpf.Tuning(args.chunk_rows, args.threads, dpf.HT_PLACE[args.ht], 0)
     prep = eng.ctx.prepare([plan], tuning)
     eng.ctx.capture_graph(prep, stream)
@@ -505,6 +512,7 @@ def main():
                      "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)"},
         "unfused": unfused,
+        "autotune": autotuned,
         "gpu_launches": args.steps,
         "clocks": clocks,
         "wall_s": wall,

@@ -46,14 +46,14 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
     TileState T;
     tile_init(P, i0, nmb, lane, T);
     tile_first_step<kHost>(Q, P, H, T, nullptr, lane, status);
-    uint32_t n = tile_compact(T, list, lane);
-    n = list_steps<kHost>(Q, P, H, list, n, nullptr, lane, status);
+    uint32_t n = tile_compact(T, list, 0, 0, lane);
+    n = list_steps<kHost>(Q, P, i0, list, n, nullptr, lane, status);
     for (uint32_t j0 = 0; j0 < n; j0 += 32) {
       const bool valid = j0 + lane < n;
       const uint32_t r = valid ? (list[j0 + lane] & ((1u << kRowBits) - 1u)) : 0u;
-      const int32_t kv = int32_t(row_value<kHost>(Q, Q.build_key, P, H, r, valid, lane, status));
-      const uint32_t c0 = Q.build_npay > 0 ? row_value<kHost>(Q, Q.build_pay[0], P, H, r, valid, lane, status) : 0u;
-      const uint32_t c1 = Q.build_npay > 1 ? row_value<kHost>(Q, Q.build_pay[1], P, H, r, valid, lane, status) : 0u;
+      const int32_t kv = int32_t(row_value<kHost>(Q, Q.build_key, P, i0, r, valid, lane, status));
+      const uint32_t c0 = Q.build_npay > 0 ? row_value<kHost>(Q, Q.build_pay[0], P, i0, r, valid, lane, status) : 0u;
+      const uint32_t c1 = Q.build_npay > 1 ? row_value<kHost>(Q, Q.build_pay[1], P, i0, r, valid, lane, status) : 0u;
       if (!valid) continue;
       if (kMode == 0) {
         ++kept;

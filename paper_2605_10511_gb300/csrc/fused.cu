@@ -119,7 +119,7 @@ __device__ void finish_query(const DevQuery& Q, unsigned long long* sacc, uint32
 // and on how its operands are read: kPoint = FOR/DICT columns, one bit field
 // per row; otherwise any codec through row_value (DELTA decodes densely).
 template <bool kHost, int kOp, bool kPoint>
-__device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, const TileHdr& Hd,
+__device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                          const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
                                          uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
   constexpr int U = kPoint ? kListUnroll : 1;  // rounds whose loads are issued together
@@ -141,11 +141,11 @@ __device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, 
     for (int u = 0; u < U; ++u) {
       va[u] = vb[u] = 0;
       if (kOp != DPF_AGG_COUNT)
-        va[u] = int32_t(kPoint ? point_value<kHost>(Q, ca, P, Hd, r[u], valid[u])
-                               : row_value<kHost>(Q, ca, P, Hd, r[u], valid[u], lane, status));
+        va[u] = int32_t(kPoint ? point_value<kHost>(Q, ca, P, seg_mb, r[u], valid[u])
+                               : row_value<kHost>(Q, ca, P, seg_mb, r[u], valid[u], lane, status));
       if (kOp == DPF_AGG_SUM_MUL || kOp == DPF_AGG_SUM_SUB)
-        vb[u] = int32_t(kPoint ? point_value<kHost>(Q, cb, P, Hd, r[u], valid[u])
-                               : row_value<kHost>(Q, cb, P, Hd, r[u], valid[u], lane, status));
+        vb[u] = int32_t(kPoint ? point_value<kHost>(Q, cb, P, seg_mb, r[u], valid[u])
+                               : row_value<kHost>(Q, cb, P, seg_mb, r[u], valid[u], lane, status));
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -167,12 +167,12 @@ __device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, 
 }
 
 template <bool kHost, int kOp>
-__device__ __forceinline__ void agg_dispatch(const DevQuery& Q, const PageState& P, const TileHdr& Hd,
+__device__ __forceinline__ void agg_dispatch(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                              const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
                                              uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
   const bool point = Q.cols[ca].codec != C_DELTA && (kOp == DPF_AGG_SUM || Q.cols[cb].codec != C_DELTA);
-  if (point) agg_pass<kHost, kOp, true>(Q, P, Hd, list, n, lane, acc, slot, ca, cb, single, status);
-  else agg_pass<kHost, kOp, false>(Q, P, Hd, list, n, lane, acc, slot, ca, cb, single, status);
+  if (point) agg_pass<kHost, kOp, true>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status);
+  else agg_pass<kHost, kOp, false>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status);
 }
 
 // Aggregation over a warp's survivor list (Kernel #3 hash aggregation;
@@ -181,7 +181,7 @@ __device__ __forceinline__ void agg_dispatch(const DevQuery& Q, const PageState&
 // atomics into the CTA's shared accumulators (or the query's global ones for
 // large domains), indexed by the dense group id.
 template <bool kHost>
-__device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageState& P, const TileHdr& Hd,
+__device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                                const uint32_t* list, uint32_t n, int lane,
                                                unsigned long long* acc, unsigned int* status) {
   const uint32_t S1 = 1 + Q.naggs;
@@ -199,16 +199,16 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
     const int ca = Q.agg_a[a], cb = Q.agg_b[a];
     switch (Q.agg_op[a]) {
       case DPF_AGG_COUNT:
-        agg_pass<kHost, DPF_AGG_COUNT, true>(Q, P, Hd, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        agg_pass<kHost, DPF_AGG_COUNT, true>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
         break;
       case DPF_AGG_SUM:
-        agg_dispatch<kHost, DPF_AGG_SUM>(Q, P, Hd, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        agg_dispatch<kHost, DPF_AGG_SUM>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
         break;
       case DPF_AGG_SUM_MUL:
-        agg_dispatch<kHost, DPF_AGG_SUM_MUL>(Q, P, Hd, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        agg_dispatch<kHost, DPF_AGG_SUM_MUL>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
         break;
       default:
-        agg_dispatch<kHost, DPF_AGG_SUM_SUB>(Q, P, Hd, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        agg_dispatch<kHost, DPF_AGG_SUM_SUB>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
         break;
     }
   }
@@ -235,6 +235,9 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
     TileHdr Hn{0, 0, 0, 0};
     if (1 < ntiles) Hn = load_headers<kHost>(Q, P, mb0 + TB, nmb_of(1), lane);
     if (!kHost) prefetch_payloads(Q, P, H, nmb_of(0), lane);
+    // the list collects the survivors of consecutive tiles (a segment of at
+    // most 2^kRowBits rows of this page) before the later steps run on them
+    uint32_t n = 0, seg_mb = mb0;
     for (uint32_t j = 0; j < ntiles; ++j) {
       const uint32_t i0 = mb0 + j * TB;
       const uint32_t nmb = nmb_of(j);
@@ -244,9 +247,14 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
       TileState T;
       tile_init(P, i0, nmb, lane, T);
       tile_first_step<kHost>(Q, P, H, T, stab, lane, status);
-      uint32_t n = tile_compact(T, list, lane);
-      n = list_steps<kHost>(Q, P, H, list, n, stab, lane, status);
-      if (n) list_aggregate<kHost>(Q, P, H, list, n, lane, acc, status);
+      n = tile_compact(T, list, n, (i0 - seg_mb) * kMB, lane);
+      const uint32_t next = i0 + TB;
+      if (j + 1 == ntiles || n + kTileRows > kListCap || next + TB - seg_mb > kSegMbs) {
+        n = list_steps<kHost>(Q, P, seg_mb, list, n, stab, lane, status);
+        if (n) list_aggregate<kHost>(Q, P, seg_mb, list, n, lane, acc, status);
+        n = 0;
+        seg_mb = next;
+      }
       H = Hn;
       Hn = Hnn;
     }
@@ -295,7 +303,7 @@ __global__ void __launch_bounds__(256, kFusedMinBlocks) fused_kernel(const DevQu
   // query order, so every warp reaches that meeting point), flushing the
   // finished query's accumulators first.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint32_t* list = lists + uint32_t(warp) * kTileRows;
+  uint32_t* list = lists + uint32_t(warp) * kListCap;
   auto draw = [&](unsigned long long& t) -> int {
     unsigned long long x = 0;
     if (lane == 0) x = atomicAdd(&sched->next, 1ull);
@@ -357,7 +365,7 @@ __global__ void __launch_bounds__(256, kFusedMinBlocks) fused_kernel(const DevQu
 
 size_t fused_dynamic_smem(uint32_t acc_slots, size_t smem_tables, int threads) {
   return ((acc_slots * sizeof(unsigned long long) + 15) & ~size_t(15)) + ((smem_tables + 15) & ~size_t(15)) +
-         size_t(threads / 32) * kTileRows * sizeof(uint32_t);
+         size_t(threads / 32) * kListCap * sizeof(uint32_t);
 }
 
 int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, bool host_data) {

@@ -16,7 +16,7 @@ constexpr uint32_t kMbPerWarpTile = 4;
 // and 3 (24 warps, 80 registers) measured fastest.
 constexpr int kFusedMinBlocks = 3;
 // Rows of one scheduling ticket (one warp's unit of work) unless tuned.
-constexpr uint32_t kDefaultChunkRows = 2048;
+constexpr uint32_t kDefaultChunkRows = 4096;
 
 // Fused persistent kernel over a batch of compiled queries (Sec. 3.2).
 // qbegin[0..nq] = first ticket of each query (qbegin[nq] = total tickets).

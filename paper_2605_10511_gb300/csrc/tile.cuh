@@ -367,9 +367,16 @@ __device__ __forceinline__ void dense_step_t(const DevQuery& Q, const DevStep& S
 // so the warp's issue slots follow the surviving rows instead of all rows.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kTileRows = kMB * TB;
-constexpr uint32_t kRowBits = 9;
+// A warp's list collects the survivors of several consecutive tiles of one
+// page (a segment of at most 2^kRowBits rows) before the later steps run,
+// so their rounds of 32 are full even when few rows survive per tile.
+constexpr uint32_t kRowBits = 12;
+constexpr uint32_t kSegMbs = (1u << kRowBits) / kMB;  // mini blocks per segment (16)
+constexpr uint32_t kListCap = 1024;                    // entries per warp list
 constexpr int kListUnroll = 1;  // survivor rounds whose loads are issued together (measured best at 1)
 static_assert(kTileRows <= (1u << kRowBits), "row index field too narrow");
+static_assert(kListCap >= kTileRows, "a list must hold one tile");
+static_assert(kSegMbs <= 32, "segment mini blocks must fit a 32-bit mask");
 
 // Dense first step of a tile (or none): live bits and group-id contributions.
 // The step's kind, table and codec are resolved here, once per tile.
@@ -383,12 +390,14 @@ __device__ __forceinline__ void tile_first_step(const DevQuery& Q, const PageSta
   else dense_step_t<kHost, false>(Q, S, P, Hd, T, stab, lane, status);
 }
 
-// Appends the tile's live rows to the warp's list; returns the list length.
-// Each lane counts its live rows, a warp exclusive scan of the counts gives
-// the lane's first slot, and the lane writes its rows there in (t, k) order
-// (the list's order is free: later steps and the aggregation visit every
-// entry once, whatever its position).
-__device__ __forceinline__ uint32_t tile_compact(const TileState& T, uint32_t* list, int lane) {
+// Appends the tile's live rows to the warp's list after its first n0
+// entries; row_base = the tile's first row within the list's segment.
+// Returns the list length.  Each lane counts its live rows, a warp exclusive
+// scan of the counts gives the lane's first slot, and the lane writes its
+// rows there in (t, k) order (the list's order is free: later steps and the
+// aggregation visit every entry once, whatever its position).
+__device__ __forceinline__ uint32_t tile_compact(const TileState& T, uint32_t* list, uint32_t n0, uint32_t row_base,
+                                                 int lane) {
   const uint32_t cnt = __popc(T.alive);
   uint32_t incl = cnt;
 #pragma unroll
@@ -397,66 +406,106 @@ __device__ __forceinline__ uint32_t tile_compact(const TileState& T, uint32_t* l
     if (lane >= d) incl += y;
   }
   const uint32_t total = __shfl_sync(kFull, incl, 31);
-  uint32_t pos = incl - cnt;
+  uint32_t pos = n0 + incl - cnt;
 #pragma unroll
   for (int t = 0; t < TB; ++t)
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if ((T.alive >> (4 * t + k)) & 1u) {
-        list[pos] = uint32_t(t * kMB + k * 32 + lane) | (T.gid[t][k] << kRowBits);
+        list[pos] = (row_base + uint32_t(t * kMB + k * 32 + lane)) | (T.gid[t][k] << kRowBits);
         ++pos;
       }
   __syncwarp();
-  return total;
+  return n0 + total;
 }
 
-// Value of FOR/DICT column c at tile row r: one bit-field read from the
-// packed payload (two words when the field straddles them).
+// Value of FOR/DICT column c at row r of the list's segment (mini blocks
+// seg_mb.. of the page): the mini block's header (an L1 hit: the tile's
+// headers were just loaded) and one bit field of its packed payload (two
+// words when the field straddles them).
 template <bool kHost>
-__device__ __forceinline__ uint32_t point_value(const DevQuery& Q, int c, const PageState& P, const TileHdr& Hd,
+__device__ __forceinline__ uint32_t point_value(const DevQuery& Q, int c, const PageState& P, uint32_t seg_mb,
                                                 uint32_t r, bool valid) {
-  const uint32_t codec = Q.cols[c].codec;
   const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, c));
-  const uint32_t* pay = reinterpret_cast<const uint32_t*>(pg + payload_offset(codec, P.prow));
-  const int src = c * TB + int(r >> 7);
-  const uint32_t base = __shfl_sync(kFull, Hd.x, src);
-  const uint32_t wob = __shfl_sync(kFull, Hd.y, src);
-  const uint32_t bw = tmin<uint32_t>(wob & 0xffu, 32u);
+  if (!valid) return 0u;
+  const uint32_t codec = Q.cols[c].codec;
+  const uint2 h = ld_u2<kHost>(reinterpret_cast<const uint2*>(pg + kPageHdr + uint64_t(seg_mb + (r >> 7)) * 8));
+  const uint32_t bw = tmin<uint32_t>(h.y & 0xffu, 32u);
   uint32_t x = 0;
-  if (valid && bw != 0) {
+  if (bw != 0) {
+    const uint32_t* pay = reinterpret_cast<const uint32_t*>(pg + payload_offset(codec, P.prow));
     const uint32_t bit = (r & (kMB - 1)) * bw;
-    const uint32_t* p = pay + (wob >> 8) + (bit >> 5);
+    const uint32_t* p = pay + (h.y >> 8) + (bit >> 5);
     const uint32_t sh = bit & 31u;
     const uint32_t lo = ld_u32<kHost>(p);
     const uint32_t hi = sh + bw > 32 ? ld_u32<kHost>(p + 1) : 0u;
     x = __funnelshift_r(lo, hi, sh);
     if (bw < 32) x &= (1u << bw) - 1u;
   }
-  return base + x;
+  return h.x + x;
 }
 
-// Value of any integer column at tile row r.  DELTA columns need the prefix
-// sum of their mini block, so the mini blocks holding the round's rows are
-// decoded densely and each lane picks its row with shuffles.
+// Dense decode of one mini block mb of column c whose header is read from
+// the page (lane i < bw loads word k*bw + i): v[k] = value of row 32k + lane.
 template <bool kHost>
-__device__ __forceinline__ uint32_t row_value(const DevQuery& Q, int c, const PageState& P, const TileHdr& Hd,
-                                              uint32_t r, bool valid, int lane, unsigned int* status) {
-  if (Q.cols[c].codec != C_DELTA) return point_value<kHost>(Q, c, P, Hd, r, valid);
-  const uint32_t need = __reduce_or_sync(kFull, valid ? 1u << (r >> 7) : 0u);
-  uint32_t alive = 0;
+__device__ __forceinline__ void mb_decode_at(const DevQuery& Q, int c, const uint8_t* pg, const PageState& P,
+                                             uint32_t mb, int lane, uint32_t (&v)[4], unsigned int* status) {
+  const uint32_t codec = Q.cols[c].codec;
+  const uint32_t* pay = reinterpret_cast<const uint32_t*>(pg + payload_offset(codec, P.prow));
+  uint32_t first, dmin = 0, wob;
+  if (codec == C_DELTA) {
+    const uint4 h = ld_u4<kHost>(reinterpret_cast<const uint4*>(pg + kPageHdr + uint64_t(mb) * 16));
+    first = h.x;
+    dmin = h.y;
+    wob = h.z;
+  } else {
+    const uint2 h = ld_u2<kHost>(reinterpret_cast<const uint2*>(pg + kPageHdr + uint64_t(mb) * 8));
+    first = h.x;
+    wob = h.y;
+  }
+  uint32_t bw = wob & 0xffu;
+  if (bw > 32) {
+    if (lane == 0) atomicOr(status, S_CORRUPT);
+    bw = 0;
+  }
+  const bool ld = uint32_t(lane) < bw;
+  const uint32_t* w = pay + (wob >> 8) + lane;
 #pragma unroll
-  for (int t = 0; t < TB; ++t)
-    if ((need >> t) & 1u) alive |= 15u << (4 * t);
-  uint32_t v[TB][4], anym;
-  tile_decode<kHost>(Q, c, P, Hd, alive, lane, v, anym, status);
-  uint32_t out = 0;
-#pragma unroll
-  for (int t = 0; t < TB; ++t) {
-    if (!((anym >> t) & 1u)) continue;
+  for (int k = 0; k < 4; ++k) v[k] = unpack_lane(ld ? ld_u32<kHost>(w + uint32_t(k) * bw) : 0u, bw, lane);
+  if (codec == C_DELTA) {
+    // x_j = first + sum_{i<=j} (dmin + p_i), modulo 2^32
+    uint32_t carry = first;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const uint32_t x = __shfl_sync(kFull, v[t][k], int(r & 31));
-      if ((r >> 5) == uint32_t(t * 4 + k)) out = x;
+      const uint32_t sc = warp_incl_scan(v[k] + dmin, lane);
+      v[k] = carry + sc;
+      carry += __shfl_sync(kFull, sc, 31);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] += first;
+  }
+}
+
+// Value of any integer column at segment row r.  DELTA columns need the
+// prefix sum of their mini block, so each mini block holding a row of the
+// round is decoded densely and the lanes pick their rows with shuffles.
+template <bool kHost>
+__device__ __forceinline__ uint32_t row_value(const DevQuery& Q, int c, const PageState& P, uint32_t seg_mb,
+                                              uint32_t r, bool valid, int lane, unsigned int* status) {
+  if (Q.cols[c].codec != C_DELTA) return point_value<kHost>(Q, c, P, seg_mb, r, valid);
+  const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, c));
+  uint32_t need = __reduce_or_sync(kFull, valid ? 1u << (r >> 7) : 0u);
+  uint32_t out = 0;
+  while (need) {
+    const uint32_t t = uint32_t(__ffs(need) - 1);
+    need &= need - 1;
+    uint32_t v[4];
+    mb_decode_at<kHost>(Q, c, pg, P, seg_mb + t, lane, v, status);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t x = __shfl_sync(kFull, v[k], int(r & 31));
+      if (valid && (r >> 5) == t * 4 + uint32_t(k)) out = x;
     }
   }
   return out;
@@ -466,34 +515,31 @@ __device__ __forceinline__ uint32_t row_value(const DevQuery& Q, int c, const Pa
 // decoded densely and gathered per lane, then the bytes are compared.
 template <bool kHost>
 __device__ __forceinline__ bool row_prefix(const DevQuery& Q, const DevStep& S, const PageState& P,
-                                           const TileHdr& Hd, uint32_t r, bool valid, int lane,
+                                           uint32_t seg_mb, uint32_t r, bool valid, int lane,
                                            unsigned int* status) {
-  const uint32_t need = __reduce_or_sync(kFull, valid ? 1u << (r >> 7) : 0u);
-  uint32_t alive = 0;
-#pragma unroll
-  for (int t = 0; t < TB; ++t)
-    if ((need >> t) & 1u) alive |= 15u << (4 * t);
-  uint32_t len[TB][4], anym;
-  tile_decode<kHost>(Q, S.col, P, Hd, alive, lane, len, anym, status);
+  const int c = S.col;
+  const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, c));
+  const uint32_t* starts = reinterpret_cast<const uint32_t*>(pg + kPageHdr + uint64_t(P.nmb_page) * 8);
+  uint32_t need = __reduce_or_sync(kFull, valid ? 1u << (r >> 7) : 0u);
   uint32_t my_len = 0, my_start = 0;
-#pragma unroll
-  for (int t = 0; t < TB; ++t) {
-    if (!((anym >> t) & 1u)) continue;
-    uint32_t st[4];
-    excl_scan128(len[t], lane, st);
-    const uint32_t mb_start = __shfl_sync(kFull, Hd.sstart, S.col * TB + t);
+  while (need) {
+    const uint32_t t = uint32_t(__ffs(need) - 1);
+    need &= need - 1;
+    uint32_t len[4], st[4];
+    mb_decode_at<kHost>(Q, c, pg, P, seg_mb + t, lane, len, status);
+    excl_scan128(len, lane, st);
+    const uint32_t mb_start = ld_u32<kHost>(starts + seg_mb + t);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const uint32_t l = __shfl_sync(kFull, len[t][k], int(r & 31));
+      const uint32_t l = __shfl_sync(kFull, len[k], int(r & 31));
       const uint32_t s0 = __shfl_sync(kFull, st[k], int(r & 31));
-      if ((r >> 5) == uint32_t(t * 4 + k)) {
+      if (valid && (r >> 5) == t * 4 + uint32_t(k)) {
         my_len = l;
         my_start = mb_start + s0;
       }
     }
   }
-  const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, S.col));
-  const uint8_t* bytes = pg + __shfl_sync(kFull, P.extra, S.col) + my_start;
+  const uint8_t* bytes = pg + __shfl_sync(kFull, P.extra, c) + my_start;
   bool match = valid && my_len >= S.plen;
   for (uint32_t i = 0; i < S.plen; ++i) {
     if (!__any_sync(kFull, match)) break;
@@ -520,7 +566,7 @@ __device__ __forceinline__ bool row_probe(const DevStep& S, const uint8_t* stab,
 // 8 = IN / FALSE.  Returns the new list length.
 template <bool kHost, int kOp>
 __device__ __forceinline__ uint32_t list_step_t(const DevQuery& Q, const DevStep& S, const PageState& P,
-                                                const TileHdr& Hd, uint32_t* list, uint32_t n, const uint8_t* stab,
+                                                uint32_t seg_mb, uint32_t* list, uint32_t n, const uint8_t* stab,
                                                 int lane, unsigned int* status) {
   // Rounds of 32 survivors are taken kListUnroll at a time: their entries
   // and packed values are all loaded before any is used, so the warp keeps
@@ -539,7 +585,7 @@ __device__ __forceinline__ uint32_t list_step_t(const DevQuery& Q, const DevStep
       gid[u] = e >> kRowBits;
     }
 #pragma unroll
-    for (int u = 0; u < kListUnroll; ++u) v[u] = point_value<kHost>(Q, S.col, P, Hd, r[u], valid[u]);
+    for (int u = 0; u < kListUnroll; ++u) v[u] = point_value<kHost>(Q, S.col, P, seg_mb, r[u], valid[u]);
     __syncwarp();
 #pragma unroll
     for (int u = 0; u < kListUnroll; ++u) {
@@ -567,7 +613,7 @@ __device__ __forceinline__ uint32_t list_step_t(const DevQuery& Q, const DevStep
 // round's mini blocks); kept out of line.
 template <bool kHost>
 __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevStep& S, const PageState& P,
-                                                   const TileHdr& Hd, uint32_t* list, uint32_t n,
+                                                   uint32_t seg_mb, uint32_t* list, uint32_t n,
                                                    const uint8_t* stab, int lane, unsigned int* status) {
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t out = 0;
@@ -578,9 +624,9 @@ __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevS
     uint32_t gid = e >> kRowBits;
     bool keep;
     if (S.kind == ST_PREFIX) {
-      keep = row_prefix<kHost>(Q, S, P, Hd, r, valid, lane, status);
+      keep = row_prefix<kHost>(Q, S, P, seg_mb, r, valid, lane, status);
     } else {
-      const uint32_t v = row_value<kHost>(Q, S.col, P, Hd, r, valid, lane, status);
+      const uint32_t v = row_value<kHost>(Q, S.col, P, seg_mb, r, valid, lane, status);
       if (S.kind == ST_PROBE) {
         switch (probe_mode(S)) {
           case PM_S1: keep = row_probe<PM_S1>(S, stab, v, valid, gid, status); break;
@@ -608,29 +654,29 @@ __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevS
 // Steps 1.. of the query over the warp's list; returns the list length.  Each
 // step is resolved to its specialised loop once, outside the loop.
 template <bool kHost>
-__device__ __forceinline__ uint32_t list_steps(const DevQuery& Q, const PageState& P, const TileHdr& Hd,
+__device__ __forceinline__ uint32_t list_steps(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                                uint32_t* list, uint32_t n, const uint8_t* stab, int lane,
                                                unsigned int* status) {
   for (uint32_t s = 1; s < Q.nsteps && n != 0; ++s) {
     const DevStep& S = Q.steps[s];
     if (S.kind == ST_PREFIX || Q.cols[S.col].codec == C_DELTA) {
-      n = list_step_generic<kHost>(Q, S, P, Hd, list, n, stab, lane, status);
+      n = list_step_generic<kHost>(Q, S, P, seg_mb, list, n, stab, lane, status);
       continue;
     }
     switch (S.kind) {
       case ST_PROBE:
         switch (probe_mode(S)) {
-          case PM_S1: n = list_step_t<kHost, PM_S1>(Q, S, P, Hd, list, n, stab, lane, status); break;
-          case PM_S2: n = list_step_t<kHost, PM_S2>(Q, S, P, Hd, list, n, stab, lane, status); break;
-          case PM_S4: n = list_step_t<kHost, PM_S4>(Q, S, P, Hd, list, n, stab, lane, status); break;
-          case PM_GDIRECT: n = list_step_t<kHost, PM_GDIRECT>(Q, S, P, Hd, list, n, stab, lane, status); break;
-          default: n = list_step_t<kHost, PM_OPEN>(Q, S, P, Hd, list, n, stab, lane, status); break;
+          case PM_S1: n = list_step_t<kHost, PM_S1>(Q, S, P, seg_mb, list, n, stab, lane, status); break;
+          case PM_S2: n = list_step_t<kHost, PM_S2>(Q, S, P, seg_mb, list, n, stab, lane, status); break;
+          case PM_S4: n = list_step_t<kHost, PM_S4>(Q, S, P, seg_mb, list, n, stab, lane, status); break;
+          case PM_GDIRECT: n = list_step_t<kHost, PM_GDIRECT>(Q, S, P, seg_mb, list, n, stab, lane, status); break;
+          default: n = list_step_t<kHost, PM_OPEN>(Q, S, P, seg_mb, list, n, stab, lane, status); break;
         }
         break;
-      case ST_KEY: n = list_step_t<kHost, 5>(Q, S, P, Hd, list, n, stab, lane, status); break;
-      case ST_RANGE: n = list_step_t<kHost, 6>(Q, S, P, Hd, list, n, stab, lane, status); break;
-      case ST_NOTRANGE: n = list_step_t<kHost, 7>(Q, S, P, Hd, list, n, stab, lane, status); break;
-      default: n = list_step_t<kHost, 8>(Q, S, P, Hd, list, n, stab, lane, status); break;
+      case ST_KEY: n = list_step_t<kHost, 5>(Q, S, P, seg_mb, list, n, stab, lane, status); break;
+      case ST_RANGE: n = list_step_t<kHost, 6>(Q, S, P, seg_mb, list, n, stab, lane, status); break;
+      case ST_NOTRANGE: n = list_step_t<kHost, 7>(Q, S, P, seg_mb, list, n, stab, lane, status); break;
+      default: n = list_step_t<kHost, 8>(Q, S, P, seg_mb, list, n, stab, lane, status); break;
     }
   }
   return n;
