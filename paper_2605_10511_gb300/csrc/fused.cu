@@ -199,7 +199,11 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
     const int ca = Q.agg_a[a], cb = Q.agg_b[a];
     switch (Q.agg_op[a]) {
       case DPF_AGG_COUNT:
-        agg_pass<kHost, DPF_AGG_COUNT, true>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        if (single) {
+          if (lane == 0) atomicAdd(acc + 1 + a, (unsigned long long)n);
+        } else {
+          agg_pass<kHost, DPF_AGG_COUNT, true>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        }
         break;
       case DPF_AGG_SUM:
         agg_dispatch<kHost, DPF_AGG_SUM>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
@@ -216,7 +220,7 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
 
 // One ticket: the rows [chunk*chunk_rows, +chunk_rows) of Q's fact table,
 // processed by one warp, cut at page boundaries into tiles.  Tile headers
-// are loaded two tiles ahead and payloads prefetched into L2 one tile ahead.
+// are loaded two tiles ahead.
 template <bool kHost>
 __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long long* acc, const uint8_t* stab,
                                uint32_t* list, int lane, unsigned int* status) {
@@ -234,7 +238,6 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
     TileHdr H = load_headers<kHost>(Q, P, mb0, nmb_of(0), lane);
     TileHdr Hn{0, 0, 0, 0};
     if (1 < ntiles) Hn = load_headers<kHost>(Q, P, mb0 + TB, nmb_of(1), lane);
-    if (!kHost) prefetch_payloads(Q, P, H, nmb_of(0), lane);
     // the list collects the survivors of consecutive tiles (a segment of at
     // most 2^kRowBits rows of this page) before the later steps run on them
     uint32_t n = 0, seg_mb = mb0;
@@ -243,7 +246,6 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
       const uint32_t nmb = nmb_of(j);
       TileHdr Hnn{0, 0, 0, 0};
       if (j + 2 < ntiles) Hnn = load_headers<kHost>(Q, P, mb0 + (j + 2) * TB, nmb_of(j + 2), lane);
-      if (!kHost && j + 1 < ntiles) prefetch_payloads(Q, P, Hn, nmb_of(j + 1), lane);
       TileState T;
       tile_init(P, i0, nmb, lane, T);
       tile_first_step<kHost>(Q, P, H, T, stab, lane, status);

@@ -71,28 +71,6 @@ __device__ __forceinline__ TileHdr load_headers(const DevQuery& Q, const PageSta
   return h;
 }
 
-// Asks L2 to fetch [p, p + bytes) (p 16-byte aligned, bytes a multiple of
-// 16): a bulk prefetch that returns at once and needs no completion.
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Prefetches the packed payload of every (column, mini block) header a lane
-// holds (see load_headers) into L2, so the tile's later loads, dense or
-// per survivor, find their lines there instead of waiting on HBM.
-__device__ __forceinline__ void prefetch_payloads(const DevQuery& Q, const PageState& P, const TileHdr& H,
-                                                  uint32_t nmb, int lane) {
-  const int hc = lane / TB, ht = lane % TB;
-  const uint64_t hpg = __shfl_sync(kFull, P.pg, hc < int(Q.ncols) ? hc : 0);
-  if (hc >= int(Q.ncols) || ht >= int(nmb)) return;
-  const uint32_t codec = Q.cols[hc].codec;
-  const uint32_t wob = codec == C_DELTA ? H.z : H.y;
-  const uint32_t bw = wob & 0xffu;
-  if (bw == 0 || bw > 32) return;
-  const uint8_t* pay = reinterpret_cast<const uint8_t*>(hpg) + payload_offset(codec, P.prow) + uint64_t(wob >> 8) * 4;
-  prefetch_l2(pay, 16u * bw);
-}
-
 struct TileState {
   uint32_t alive;         // bit 4t+k: row 32k+lane of mini block t is live
   uint32_t gid[TB][4];    // dense group id of each row
@@ -487,16 +465,25 @@ __device__ __forceinline__ void mb_decode_at(const DevQuery& Q, int c, const uin
   }
 }
 
-// Value of any integer column at segment row r.  DELTA columns need the
-// prefix sum of their mini block, so each mini block holding a row of the
-// round is decoded densely and the lanes pick their rows with shuffles.
+// Value of any integer column at segment row r.  A DELTA mini block with
+// bit width 0 holds one repeated value (every delta is dmin = 0: the runs of
+// equal keys of a sorted load), which its header gives directly.  Other
+// DELTA mini blocks need the prefix sum of their deltas, so each one holding
+// a row of the round is decoded densely and the lanes pick their rows with
+// shuffles.
 template <bool kHost>
 __device__ __forceinline__ uint32_t row_value(const DevQuery& Q, int c, const PageState& P, uint32_t seg_mb,
                                               uint32_t r, bool valid, int lane, unsigned int* status) {
   if (Q.cols[c].codec != C_DELTA) return point_value<kHost>(Q, c, P, seg_mb, r, valid);
   const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, c));
-  uint32_t need = __reduce_or_sync(kFull, valid ? 1u << (r >> 7) : 0u);
   uint32_t out = 0;
+  bool dense = false;
+  if (valid) {
+    const uint4 h = ld_u4<kHost>(reinterpret_cast<const uint4*>(pg + kPageHdr + uint64_t(seg_mb + (r >> 7)) * 16));
+    if ((h.z & 0xffu) == 0 && h.y == 0) out = h.x;  // constant mini block
+    else dense = true;
+  }
+  uint32_t need = __reduce_or_sync(kFull, dense ? 1u << (r >> 7) : 0u);
   while (need) {
     const uint32_t t = uint32_t(__ffs(need) - 1);
     need &= need - 1;
@@ -505,7 +492,7 @@ __device__ __forceinline__ uint32_t row_value(const DevQuery& Q, int c, const Pa
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const uint32_t x = __shfl_sync(kFull, v[k], int(r & 31));
-      if (valid && (r >> 5) == t * 4 + uint32_t(k)) out = x;
+      if (dense && (r >> 5) == t * 4 + uint32_t(k)) out = x;
     }
   }
   return out;
