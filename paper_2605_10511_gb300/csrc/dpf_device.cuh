@@ -55,8 +55,8 @@ __device__ __forceinline__ MbHdr parse_hdr(uint4 h, uint32_t codec) {
 // Loads of compressed bytes.  Both device-resident and host-resident
 // (mapped pinned) columns are immutable while a kernel runs, so both use
 // the read-only path: full-width vector loads that the host link serves in
-// whole lines.  (kHost only switches off the L2 bulk prefetch, which is
-// issued for device memory alone.)
+// whole lines.  (kHost selects the kernel instantiation for host-resident
+// pages; the loads are the same.)
 template <bool kHost>
 __device__ __forceinline__ uint32_t ld_u32(const uint32_t* p) {
   return __ldg(p);

@@ -202,7 +202,7 @@ __device__ __forceinline__ int probe_mode(const DevStep& S) {
 
 // Direct-table probe of one key: true on a hit, which adds the join's
 // group-id contribution to gid.
-template <int kMode>
+template <int kMode, bool kContrib = true>
 __device__ __forceinline__ bool probe_direct(const DevStep& S, const uint8_t* stab, uint32_t key, bool valid,
                                              uint32_t& gid) {
   const uint32_t off = key - uint32_t(S.kmin);
@@ -221,25 +221,27 @@ __device__ __forceinline__ bool probe_direct(const DevStep& S, const uint8_t* st
   } else {
     e = look ? __ldg(static_cast<const uint32_t*>(S.ht) + off) : kAbsent;
     hit = e != kAbsent;
-    e = (e & 0xffffu) * S.mul0 + (e >> 16) * S.mul1;
+    e = kContrib ? (e & 0xffffu) * S.mul0 + (e >> 16) * S.mul1 : 0u;
   }
-  gid += hit ? e : 0u;
+  if (kContrib) gid += hit ? e : 0u;
   return hit;
 }
 
 // Join probe step over a decoded tile: live rows that miss are dropped;
 // hits add this join's group-id contribution.
-template <int kMode>
+template <int kMode, bool kContrib = true>
 __device__ __forceinline__ void dense_probe(const DevStep& S, const uint8_t* stab, const uint32_t (&v)[TB][4],
                                             uint32_t anym, TileState& T, unsigned int* status) {
   if (kMode != PM_OPEN) {
+    // every row is probed (the bounds check keeps dead rows' lookups inside
+    // the table); the result is masked with the live bits
 #pragma unroll
     for (int t = 0; t < TB; ++t) {
       if (!((anym >> t) & 1u)) continue;
       uint32_t keep = 0;
 #pragma unroll
       for (int k = 0; k < 4; ++k)
-        keep |= uint32_t(probe_direct<kMode>(S, stab, v[t][k], (T.alive >> (4 * t + k)) & 1u, T.gid[t][k])) << k;
+        keep |= uint32_t(probe_direct<kMode, kContrib>(S, stab, v[t][k], true, T.gid[t][k])) << k;
       T.alive &= ~((~keep & 15u) << (4 * t));
     }
     return;
@@ -298,7 +300,10 @@ __device__ __forceinline__ void dense_step_t(const DevQuery& Q, const DevStep& S
         case PM_S1: dense_probe<PM_S1>(S, stab, v, anym, T, status); break;
         case PM_S2: dense_probe<PM_S2>(S, stab, v, anym, T, status); break;
         case PM_S4: dense_probe<PM_S4>(S, stab, v, anym, T, status); break;
-        case PM_GDIRECT: dense_probe<PM_GDIRECT>(S, stab, v, anym, T, status); break;
+        case PM_GDIRECT:
+          if (S.mul0 | S.mul1) dense_probe<PM_GDIRECT, true>(S, stab, v, anym, T, status);
+          else dense_probe<PM_GDIRECT, false>(S, stab, v, anym, T, status);
+          break;
         default: dense_probe<PM_OPEN>(S, stab, v, anym, T, status); break;
       }
       return;
