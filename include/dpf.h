@@ -233,6 +233,11 @@ typedef struct dpf_plan {
 
 /* Launch configuration; 0 in a field = chosen by the library (tuning cache,
  * then defaults). */
+/* Join-table placement (Sec. 4.3 keeps the build side in GPU memory; where
+ * in it is ours): AUTO = the table of the first (dense) step in shared memory
+ * when it fits 48 KB, the tables of later steps in device memory; SMEM = every
+ * table that fits the opt-in shared memory, in probe order; GLOBAL = every
+ * table in device memory (served by L1/L2). */
 enum dpf_ht_place { DPF_HT_AUTO = 0, DPF_HT_SMEM = 1, DPF_HT_GLOBAL = 2 };
 typedef struct dpf_tuning {
   uint32_t chunk_rows;   /* rows per scheduling ticket (one warp's unit of work):

@@ -489,16 +489,21 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
   return DPF_OK;
 }
 
-// Places join tables in the CTA's shared-memory region, in probe order,
-// while they fit the budget: open-addressing tables as 8-byte slots, direct
-// tables as 1/2/4-byte group-id contributions.  Returns the bytes used.
-size_t place_tables(DevQuery& Q, size_t budget) {
+// Places join tables in the CTA's shared-memory region while they fit the
+// budget: open-addressing tables as 8-byte slots, direct tables as 1/2/4-byte
+// group-id contributions.  With first_only, only a table probed by the first
+// (dense) step is a candidate: that step probes every row, so its lookups
+// gain most from shared memory, while later steps probe few survivors and
+// their tables serve from L1/L2 without taking shared memory from the other
+// resident CTAs.  Returns the bytes used.
+size_t place_tables(DevQuery& Q, size_t budget, bool first_only) {
   const uint32_t width = Q.domain <= 255 ? 1u : (Q.domain <= 65535 ? 2u : 4u);
   size_t used = 0;
   for (uint32_t s = 0; s < Q.nsteps; ++s) {
     DevStep& S = Q.steps[s];
     if (S.kind != ST_PROBE) continue;
     S.smem_width = 0;
+    if (first_only && s != 0) continue;
     const uint32_t w = S.ht_kind == HT_DIRECT ? width : 8u;
     const size_t bytes = S.ht_kind == HT_DIRECT ? size_t(S.krange) * w : size_t(S.ht_mask + 1) * 8;
     const size_t at = (used + 15) & ~size_t(15);
@@ -625,7 +630,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
     dpf_status st = compile_plan(c, plans[i], Q, &h, probes);
     if (st) return fail(st, "plan %d: %s", i, t_last_error.c_str());
     host |= h;
-    const size_t used = place_tables(Q, table_budget);
+    const size_t used = place_tables(Q, table_budget, t.ht_placement == DPF_HT_AUTO);
     max_tables = std::max(max_tables, used);
     Q.chunk_rows = t.chunk_rows;
     Q.nchunks = (Q.nrows + t.chunk_rows - 1) / t.chunk_rows;
@@ -747,7 +752,7 @@ dpf_status noalloc_compile(dpf_ctx* c, const dpf_plan* plan, DevQuery* Q, size_t
   std::vector<const HashTable*> probes;
   dpf_status st = compile_plan(c, *plan, *Q, host, probes);
   if (st) return st;
-  const size_t used = place_tables(*Q, size_t(48 * 1024));
+  const size_t used = place_tables(*Q, size_t(48 * 1024), true);
   *smem_tables = used;
   *device = c->device;
   *num_sms = c->num_sms;
