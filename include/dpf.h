@@ -69,7 +69,10 @@ dpf_status dpf_create(dpf_ctx** out, int32_t device, uint64_t hbm_budget,
                       const dpf_alloc_hooks* hooks);
 /* Waits for the context's work, frees every object it owns. */
 dpf_status dpf_destroy(dpf_ctx* ctx);
-/* Device bytes currently held by the context. */
+/* Device bytes held by the context's live objects (columns, hash tables,
+ * prepared batches).  Without allocation hooks, freed blocks of up to 64 MiB
+ * (1 GiB in all) are kept for reuse and not counted here; with a budget, live
+ * plus kept bytes stay within it.  dpf_destroy returns all of them. */
 dpf_status dpf_memory_used(dpf_ctx* ctx, uint64_t* bytes);
 /* CUDA device the context is bound to. */
 dpf_status dpf_context_device(dpf_ctx* ctx, int32_t* device);

@@ -113,6 +113,12 @@ struct dpf_ctx {
   int num_sms = 0;
   int smem_optin = 0;
   std::map<uint64_t, dpf_tuning> tune_cache;  // plan-set signature -> tuning chosen by dpf_autotune
+  // Freed device blocks kept for reuse (without allocation hooks): a batch's
+  // scratch is allocated at dpf_prepare and freed at dpf_release, and
+  // cudaFree would wait for every kernel on the device, serialising a
+  // serving loop's overlapping batches.
+  std::multimap<uint64_t, void*> cache;
+  uint64_t cached = 0;
 };
 
 namespace {
@@ -129,22 +135,55 @@ struct DeviceGuard {
   }
 };
 
+constexpr uint64_t kCacheMaxBytes = uint64_t(1) << 30;  // freed bytes kept for reuse
+constexpr uint64_t kCacheMaxBlock = uint64_t(64) << 20; // larger blocks are returned at once
+
+void drop_cache(dpf_ctx* c) {
+  for (auto& kv : c->cache) cudaFree(kv.second);
+  c->cache.clear();
+  c->cached = 0;
+}
+
 dpf_status dev_alloc(dpf_ctx* c, uint64_t bytes, void** out) {
   *out = nullptr;
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~uint64_t(255);
-  if (c->budget && c->used + bytes > c->budget)
+  void* p = nullptr;
+  if (!c->has_hooks) {
+    // reuse a cached block of at most 25 % more than asked for
+    auto it = c->cache.lower_bound(bytes);
+    if (it != c->cache.end() && it->first <= bytes + bytes / 4) {
+      bytes = it->first;
+      p = it->second;
+      c->cache.erase(it);
+      c->cached -= bytes;
+    } else if (c->budget && c->used + c->cached + bytes > c->budget) {
+      drop_cache(c);
+    }
+  }
+  if (c->budget && c->used + bytes > c->budget) {
+    if (p) {
+      c->cache.emplace(bytes, p);
+      c->cached += bytes;
+    }
     return fail(DPF_ENOMEM, "device budget exceeded: %llu used + %llu > %llu", (unsigned long long)c->used,
                 (unsigned long long)bytes, (unsigned long long)c->budget);
-  void* p = nullptr;
-  if (c->has_hooks) {
-    p = c->hooks.alloc(bytes, c->hooks.user);
-    if (!p) return fail(DPF_ENOMEM, "allocation hook failed for %llu bytes", (unsigned long long)bytes);
-  } else {
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(DPF_ENOMEM, "cudaMalloc(%llu): %s", (unsigned long long)bytes, cudaGetErrorString(e));
+  }
+  if (!p) {
+    if (c->has_hooks) {
+      p = c->hooks.alloc(bytes, c->hooks.user);
+      if (!p) return fail(DPF_ENOMEM, "allocation hook failed for %llu bytes", (unsigned long long)bytes);
+    } else {
+      cudaError_t e = cudaMalloc(&p, bytes);
+      if (e != cudaSuccess && !c->cache.empty()) {  // give the cached blocks back and retry
+        cudaGetLastError();
+        drop_cache(c);
+        e = cudaMalloc(&p, bytes);
+      }
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DPF_ENOMEM, "cudaMalloc(%llu): %s", (unsigned long long)bytes, cudaGetErrorString(e));
+      }
     }
   }
   c->dev_sizes[p] = bytes;
@@ -157,10 +196,18 @@ void dev_free(dpf_ctx* c, void* p) {
   if (!p) return;
   auto it = c->dev_sizes.find(p);
   if (it == c->dev_sizes.end()) return;
-  c->used -= it->second;
+  const uint64_t bytes = it->second;
+  c->used -= bytes;
   c->dev_sizes.erase(it);
-  if (c->has_hooks) c->hooks.free(p, c->hooks.user);
-  else cudaFree(p);
+  if (c->has_hooks) {
+    c->hooks.free(p, c->hooks.user);
+  } else if (bytes <= kCacheMaxBlock && c->cached + bytes <= kCacheMaxBytes &&
+             (!c->budget || c->used + c->cached + bytes <= c->budget)) {
+    c->cache.emplace(bytes, p);
+    c->cached += bytes;
+  } else {
+    cudaFree(p);
+  }
 }
 
 template <class T>
@@ -817,6 +864,7 @@ dpf_status dpf_destroy(dpf_ctx* c) {
     dev_free(c, c->bsched);
     dev_free(c, c->bcount);
     dev_free(c, c->bkminmax);
+    drop_cache(c);
     if (c->io) cudaStreamDestroy(c->io);
   }
   delete c;

@@ -189,3 +189,49 @@ def test_loaded_pages_are_the_encoded_pages(eng):
             got = eng.ctx.column_bytes(eng.col(w, tname, cname))
             want = oracle.encode_column(c, t["page_rows"])["blob"]
             assert np.array_equal(got, want), (tname, cname)
+
+
+@pytest.mark.parametrize("rows,page_rows", [(1, 128), (127, 128), (129, 128), (5000, 4096),
+                                            (1 << 20, 1 << 20), ((1 << 20) + 3, 1 << 20)])
+def test_edge_sizes(eng, rows, page_rows):
+    """One row, ragged single mini blocks, one row past a page, and the
+    largest page (2^20 rows) with a 3-row second page."""
+    w = synth.tiny_random_workload(77, rows=rows, page_rows=page_rows)
+    w["name"] = f"edge_{rows}_{page_rows}"
+    assert_same(eng.run(w), expect(w), w["name"])
+
+
+def test_largest_ticket(eng, shapes):
+    """A ticket of 2^24 rows (the most dpf_prepare accepts) covers many pages."""
+    w = shapes["star"]
+    t = dpf.Tuning(1 << 24, 256, 0, 0)
+    assert_same(eng.run(w, tuning=t), expect(w), "chunk 2^24")
+
+
+def test_memory_returns_after_release_and_blocks_are_reused(shapes):
+    e = dpf.Engine(device=0)
+    try:
+        w = shapes["scan"]
+        e.load_workload(w)
+        h = e.plan(w)
+        base = e.ctx.memory_used()
+        for _ in range(5):
+            p = e.ctx.prepare([h])
+            e.ctx.launch(p)
+            assert_same(e.ctx.read_result(p, 0), expect(w), "reuse")
+            e.ctx.release(p)
+            assert e.ctx.memory_used() == base
+    finally:
+        e.close()
+
+
+def test_budget_is_enforced():
+    e = dpf.Engine(device=0, hbm_budget=1 << 20)
+    try:
+        w = synth.scan_filter_aggregate(rows=1 << 20)  # 4.6 MB of pages
+        w["name"] = "budget_scan"
+        with pytest.raises(dpf.DpfError) as ex:
+            e.load_workload(w)
+        assert ex.value.status == -2  # DPF_ENOMEM
+    finally:
+        e.close()
