@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -57,6 +58,7 @@ struct Column {
   int32_t* d_dict = nullptr;
   std::vector<uint64_t> page_off, row_prefix;
   std::vector<int32_t> dict;
+  int64_t vmin = 0, vmax = -1;    // value bounds from the mini block headers (planner statistics)
 };
 
 struct HashTable {
@@ -67,6 +69,7 @@ struct HashTable {
   uint32_t* direct = nullptr;     // HT_DIRECT
   int32_t kmin = 0;
   uint64_t entries = 0;
+  uint64_t dim_rows = 0;          // rows of the dimension the table was built from
   uint32_t pay_dom[2] = {0, 0};
   const int32_t* pay_dict[2] = {nullptr, nullptr};
 };
@@ -376,6 +379,64 @@ dpf_status compile_pred(const Column& c, const dpf_pred& p, DevStep& S, int col_
   return DPF_OK;
 }
 
+// Value bounds of a column for the planner, read from the validated mini
+// block headers: FOR: [min base, max base + 2^bw - 1] (the upper end is a
+// bound, not exact); DICT: the code range; DELTA: the range of the mini
+// blocks' first values (exact for runs of sorted keys); STR: unused.
+void value_bounds(uint32_t codec, const uint8_t* pages, const uint64_t* page_off, uint64_t npages, uint64_t nrows,
+                  uint32_t P, uint64_t dict_n, int64_t* vmin, int64_t* vmax) {
+  *vmin = 0;
+  *vmax = -1;
+  if (codec == C_DICT) {
+    *vmax = int64_t(dict_n) - 1;
+    return;
+  }
+  if (codec == C_STR) return;
+  int64_t lo = INT64_MAX, hi = INT64_MIN;
+  for (uint64_t p = 0; p < npages; ++p) {
+    const uint8_t* pg = pages + page_off[p];
+    const uint32_t rows = uint32_t(std::min<uint64_t>(P, nrows - p * uint64_t(P)));
+    const uint32_t nmb = (rows + kMB - 1) / kMB;
+    for (uint32_t m = 0; m < nmb; ++m) {
+      const uint8_t* h = pg + kPageHdr + uint64_t(m) * mb_hdr_bytes(codec);
+      const int64_t base = int32_t(rd32(h));
+      if (codec == C_DELTA) {
+        lo = std::min(lo, base);
+        hi = std::max(hi, base);
+      } else {
+        const uint32_t bw = rd32(h + 4) & 0xffu;
+        lo = std::min(lo, base);
+        hi = std::max(hi, base + (bw >= 32 ? int64_t(0xffffffffll) : (int64_t(1) << bw) - 1));
+      }
+    }
+  }
+  if (lo <= hi) {
+    *vmin = lo;
+    *vmax = hi;
+  }
+}
+
+// Estimated fraction of rows a step keeps, for ordering the steps: range
+// predicates assume values spread evenly over the column's bounds; a join
+// keeps the fraction of dimension rows that passed its build predicates
+// (foreign keys spread over the dimension); group keys keep every row.
+double step_selectivity(const DevStep& S, const Column* col, const HashTable* ht) {
+  switch (S.kind) {
+    case ST_FALSE: return 0.0;
+    case ST_KEY: return 2.0;  // not a filter: after every filter
+    case ST_PROBE: return ht && ht->dim_rows ? double(ht->entries) / double(ht->dim_rows) : 1.0;
+    case ST_PREFIX: return std::pow(0.1, double(S.plen));
+    default: break;
+  }
+  if (!col || col->vmax < col->vmin) return 0.5;
+  const double width = double(col->vmax - col->vmin) + 1.0;
+  if (S.kind == ST_IN) return std::min(1.0, double(S.nin) / width);
+  const double lo = std::max<double>(double(S.lo), double(col->vmin));
+  const double hi = std::min<double>(double(S.hi), double(col->vmax));
+  const double in = hi >= lo ? (hi - lo + 1.0) / width : 0.0;
+  return S.kind == ST_NOTRANGE ? 1.0 - in : in;
+}
+
 struct ColumnSet {
   dpf_ctx* c;
   DevQuery& Q;
@@ -420,6 +481,7 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
   if ((P.n_preds && !P.preds) || (P.n_joins && !P.joins) || (P.n_keys && !P.keys) || (P.n_aggs && !P.aggs))
     return fail(DPF_EINVAL, "plan array pointer is NULL");
   std::vector<DevStep> steps;
+  std::vector<double> sel;  // estimated selectivity of each step
   for (int i = 0; i < P.n_preds; ++i) {
     int idx;
     dpf_status st = cs.add(P.preds[i].col, &idx);
@@ -427,6 +489,7 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
     DevStep S;
     st = compile_pred(c->cols[P.preds[i].col], P.preds[i], S, idx);
     if (st) return st;
+    sel.push_back(step_selectivity(S, &c->cols[P.preds[i].col], nullptr));
     steps.push_back(S);
   }
   probes.clear();
@@ -455,6 +518,7 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
       S.ht_mask = H.capacity - 1;
     }
     probe_step.push_back(steps.size());
+    sel.push_back(step_selectivity(S, nullptr, &ht->second));
     steps.push_back(S);
     probes.push_back(&ht->second);
   }
@@ -500,7 +564,8 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
       S.kind = ST_KEY;
       S.col = uint8_t(idx);
       S.key_mul = Q.key_div[k];
-          steps.push_back(S);
+      sel.push_back(step_selectivity(S, nullptr, nullptr));
+      steps.push_back(S);
     }
   }
   Q.naggs = uint32_t(P.n_aggs);
@@ -528,8 +593,57 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
   }
   if (cs.ids.empty()) return fail(DPF_EINVAL, "plan names no column of the scanned table");
   if (steps.size() > size_t(kMaxSteps)) return fail(DPF_EINVAL, "plan compiles to more than %d steps", kMaxSteps);
+  // Step order from a small cost model (the result does not depend on it: a
+  // conjunction, and group-id contributions add).  The first step runs
+  // densely over every row at a cost of about its column's bits per row; every
+  // later step runs over the survivors of the steps before it at about
+  // kSparseCost bit-equivalents per survivor (a sector read and a probe).  For
+  // a given first step, later filters go most selective first; group keys
+  // come last.  The plan's own first filter is kept unless another first
+  // step is estimated 5 % cheaper.
+  constexpr double kSparseCost = 64.0;
+  std::vector<size_t> filters, keys;
+  for (size_t i = 0; i < steps.size(); ++i) (steps[i].kind == ST_KEY ? keys : filters).push_back(i);
+  std::vector<double> bits(steps.size(), 32.0);
+  for (size_t i = 0; i < steps.size(); ++i) {
+    const Column& col = c->cols[cs.ids[steps[i].col]];
+    if (col.nrows) bits[i] = 8.0 * double(col.bytes) / double(col.nrows) + (steps[i].kind == ST_PROBE ? 4.0 : 0.0);
+  }
+  auto plan_cost = [&](size_t first, std::vector<size_t>* out) {
+    std::vector<size_t> rest;
+    for (size_t i : filters)
+      if (i != first) rest.push_back(i);
+    std::stable_sort(rest.begin(), rest.end(), [&](size_t a, size_t b) { return sel[a] < sel[b]; });
+    double cost = bits[first], surv = std::min(1.0, sel[first]);
+    for (size_t i : rest) {
+      cost += surv * kSparseCost;
+      surv *= std::min(1.0, sel[i]);
+    }
+    cost += surv * kSparseCost * double(keys.size());
+    if (out) {
+      out->assign(1, first);
+      out->insert(out->end(), rest.begin(), rest.end());
+      out->insert(out->end(), keys.begin(), keys.end());
+    }
+    return cost;
+  };
+  std::vector<size_t> order(steps.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  if (!filters.empty()) {
+    size_t best = filters[0];
+    double best_cost = plan_cost(best, nullptr);
+    const double own = best_cost;
+    for (size_t f : filters) {
+      const double cst = plan_cost(f, nullptr);
+      if (cst < best_cost && cst < 0.95 * own) {
+        best = f;
+        best_cost = cst;
+      }
+    }
+    plan_cost(best, &order);
+  }
   Q.nsteps = uint32_t(steps.size());
-  for (size_t i = 0; i < steps.size(); ++i) Q.steps[i] = steps[i];
+  for (size_t i = 0; i < steps.size(); ++i) Q.steps[i] = steps[order[i]];
   Q.nrows = cs.nrows;
   Q.page_rows = cs.page_rows;
   *host = cs.host;
@@ -910,6 +1024,7 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
   col.page_off.assign(page_off, page_off + npages + 1);
   col.row_prefix.assign(row_prefix, row_prefix + npages);
   if (codec == C_DICT) col.dict.assign(dict, dict + dict_n);
+  value_bounds(codec, pages, page_off, npages, nrows, P, dict_n, &col.vmin, &col.vmax);
   if (codec == C_STR) {
     uint64_t sb = 0;
     for (uint64_t p = 0; p < npages; ++p) {
@@ -1034,6 +1149,7 @@ dpf_status dpf_build_hash(dpf_ctx* c, dpf_col_id key_col, const dpf_col_id* payl
   if (kc.codec != C_FOR && kc.codec != C_DELTA) return fail(DPF_EINVAL, "key column %d must be FOR or DELTA", key_col);
   HashTable ht;
   ht.npay = n_payload;
+  ht.dim_rows = kc.nrows;
   Q.build_key = kidx;
   Q.build_npay = n_payload;
   for (int f = 0; f < n_payload; ++f) {
