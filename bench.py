@@ -81,6 +81,10 @@ def _workload(name, rows):
         return synth.star_join(rows=rows or (1 << 26), clustered=True)
     if name == "star_unsorted":
         return synth.star_join(rows=rows or (1 << 26), clustered=False)
+    if name == "star_year":  # one year of dates on the date-clustered fact (mini block pruning)
+        return synth.star_join(rows=rows or (1 << 26), clustered=True, date_year=1994)
+    if name == "star_year_unsorted":
+        return synth.star_join(rows=rows or (1 << 26), clustered=False, date_year=1994)
     if name == "scan":
         return synth.scan_filter_aggregate(rows=rows or (1 << 20))
     if name == "strings":
@@ -394,7 +398,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dpf", choices=["dpf", "reference"])
     ap.add_argument("--workload", default="star",
-                    choices=["star", "star_unsorted", "scan", "strings", "batched"])
+                    choices=["star", "star_unsorted", "star_year", "star_year_unsorted", "scan", "strings",
+                             "batched"])
     ap.add_argument("--batch-queries", type=int, default=64)
     ap.add_argument("--serve", action="store_true", help="Poisson serving run instead of the step benchmark")
     ap.add_argument("--serve-rates", default="10,100,500,1000,2000")

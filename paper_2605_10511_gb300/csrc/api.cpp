@@ -55,6 +55,7 @@ struct Column {
   uint8_t* blob = nullptr;        // address the kernel reads (device or mapped host)
   uint8_t* host_blob = nullptr;   // pinned host allocation (HOST_PINNED)
   uint64_t* d_page_off = nullptr;
+  int2* d_zone = nullptr;         // per-page value bounds (zone map)
   int32_t* d_dict = nullptr;
   std::vector<uint64_t> page_off, row_prefix;
   std::vector<int32_t> dict;
@@ -70,6 +71,7 @@ struct HashTable {
   int32_t kmin = 0;
   uint64_t entries = 0;
   uint64_t dim_rows = 0;          // rows of the dimension the table was built from
+  int32_t key_lo = 1, key_hi = 0; // smallest and largest stored key (empty: lo > hi)
   uint32_t pay_dom[2] = {0, 0};
   const int32_t* pay_dict[2] = {nullptr, nullptr};
 };
@@ -234,6 +236,7 @@ void free_column(dpf_ctx* c, Column& col) {
     dev_free(c, col.blob);
   }
   dev_free(c, col.d_page_off);
+  dev_free(c, col.d_zone);
   dev_free(c, col.d_dict);
   col.blob = col.host_blob = nullptr;
 }
@@ -306,7 +309,7 @@ dpf_status validate_pages(uint32_t codec, const uint8_t* pages, uint64_t size, c
 }
 
 // ---------------------------------------------------------------- plans
-dpf_status compile_pred(const Column& c, const dpf_pred& p, DevStep& S, int col_index) {
+dpf_status compile_pred_body(const Column& c, const dpf_pred& p, DevStep& S, int col_index) {
   std::memset(&S, 0, sizeof S);
   S.col = uint8_t(col_index);
   if (p.op == DPF_OP_PREFIX) {
@@ -379,40 +382,68 @@ dpf_status compile_pred(const Column& c, const dpf_pred& p, DevStep& S, int col_
   return DPF_OK;
 }
 
-// Value bounds of a column for the planner, read from the validated mini
-// block headers: FOR: [min base, max base + 2^bw - 1] (the upper end is a
-// bound, not exact); DICT: the code range; DELTA: the range of the mini
-// blocks' first values (exact for runs of sorted keys); STR: unused.
+// Compiles one predicate and sets the value range a row needs to pass it
+// (used to skip mini blocks whose header bounds miss it).
+dpf_status compile_pred(const Column& c, const dpf_pred& p, DevStep& S, int col_index) {
+  const dpf_status st = compile_pred_body(c, p, S, col_index);
+  if (st) return st;
+  S.zlo = INT32_MIN;
+  S.zhi = INT32_MAX;
+  if (S.kind == ST_RANGE) {
+    S.zlo = S.lo;
+    S.zhi = S.hi;
+  } else if (S.kind == ST_IN) {
+    S.zlo = *std::min_element(S.in, S.in + S.nin);
+    S.zhi = *std::max_element(S.in, S.in + S.nin);
+  } else if (S.kind == ST_FALSE) {
+    S.zlo = 1;
+    S.zhi = 0;
+  }
+  return DPF_OK;
+}
+
+// Value bounds of a column, read from its validated mini block headers: per
+// page (a zone map the kernel uses to skip pages) and for the whole column
+// (planner statistics).  FOR and DICT (codes): [base, base + 2^bw - 1] per
+// mini block (the upper end is a bound, not exact).  DELTA: every value lies
+// within 127 steps of the mini block's first value, each step in
+// [min(0, dmin), max(0, dmin + 2^bw - 1)]; a page whose bound leaves int32
+// (values may have wrapped) gets the full range.  STR: the full range.
 void value_bounds(uint32_t codec, const uint8_t* pages, const uint64_t* page_off, uint64_t npages, uint64_t nrows,
-                  uint32_t P, uint64_t dict_n, int64_t* vmin, int64_t* vmax) {
+                  uint32_t P, int64_t* vmin, int64_t* vmax, std::vector<int2>* zones) {
   *vmin = 0;
   *vmax = -1;
-  if (codec == C_DICT) {
-    *vmax = int64_t(dict_n) - 1;
-    return;
-  }
+  zones->assign(npages, make_int2(INT32_MIN, INT32_MAX));
   if (codec == C_STR) return;
-  int64_t lo = INT64_MAX, hi = INT64_MIN;
+  int64_t clo = INT64_MAX, chi = INT64_MIN;
   for (uint64_t p = 0; p < npages; ++p) {
     const uint8_t* pg = pages + page_off[p];
     const uint32_t rows = uint32_t(std::min<uint64_t>(P, nrows - p * uint64_t(P)));
     const uint32_t nmb = (rows + kMB - 1) / kMB;
+    int64_t lo = INT64_MAX, hi = INT64_MIN;
     for (uint32_t m = 0; m < nmb; ++m) {
       const uint8_t* h = pg + kPageHdr + uint64_t(m) * mb_hdr_bytes(codec);
       const int64_t base = int32_t(rd32(h));
       if (codec == C_DELTA) {
-        lo = std::min(lo, base);
-        hi = std::max(hi, base);
+        const int64_t dmin = int32_t(rd32(h + 4));
+        const uint32_t bw = std::min<uint32_t>(rd32(h + 8) & 0xffu, 32u);
+        const int64_t span = bw >= 32 ? int64_t(0xffffffffll) : (int64_t(1) << bw) - 1;
+        lo = std::min(lo, base + 127 * std::min<int64_t>(0, dmin));
+        hi = std::max(hi, base + 127 * std::max<int64_t>(0, dmin + span));
       } else {
-        const uint32_t bw = rd32(h + 4) & 0xffu;
+        const uint32_t bw = std::min<uint32_t>(rd32(h + 4) & 0xffu, 32u);
         lo = std::min(lo, base);
         hi = std::max(hi, base + (bw >= 32 ? int64_t(0xffffffffll) : (int64_t(1) << bw) - 1));
       }
     }
+    if (lo > hi) continue;
+    clo = std::min(clo, lo);
+    chi = std::max(chi, hi);
+    if (lo >= INT32_MIN && hi <= INT32_MAX) (*zones)[p] = make_int2(int32_t(lo), int32_t(hi));
   }
-  if (lo <= hi) {
-    *vmin = lo;
-    *vmax = hi;
+  if (clo <= chi) {
+    *vmin = std::max<int64_t>(clo, INT32_MIN);
+    *vmax = std::min<int64_t>(chi, INT32_MAX);
   }
 }
 
@@ -460,6 +491,7 @@ struct ColumnSet {
     DevColumn& d = Q.cols[ids.size()];
     d.blob = col.blob;
     d.page_off = col.d_page_off;
+    d.zone = col.d_zone;
     d.nrows = col.nrows;
     d.codec = uint32_t(col.codec);
     d.page_rows = col.page_rows;
@@ -517,6 +549,8 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
       S.ht = H.slots;
       S.ht_mask = H.capacity - 1;
     }
+    S.zlo = H.key_lo;
+    S.zhi = H.key_hi;
     probe_step.push_back(steps.size());
     sel.push_back(step_selectivity(S, nullptr, &ht->second));
     steps.push_back(S);
@@ -564,6 +598,8 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
       S.kind = ST_KEY;
       S.col = uint8_t(idx);
       S.key_mul = Q.key_div[k];
+      S.zlo = INT32_MIN;
+      S.zhi = INT32_MAX;
       sel.push_back(step_selectivity(S, nullptr, nullptr));
       steps.push_back(S);
     }
@@ -1024,7 +1060,8 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
   col.page_off.assign(page_off, page_off + npages + 1);
   col.row_prefix.assign(row_prefix, row_prefix + npages);
   if (codec == C_DICT) col.dict.assign(dict, dict + dict_n);
-  value_bounds(codec, pages, page_off, npages, nrows, P, dict_n, &col.vmin, &col.vmax);
+  std::vector<int2> zones;
+  value_bounds(codec, pages, page_off, npages, nrows, P, &col.vmin, &col.vmax, &zones);
   if (codec == C_STR) {
     uint64_t sb = 0;
     for (uint64_t p = 0; p < npages; ++p) {
@@ -1055,7 +1092,9 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
     col.blob = static_cast<uint8_t*>(dp);
     if ((st = upload(c, col.blob, pages, size))) { free_column(c, col); return st; }
   }
-  if ((st = dev_alloc_t(c, npages + 1, &col.d_page_off)) || (st = upload(c, col.d_page_off, page_off, 8 * (npages + 1)))) {
+  if ((st = dev_alloc_t(c, npages + 1, &col.d_page_off)) || (st = upload(c, col.d_page_off, page_off, 8 * (npages + 1))) ||
+      (st = dev_alloc_t(c, std::max<uint64_t>(npages, 1), &col.d_zone)) ||
+      (st = upload(c, col.d_zone, zones.data(), sizeof(int2) * npages))) {
     free_column(c, col);
     return st;
   }
@@ -1198,6 +1237,10 @@ dpf_status dpf_build_hash(dpf_ctx* c, dpf_col_id key_col, const dpf_col_id* payl
   // dense key ranges get a direct table (one load per probe); others open
   // addressing with capacity a power of two >= 2 x entries
   const uint64_t range = kept ? uint64_t(int64_t(minmax[1]) - int64_t(minmax[0]) + 1) : 0;
+  if (kept) {
+    ht.key_lo = minmax[0];
+    ht.key_hi = minmax[1];
+  }
   const bool wide_payload = n_payload == 2 && ht.pay_dom[0] == 65536 && ht.pay_dom[1] == 65536;
   if (!wide_payload && range <= std::max<uint64_t>(64 * kept, 1u << 20) && range <= (1u << 26)) {
     ht.kind = HT_DIRECT;

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
     const TileHdr H = load_headers<kHost>(Q, P, i0, nmb, lane);
     TileState T;
     tile_init(P, i0, nmb, lane, T);
-    tile_first_step<kHost>(Q, P, H, T, nullptr, lane, status);
+    tile_dense_step<kHost>(Q, 0, P, H, T, nullptr, lane, status);
     uint32_t n = tile_compact(T, list, 0, 0, lane);
     n = list_steps<kHost>(Q, P, i0, list, n, nullptr, lane, status);
     for (uint32_t j0 = 0; j0 < n; j0 += 32) {

@@ -50,6 +50,7 @@ enum StatusBits : uint32_t { S_CORRUPT = 1u, S_INTERNAL = 2u, S_DUPKEY = 4u, S_T
 struct DevColumn {
   const uint8_t* blob;        // page images (device, or mapped pinned host)
   const uint64_t* page_off;   // [npages + 1] byte offset of each page (device)
+  const int2* zone;           // [npages] bounds {lo, hi} of each page's values (device): a zone map
   uint64_t nrows;
   uint32_t codec;
   uint32_t page_rows;
@@ -88,6 +89,11 @@ struct DevStep {
   uint16_t pad_;
   uint32_t smem_off;      // byte offset of the copy in the CTA's table region
   uint32_t mul0, mul1;    // gid multipliers of payload fields 0 and 1 (0 = unused)
+  // Values a row needs to pass (a superset: [zlo, zhi] empty when nothing
+  // passes; the full int32 range when the step cannot prune): the range of a
+  // predicate, the key range of a join table.  Mini blocks whose header
+  // bounds miss it are skipped by the first step.
+  int32_t zlo, zhi;
   // ST_KEY
   uint32_t key_mul;
   uint8_t pfx[kMaxPrefix];

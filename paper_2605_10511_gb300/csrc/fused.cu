@@ -219,8 +219,10 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
 }
 
 // One ticket: the rows [chunk*chunk_rows, +chunk_rows) of Q's fact table,
-// processed by one warp, cut at page boundaries into tiles.  Tile headers
-// are loaded two tiles ahead.
+// processed by one warp, cut at page boundaries into tiles.  A page whose
+// zone map misses the first step's value range is skipped whole; inside a
+// page, mini blocks whose headers miss it are skipped by the first step.
+// Tile headers are loaded two tiles ahead.
 template <bool kHost>
 __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long long* acc, const uint8_t* stab,
                                uint32_t* list, int lane, unsigned int* status) {
@@ -232,6 +234,11 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
     const uint32_t mb0 = uint32_t((pr0 - p * PR) / kMB);
     const uint32_t mb1 = uint32_t((pr1 - p * PR + kMB - 1) / kMB);
     const uint32_t ntiles = (mb1 - mb0 + TB - 1) / TB;
+    if (Q.nsteps != 0) {  // zone map: skip a page the first step's range misses
+      const DevStep& S0 = Q.steps[0];
+      const int2 z = __ldg(Q.cols[S0.col].zone + p);
+      if (S0.zlo > S0.zhi || z.y < S0.zlo || z.x > S0.zhi) continue;
+    }
     PageState P;
     page_begin<kHost>(Q, p, lane, P);
     auto nmb_of = [&](uint32_t jj) { return tmin<uint32_t>(TB, mb1 - (mb0 + jj * TB)); };
@@ -240,7 +247,9 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
     if (1 < ntiles) Hn = load_headers<kHost>(Q, P, mb0 + TB, nmb_of(1), lane);
     // the list collects the survivors of consecutive tiles (a segment of at
     // most 2^kRowBits rows of this page) before the later steps run on them
-    uint32_t n = 0, seg_mb = mb0;
+    // the list collects the survivors of consecutive tiles (a segment of at
+    // most 2^kRowBits rows of this page) before the later steps run on them
+    uint32_t n = 0, seg_mb = mb0, nd = 0;
     for (uint32_t j = 0; j < ntiles; ++j) {
       const uint32_t i0 = mb0 + j * TB;
       const uint32_t nmb = nmb_of(j);
@@ -248,13 +257,15 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
       if (j + 2 < ntiles) Hnn = load_headers<kHost>(Q, P, mb0 + (j + 2) * TB, nmb_of(j + 2), lane);
       TileState T;
       tile_init(P, i0, nmb, lane, T);
-      tile_first_step<kHost>(Q, P, H, T, stab, lane, status);
+      tile_dense_step<kHost>(Q, 0, P, H, T, stab, lane, status);
+      nd = 1;  // steps run densely (the first); the rest run over the list
       n = tile_compact(T, list, n, (i0 - seg_mb) * kMB, lane);
       const uint32_t next = i0 + TB;
       if (j + 1 == ntiles || n + kTileRows > kListCap || next + TB - seg_mb > kSegMbs) {
-        n = list_steps<kHost>(Q, P, seg_mb, list, n, stab, lane, status);
+        n = list_steps<kHost>(Q, P, seg_mb, list, n, stab, lane, status, nd);
         if (n) list_aggregate<kHost>(Q, P, seg_mb, list, n, lane, acc, status);
         n = 0;
+        nd = 0;
         seg_mb = next;
       }
       H = Hn;

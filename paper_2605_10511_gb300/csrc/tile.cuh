@@ -287,10 +287,45 @@ __device__ __forceinline__ void dense_probe(const DevStep& S, const uint8_t* sta
 
 // Dense step over one tile, specialised on the column's codec: a probe, a
 // group key or a predicate (RANGE / NOTRANGE / IN / FALSE).
+// Mini blocks of column c in the tile (bit t) whose values all lie outside
+// [zlo, zhi], from their headers alone: FOR/DICT values lie in
+// [base, base + 2^bw - 1]; a DELTA mini block's values lie within 127 steps
+// of its first value, each step in [min(0, dmin), max(0, dmin + 2^bw - 1)]
+// (used only when that bound stays inside int32, i.e. nothing wrapped).
+template <bool kDelta>
+__device__ __forceinline__ uint32_t pruned_mbs(const TileHdr& Hd, int c, int32_t zlo, int32_t zhi, int lane) {
+  bool out = false;
+  if (lane / TB == c) {
+    int64_t lo, hi;
+    if (kDelta) {
+      const int64_t first = int32_t(Hd.x), dmin = int32_t(Hd.y);
+      const uint32_t bw = tmin<uint32_t>(Hd.z & 0xffu, 32u);
+      const int64_t span = bw >= 32 ? int64_t(0xffffffffll) : (int64_t(1) << bw) - 1;
+      lo = first + 127 * tmin<int64_t>(0, dmin);
+      hi = first + 127 * tmax<int64_t>(0, dmin + span);
+      if (lo < INT32_MIN || hi > INT32_MAX) {
+        lo = INT32_MIN;
+        hi = INT32_MAX;
+      }
+    } else {
+      const uint32_t bw = tmin<uint32_t>(Hd.y & 0xffu, 32u);
+      lo = int32_t(Hd.x);
+      hi = lo + (bw >= 32 ? int64_t(0xffffffffll) : (int64_t(1) << bw) - 1);
+    }
+    out = zlo > zhi || hi < int64_t(zlo) || lo > int64_t(zhi);
+  }
+  return (__ballot_sync(kFull, out) >> (c * TB)) & ((1u << TB) - 1u);
+}
+
 template <bool kHost, bool kDelta>
 __device__ __forceinline__ void dense_step_t(const DevQuery& Q, const DevStep& S, const PageState& P,
                                              const TileHdr& Hd, TileState& T, const uint8_t* stab, int lane,
                                              unsigned int* status) {
+  // mini blocks that cannot hold a passing value are neither loaded nor decoded
+  const uint32_t pruned = pruned_mbs<kDelta>(Hd, S.col, S.zlo, S.zhi, lane);
+#pragma unroll
+  for (int t = 0; t < TB; ++t)
+    if ((pruned >> t) & 1u) T.alive &= ~(15u << (4 * t));
   uint32_t v[TB][4];
   uint32_t anym;
   decode_t<kHost, kDelta>(Q, S.col, P, Hd, T.alive, lane, v, anym, status);
@@ -361,13 +396,13 @@ static_assert(kTileRows <= (1u << kRowBits), "row index field too narrow");
 static_assert(kListCap >= kTileRows, "a list must hold one tile");
 static_assert(kSegMbs <= 32, "segment mini blocks must fit a 32-bit mask");
 
-// Dense first step of a tile (or none): live bits and group-id contributions.
+// Dense step s of a tile (or none): live bits and group-id contributions.
 // The step's kind, table and codec are resolved here, once per tile.
 template <bool kHost>
-__device__ __forceinline__ void tile_first_step(const DevQuery& Q, const PageState& P, const TileHdr& Hd,
+__device__ __forceinline__ void tile_dense_step(const DevQuery& Q, uint32_t s, const PageState& P, const TileHdr& Hd,
                                                 TileState& T, const uint8_t* stab, int lane, unsigned int* status) {
-  if (Q.nsteps == 0) return;
-  const DevStep& S = Q.steps[0];
+  if (s >= Q.nsteps) return;
+  const DevStep& S = Q.steps[s];
   if (S.kind == ST_PREFIX) tile_prefix<kHost>(Q, S, P, Hd, T, lane, status);
   else if (Q.cols[S.col].codec == C_DELTA) dense_step_t<kHost, true>(Q, S, P, Hd, T, stab, lane, status);
   else dense_step_t<kHost, false>(Q, S, P, Hd, T, stab, lane, status);
@@ -643,13 +678,13 @@ __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevS
   return out;
 }
 
-// Steps 1.. of the query over the warp's list; returns the list length.  Each
+// Steps first.. of the query over the warp's list; returns the list length.  Each
 // step is resolved to its specialised loop once, outside the loop.
 template <bool kHost>
 __device__ __forceinline__ uint32_t list_steps(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                                uint32_t* list, uint32_t n, const uint8_t* stab, int lane,
-                                               unsigned int* status) {
-  for (uint32_t s = 1; s < Q.nsteps && n != 0; ++s) {
+                                               unsigned int* status, uint32_t first = 1) {
+  for (uint32_t s = first; s < Q.nsteps && n != 0; ++s) {
     const DevStep& S = Q.steps[s];
     if (S.kind == ST_PREFIX || Q.cols[S.col].codec == C_DELTA) {
       n = list_step_generic<kHost>(Q, S, P, seg_mb, list, n, stab, lane, status);

@@ -154,13 +154,14 @@ def _star_query(rng, attrs):
 
 
 def star_join(rows=1 << 26, seed=2, page_rows=DEFAULT_PAGE_ROWS, clustered=True,
-              dim_rows=(2000, 30000, 200000)):
+              dim_rows=(2000, 30000, 200000), date_year=None):
     """Fact table with 4 uniform foreign keys and 2 measures, 4 dimensions.
 
     Filters three dimensions (10 %, 4 %, 8 %), joins all four and groups by
     (dim3.B3, date.year) computing SUM(int64 m1).  With ``clustered`` the
     fact rows are ordered by date key (a sorted load) and the date key is
     stored delta-coded; otherwise it is stored frame-of-reference coded.
+    ``date_year`` adds a filter keeping one year of the date dimension.
     """
     rng = _rng(seed)
     dims, attrs = _star_dimensions(rng, dim_rows, page_rows)
@@ -182,8 +183,13 @@ def star_join(rows=1 << 26, seed=2, page_rows=DEFAULT_PAGE_ROWS, clustered=True,
     }}
     tables = dict(dims)
     tables["fact"] = fact
-    return {"name": f"star_join_{rows}{'_clustered' if clustered else ''}",
-            "tables": tables, "fact": "fact", "query": _star_query(rng, attrs)}
+    query = _star_query(rng, attrs)
+    name = f"star_join_{rows}{'_clustered' if clustered else ''}"
+    if date_year is not None:
+        # one year of the date dimension (an SSB Q1/Q3-style date filter);
+        # the fact tables are the same as without it
+        query["joins"][3]["preds"] = [{"col": "year", "op": "eq", "args": [int(date_year)]}]
+    return {"name": name, "tables": tables, "fact": "fact", "query": query}
 
 
 # ---------------------------------------------------------------------------

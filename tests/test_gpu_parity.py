@@ -235,3 +235,14 @@ def test_budget_is_enforced():
         assert ex.value.status == -2  # DPF_ENOMEM
     finally:
         e.close()
+
+
+@pytest.mark.parametrize("clustered", [True, False])
+def test_star_with_date_filter_prunes_and_matches(eng, clustered):
+    """One year of the date dimension: on the date-clustered fact most mini
+    blocks of the date key are skipped from their headers; the unsorted fact
+    prunes nothing.  Both equal the oracle and each other."""
+    w = synth.star_join(rows=(1 << 21) + 333, page_rows=65536, clustered=clustered, date_year=1994)
+    got = eng.run(w)
+    assert_same(got, expect(w), ("date filter", clustered))
+    assert got.shape[0] >= 1 and int(got["count"].sum()) > 0

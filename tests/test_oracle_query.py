@@ -127,3 +127,13 @@ def test_config1_statistical_sanity(oracle_lib):
     assert abs(int(r["count"][0]) - mean) < 5 * sd
     avg = int(r["val"][0, 0]) / int(r["count"][0])
     assert abs(avg - 5.5 * 52950) < 0.05 * 5.5 * 52950
+
+
+@pytest.mark.parametrize("clustered", [True, False])
+def test_star_join_with_date_filter(oracle_lib, clustered):
+    """The one-year date filter: equal to the numpy evaluator, and the
+    year key of every record is the filtered year."""
+    w = synth.star_join(rows=60000, page_rows=4096, clustered=clustered, date_year=1995)
+    got = oracle_lib.run_query(w, from_encoded=True)
+    _records_equal(got, npeval.evaluate(w))
+    assert got.shape[0] > 0 and np.all(got["key"][:, 1] == 1995)
