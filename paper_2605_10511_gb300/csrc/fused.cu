@@ -222,7 +222,8 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
 // processed by one warp, cut at page boundaries into tiles.  A page whose
 // zone map misses the first step's value range is skipped whole; inside a
 // page, mini blocks whose headers miss it are skipped by the first step.
-// Tile headers are loaded one tile ahead.
+// Each tile loads its headers as it starts (the other resident warps hide
+// the latency).
 template <bool kHost>
 __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long long* acc, const uint8_t* stab,
                                uint32_t* list, int lane, unsigned int* status) {
@@ -242,7 +243,7 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
     PageState P;
     page_begin<kHost>(Q, p, lane, P);
     auto nmb_of = [&](uint32_t jj) { return tmin<uint32_t>(TB, mb1 - (mb0 + jj * TB)); };
-    TileHdr H = load_headers<kHost>(Q, P, mb0, nmb_of(0), lane);
+    TileHdr H;
     // the list collects the survivors of consecutive tiles (a segment of at
     // most 2^kRowBits rows of this page) before the later steps run on them
     // the list collects the survivors of consecutive tiles (a segment of at
@@ -251,8 +252,7 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
     for (uint32_t j = 0; j < ntiles; ++j) {
       const uint32_t i0 = mb0 + j * TB;
       const uint32_t nmb = nmb_of(j);
-      TileHdr Hn{0, 0, 0, 0};
-      if (j + 1 < ntiles) Hn = load_headers<kHost>(Q, P, mb0 + (j + 1) * TB, nmb_of(j + 1), lane);
+      H = load_headers<kHost>(Q, P, i0, nmb, lane);
       TileState T;
       tile_init(P, i0, nmb, lane, T);
       tile_dense_step<kHost>(Q, 0, P, H, T, stab, lane, status);
@@ -266,7 +266,6 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
         nd = 0;
         seg_mb = next;
       }
-      H = Hn;
     }
   }
 }
