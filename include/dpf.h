@@ -247,7 +247,10 @@ typedef struct dpf_tuning {
                             multiple of 512, at most 2^24; default 2048        */
   uint32_t threads;      /* threads per CTA: 128 or 256                          */
   int32_t ht_placement;  /* enum dpf_ht_place                                     */
-  uint32_t ctas_per_sm;  /* persistent CTAs per SM                                */
+  uint32_t ctas_per_sm;  /* persistent CTAs per SM: 0 = as many as fit of the
+                            kernel build for 3 resident 256-thread CTAs
+                            (80 registers); >= 4 = the build for 4 (64
+                            registers) when four fit, else as for 0          */
 } dpf_tuning;
 
 /* Result record: keys are dictionary values (0 when unused); count = rows
@@ -287,7 +290,7 @@ dpf_status dpf_release(dpf_ctx* ctx, dpf_prep_id prep);
  * where the join tables live (shared memory vs device memory, Sec. 4.3) are
  * the launch configuration.  dpf_autotune prepares the n plans under each
  * configuration of a fixed grid (chunk_rows 1K..256K, threads 128/256,
- * tables AUTO/GLOBAL), times `reps` launches of each on `stream` with CUDA
+ * tables AUTO/GLOBAL, kernel build for 3 or 4 CTAs per SM), times `reps` launches of each on `stream` with CUDA
  * events after one warm-up launch (reps 0 = 3), and keeps the fastest in the
  * context's tuning cache under the plans' signature (the rows and encodings
  * of the columns they read, their steps, tables, groups and aggregates; not

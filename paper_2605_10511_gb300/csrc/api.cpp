@@ -760,12 +760,13 @@ uint64_t plans_signature(dpf_ctx* c, const dpf_plan* plans, int32_t n) {
 // Fields left 0 take the tuning dpf_autotune stored for these plans, else the
 // defaults.
 void fill_tuning_defaults(dpf_ctx* c, dpf_tuning& t, const dpf_plan* plans, int32_t n) {
-  if (t.chunk_rows == 0 || t.threads == 0 || t.ht_placement == 0) {
+  if (t.chunk_rows == 0 || t.threads == 0 || t.ht_placement == 0 || t.ctas_per_sm == 0) {
     auto it = c->tune_cache.find(plans_signature(c, plans, n));
     if (it != c->tune_cache.end()) {
       if (t.chunk_rows == 0) t.chunk_rows = it->second.chunk_rows;
       if (t.threads == 0) t.threads = it->second.threads;
       if (t.ht_placement == 0) t.ht_placement = it->second.ht_placement;
+      if (t.ctas_per_sm == 0) t.ctas_per_sm = it->second.ctas_per_sm;
     }
   }
   if (t.chunk_rows == 0) t.chunk_rows = kDefaultChunkRows;
@@ -867,12 +868,21 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
     release_prep(c, p.get());
     return fail(DPF_ECUDA, "prepare: %s", cudaGetErrorString(e));
   }
-  int per_sm = fused_blocks_per_sm(int(t.threads), acc_slots, max_tables, host);
+  // ctas_per_sm >= 4 selects the kernel build for four resident CTAs per SM
+  // (64 registers) when four fit; otherwise the build for three (80)
+  int min_blocks = kFusedMinBlocksLo;
+  int per_sm = 0;
+  if (t.ctas_per_sm >= uint32_t(kFusedMinBlocksHi)) {
+    per_sm = fused_blocks_per_sm(int(t.threads), acc_slots, max_tables, host, kFusedMinBlocksHi);
+    if (per_sm >= kFusedMinBlocksHi * 256 / int(t.threads)) min_blocks = kFusedMinBlocksHi;
+  }
+  if (min_blocks == kFusedMinBlocksLo) per_sm = fused_blocks_per_sm(int(t.threads), acc_slots, max_tables, host, kFusedMinBlocksLo);
   if (per_sm < 1) {
     release_prep(c, p.get());
     return fail(DPF_EINVAL, "fused kernel does not fit on an SM with %u threads and %zu table bytes", t.threads, max_tables);
   }
-  if (t.ctas_per_sm == 0 || int(t.ctas_per_sm) > per_sm) t.ctas_per_sm = uint32_t(per_sm);
+  if (t.ctas_per_sm == 0 || int(t.ctas_per_sm) > per_sm || min_blocks == kFusedMinBlocksHi) t.ctas_per_sm = uint32_t(per_sm);
+  p->L.min_blocks = min_blocks;
   p->tuning = t;
   p->L.queries = p->dq;
   p->L.qbegin = p->dqbegin;
@@ -1340,13 +1350,16 @@ dpf_status dpf_autotune(dpf_ctx* c, const dpf_plan* plans, int32_t n, void* stre
   dpf_tuning top{};
   float top_ms = -1.f;
   dpf_status last = DPF_OK;
+  static const uint32_t kCtas[] = {0, uint32_t(kFusedMinBlocksHi)};
   for (uint32_t cr : kChunk)
     for (uint32_t th : kThreads)
-      for (int32_t pl : kPlace) {
+      for (int32_t pl : kPlace)
+        for (uint32_t ct : kCtas) {
         dpf_tuning t{};
         t.chunk_rows = cr;
         t.threads = th;
         t.ht_placement = pl;
+        t.ctas_per_sm = ct;
         Prep* p = nullptr;
         dpf_status st = prepare(c, plans, n, &t, &p);
         if (st) {  // e.g. the tables do not fit this configuration
@@ -1380,7 +1393,7 @@ dpf_status dpf_autotune(dpf_ctx* c, const dpf_plan* plans, int32_t n, void* stre
         if (top_ms < 0.f || ms < top_ms) {
           top_ms = ms;
           top = used;
-          top.ctas_per_sm = 0;  // recomputed per prepare
+          top.ctas_per_sm = ct;  // 0: the 3-CTA build at its occupancy; 4: the 4-CTA build
         }
       }
   cudaEventDestroy(e0);
@@ -1430,7 +1443,7 @@ dpf_status dpf_capture_graph(dpf_ctx* c, dpf_prep_id id, void* stream) {
   if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
   if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
   // set the smem attribute before capture (not a stream operation)
-  fused_blocks_per_sm(p->L.threads, p->L.acc_slots, p->L.smem_tables, p->L.host_data);
+  fused_blocks_per_sm(p->L.threads, p->L.acc_slots, p->L.smem_tables, p->L.host_data, p->L.min_blocks);
   CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = launch_prep(p, s);
   cudaGraph_t graph = nullptr;

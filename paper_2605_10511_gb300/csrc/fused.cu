@@ -295,8 +295,8 @@ __device__ void load_smem_tables(const DevQuery& Q, uint8_t* stab) {
   }
 }
 
-template <bool kHost>
-__global__ void __launch_bounds__(256, kFusedMinBlocks) fused_kernel(const DevQuery* __restrict__ queries,
+template <bool kHost, int kMinBlocks>
+__global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* __restrict__ queries,
                                                        const uint64_t* __restrict__ qbegin, int nq,
                                                        uint64_t total, Sched* sched, uint32_t acc_slots,
                                                      uint32_t tables_bytes) {
@@ -377,34 +377,41 @@ size_t fused_dynamic_smem(uint32_t acc_slots, size_t smem_tables, int threads) {
          size_t(threads / 32) * kListCap * sizeof(uint32_t);
 }
 
-int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, bool host_data) {
-  const size_t smem = fused_dynamic_smem(acc_slots, smem_tables, threads);
+namespace {
+template <bool kHost, int kMinBlocks>
+int occupancy_of(int threads, size_t smem) {
   int n = 0;
-  if (host_data) {
-    cudaFuncSetAttribute(fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_kernel<true>, threads, smem);
-  } else {
-    cudaFuncSetAttribute(fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_kernel<false>, threads, smem);
-  }
+  cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_kernel<kHost, kMinBlocks>, threads, smem);
   return n;
+}
+
+template <bool kHost, int kMinBlocks>
+cudaError_t launch_as(const FusedLaunch& L, size_t smem, uint32_t tb, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(smem));
+  if (e != cudaSuccess) return e;
+  fused_kernel<kHost, kMinBlocks><<<L.grid, L.threads, smem, s>>>(L.queries, L.qbegin, L.nq, L.total_chunks,
+                                                                  L.sched, L.acc_slots, tb);
+  return cudaGetLastError();
+}
+}  // namespace
+
+int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, bool host_data, int min_blocks) {
+  const size_t smem = fused_dynamic_smem(acc_slots, smem_tables, threads);
+  const bool hi = min_blocks == kFusedMinBlocksHi;
+  if (host_data)
+    return hi ? occupancy_of<true, kFusedMinBlocksHi>(threads, smem) : occupancy_of<true, kFusedMinBlocksLo>(threads, smem);
+  return hi ? occupancy_of<false, kFusedMinBlocksHi>(threads, smem) : occupancy_of<false, kFusedMinBlocksLo>(threads, smem);
 }
 
 cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s) {
   const size_t smem = fused_dynamic_smem(L.acc_slots, L.smem_tables, L.threads);
   const uint32_t tb = uint32_t((L.smem_tables + 15) & ~size_t(15));
-  if (L.host_data) {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    fused_kernel<true><<<L.grid, L.threads, smem, s>>>(L.queries, L.qbegin, L.nq, L.total_chunks, L.sched,
-                                                       L.acc_slots, tb);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (e != cudaSuccess) return e;
-    fused_kernel<false><<<L.grid, L.threads, smem, s>>>(L.queries, L.qbegin, L.nq, L.total_chunks, L.sched,
-                                                        L.acc_slots, tb);
-  }
-  return cudaGetLastError();
+  const bool hi = L.min_blocks == kFusedMinBlocksHi;
+  if (L.host_data)
+    return hi ? launch_as<true, kFusedMinBlocksHi>(L, smem, tb, s) : launch_as<true, kFusedMinBlocksLo>(L, smem, tb, s);
+  return hi ? launch_as<false, kFusedMinBlocksHi>(L, smem, tb, s) : launch_as<false, kFusedMinBlocksLo>(L, smem, tb, s);
 }
 
 }  // namespace dpf

@@ -11,10 +11,12 @@ namespace dpf {
 // Shared-memory accumulator capacity of one CTA (int64 slots).
 constexpr uint32_t kSmemAccSlots = 4096;
 constexpr uint32_t kMbPerWarpTile = 4;
-// Resident 256-thread CTAs per SM the fused kernel is compiled for (register
-// budget 65536 / (256 x this)): occupancy, more than issue, bounds the kernel,
-// and 3 (24 warps, 80 registers) measured fastest.
-constexpr int kFusedMinBlocks = 3;
+// The fused kernel is compiled twice, for 3 and for 4 resident 256-thread CTAs
+// per SM (register budgets of 80 and 64 per thread): occupancy, more than
+// issue, bounds it.  The 4-CTA build spills a little and wins when four CTAs'
+// shared memory fits; the launch configuration (ctas_per_sm) picks one.
+constexpr int kFusedMinBlocksLo = 3;
+constexpr int kFusedMinBlocksHi = 4;
 // Rows of one scheduling ticket (one warp's unit of work) unless tuned.
 constexpr uint32_t kDefaultChunkRows = 4096;
 
@@ -30,11 +32,12 @@ struct FusedLaunch {
   uint32_t acc_slots;   // int64 shared accumulators per CTA (max over the batch)
   size_t smem_tables;   // bytes of the CTA's join-table region
   bool host_data;       // some column lives in mapped pinned host memory
+  int min_blocks;       // kFusedMinBlocksLo or kFusedMinBlocksHi: which build runs
 };
 cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s);
 // Occupancy of the fused kernel for (threads, dynamic smem); also sets the
 // kernel's dynamic shared-memory limit.
-int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, bool host_data);
+int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, bool host_data, int min_blocks);
 size_t fused_dynamic_smem(uint32_t acc_slots, size_t smem_tables, int threads);
 
 // Hash build (Kernel #1 of Sec. 3.1).  `q` describes the dimension scan:

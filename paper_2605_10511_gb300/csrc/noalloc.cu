@@ -128,7 +128,8 @@ extern "C" dpf_status dpf_execute_noalloc(dpf_ctx* ctx, const dpf_plan* plan, vo
   L.smem_tables = smem_tables;
   L.acc_slots = Q.use_smem_acc ? uint32_t(slots) : 0u;
   L.host_data = host;
-  const int per_sm = fused_blocks_per_sm(L.threads, L.acc_slots, smem_tables, host);
+  L.min_blocks = kFusedMinBlocksLo;
+  const int per_sm = fused_blocks_per_sm(L.threads, L.acc_slots, smem_tables, host, L.min_blocks);
   if (per_sm < 1) return fail(DPF_EINVAL, "dpf_execute_noalloc: fused kernel does not fit on an SM");
   L.grid = int(std::max<uint64_t>(1, std::min<uint64_t>(uint64_t(num_sms) * per_sm, Q.nchunks)));
   e = launch_fused(L, s);

@@ -246,3 +246,10 @@ def test_star_with_date_filter_prunes_and_matches(eng, clustered):
     got = eng.run(w)
     assert_same(got, expect(w), ("date filter", clustered))
     assert got.shape[0] >= 1 and int(got["count"].sum()) > 0
+
+
+@pytest.mark.parametrize("name", ["scan", "star", "strings"])
+def test_four_cta_build_matches(eng, shapes, name):
+    """The kernel build for four resident CTAs per SM (ctas_per_sm = 4)."""
+    w = shapes[name]
+    assert_same(eng.run(w, tuning=dpf.Tuning(0, 256, 0, 4)), expect(w), (name, "4 CTAs"))
