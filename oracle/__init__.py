@@ -28,9 +28,10 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CODECS = {"for": 1, "delta": 2, "dict": 3, "str": 4}
+CODECS = {"for": 1, "delta": 2, "dict": 3, "str": 4, "fsst": 5}
+STRING_CODECS = ("str", "fsst")
 PRED_OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7,
-            "prefix": 8}
+            "prefix": 8, "contains": 9}
 AGG_OPS = {"count": 0, "sum": 1, "sum_mul": 2, "sum_sub": 3}
 
 RECORD_DTYPE = np.dtype([("key", np.int32, (2,)), ("count", np.int64), ("val", np.int64, (4,))])
@@ -97,6 +98,13 @@ def lib():
             L.orc_decode_str.restype = C.c_int64
             L.orc_decode_str.argtypes = [P, P, C.c_uint64, C.c_uint64, C.c_uint32, P, P,
                                          C.c_uint64]
+            L.orc_fsst_build.restype = C.c_int64
+            L.orc_fsst_build.argtypes = [P, P, C.c_uint64, P]
+            L.orc_encode_fsst.restype = C.c_int64
+            L.orc_encode_fsst.argtypes = [P, P, C.c_uint64, P, C.c_uint64, C.c_uint32, P, C.c_uint64, P, P]
+            L.orc_decode_fsst.restype = C.c_int64
+            L.orc_decode_fsst.argtypes = [P, P, C.c_uint64, C.c_uint64, C.c_uint32, P, C.c_uint64, P, P,
+                                          C.c_uint64]
             L.orc_query.restype = C.c_int64
             L.orc_query.argtypes = [C.POINTER(_Table), C.c_int32, C.POINTER(_Pred), C.c_int32,
                                     C.POINTER(_Join), C.c_int32, C.POINTER(_Key), C.c_int32,
@@ -117,7 +125,8 @@ class use_library:
         self._saved = lib()
         L = C.CDLL(self.path)
         for name in ("orc_encode_int", "orc_decode_int", "orc_decode_int_row",
-                     "orc_encode_str", "orc_decode_str", "orc_query"):
+                     "orc_encode_str", "orc_decode_str", "orc_fsst_build", "orc_encode_fsst",
+                     "orc_decode_fsst", "orc_query"):
             f, g = getattr(L, name), getattr(self._saved, name)
             f.restype, f.argtypes = g.restype, g.argtypes
         _lib = L
@@ -155,6 +164,27 @@ def encode_column(col, page_rows):
     """
     L = lib()
     codec = col["codec"]
+    if codec == "fsst":
+        offsets = np.ascontiguousarray(col["offsets"], dtype=np.uint64)
+        data = np.ascontiguousarray(col["bytes"], dtype=np.uint8)
+        n = offsets.size - 1
+        table = col.get("table")
+        if table is None:
+            table = np.zeros(3 * 255, np.int32)
+            nsym = _check(L.orc_fsst_build(_ptr(data) or offsets.ctypes.data, _ptr(offsets), n,
+                                           _ptr(table)), "fsst_build")
+            table = table[: 3 * nsym].copy()
+        table = np.ascontiguousarray(table, np.int32)
+        npages = (n + page_rows - 1) // page_rows
+        page_off = np.zeros(npages + 1, np.uint64)
+        row_prefix = np.zeros(npages, np.uint64)
+        args = (_ptr(data) or offsets.ctypes.data, _ptr(offsets), n, _ptr(table) or offsets.ctypes.data,
+                table.size, page_rows)
+        size = _check(L.orc_encode_fsst(*args, None, 0, _ptr(page_off), _ptr(row_prefix)), "encode_fsst")
+        blob = np.zeros(size, np.uint8)
+        _check(L.orc_encode_fsst(*args, _ptr(blob), size, _ptr(page_off), _ptr(row_prefix)), "encode_fsst")
+        return {"codec": codec, "rows": n, "page_rows": page_rows, "blob": blob,
+                "page_off": page_off, "row_prefix": row_prefix, "dict": table}
     if codec == "str":
         offsets = np.ascontiguousarray(col["offsets"], dtype=np.uint64)
         data = np.ascontiguousarray(col["bytes"], dtype=np.uint8)
@@ -193,6 +223,15 @@ def decode_column(enc):
     """Decode a whole encoded column: int32 values, or (bytes, offsets)."""
     L = lib()
     n, npages = enc["rows"], enc["page_off"].size - 1
+    if enc["codec"] == "fsst":
+        offsets = np.zeros(n + 1, np.uint64)
+        table = np.ascontiguousarray(enc["dict"], np.int32)
+        cap = 8 * max(enc["blob"].size, 1)  # a code expands to at most 8 bytes
+        data = np.zeros(cap, np.uint8)
+        _check(L.orc_decode_fsst(_ptr(enc["blob"]), _ptr(enc["page_off"]), npages, n, enc["page_rows"],
+                                 _ptr(table) or offsets.ctypes.data, table.size, _ptr(offsets), _ptr(data),
+                                 data.size), "decode_fsst")
+        return data[: int(offsets[-1])].copy(), offsets
     if enc["codec"] == "str":
         # byte count = blob bytes is an upper bound on the string bytes
         offsets = np.zeros(n + 1, np.uint64)
@@ -229,7 +268,7 @@ def _make_pred(pred, names):
     p = _Pred()
     p.col = names.index(pred["col"])
     p.op = PRED_OPS[pred["op"]]
-    if pred["op"] == "prefix":
+    if pred["op"] in ("prefix", "contains"):
         pfx = bytes(pred["args"][0])
         buf = C.create_string_buffer(pfx, max(len(pfx), 1))
         p.pfx = C.cast(buf, C.c_void_p)
@@ -279,9 +318,9 @@ def decoded_tables(workload, from_encoded=True):
             if from_encoded:
                 enc = encode_column(c, t["page_rows"])
                 d = decode_column(enc)
-                cols[cname] = d if c["codec"] == "str" else d
+                cols[cname] = d
             else:
-                cols[cname] = (c["bytes"], c["offsets"]) if c["codec"] == "str" else c["values"]
+                cols[cname] = (c["bytes"], c["offsets"]) if c["codec"] in STRING_CODECS else c["values"]
         out[tname] = {"rows": t["rows"], "cols": cols}
     return out
 

@@ -38,7 +38,7 @@ namespace {
 constexpr uint32_t kMiniBlock = 128;           // values per mini block
 constexpr uint32_t kPageHeaderBytes = 16;      // magic|codec, nrows, payload_off, extra_off
 constexpr uint32_t kMagic = 0x00465044u;       // 'D' 'P' 'F' in the low three bytes
-enum Codec : uint32_t { FOR = 1, DELTA = 2, DICT = 3, STR = 4 };
+enum Codec : uint32_t { FOR = 1, DELTA = 2, DICT = 3, STR = 4, FSST = 5 };
 
 enum Status : int64_t {
   OK = 0,
@@ -320,9 +320,9 @@ int64_t orc_decode_int_row(uint32_t codec, const uint8_t* blob, const uint64_t* 
 // region, and the raw bytes follow.  offsets[0..n] are the caller's byte
 // offsets into bytes (offsets[r+1] - offsets[r] = length of row r).
 // ---------------------------------------------------------------------------
-int64_t orc_encode_str(const uint8_t* bytes, const uint64_t* offsets, uint64_t n,
-                       uint32_t page_rows, uint8_t* out, uint64_t cap, uint64_t* page_off,
-                       uint64_t* row_prefix) {
+static int64_t encode_str_pages(uint32_t codec, const uint8_t* bytes, const uint64_t* offsets, uint64_t n,
+                                uint32_t page_rows, uint8_t* out, uint64_t cap, uint64_t* page_off,
+                                uint64_t* row_prefix) {
   if (n == 0 || page_rows == 0 || page_rows % kMiniBlock != 0 || page_rows > (1u << 20))
     return EINVAL;
   const uint64_t npages = (n + page_rows - 1) / page_rows;
@@ -360,7 +360,7 @@ int64_t orc_encode_str(const uint8_t* bytes, const uint64_t* offsets, uint64_t n
       if (off + page_bytes > cap) return ETRUNC;
       uint8_t* pg = out + off;
       std::memset(pg, 0, page_bytes);
-      const uint32_t hdr[4] = {kMagic | (uint32_t(STR) << 24), rows, payload_off, extra_off};
+      const uint32_t hdr[4] = {kMagic | (codec << 24), rows, payload_off, extra_off};
       std::memcpy(pg, hdr, sizeof hdr);
       uint32_t* pay = reinterpret_cast<uint32_t*>(pg + payload_off);
       uint32_t woff = 0;
@@ -388,17 +388,24 @@ int64_t orc_encode_str(const uint8_t* bytes, const uint64_t* offsets, uint64_t n
   return int64_t(off);
 }
 
-// Decodes a string column back into byte offsets (n+1 entries, starting at
-// 0) and the concatenated bytes (capacity bytes_cap).
-int64_t orc_decode_str(const uint8_t* blob, const uint64_t* page_off, uint64_t npages, uint64_t n,
-                       uint32_t page_rows, uint64_t* offsets, uint8_t* bytes, uint64_t bytes_cap) {
+int64_t orc_encode_str(const uint8_t* bytes, const uint64_t* offsets, uint64_t n,
+                       uint32_t page_rows, uint8_t* out, uint64_t cap, uint64_t* page_off,
+                       uint64_t* row_prefix) {
+  return encode_str_pages(STR, bytes, offsets, n, page_rows, out, cap, page_off, row_prefix);
+}
+
+// Decodes the string pages of a column (codec STR or FSST) back into byte
+// offsets (n+1 entries, starting at 0) and the concatenated stored bytes.
+static int64_t decode_str_pages(uint32_t codec, const uint8_t* blob, const uint64_t* page_off, uint64_t npages,
+                                uint64_t n, uint32_t page_rows, uint64_t* offsets, uint8_t* bytes,
+                                uint64_t bytes_cap) {
   uint64_t r = 0, pos = 0;
   offsets[0] = 0;
   for (uint64_t p = 0; p < npages; ++p) {
     const uint8_t* pg = blob + page_off[p];
     uint32_t hdr[4];
     std::memcpy(hdr, pg, sizeof hdr);
-    if (hdr[0] != (kMagic | (uint32_t(STR) << 24))) return ECORRUPT;
+    if (hdr[0] != (kMagic | (codec << 24))) return ECORRUPT;
     const uint32_t rows = hdr[1];
     if (rows == 0 || rows > page_rows || r + rows > n) return ECORRUPT;
     const uint32_t nmb = (rows + kMiniBlock - 1) / kMiniBlock;
@@ -429,11 +436,202 @@ int64_t orc_decode_str(const uint8_t* blob, const uint64_t* page_off, uint64_t n
   return r == n ? OK : ECORRUPT;
 }
 
+int64_t orc_decode_str(const uint8_t* blob, const uint64_t* page_off, uint64_t npages, uint64_t n,
+                       uint32_t page_rows, uint64_t* offsets, uint8_t* bytes, uint64_t bytes_cap) {
+  return decode_str_pages(STR, blob, page_off, npages, n, page_rows, offsets, bytes, bytes_cap);
+}
+
+// ---------------------------------------------------------------------------
+// FSST strings: the paper's string codec (Sec. 3.4.2, Sec. 4.1), written from
+// the published method of Boncz, Neumann and Leis (FSST, VLDB 2020).  A
+// symbol table holds up to 255 symbols of 1..8 bytes; an encoded string is a
+// sequence of codes, code c < nsym standing for symbol c and code 255
+// (escape) for the byte that follows it.  The table is kept with the column
+// as nsym int32 triples {bytes 0..3, bytes 4..7 (little endian), length}.
+// Pages: the STR page layout (codec FSST) over the encoded strings, whose
+// lengths are the encoded lengths.
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+constexpr uint32_t kFsstEscape = 255;
+constexpr uint32_t kFsstMaxSymbols = 255;
+
+// A symbol or an escaped byte: 1..8 bytes.
+struct Tok {
+  uint8_t len = 0;
+  uint8_t b[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  bool operator<(const Tok& o) const {
+    const int c = std::memcmp(b, o.b, std::min(len, o.len));
+    return c != 0 ? c < 0 : len < o.len;
+  }
+};
+
+static Tok make_tok(const uint8_t* p, uint32_t len) {
+  Tok t;
+  t.len = uint8_t(len);
+  std::memcpy(t.b, p, len);
+  return t;
+}
+
+struct FsstSymbols {
+  std::vector<Tok> sym;          // code -> bytes
+  std::map<Tok, int> code;       // bytes -> code
+};
+
+static bool fsst_from_triples(const int32_t* t, uint64_t nt, FsstSymbols* out) {
+  if (nt % 3 != 0 || nt / 3 > kFsstMaxSymbols) return false;
+  out->sym.clear();
+  out->code.clear();
+  for (uint64_t i = 0; i < nt / 3; ++i) {
+    const uint32_t len = uint32_t(t[3 * i + 2]);
+    if (len < 1 || len > 8) return false;
+    uint8_t b[8];
+    std::memcpy(b, &t[3 * i], 4);
+    std::memcpy(b + 4, &t[3 * i + 1], 4);
+    const Tok s = make_tok(b, len);
+    out->code.emplace(s, int(i));
+    out->sym.push_back(s);
+  }
+  return true;
+}
+
+// Parses one string greedily with the table: at each position the longest
+// symbol that matches, else an escaped byte.  Calls emit(token, code or -1).
+template <class F>
+static void fsst_parse(const FsstSymbols& T, const uint8_t* s, uint64_t len, F&& emit) {
+  uint64_t i = 0;
+  while (i < len) {
+    int found = -1;
+    uint32_t flen = 0;
+    for (uint32_t L = uint32_t(std::min<uint64_t>(8, len - i)); L >= 1 && found < 0; --L) {
+      auto it = T.code.find(make_tok(s + i, L));
+      if (it != T.code.end()) {
+        found = it->second;
+        flen = L;
+      }
+    }
+    if (found >= 0) {
+      emit(make_tok(s + i, flen), found);
+      i += flen;
+    } else {
+      emit(make_tok(s + i, 1), -1);
+      i += 1;
+    }
+  }
+}
+
+extern "C" {
+
+// Builds a symbol table from (a sample of) the strings, as the published
+// method does: over a few generations, parse the sample with the current
+// table, count how often each token (symbol or escaped byte) and each pair of
+// consecutive tokens (when together at most 8 bytes) occurs, and keep the 255
+// candidates of largest gain = count x length (ties: shorter, then smaller
+// bytes).  Writes nsym triples to table (capacity 3 * 255); returns nsym.
+int64_t orc_fsst_build(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, int32_t* table) {
+  FsstSymbols T;
+  const uint64_t sample = std::min<uint64_t>(n, 4096);
+  for (int gen = 0; gen < 5; ++gen) {
+    std::map<Tok, uint64_t> count;
+    for (uint64_t r = 0; r < sample; ++r) {
+      Tok prev;
+      bool have_prev = false;
+      fsst_parse(T, bytes + offsets[r], offsets[r + 1] - offsets[r], [&](const Tok& tok, int) {
+        count[tok] += 1;
+        if (have_prev && prev.len + tok.len <= 8) {
+          Tok pair = prev;
+          std::memcpy(pair.b + prev.len, tok.b, tok.len);
+          pair.len = uint8_t(prev.len + tok.len);
+          count[pair] += 1;
+        }
+        prev = tok;
+        have_prev = true;
+      });
+    }
+    std::vector<std::pair<Tok, uint64_t>> cand(count.begin(), count.end());
+    std::sort(cand.begin(), cand.end(), [](const std::pair<Tok, uint64_t>& a, const std::pair<Tok, uint64_t>& b) {
+      const uint64_t ga = a.second * a.first.len, gb = b.second * b.first.len;
+      if (ga != gb) return ga > gb;
+      if (a.first.len != b.first.len) return a.first.len < b.first.len;
+      return a.first < b.first;
+    });
+    FsstSymbols next;
+    for (size_t i = 0; i < cand.size() && next.sym.size() < kFsstMaxSymbols; ++i) {
+      next.code.emplace(cand[i].first, int(next.sym.size()));
+      next.sym.push_back(cand[i].first);
+    }
+    T = std::move(next);
+  }
+  for (size_t i = 0; i < T.sym.size(); ++i) {
+    std::memcpy(&table[3 * i], T.sym[i].b, 4);
+    std::memcpy(&table[3 * i + 1], T.sym[i].b + 4, 4);
+    table[3 * i + 2] = int32_t(T.sym[i].len);
+  }
+  return int64_t(T.sym.size());
+}
+
+// Encodes the strings with the table and writes FSST pages (sizes as for
+// orc_encode_str; out == NULL: sizes only).
+int64_t orc_encode_fsst(const uint8_t* bytes, const uint64_t* offsets, uint64_t n, const int32_t* table,
+                        uint64_t ntab, uint32_t page_rows, uint8_t* out, uint64_t cap, uint64_t* page_off,
+                        uint64_t* row_prefix) {
+  FsstSymbols T;
+  if (!fsst_from_triples(table, ntab, &T)) return EINVAL;
+  std::vector<uint8_t> enc;
+  std::vector<uint64_t> eoff(n + 1, 0);
+  for (uint64_t r = 0; r < n; ++r) {
+    fsst_parse(T, bytes + offsets[r], offsets[r + 1] - offsets[r], [&](const Tok& tok, int code) {
+      if (code >= 0) {
+        enc.push_back(uint8_t(code));
+      } else {
+        enc.push_back(uint8_t(kFsstEscape));
+        enc.push_back(tok.b[0]);
+      }
+    });
+    eoff[r + 1] = enc.size();
+  }
+  if (enc.empty()) enc.push_back(0);  // a valid pointer; no string reads it
+  return encode_str_pages(FSST, enc.data(), eoff.data(), n, page_rows, out, cap, page_off, row_prefix);
+}
+
+// Decodes FSST pages back into the strings' byte offsets (n+1) and bytes.
+int64_t orc_decode_fsst(const uint8_t* blob, const uint64_t* page_off, uint64_t npages, uint64_t n,
+                        uint32_t page_rows, const int32_t* table, uint64_t ntab, uint64_t* offsets,
+                        uint8_t* bytes, uint64_t bytes_cap) {
+  FsstSymbols T;
+  if (!fsst_from_triples(table, ntab, &T)) return EINVAL;
+  const uint64_t stored_cap = page_off[npages];
+  std::vector<uint64_t> eoff(n + 1);
+  std::vector<uint8_t> enc(std::max<uint64_t>(stored_cap, 1));
+  const int64_t st = decode_str_pages(FSST, blob, page_off, npages, n, page_rows, eoff.data(), enc.data(),
+                                      enc.size());
+  if (st < 0) return st;
+  uint64_t pos = 0;
+  offsets[0] = 0;
+  for (uint64_t r = 0; r < n; ++r) {
+    for (uint64_t i = eoff[r]; i < eoff[r + 1];) {
+      const uint32_t c = enc[i++];
+      if (c == kFsstEscape) {
+        if (i >= eoff[r + 1] || pos + 1 > bytes_cap) return ECORRUPT;
+        bytes[pos++] = enc[i++];
+      } else {
+        if (c >= T.sym.size()) return ECORRUPT;
+        const Tok& sy = T.sym[c];
+        if (pos + sy.len > bytes_cap) return ECORRUPT;
+        std::memcpy(bytes + pos, sy.b, sy.len);
+        pos += sy.len;
+      }
+    }
+    offsets[r + 1] = pos;
+  }
+  return OK;
+}
+
 // ---------------------------------------------------------------------------
 // Query evaluation over decoded columns.
 // ---------------------------------------------------------------------------
 
-enum PredOp : int32_t { LT = 0, LE, GT, GE, EQ, NE, BETWEEN, IN, PREFIX };
+enum PredOp : int32_t { LT = 0, LE, GT, GE, EQ, NE, BETWEEN, IN, PREFIX, CONTAINS };
 enum AggOp : int32_t { COUNT = 0, SUM, SUM_MUL, SUM_SUB };
 
 struct OrcColumn {          // one decoded column
@@ -486,6 +684,13 @@ static bool eval_pred(const OrcTable& t, const OrcPred& p, uint64_t r) {
     const uint64_t len = c.offsets[r + 1] - c.offsets[r];
     if (len < uint64_t(p.pfx_len)) return false;
     return std::memcmp(c.bytes + c.offsets[r], p.pfx, size_t(p.pfx_len)) == 0;
+  }
+  if (p.op == CONTAINS) {  // LIKE '%pattern%': the pattern occurs at some position
+    const uint64_t len = c.offsets[r + 1] - c.offsets[r], m = uint64_t(p.pfx_len);
+    if (m == 0) return true;
+    for (uint64_t i = 0; i + m <= len; ++i)
+      if (std::memcmp(c.bytes + c.offsets[r] + i, p.pfx, m) == 0) return true;
+    return false;
   }
   const int64_t x = c.v[r];
   switch (p.op) {

@@ -214,28 +214,66 @@ def random_strings(rng, rows, min_len=10, max_len=44):
     return np.ascontiguousarray(data), offsets
 
 
+def text_strings(rng, rows, min_len=10, max_len=44, n_words=512):
+    """Strings of words: a stream of words from a vocabulary of n_words words
+    of 3..9 letters (Zipf(1.1) word frequencies), each followed by a space,
+    cut into consecutive pieces of lengths drawn uniformly from
+    min_len..max_len.  Text-like, so a symbol-table codec (FSST) compresses
+    it, unlike uniform random bytes."""
+    letters = ALPHABET[ALPHABET != ord(" ")]
+    wl = rng.integers(3, 10, n_words)
+    W = np.full((n_words, 10), ord(" "), dtype=np.uint8)
+    for i, k in enumerate(wl):
+        W[i, :k] = letters[rng.integers(0, letters.size, int(k))]
+    wlen = wl + 1  # the word and its space
+    w = np.arange(1, n_words + 1, dtype=np.float64) ** (-1.1)
+    cdf = np.cumsum(w) / w.sum()
+    lengths = rng.integers(min_len, max_len + 1, rows, dtype=np.int64)
+    total = int(lengths.sum())
+    need = int(total / (wlen.mean() * 0.9)) + 16
+    while True:
+        pick = np.minimum(np.searchsorted(cdf, rng.random(need), side="right"), n_words - 1)
+        stream = W[pick][np.arange(10)[None, :] < wlen[pick][:, None]]
+        if stream.size >= total:
+            break
+        need *= 2
+    offsets = np.zeros(rows + 1, dtype=np.uint64)
+    np.cumsum(lengths, out=offsets[1:])
+    words = [bytes(W[i, :k]) for i, k in enumerate(wl)]
+    return np.ascontiguousarray(stream[:total]), offsets, words
+
+
 def strings(rows=1 << 25, seed=3, page_rows=DEFAULT_PAGE_ROWS, prefix=b"q",
-            n_keys=1024):
-    """COUNT(*), SUM(int64 m) WHERE s LIKE 'prefix%' GROUP BY key."""
+            n_keys=1024, codec="str", text=False, contains=None):
+    """COUNT(*), SUM(int64 m) WHERE s LIKE 'prefix%' GROUP BY key.
+
+    ``text``: word-based strings instead of uniform random bytes; ``codec``:
+    "str" (offsets + raw bytes) or "fsst"; ``contains``: the predicate
+    becomes s LIKE '%contains%' (a substring anywhere)."""
     rng = _rng(seed)
-    data, offsets = random_strings(rng, rows)
+    if text:
+        data, offsets, _ = text_strings(rng, rows)
+    else:
+        data, offsets = random_strings(rng, rows)
     key_values = rng.choice(np.arange(-32768, 32768, dtype=np.int32), size=n_keys,
                             replace=False).astype(np.int32)
     key = key_values[_zipf_codes(rng, rows, n_keys)]
     m = rng.integers(1, 1_000_001, rows, dtype=np.int32)
     fact = {"rows": rows, "page_rows": page_rows, "cols": {
-        "s": {"codec": "str", "bytes": data, "offsets": offsets},
+        "s": {"codec": codec, "bytes": data, "offsets": offsets},
         "key": _int_col(key, "dict"),
         "m": _int_col(m),
     }}
+    pred = ({"col": "s", "op": "contains", "args": [bytes(contains)]} if contains is not None
+            else {"col": "s", "op": "prefix", "args": [bytes(prefix)]})
     query = {
-        "preds": [{"col": "s", "op": "prefix", "args": [bytes(prefix)]}],
+        "preds": [pred],
         "joins": [],
         "group": [{"col": "key"}],
         "aggs": [{"op": "count"}, {"op": "sum", "cols": ["m"]}],
     }
-    return {"name": f"strings_{rows}", "tables": {"fact": fact}, "fact": "fact",
-            "query": query}
+    name = f"strings_{rows}" + ("_text" if text else "") + ("" if codec == "str" else f"_{codec}")
+    return {"name": name, "tables": {"fact": fact}, "fact": "fact", "query": query}
 
 
 # ---------------------------------------------------------------------------

@@ -25,6 +25,22 @@ def _pred_mask(cols, pred, n):
             idx = np.where(ok, offs[:-1] + i, 0)
             ok &= (data[idx] == pfx[i]) if data.size else np.zeros(n, bool)
         return ok
+    if op == "contains":
+        # vectorised over candidate start positions: row r matches if the
+        # pattern equals bytes [offs[r] + i, offs[r] + i + m) for some i
+        pat = np.frombuffer(bytes(args[0]), dtype=np.uint8)
+        data, offs = c["bytes"], c["offsets"].astype(np.int64)
+        lens = offs[1:] - offs[:-1]
+        if pat.size == 0:
+            return np.ones(n, bool)
+        found = np.zeros(n, bool)
+        for i in range(int(lens.max(initial=0)) - pat.size + 1):
+            ok = lens >= i + pat.size
+            for k in range(pat.size):
+                idx = np.where(ok, offs[:-1] + i + k, 0)
+                ok &= (data[idx] == pat[k]) if data.size else np.zeros(n, bool)
+            found |= ok
+        return found
     x = c["values"].astype(np.int64)
     a = [int(v) for v in args]
     if op == "lt":
