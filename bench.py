@@ -89,6 +89,11 @@ def _workload(name, rows):
         return synth.scan_filter_aggregate(rows=rows or (1 << 20))
     if name == "strings":
         return synth.strings(rows=rows or (1 << 25))
+    # NEXT-2: word-based strings, LIKE '%ab%', raw bytes vs FSST
+    if name == "strings_text":
+        return synth.strings(rows=rows or (1 << 25), text=True, contains=b"ab")
+    if name == "strings_fsst":
+        return synth.strings(rows=rows or (1 << 25), text=True, contains=b"ab", codec="fsst")
     raise ValueError(name)
 
 
@@ -161,7 +166,7 @@ def oracle_rows_per_s(w, budget_s=15.0, max_rows=None):
         t = dict(w["tables"][f])
         cols = {}
         for name, c in t["cols"].items():
-            if c["codec"] == "str":
+            if c["codec"] in ("str", "fsst"):
                 offs = c["offsets"][: rows + 1]
                 cols[name] = {"codec": "str", "bytes": c["bytes"][: int(offs[-1])], "offsets": offs}
             else:
@@ -342,7 +347,7 @@ def _fact_prefix(w, rows):
     t = dict(w["tables"][f])
     cols = {}
     for name, c in t["cols"].items():
-        if c["codec"] == "str":
+        if c["codec"] in ("str", "fsst"):
             offs = c["offsets"][: rows + 1]
             cols[name] = {"codec": "str", "bytes": c["bytes"][: int(offs[-1])], "offsets": offs}
         else:
@@ -399,7 +404,7 @@ def main():
     ap.add_argument("--impl", default="dpf", choices=["dpf", "reference"])
     ap.add_argument("--workload", default="star",
                     choices=["star", "star_unsorted", "star_year", "star_year_unsorted", "scan", "strings",
-                             "batched"])
+                             "strings_text", "strings_fsst", "batched"])
     ap.add_argument("--batch-queries", type=int, default=64)
     ap.add_argument("--serve", action="store_true", help="Poisson serving run instead of the step benchmark")
     ap.add_argument("--serve-rates", default="10,100,500,1000,2000")
@@ -557,7 +562,11 @@ def time_unfused(eng, plan, stream, fused_records, reps, fused_ms):
     intermediate bytes, checked against the fused result."""
     import numpy as np
     import torch
-    prep = eng.ctx.prepare_unfused(plan)
+    import paper_2605_10511_gb300 as dpf
+    try:
+        prep = eng.ctx.prepare_unfused(plan)
+    except dpf.DpfError as e:  # the chain evaluates PREFIX on STR columns only
+        return {"unsupported": str(e)}
     try:
         for _ in range(2):
             eng.ctx.launch(prep, stream)

@@ -88,8 +88,13 @@ enum dpf_codec {
   DPF_CODEC_DELTA = 2, /* int32: deltas of consecutive rows, FOR-packed (sorted keys) */
   DPF_CODEC_DICT = 3,  /* int32 with <= 65536 distinct values: sorted dictionary,
                           FOR-packed ranks (Sec. 3.4.1, short CHAR as integers)       */
-  DPF_CODEC_STR = 4    /* bytes: FOR-packed lengths + per-mini-block start + raw bytes
+  DPF_CODEC_STR = 4,   /* bytes: FOR-packed lengths + per-mini-block start + raw bytes
                           (Sec. 3.4.2 variable-length page)                           */
+  DPF_CODEC_FSST = 5   /* bytes: FSST-encoded strings (Sec. 3.4.2, Sec. 4.1) in the STR
+                          page layout.  A column table of <= 255 symbols of 1..8 bytes;
+                          code c < nsym stands for symbol c, code 255 for the literal
+                          byte that follows.  The table travels in the dict arrays as
+                          nsym int32 triples {bytes 0..3, bytes 4..7, length}         */
 };
 /* Where a column's pages live: device HBM, or pinned host memory read by
  * the kernel directly through the host link (oversize tables). */
@@ -104,14 +109,15 @@ typedef struct dpf_column_desc {
 } dpf_column_desc;
 
 /* Host-side encoder (the data loader of Sec. 4.2), no device work.
- *   values: host int32[nrows] (FOR/DELTA/DICT) or host bytes (STR)
- *   str_offsets: host uint64[nrows+1] byte offsets into values (STR only,
- *                str_offsets[0] may be non-zero), else NULL
+ *   values: host int32[nrows] (FOR/DELTA/DICT) or host bytes (STR/FSST)
+ *   str_offsets: host uint64[nrows+1] byte offsets into values (STR/FSST
+ *                only, str_offsets[0] may be non-zero), else NULL
  *   out: host buffer of `cap` bytes for the page images, or NULL to size
  *   page_off: host uint64[npages+1] (npages = ceil(nrows/page_rows)), filled
  *   row_prefix: host uint64[npages] RID index (cumulative rows, Sec. 3.4.2)
- *   dict/dict_cap/dict_n: DICT only: sorted distinct values (may be NULL
- *                to size), *dict_n receives their count
+ *   dict/dict_cap/dict_n: DICT: sorted distinct values; FSST: the symbol
+ *                table as 3 int32 per symbol (<= 765); may be NULL to size,
+ *                *dict_n receives the int32 count
  *   size_out: receives the encoded byte size
  * Errors: DPF_EINVAL (nrows = 0, bad codec/page_rows, > 65536 distinct for
  * DICT, a page too large for the format), DPF_ETRUNC (cap or dict_cap too
@@ -153,9 +159,12 @@ enum dpf_op {
   DPF_OP_NE = 5,
   DPF_OP_BETWEEN = 6, /* v[0] <= x <= v[1], both ends inclusive                 */
   DPF_OP_IN = 7,      /* x in {v[0..n)}, 1 <= n <= DPF_MAX_IN                     */
-  DPF_OP_PREFIX = 8   /* STR: string starts with prefix[0..prefix_len); a prefix
-                         longer than the string does not match; an empty prefix
-                         matches every row (Sec. 4.1 variable-length scan)        */
+  DPF_OP_PREFIX = 8,  /* STR/FSST: string starts with prefix[0..prefix_len); a
+                         prefix longer than the string does not match; an empty
+                         prefix matches every row (Sec. 4.1 variable-length scan) */
+  DPF_OP_CONTAINS = 9 /* STR/FSST: prefix[0..prefix_len) occurs anywhere in the
+                         string (LIKE '%pattern%'; Sec. 4.1 names KMP matching);
+                         an empty pattern matches every row                       */
 };
 #define DPF_MAX_IN 8
 #define DPF_MAX_PREFIX 32
@@ -164,7 +173,7 @@ typedef struct dpf_pred {
   dpf_col_id col;          /* column of the scanned table                          */
   int32_t op;              /* enum dpf_op                                          */
   int32_t n;               /* IN: number of operands                               */
-  int32_t prefix_len;      /* PREFIX: 0..DPF_MAX_PREFIX                            */
+  int32_t prefix_len;      /* PREFIX / CONTAINS: 0..DPF_MAX_PREFIX                 */
   int64_t v[DPF_MAX_IN];   /* operands, compared with the int32 value as int64;
                               for DICT columns they are dictionary values          */
   uint8_t prefix[DPF_MAX_PREFIX];

@@ -22,9 +22,11 @@ from . import _build
 DPF_OK = 0
 STATUS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EDUPKEY", -5: "EBUSY", -6: "ETIMEOUT",
           -7: "ETRUNC", -8: "ENOTFOUND", -9: "ECORRUPT", -10: "EINTERNAL"}
-CODEC = {"for": 1, "delta": 2, "dict": 3, "str": 4}
+CODEC = {"for": 1, "delta": 2, "dict": 3, "str": 4, "fsst": 5}
+STRING_CODECS = ("str", "fsst")
 PLACE = {"device": 0, "host": 1}
-OP = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7, "prefix": 8}
+OP = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7, "prefix": 8,
+      "contains": 9}
 AGG = {"count": 0, "sum": 1, "sum_mul": 2, "sum_sub": 3}
 HT_PLACE = {"auto": 0, "smem": 1, "global": 2}
 MAX_IN = 8
@@ -202,10 +204,10 @@ def make_pred(col_id, op, args):
     p = Pred()
     p.col = col_id
     p.op = OP[op]
-    if op == "prefix":
+    if op in ("prefix", "contains"):
         pfx = bytes(args[0])
         if len(pfx) > MAX_PREFIX:
-            raise ValueError(f"prefix longer than {MAX_PREFIX} bytes")
+            raise ValueError(f"pattern longer than {MAX_PREFIX} bytes")
         p.prefix_len = len(pfx)
         for i, b in enumerate(pfx):
             p.prefix[i] = b
@@ -268,11 +270,11 @@ class Context:
 
     # ------------------------------------------------------------ columns
     def load_column(self, col, table=0, page_rows=0, placement="device"):
-        """Load one column dict (``{"codec", "values"}`` or ``{"codec": "str",
-        "bytes", "offsets"}``); returns its id."""
+        """Load one column dict (``{"codec", "values"}`` or ``{"codec": "str"
+        or "fsst", "bytes", "offsets"}``); returns its id."""
         d = ColumnDesc(CODEC[col["codec"]], PLACE[placement], int(page_rows), int(table))
         out = C.c_int32()
-        if col["codec"] == "str":
+        if col["codec"] in STRING_CODECS:
             data = np.ascontiguousarray(col["bytes"], np.uint8)
             offs = np.ascontiguousarray(col["offsets"], np.uint64)
             src = data if data.size else np.zeros(1, np.uint8)
@@ -477,7 +479,7 @@ def encode_column(col, page_rows=0):
     codec = col["codec"]
     d = ColumnDesc(CODEC[codec], 0, int(page_rows), 0)
     P = page_rows or 65536
-    if codec == "str":
+    if codec in STRING_CODECS:
         offs = np.ascontiguousarray(col["offsets"], np.uint64)
         data = np.ascontiguousarray(col["bytes"], np.uint8)
         values = data if data.size else np.zeros(1, np.uint8)
@@ -498,7 +500,8 @@ def encode_column(col, page_rows=0):
                                _ptr(page_off), _ptr(row_prefix), _ptr(dct), dct.size, C.byref(dict_n),
                                C.byref(size)))
     return {"codec": codec, "rows": n, "page_rows": P, "blob": blob, "page_off": page_off,
-            "row_prefix": row_prefix[:npages], "dict": dct[: dict_n.value] if codec == "dict" else None}
+            "row_prefix": row_prefix[:npages],
+            "dict": dct[: dict_n.value] if codec in ("dict", "fsst") else None}
 
 
 from .engine import Engine, PlanHandle  # noqa: E402,F401

@@ -56,6 +56,7 @@ struct Column {
   uint8_t* host_blob = nullptr;   // pinned host allocation (HOST_PINNED)
   uint64_t* d_page_off = nullptr;
   int2* d_zone = nullptr;         // per-page value bounds (zone map)
+  int4* d_sym = nullptr;          // FSST: symbol table {bytes 0..3, bytes 4..7, length, 0}
   int32_t* d_dict = nullptr;
   std::vector<uint64_t> page_off, row_prefix;
   std::vector<int32_t> dict;
@@ -237,6 +238,7 @@ void free_column(dpf_ctx* c, Column& col) {
   }
   dev_free(c, col.d_page_off);
   dev_free(c, col.d_zone);
+  dev_free(c, col.d_sym);
   dev_free(c, col.d_dict);
   col.blob = col.host_blob = nullptr;
 }
@@ -270,8 +272,8 @@ dpf_status validate_pages(uint32_t codec, const uint8_t* pages, uint64_t size, c
     if (rd32(pg) != (kMagic | (codec << 24)) || rd32(pg + 4) != rows) return flag();
     const uint32_t poff = rd32(pg + 8), extra = rd32(pg + 12);
     if (poff != payload_offset(codec, rows) || poff > pbytes) return flag();
-    const uint64_t pay_end = codec == C_STR ? extra : pbytes;
-    if (codec == C_STR && (extra < poff || extra > pbytes || extra % 16)) return flag();
+    const uint64_t pay_end = is_str_codec(codec) ? extra : pbytes;
+    if (is_str_codec(codec) && (extra < poff || extra > pbytes || extra % 16)) return flag();
     const uint64_t pay_words = (pay_end - poff) / 4;
     const uint32_t nmb = (rows + kMB - 1) / kMB;
     for (uint32_t m2 = 0; m2 < nmb; ++m2) {
@@ -283,7 +285,7 @@ dpf_status validate_pages(uint32_t codec, const uint8_t* pages, uint64_t size, c
         const int32_t base = int32_t(rd32(h));
         if (base < 0 || uint64_t(base) >= dict_n) return flag();
       }
-      if (codec == C_STR) {
+      if (is_str_codec(codec)) {
         // lengths of the mini block must stay inside the page's byte region
         const uint32_t start = rd32(pg + kPageHdr + uint64_t(nmb) * 8 + uint64_t(m2) * 4);
         const uint32_t* w = reinterpret_cast<const uint32_t*>(pg + poff) + woff;
@@ -309,18 +311,81 @@ dpf_status validate_pages(uint32_t codec, const uint8_t* pages, uint64_t size, c
 }
 
 // ---------------------------------------------------------------- plans
+// Every FSST code of every string must name a symbol of the table, and an
+// escape must be followed by its literal inside the same string, so the
+// kernels can decode without bounds checks on the table.
+dpf_status validate_fsst_codes(const uint8_t* pages, const uint64_t* page_off, uint64_t npages, uint64_t nrows,
+                               uint32_t P, uint32_t nsym) {
+  bool bad = false;
+  std::mutex m;
+  parallel_for(npages, [&](uint64_t p) {
+    const uint8_t* pg = pages + page_off[p];
+    const uint32_t rows = uint32_t(std::min<uint64_t>(P, nrows - p * uint64_t(P)));
+    const uint32_t nmb = (rows + kMB - 1) / kMB;
+    const uint8_t* region = pg + rd32(pg + 12);
+    const uint32_t* pay = reinterpret_cast<const uint32_t*>(pg + rd32(pg + 8));
+    for (uint32_t mb = 0; mb < nmb && !bad; ++mb) {
+      const uint8_t* h = pg + kPageHdr + uint64_t(mb) * 8;
+      const uint32_t base = rd32(h), wob = rd32(h + 4), bw = wob & 0xffu;
+      uint64_t pos = rd32(pg + kPageHdr + uint64_t(nmb) * 8 + uint64_t(mb) * 4);
+      const uint32_t cnt = std::min<uint32_t>(kMB, rows - mb * kMB);
+      for (uint32_t j = 0; j < cnt; ++j) {
+        uint32_t f = 0;
+        if (bw) {
+          const uint64_t bit = uint64_t(j) * bw;
+          uint64_t win = pay[(wob >> 8) + (bit >> 5)];
+          if ((bit & 31) + bw > 32) win |= uint64_t(pay[(wob >> 8) + (bit >> 5) + 1]) << 32;
+          f = uint32_t((win >> (bit & 31)) & (bw == 32 ? 0xffffffffull : ((1ull << bw) - 1)));
+        }
+        const uint64_t end = pos + base + f;
+        for (uint64_t i = pos; i < end;) {
+          const uint32_t code = region[i++];
+          if (code == kFsstEscape) {
+            if (i >= end) { std::lock_guard<std::mutex> g(m); bad = true; break; }
+            ++i;
+          } else if (code >= nsym) {
+            std::lock_guard<std::mutex> g(m);
+            bad = true;
+            break;
+          }
+        }
+        pos = end;
+      }
+    }
+  });
+  return bad ? fail(DPF_ECORRUPT, "an FSST code names no symbol of the table, or an escape ends a string") : DPF_OK;
+}
+
 dpf_status compile_pred_body(const Column& c, const dpf_pred& p, DevStep& S, int col_index) {
   std::memset(&S, 0, sizeof S);
   S.col = uint8_t(col_index);
-  if (p.op == DPF_OP_PREFIX) {
-    if (c.codec != C_STR) return fail(DPF_EINVAL, "PREFIX needs a STR column (column %d)", c.id);
+  if (p.op == DPF_OP_PREFIX || p.op == DPF_OP_CONTAINS) {
+    if (!is_str_codec(uint32_t(c.codec)))
+      return fail(DPF_EINVAL, "PREFIX / CONTAINS need a STR or FSST column (column %d)", c.id);
     if (p.prefix_len < 0 || p.prefix_len > DPF_MAX_PREFIX) return fail(DPF_EINVAL, "prefix_len %d out of range", p.prefix_len);
-    S.kind = ST_PREFIX;
+    S.kind = p.op == DPF_OP_PREFIX ? ST_PREFIX : ST_CONTAINS;
     S.plen = uint8_t(p.prefix_len);
     std::memcpy(S.pfx, p.prefix, size_t(p.prefix_len));
+    if (S.kind == ST_CONTAINS) {
+      // a pattern of <= 8 bytes packed for the sliding-window compare: byte k
+      // of the pattern at bits 8 * (plen - 1 - k) (the newest byte lowest)
+      uint64_t pat = 0;
+      for (uint32_t k = 0; k < S.plen && S.plen <= 8; ++k) pat |= uint64_t(S.pfx[k]) << (8 * (S.plen - 1 - k));
+      S.in[0] = int32_t(uint32_t(pat));
+      S.in[1] = int32_t(uint32_t(pat >> 32));
+      // Knuth-Morris-Pratt failure function: kmp[i] = length of the longest
+      // proper border of pattern[0..i]
+      uint32_t k = 0;
+      if (S.plen) S.kmp[0] = 0;
+      for (uint32_t i = 1; i < S.plen; ++i) {
+        while (k > 0 && S.pfx[i] != S.pfx[k]) k = S.kmp[k - 1];
+        if (S.pfx[i] == S.pfx[k]) ++k;
+        S.kmp[i] = uint8_t(k);
+      }
+    }
     return DPF_OK;
   }
-  if (c.codec == C_STR) return fail(DPF_EINVAL, "only PREFIX applies to STR column %d", c.id);
+  if (is_str_codec(uint32_t(c.codec))) return fail(DPF_EINVAL, "only PREFIX and CONTAINS apply to string column %d", c.id);
   const int64_t MN = INT32_MIN, MX = INT32_MAX;
   int64_t lo, hi;
   bool neg = false;
@@ -414,7 +479,7 @@ void value_bounds(uint32_t codec, const uint8_t* pages, const uint64_t* page_off
   *vmin = 0;
   *vmax = -1;
   zones->assign(npages, make_int2(INT32_MIN, INT32_MAX));
-  if (codec == C_STR) return;
+  if (is_str_codec(codec)) return;
   int64_t clo = INT64_MAX, chi = INT64_MIN;
   for (uint64_t p = 0; p < npages; ++p) {
     const uint8_t* pg = pages + page_off[p];
@@ -457,6 +522,7 @@ double step_selectivity(const DevStep& S, const Column* col, const HashTable* ht
     case ST_KEY: return 2.0;  // not a filter: after every filter
     case ST_PROBE: return ht && ht->dim_rows ? double(ht->entries) / double(ht->dim_rows) : 1.0;
     case ST_PREFIX: return std::pow(0.1, double(S.plen));
+    case ST_CONTAINS: return std::min(1.0, 30.0 * std::pow(0.1, double(S.plen)));
     default: break;
   }
   if (!col || col->vmax < col->vmin) return 0.5;
@@ -492,6 +558,7 @@ struct ColumnSet {
     d.blob = col.blob;
     d.page_off = col.d_page_off;
     d.zone = col.d_zone;
+    d.sym = col.d_sym;
     d.nrows = col.nrows;
     d.codec = uint32_t(col.codec);
     d.page_rows = col.page_rows;
@@ -1046,8 +1113,14 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
   DeviceGuard g(c->device);
   const uint32_t codec = uint32_t(d->codec);
   const uint32_t P = d->page_rows ? d->page_rows : kDefaultPageRows;
-  if (codec < C_FOR || codec > C_STR) return fail(DPF_EINVAL, "unknown codec %u", codec);
+  if (codec < C_FOR || codec > C_FSST) return fail(DPF_EINVAL, "unknown codec %u", codec);
   if (nrows == 0 || P % kMB || P > kMaxPageRows) return fail(DPF_EINVAL, "bad nrows or page_rows");
+  if (codec == C_FSST) {
+    if (!dict || dict_n == 0 || dict_n % 3 || dict_n / 3 > kFsstMaxSymbols)
+      return fail(DPF_EINVAL, "FSST column needs a table of 1..255 symbols (3 int32 each)");
+    for (uint64_t i = 0; i < dict_n / 3; ++i)
+      if (dict[3 * i + 2] < 1 || dict[3 * i + 2] > 8) return fail(DPF_EINVAL, "FSST symbol %llu has length %d", (unsigned long long)i, dict[3 * i + 2]);
+  }
   if (d->placement != DPF_PLACE_DEVICE && d->placement != DPF_PLACE_HOST_PINNED) return fail(DPF_EINVAL, "bad placement");
   if (codec == C_DICT && (!dict || dict_n == 0 || dict_n > 65536)) return fail(DPF_EINVAL, "DICT column needs 1..65536 dictionary values");
   if (codec == C_DICT)
@@ -1059,6 +1132,7 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
       return fail(DPF_ECORRUPT, "RID index entry %llu is inconsistent", (unsigned long long)p);
   dpf_status st = validate_pages(codec, pages, size, page_off, npages, nrows, P, dict_n);
   if (st) return st;
+  if (codec == C_FSST && (st = validate_fsst_codes(pages, page_off, npages, nrows, P, uint32_t(dict_n / 3)))) return st;
   Column col;
   col.codec = int32_t(codec);
   col.placement = d->placement;
@@ -1072,7 +1146,7 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
   if (codec == C_DICT) col.dict.assign(dict, dict + dict_n);
   std::vector<int2> zones;
   value_bounds(codec, pages, page_off, npages, nrows, P, &col.vmin, &col.vmax, &zones);
-  if (codec == C_STR) {
+  if (is_str_codec(codec)) {
     uint64_t sb = 0;
     for (uint64_t p = 0; p < npages; ++p) {
       const uint8_t* pg = pages + page_off[p];
@@ -1114,6 +1188,14 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
       return st;
     }
   }
+  if (codec == C_FSST) {
+    std::vector<int4> sym(dict_n / 3);
+    for (uint64_t i = 0; i < sym.size(); ++i) sym[i] = make_int4(dict[3 * i], dict[3 * i + 1], dict[3 * i + 2], 0);
+    if ((st = dev_alloc_t(c, sym.size(), &col.d_sym)) || (st = upload(c, col.d_sym, sym.data(), sizeof(int4) * sym.size()))) {
+      free_column(c, col);
+      return st;
+    }
+  }
   col.id = c->next_col++;
   *out = col.id;
   c->cols[col.id] = std::move(col);
@@ -1137,7 +1219,7 @@ dpf_status dpf_load_column(dpf_ctx* c, const dpf_column_desc* d, const void* val
                          dict.data(), dict.size(), &dict_n, &size);
   if (st) return st;
   return dpf_load_encoded(c, d, pages.data(), size, page_off.data(), row_prefix.data(), nrows,
-                          d->codec == C_DICT ? dict.data() : nullptr, dict_n, out);
+                          (d->codec == C_DICT || d->codec == C_FSST) ? dict.data() : nullptr, dict_n, out);
 }
 
 dpf_status dpf_column_info(dpf_ctx* c, dpf_col_id id, uint64_t* rows, uint64_t* enc, uint64_t* raw) {
@@ -1494,6 +1576,11 @@ dpf_status dpf_prepare_unfused(dpf_ctx* c, const dpf_plan* plan, dpf_prep_id* ou
     dpf_release(c, p->id);
     return fail(DPF_EINVAL, "the unfused chain reads device-resident columns only");
   }
+  for (uint32_t k = 0; k < Q.nsteps; ++k)
+    if (Q.steps[k].kind == ST_CONTAINS || Q.cols[Q.steps[k].col].codec == C_FSST) {
+      dpf_release(c, p->id);
+      return fail(DPF_EINVAL, "the unfused chain evaluates PREFIX on STR columns only (no FSST, no CONTAINS)");
+    }
   const uint64_t n = Q.nrows;
   // layout: per column decoded arrays, flags, two (rid, gid) lists, counts
   uint64_t bytes = 0;

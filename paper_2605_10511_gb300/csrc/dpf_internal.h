@@ -18,7 +18,12 @@ constexpr uint32_t kMagic = 0x00465044u;      // 'D' 'P' 'F', codec in the top b
 constexpr uint32_t kMaxPageRows = 1u << 20;
 constexpr uint32_t kDefaultPageRows = 65536;
 
-enum Codec : uint32_t { C_FOR = 1, C_DELTA = 2, C_DICT = 3, C_STR = 4 };
+enum Codec : uint32_t { C_FOR = 1, C_DELTA = 2, C_DICT = 3, C_STR = 4, C_FSST = 5 };
+// STR and FSST share the variable-length page layout (FSST pages hold the
+// encoded strings; their lengths are the encoded lengths).
+__host__ __device__ inline bool is_str_codec(uint32_t codec) { return codec == C_STR || codec == C_FSST; }
+constexpr uint32_t kFsstEscape = 255;     // FSST code: the next byte stands for itself
+constexpr uint32_t kFsstMaxSymbols = 255;
 
 // Bytes of one mini block header in the header array that follows the
 // page header (STR: the lengths' FOR header; the u32 starts come after all
@@ -27,7 +32,7 @@ __host__ __device__ inline uint32_t mb_hdr_bytes(uint32_t codec) {
   return codec == C_DELTA ? 16u : 8u;
 }
 __host__ __device__ inline uint32_t mb_meta_bytes(uint32_t codec) {
-  return codec == C_DELTA ? 16u : (codec == C_STR ? 12u : 8u);
+  return codec == C_DELTA ? 16u : (is_str_codec(codec) ? 12u : 8u);
 }
 __host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15u) & ~uint64_t(15); }
 // Byte offset of the packed payload inside a page of `rows` rows.
@@ -51,6 +56,7 @@ struct DevColumn {
   const uint8_t* blob;        // page images (device, or mapped pinned host)
   const uint64_t* page_off;   // [npages + 1] byte offset of each page (device)
   const int2* zone;           // [npages] bounds {lo, hi} of each page's values (device): a zone map
+  const int4* sym;            // FSST: symbol table {bytes 0..3, bytes 4..7, length, 0} (device)
   uint64_t nrows;
   uint32_t codec;
   uint32_t page_rows;
@@ -61,6 +67,7 @@ enum StepKind : uint8_t {
   ST_NOTRANGE = 2,  // !(lo <= x <= hi)
   ST_IN = 3,        // x in in[0..nin)
   ST_FALSE = 4,     // no row passes (e.g. an equality on a value absent from a dictionary)
+  ST_CONTAINS = 9,  // the string contains pfx[0..plen) (LIKE '%pattern%'), matched by KMP
   ST_PREFIX = 5,    // STR column starts with pfx[0..plen)
   ST_PROBE = 6,     // hash probe; a miss drops the row, a hit adds payload fields to gid
   ST_KEY = 7,       // DICT column code added to gid
@@ -76,7 +83,8 @@ constexpr uint32_t kAbsent = 0xffffffffu;
 struct DevStep {
   uint8_t kind, col, nin, plen;
   int32_t lo, hi;
-  int32_t in[kMaxIn];
+  int32_t in[kMaxIn];     // IN operands; ST_CONTAINS: in[0..1] = a pattern of <= 8 bytes
+                          // packed for the sliding-window compare
   // ST_PROBE
   const void* ht;         // OPEN: uint2 slots; DIRECT: uint32 entries (global)
   uint32_t ht_mask;       // OPEN: capacity - 1 (power of two)
@@ -97,6 +105,7 @@ struct DevStep {
   // ST_KEY
   uint32_t key_mul;
   uint8_t pfx[kMaxPrefix];
+  uint8_t kmp[kMaxPrefix];  // ST_CONTAINS: Knuth-Morris-Pratt failure function of pfx
 };
 
 struct alignas(16) DevQuery {

@@ -6,6 +6,7 @@
 // prefix-summed offsets (the two-pass loading of Sec. 4.2, in memory).
 #include <algorithm>
 #include <cstring>
+#include <unordered_map>
 #include <vector>
 
 #include "dpf_internal.h"
@@ -124,6 +125,7 @@ void write_int_page(const IntSource& src, uint32_t codec, uint64_t r0, const Pag
 }
 
 void plan_str_page(const uint64_t* offs, uint64_t r0, uint32_t rows, PagePlan& pp, bool* bad) {
+  // (STR and FSST pages share this layout)
   pp.rows = rows;
   pp.nmb = (rows + kMB - 1) / kMB;
   pp.mb.resize(pp.nmb);
@@ -157,10 +159,10 @@ void plan_str_page(const uint64_t* offs, uint64_t r0, uint32_t rows, PagePlan& p
   pp.bytes = align16(uint64_t(pp.extra_off) + bytes);
 }
 
-void write_str_page(const uint8_t* data, const uint64_t* offs, uint64_t r0, const PagePlan& pp,
+void write_str_page(uint32_t codec, const uint8_t* data, const uint64_t* offs, uint64_t r0, const PagePlan& pp,
                     uint8_t* pg) {
   std::memset(pg, 0, pp.extra_off);
-  const uint32_t hdr[4] = {kMagic | (uint32_t(C_STR) << 24), pp.rows, pp.payload_off, pp.extra_off};
+  const uint32_t hdr[4] = {kMagic | (codec << 24), pp.rows, pp.payload_off, pp.extra_off};
   std::memcpy(pg, hdr, sizeof hdr);
   uint32_t* pay = reinterpret_cast<uint32_t*>(pg + pp.payload_off);
   uint32_t q[kMB];
@@ -177,6 +179,111 @@ void write_str_page(const uint8_t* data, const uint64_t* offs, uint64_t r0, cons
   }
   std::memcpy(pg + pp.extra_off, data + offs[r0], pp.str_bytes);
   std::memset(pg + pp.extra_off + pp.str_bytes, 0, pp.bytes - pp.extra_off - pp.str_bytes);
+}
+
+// ---------------------------------------------------------------- FSST
+// Symbol table of the FSST string codec (Sec. 3.4.2, Sec. 4.1), built with
+// the construction of Boncz, Neumann and Leis (VLDB 2020): up to 255 symbols
+// of 1..8 bytes; an encoded string is a sequence of codes, c < nsym for
+// symbol c and 255 (escape) followed by a literal byte.  Over five
+// generations a sample of the strings is parsed greedily with the current
+// table; every token (a symbol, or an escaped byte) and every concatenation
+// of two consecutive tokens of at most 8 bytes is counted, and the 255
+// candidates of largest count x length form the next table.  Encoding is
+// greedy: the longest symbol matching at each position.
+struct FsstTable {
+  uint32_t n = 0;
+  uint8_t len[kFsstMaxSymbols];
+  uint64_t sym[kFsstMaxSymbols];             // bytes, little endian
+  std::vector<uint8_t> by_first[256];         // codes starting with a byte, longest first
+  void index() {
+    for (auto& v : by_first) v.clear();
+    for (uint32_t c = 0; c < n; ++c) by_first[sym[c] & 0xffu].push_back(uint8_t(c));
+    for (auto& v : by_first)
+      std::stable_sort(v.begin(), v.end(), [&](uint8_t a, uint8_t b) { return len[a] > len[b]; });
+  }
+  // Longest symbol at s[0..avail): its code, or -1.
+  int match(const uint8_t* s, uint64_t avail) const;
+};
+
+inline uint64_t load_bytes(const uint8_t* p, uint32_t len) {
+  uint64_t x = 0;
+  std::memcpy(&x, p, len);
+  return x;
+}
+
+int FsstTable::match(const uint8_t* s, uint64_t avail) const {
+  for (uint8_t c : by_first[s[0]]) {
+    const uint32_t l = len[c];
+    if (l <= avail && load_bytes(s, l) == sym[c]) return c;
+  }
+  return -1;
+}
+
+// A token as a 64-bit key: its bytes in the low 56 bits... does not fit 8
+// bytes, so tokens are kept as (bytes, length) pairs in one 128-bit word.
+struct TokKey {
+  uint64_t bytes;
+  uint32_t len;
+  bool operator==(const TokKey& o) const { return bytes == o.bytes && len == o.len; }
+};
+struct TokHash {
+  size_t operator()(const TokKey& k) const { return std::hash<uint64_t>()(k.bytes * 0x9e3779b97f4a7c15ull ^ k.len); }
+};
+
+FsstTable fsst_choose(const uint8_t* data, const uint64_t* offs, uint64_t n) {
+  FsstTable t;
+  t.index();
+  const uint64_t sample = std::min<uint64_t>(n, 16384);
+  for (int gen = 0; gen < 5; ++gen) {
+    std::unordered_map<TokKey, uint64_t, TokHash> count;
+    for (uint64_t r = 0; r < sample; ++r) {
+      const uint8_t* s = data + offs[r];
+      const uint64_t L = offs[r + 1] - offs[r];
+      TokKey prev{0, 0};
+      for (uint64_t i = 0; i < L;) {
+        const int c = t.match(s + i, L - i);
+        const uint32_t l = c >= 0 ? t.len[c] : 1u;
+        const TokKey tok{load_bytes(s + i, l), l};
+        ++count[tok];
+        if (prev.len && prev.len + l <= 8) ++count[TokKey{prev.bytes | (tok.bytes << (8 * prev.len)), prev.len + l}];
+        prev = tok;
+        i += l;
+      }
+    }
+    std::vector<std::pair<TokKey, uint64_t>> cand(count.begin(), count.end());
+    std::sort(cand.begin(), cand.end(), [](const std::pair<TokKey, uint64_t>& a, const std::pair<TokKey, uint64_t>& b) {
+      const uint64_t ga = a.second * a.first.len, gb = b.second * b.first.len;
+      if (ga != gb) return ga > gb;
+      if (a.first.len != b.first.len) return a.first.len < b.first.len;
+      return a.first.bytes < b.first.bytes;
+    });
+    t.n = 0;
+    for (const auto& c : cand) {
+      if (t.n == kFsstMaxSymbols) break;
+      t.len[t.n] = uint8_t(c.first.len);
+      t.sym[t.n] = c.first.bytes;
+      ++t.n;
+    }
+    t.index();
+  }
+  return t;
+}
+
+// Encodes one string; returns the encoded length (out: room for 2 * len).
+uint64_t fsst_encode(const FsstTable& t, const uint8_t* s, uint64_t len, uint8_t* out) {
+  uint64_t o = 0;
+  for (uint64_t i = 0; i < len;) {
+    const int code = t.match(s + i, len - i);
+    if (code >= 0) {
+      out[o++] = uint8_t(code);
+      i += t.len[code];
+    } else {
+      out[o++] = uint8_t(kFsstEscape);
+      out[o++] = s[i++];
+    }
+  }
+  return o;
 }
 
 // Sorted distinct values (at most `limit`, else returns false).
@@ -230,9 +337,9 @@ extern "C" dpf_status dpf_encode_column(const dpf_column_desc* desc, const void*
   const uint32_t P = desc->page_rows ? desc->page_rows : kDefaultPageRows;
   if (nrows == 0) return fail(DPF_EINVAL, "encode: nrows must be > 0");
   if (P % kMB != 0 || P > kMaxPageRows) return fail(DPF_EINVAL, "encode: page_rows %u not a multiple of 128 in [128, 2^20]", P);
-  if (codec < C_FOR || codec > C_STR) return fail(DPF_EINVAL, "encode: unknown codec %u", codec);
-  if (!values && !(codec == C_STR)) return fail(DPF_EINVAL, "encode: values is NULL");
-  if (codec == C_STR && !str_offsets) return fail(DPF_EINVAL, "encode: STR needs str_offsets");
+  if (codec < C_FOR || codec > C_FSST) return fail(DPF_EINVAL, "encode: unknown codec %u", codec);
+  if (!values && !is_str_codec(codec)) return fail(DPF_EINVAL, "encode: values is NULL");
+  if (is_str_codec(codec) && !str_offsets) return fail(DPF_EINVAL, "encode: STR/FSST needs str_offsets");
   if (!page_off || !row_prefix || !size_out) return fail(DPF_EINVAL, "encode: page_off/row_prefix/size_out NULL");
 
   const uint64_t npages = (nrows + P - 1) / P;
@@ -240,13 +347,61 @@ extern "C" dpf_status dpf_encode_column(const dpf_column_desc* desc, const void*
   std::vector<uint32_t> codes;
   std::vector<int32_t> dvals;
   IntSource src{codec, static_cast<const int32_t*>(values), nullptr};
-  if (codec == C_STR) {
+  // FSST: the strings encoded with the column's symbol table, then written as
+  // STR pages of the encoded bytes
+  std::vector<uint8_t> fenc;
+  std::vector<uint64_t> foff;
+  const uint8_t* sbytes = static_cast<const uint8_t*>(values);
+  const uint64_t* soffs = str_offsets;
+  if (is_str_codec(codec)) {
     for (uint64_t r = 0; r < nrows; ++r)
       if (str_offsets[r + 1] < str_offsets[r]) return fail(DPF_EINVAL, "encode: str_offsets not monotone at row %llu", (unsigned long long)r);
+    if (str_offsets[nrows] != str_offsets[0] && !values) return fail(DPF_EINVAL, "encode: values is NULL");
+  }
+  if (codec == C_FSST) {
+    const uint8_t* raw = sbytes;
+    const FsstTable t = fsst_choose(raw, str_offsets, nrows);
+    if (dict_n) *dict_n = 3ull * t.n;
+    if (dict) {
+      if (dict_cap < 3ull * t.n) return fail(DPF_ETRUNC, "encode: dict_cap %llu < %u", (unsigned long long)dict_cap, 3 * t.n);
+      for (uint32_t c = 0; c < t.n; ++c) {
+        dict[3 * c] = int32_t(uint32_t(t.sym[c]));
+        dict[3 * c + 1] = int32_t(uint32_t(t.sym[c] >> 32));
+        dict[3 * c + 2] = int32_t(t.len[c]);
+      }
+    }
+    // encode page by page in parallel into per-page buffers, then join
+    std::vector<std::vector<uint8_t>> pe(npages);
+    std::vector<std::vector<uint64_t>> po(npages);
+    parallel_for(npages, [&](uint64_t p) {
+      const uint64_t r0 = p * P, r1 = std::min<uint64_t>(nrows, r0 + P);
+      pe[p].resize(2 * (str_offsets[r1] - str_offsets[r0]) + 1);
+      po[p].assign(r1 - r0, 0);
+      uint64_t o = 0;
+      for (uint64_t r = r0; r < r1; ++r) {
+        o += fsst_encode(t, raw + str_offsets[r], str_offsets[r + 1] - str_offsets[r], pe[p].data() + o);
+        po[p][r - r0] = o;
+      }
+      pe[p].resize(o);
+    });
+    foff.assign(nrows + 1, 0);
+    uint64_t total = 0;
+    for (uint64_t p = 0; p < npages; ++p) {
+      for (uint64_t i = 0; i < po[p].size(); ++i) foff[p * P + i + 1] = total + po[p][i];
+      total += pe[p].size();
+    }
+    fenc.resize(std::max<uint64_t>(total, 1));
+    parallel_for(npages, [&](uint64_t p) {
+      if (!pe[p].empty()) std::memcpy(fenc.data() + foff[p * P], pe[p].data(), pe[p].size());
+    });
+    sbytes = fenc.data();
+    soffs = foff.data();
+  }
+  if (is_str_codec(codec)) {
     bool bad = false;
     parallel_for(npages, [&](uint64_t p) {
       const uint64_t r0 = p * P;
-      plan_str_page(str_offsets, r0, uint32_t(std::min<uint64_t>(P, nrows - r0)), plans[p], &bad);
+      plan_str_page(soffs, r0, uint32_t(std::min<uint64_t>(P, nrows - r0)), plans[p], &bad);
     });
     if (bad) return fail(DPF_EINVAL, "encode: a page holds >= 4 GiB of string bytes or a string >= 2 GiB");
   } else {
@@ -281,8 +436,8 @@ extern "C" dpf_status dpf_encode_column(const dpf_column_desc* desc, const void*
   if (!out) return DPF_OK;
   if (cap < off) return fail(DPF_ETRUNC, "encode: cap %llu < %llu", (unsigned long long)cap, (unsigned long long)off);
   parallel_for(npages, [&](uint64_t p) {
-    if (codec == C_STR)
-      write_str_page(static_cast<const uint8_t*>(values), str_offsets, p * P, plans[p], out + page_off[p]);
+    if (is_str_codec(codec))
+      write_str_page(codec, sbytes, soffs, p * P, plans[p], out + page_off[p]);
     else
       write_int_page(src, codec, p * P, plans[p], out + page_off[p]);
   });

@@ -35,7 +35,7 @@ __device__ __forceinline__ void page_begin(const DevQuery& Q, uint64_t page, int
   if (lane < int(Q.ncols)) {
     const DevColumn& C = Q.cols[lane];
     P.pg = reinterpret_cast<uint64_t>(C.blob) + __ldg(C.page_off + page);
-    if (C.codec == C_STR) P.extra = ld_u32<kHost>(reinterpret_cast<const uint32_t*>(P.pg + 12));
+    if (is_str_codec(C.codec)) P.extra = ld_u32<kHost>(reinterpret_cast<const uint32_t*>(P.pg + 12));
   }
 }
 
@@ -63,7 +63,7 @@ __device__ __forceinline__ TileHdr load_headers(const DevQuery& Q, const PageSta
       const uint2 v = ld_u2<kHost>(reinterpret_cast<const uint2*>(pg + kPageHdr + uint64_t(i0 + ht) * 8));
       h.x = v.x;
       h.y = v.y;
-      if (codec == C_STR)
+      if (is_str_codec(codec))
         h.sstart = ld_u32<kHost>(reinterpret_cast<const uint32_t*>(
             pg + kPageHdr + uint64_t(P.nmb_page) * 8 + uint64_t(i0 + ht) * 4));
     }
@@ -156,8 +156,94 @@ __device__ __forceinline__ void tile_decode(const DevQuery& Q, int c, const Page
   else decode_t<kHost, false>(Q, c, P, Hd, alive, lane, v, anym, status);
 }
 
-// PREFIX step over a STR column: lengths are decoded, their exclusive scan
-// gives each string's start, and the first plen bytes are compared.
+// ------------------------------------------------------------ strings
+// A string predicate on one stored string: PREFIX compares its first plen
+// bytes; CONTAINS runs the Knuth-Morris-Pratt automaton of the pattern over
+// all its bytes (the matcher Sec. 4.1 integrates for LIKE).  FSST strings
+// are decoded on the fly, symbol by symbol (code < nsym: the symbol's bytes;
+// code 255: the next stored byte), and never written anywhere.
+// Scan kinds of string_scan: ST_PREFIX, ST_CONTAINS (KMP), and a CONTAINS
+// of at most 8 bytes compared through a sliding window.
+constexpr int kScanContainsShort = 256;
+
+struct StrMatch {
+  const DevStep* S;
+  uint32_t pos = 0;     // PREFIX: bytes matched; CONTAINS (KMP): automaton state
+  uint64_t win = 0;     // CONTAINS of <= 8 bytes: the last 8 bytes seen
+  bool hit = false;
+  // Feeds one decoded byte; returns false once the outcome is decided.
+  template <int kKind>
+  __device__ __forceinline__ bool feed(uint8_t b) {
+    if (kKind == ST_PREFIX) {
+      if (b != S->pfx[pos]) return false;
+      if (++pos == S->plen) { hit = true; return false; }
+      return true;
+    }
+    if (kKind == kScanContainsShort) {  // short pattern: compare a sliding window
+      win = (win << 8) | b;
+      ++pos;
+      const uint64_t pat = uint32_t(S->in[0]) | (uint64_t(uint32_t(S->in[1])) << 32);
+      const uint64_t mask = S->plen >= 8 ? ~0ull : ((1ull << (8 * S->plen)) - 1);
+      if (pos >= S->plen && (win & mask) == pat) { hit = true; return false; }
+      return true;
+    }
+    uint32_t q = pos;
+    while (q > 0 && b != S->pfx[q]) q = S->kmp[q - 1];
+    if (b == S->pfx[q]) ++q;
+    pos = q;
+    if (q == S->plen) { hit = true; return false; }
+    return true;
+  }
+};
+
+template <bool kHost, int kKind>
+__device__ __forceinline__ bool string_scan(const DevStep& S, const uint8_t* s, uint32_t len, const int4* sym) {
+  StrMatch m;
+  m.S = &S;
+  if (sym == nullptr) {                                 // STR: raw bytes
+    // 4-byte aligned words cover the string (inside the 16-byte padded page)
+    const uint8_t* w0 = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(s) & ~uintptr_t(3));
+    const uint8_t* end = s + len;
+    uint32_t skip = uint32_t(s - w0);
+    for (const uint8_t* w = w0; w < end; w += 4) {
+      uint32_t x = ld_u32<kHost>(reinterpret_cast<const uint32_t*>(w)) >> (8 * skip);
+      const uint32_t nb = tmin<uint32_t>(4u - skip, uint32_t(end - (w + skip)));
+      skip = 0;
+      bool go = true;
+      for (uint32_t k = 0; k < nb && go; ++k, x >>= 8) go = m.template feed<kKind>(uint8_t(x));
+      if (!go) break;
+    }
+    return m.hit;
+  }
+  for (uint32_t i = 0; i < len;) {                      // FSST: decode symbol by symbol
+    const uint32_t c = ld_u8<kHost>(s + i++);
+    if (c == kFsstEscape) {                             // load-time validation: a literal follows
+      if (!m.template feed<kKind>(ld_u8<kHost>(s + i++))) break;
+      continue;
+    }
+    const int4 e = __ldg(sym + c);                      // load-time validation: c < nsym
+    uint64_t w = uint32_t(e.x) | (uint64_t(uint32_t(e.y)) << 32);
+    bool go = true;
+    for (int k = 0; k < e.z && go; ++k, w >>= 8) go = m.template feed<kKind>(uint8_t(w));
+    if (!go) break;
+  }
+  return m.hit;
+}
+
+template <bool kHost>
+__device__ __forceinline__ bool string_match(const DevStep& S, const uint8_t* s, uint32_t len, const int4* sym) {
+  if (S.plen == 0) return true;                         // an empty pattern matches
+  if (S.kind == ST_PREFIX) {
+    if (sym == nullptr && len < S.plen) return false;
+    return string_scan<kHost, ST_PREFIX>(S, s, len, sym);
+  }
+  if (S.plen <= 8) return string_scan<kHost, kScanContainsShort>(S, s, len, sym);
+  return string_scan<kHost, ST_CONTAINS>(S, s, len, sym);
+}
+
+// PREFIX / CONTAINS step over a string column, dense: lengths decoded, their
+// exclusive scan gives each string's start, then each live row's string is
+// matched.
 template <bool kHost>
 __device__ __forceinline__ void tile_prefix(const DevQuery& Q, const DevStep& S, const PageState& P,
                                             const TileHdr& Hd, TileState& T, int lane, unsigned int* status) {
@@ -166,7 +252,8 @@ __device__ __forceinline__ void tile_prefix(const DevQuery& Q, const DevStep& S,
   tile_decode<kHost>(Q, S.col, P, Hd, T.alive, lane, len, anym, status);
   const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, S.col));
   const uint8_t* bytes = pg + __shfl_sync(kFull, P.extra, S.col);
-  const uint32_t plen = S.plen;
+  const int4* sym = Q.cols[S.col].codec == C_FSST ? Q.cols[S.col].sym : nullptr;
+  const bool lockstep = S.kind == ST_PREFIX && sym == nullptr;
 #pragma unroll
   for (int t = 0; t < TB; ++t) {
     if (!((anym >> t) & 1u)) continue;
@@ -174,18 +261,26 @@ __device__ __forceinline__ void tile_prefix(const DevQuery& Q, const DevStep& S,
     excl_scan128(len[t], lane, st);
     const uint8_t* mb = bytes + __shfl_sync(kFull, Hd.sstart, S.col * TB + t);
     uint32_t match = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (((T.alive >> (4 * t + k)) & 1u) && len[t][k] >= plen) match |= 1u << k;
-    for (uint32_t i = 0; i < plen; ++i) {
-      if (!__any_sync(kFull, match)) break;
-      const uint8_t want = S.pfx[i];
-      uint8_t b[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) b[k] = ((match >> k) & 1u) ? ld_u8<kHost>(mb + st[k] + i) : want;
+    if (lockstep) {
+      // raw PREFIX: the warp compares byte i of all its rows' strings at once
+      const uint32_t plen = S.plen;
 #pragma unroll
       for (int k = 0; k < 4; ++k)
-        if (b[k] != want) match &= ~(1u << k);
+        if (((T.alive >> (4 * t + k)) & 1u) && len[t][k] >= plen) match |= 1u << k;
+      for (uint32_t i = 0; i < plen; ++i) {
+        if (!__any_sync(kFull, match)) break;
+        const uint8_t want = S.pfx[i];
+        uint8_t b[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) b[k] = ((match >> k) & 1u) ? ld_u8<kHost>(mb + st[k] + i) : want;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (b[k] != want) match &= ~(1u << k);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (((T.alive >> (4 * t + k)) & 1u) && string_match<kHost>(S, mb + st[k], len[t][k], sym)) match |= 1u << k;
     }
     T.alive &= ~((~match & 15u) << (4 * t));
   }
@@ -403,7 +498,7 @@ __device__ __forceinline__ void tile_dense_step(const DevQuery& Q, uint32_t s, c
                                                 TileState& T, const uint8_t* stab, int lane, unsigned int* status) {
   if (s >= Q.nsteps) return;
   const DevStep& S = Q.steps[s];
-  if (S.kind == ST_PREFIX) tile_prefix<kHost>(Q, S, P, Hd, T, lane, status);
+  if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) tile_prefix<kHost>(Q, S, P, Hd, T, lane, status);
   else if (Q.cols[S.col].codec == C_DELTA) dense_step_t<kHost, true>(Q, S, P, Hd, T, stab, lane, status);
   else dense_step_t<kHost, false>(Q, S, P, Hd, T, stab, lane, status);
 }
@@ -538,8 +633,9 @@ __device__ __forceinline__ uint32_t row_value(const DevQuery& Q, int c, const Pa
   return out;
 }
 
-// PREFIX on a list: lengths and starts of the round's mini blocks are
-// decoded densely and gathered per lane, then the bytes are compared.
+// PREFIX / CONTAINS on a list: lengths and starts of the round's mini
+// blocks are decoded densely and gathered per lane, then each string is
+// matched.
 template <bool kHost>
 __device__ __forceinline__ bool row_prefix(const DevQuery& Q, const DevStep& S, const PageState& P,
                                            uint32_t seg_mb, uint32_t r, bool valid, int lane,
@@ -567,12 +663,8 @@ __device__ __forceinline__ bool row_prefix(const DevQuery& Q, const DevStep& S, 
     }
   }
   const uint8_t* bytes = pg + __shfl_sync(kFull, P.extra, c) + my_start;
-  bool match = valid && my_len >= S.plen;
-  for (uint32_t i = 0; i < S.plen; ++i) {
-    if (!__any_sync(kFull, match)) break;
-    if (match && ld_u8<kHost>(bytes + i) != S.pfx[i]) match = false;
-  }
-  return match;
+  const int4* sym = Q.cols[c].codec == C_FSST ? Q.cols[c].sym : nullptr;
+  return valid && string_match<kHost>(S, bytes, my_len, sym);
 }
 
 // Join probe of one key; on a hit adds the join's group-id contribution.
@@ -650,7 +742,7 @@ __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevS
     const uint32_t r = e & ((1u << kRowBits) - 1u);
     uint32_t gid = e >> kRowBits;
     bool keep;
-    if (S.kind == ST_PREFIX) {
+    if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) {
       keep = row_prefix<kHost>(Q, S, P, seg_mb, r, valid, lane, status);
     } else {
       const uint32_t v = row_value<kHost>(Q, S.col, P, seg_mb, r, valid, lane, status);
@@ -686,7 +778,7 @@ __device__ __forceinline__ uint32_t list_steps(const DevQuery& Q, const PageStat
                                                unsigned int* status, uint32_t first = 1) {
   for (uint32_t s = first; s < Q.nsteps && n != 0; ++s) {
     const DevStep& S = Q.steps[s];
-    if (S.kind == ST_PREFIX || Q.cols[S.col].codec == C_DELTA) {
+    if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS || Q.cols[S.col].codec == C_DELTA) {
       n = list_step_generic<kHost>(Q, S, P, seg_mb, list, n, stab, lane, status);
       continue;
     }

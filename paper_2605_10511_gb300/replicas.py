@@ -31,7 +31,7 @@ def slice_workload(w, lo, hi):
     t = dict(w["tables"][f])
     cols = {}
     for name, c in t["cols"].items():
-        if c["codec"] == "str":
+        if c["codec"] in ("str", "fsst"):
             offs = np.asarray(c["offsets"], np.uint64)
             a, b = int(offs[lo]), int(offs[hi])
             cols[name] = {"codec": "str", "bytes": c["bytes"][a:b], "offsets": offs[lo:hi + 1] - offs[lo]}

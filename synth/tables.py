@@ -395,6 +395,14 @@ def tiny_random_workload(seed, rows=None, page_rows=None):
         op = str(rng.choice(["sum", "sum_mul", "sum_sub"]))
         cols = ["x"] if op == "sum" else [str(rng.choice(["x", "y"])), str(rng.choice(["x", "y"]))]
         aggs.append({"op": op, "cols": cols})
+    # the string column's codec and the string predicate's kind come from a
+    # second stream, so the draws above (and earlier seeds' tables) are unchanged
+    rng2 = _rng(seed + 7919)
+    if rng2.integers(0, 2):
+        fact["cols"]["s"] = dict(fact["cols"]["s"], codec="fsst")
+    for p in preds:
+        if p["col"] == "s" and rng2.integers(0, 2):
+            p["op"] = "contains"
     query = {"preds": preds, "joins": joins, "group": group, "aggs": aggs}
     return {"name": f"tiny_{seed}", "tables": {"fact": fact, "dim": dim},
             "fact": "fact", "query": query}

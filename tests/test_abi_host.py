@@ -51,6 +51,13 @@ def test_binding_covers_every_declared_symbol():
 def _compare(col, page_rows):
     import oracle
     a = dpf.encode_column(col, page_rows)
+    if col["codec"] == "fsst":
+        # the two FSST encoders choose their symbol tables independently; the
+        # library's pages must decode, with the oracle's decoder, to the input
+        d, o = oracle.decode_column(a)
+        assert np.array_equal(o, np.asarray(col["offsets"], np.uint64) - np.uint64(col["offsets"][0]))
+        assert d.tobytes() == np.asarray(col["bytes"], np.uint8).tobytes()
+        return
     b = oracle.encode_column(col, page_rows)
     assert a["blob"].tobytes() == b["blob"].tobytes()
     assert np.array_equal(a["page_off"], b["page_off"])
@@ -108,3 +115,29 @@ def test_no_gpu_fails_loudly():
     with pytest.raises(dpf.DpfError) as e:
         dpf.Context(0)
     assert e.value.status == -3
+
+
+@pytest.mark.parametrize("text", [False, True])
+def test_library_fsst_pages_decode_with_the_oracle(oracle_lib, text):
+    """The library's FSST encoder (its own symbol table) writes pages that the
+    oracle's independent decoder turns back into the same strings."""
+    import synth
+    w = synth.strings(rows=9000, seed=5, page_rows=2048, codec="fsst", text=text)
+    c = w["tables"]["fact"]["cols"]["s"]
+    enc = dpf.encode_column(c, 2048)
+    assert enc["dict"] is not None and enc["dict"].size % 3 == 0 and 0 < enc["dict"].size <= 765
+    d, o = oracle_lib.decode_column(enc)
+    assert np.array_equal(o, c["offsets"]) and np.array_equal(d, c["bytes"])
+    if text:
+        assert enc["blob"].size < 0.6 * c["bytes"].size
+
+
+@pytest.mark.parametrize("strs", [[b""], [b"", b"a", b""], [bytes(range(256)) * 2], [b"\\xff" * 40]])
+def test_library_fsst_edges_decode_with_the_oracle(oracle_lib, strs):
+    offs = np.zeros(len(strs) + 1, np.uint64)
+    np.cumsum([len(x) for x in strs], out=offs[1:])
+    data = np.frombuffer(b"".join(strs), np.uint8).copy()
+    col = {"codec": "fsst", "bytes": data, "offsets": offs}
+    enc = dpf.encode_column(col, 128)
+    d, o = oracle_lib.decode_column(enc)
+    assert np.array_equal(o, offs) and d.tobytes() == b"".join(strs)

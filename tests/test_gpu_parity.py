@@ -70,6 +70,14 @@ def test_workload_shapes(eng, shapes, name):
 @pytest.mark.parametrize("seed", range(0, 40, 3))
 def test_unfused_chain_random_small(eng, seed):
     w = synth.tiny_random_workload(seed)
+    q = w["query"]
+    if w["tables"]["fact"]["cols"]["s"]["codec"] == "fsst" and any(p["col"] == "s" for p in q["preds"]) \
+            or any(p["op"] == "contains" for p in q["preds"]):
+        # the unfused baseline evaluates PREFIX on STR columns only
+        with pytest.raises(dpf.DpfError) as ex:
+            eng.run_unfused(w)
+        assert ex.value.status == -1  # DPF_EINVAL
+        return
     assert_same(eng.run_unfused(w), expect(w), w["name"])
 
 
@@ -186,6 +194,8 @@ def test_loaded_pages_are_the_encoded_pages(eng):
     eng.load_workload(w)
     for tname, t in w["tables"].items():
         for cname, c in t["cols"].items():
+            if c["codec"] == "fsst":
+                continue  # independent symbol tables; the CPU tests cross-decode these pages
             got = eng.ctx.column_bytes(eng.col(w, tname, cname))
             want = oracle.encode_column(c, t["page_rows"])["blob"]
             assert np.array_equal(got, want), (tname, cname)
@@ -253,3 +263,24 @@ def test_four_cta_build_matches(eng, shapes, name):
     """The kernel build for four resident CTAs per SM (ctas_per_sm = 4)."""
     w = shapes[name]
     assert_same(eng.run(w, tuning=dpf.Tuning(0, 256, 0, 4)), expect(w), (name, "4 CTAs"))
+
+
+@pytest.mark.parametrize("text", [False, True])
+@pytest.mark.parametrize("op,pat", [("prefix", b"q"), ("contains", b"ab"), ("contains", b"q q"),
+                                    ("contains", b""), ("prefix", b""), ("contains", b"x" * 32)])
+@pytest.mark.parametrize("codec", ["str", "fsst"])
+def test_string_predicates_on_str_and_fsst(eng, codec, op, pat, text):
+    """PREFIX and CONTAINS (KMP) on raw and FSST-coded strings, random and
+    text-like, with an empty pattern and one longer than every string."""
+    w = synth.strings(rows=(1 << 18) + 77, seed=13, page_rows=32768, codec=codec, text=text)
+    w["query"]["preds"] = [{"col": "s", "op": op, "args": [pat]}]
+    assert_same(eng.run(w), expect(w), (codec, op, pat, text))
+
+
+def test_fsst_codes_outside_the_table_are_rejected(eng):
+    w = synth.strings(rows=5000, seed=3, page_rows=1024, codec="fsst", text=True)
+    enc = dpf.encode_column(w["tables"]["fact"]["cols"]["s"], 1024)
+    bad = dict(enc, dict=enc["dict"][:6])  # two symbols left: most codes name none
+    with pytest.raises(dpf.DpfError) as ex:
+        eng.ctx.load_encoded(bad)
+    assert ex.value.status == -9  # DPF_ECORRUPT
