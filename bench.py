@@ -6,7 +6,11 @@ with delta-coded date keys), grouped by (dim3 attribute, year), SUM(int64).
 One step = one replay of the CUDA graph holding the fused persistent kernel
 (chunk scheduling, staging, decode, predicates, probes, aggregation and
 result assembly).  The dimension hash builds run once before timing and are
-reported separately (``build_ms``).
+reported separately (``build_ms``).  ``--workload chain`` runs LINEITEM ->
+ORDERS -> CUSTOMER: CUSTOMER's table is built by a scan+build kernel,
+ORDERS' by a scan+probe+build kernel probing it, and the timed step is the
+fused LINEITEM pipeline probing ORDERS' table; each build is timed too
+(``chain``).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
 on a bounded sample of the same workload instead.
@@ -87,6 +91,11 @@ def _workload(name, rows):
         return synth.star_join(rows=rows or (1 << 26), clustered=False, date_year=1994)
     if name == "scan":
         return synth.scan_filter_aggregate(rows=rows or (1 << 20))
+    # NEXT-3: LINEITEM -> ORDERS -> CUSTOMER (scan+build, scan+probe+build, fused)
+    if name == "chain":
+        return synth.chain_join(rows=rows or (1 << 26))
+    if name == "chain_sparse":
+        return synth.chain_join(rows=rows or (1 << 26), sparse_orderkeys=True)
     if name == "strings":
         return synth.strings(rows=rows or (1 << 25))
     # NEXT-2: word-based strings, LIKE '%ab%', raw bytes vs FSST
@@ -404,7 +413,7 @@ def main():
     ap.add_argument("--impl", default="dpf", choices=["dpf", "reference"])
     ap.add_argument("--workload", default="star",
                     choices=["star", "star_unsorted", "star_year", "star_year_unsorted", "scan", "strings",
-                             "strings_text", "strings_fsst", "batched"])
+                             "strings_text", "strings_fsst", "chain", "chain_sparse", "batched"])
     ap.add_argument("--batch-queries", type=int, default=64)
     ap.add_argument("--serve", action="store_true", help="Poisson serving run instead of the step benchmark")
     ap.add_argument("--serve-rates", default="10,100,500,1000,2000")
@@ -458,6 +467,7 @@ def main():
     eng = dpf.Engine(device=local)
     eng.load_workload(w)
     stream = torch.cuda.Stream()
+    chain = time_chain_builds(eng, w, stream, torch)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
@@ -542,6 +552,11 @@ def main():
         "wall_s": wall,
     }
 
+    if chain:
+        link_ms = sum(x["ms"] for x in chain)
+        rows_all = fact_rows + sum(x["rows"] for x in chain)
+        out["chain"] = {"links": chain, "fused_ms": ms_step, "pipeline_ms": link_ms + ms_step,
+                        "pipeline_rows_per_s": rows_all / ((link_ms + ms_step) * 1e-3)}
     if not args.no_e2e:
         out["e2e"] = e2e_host_resident(dpf, w, args, local, tuning)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -554,6 +569,40 @@ def main():
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def time_chain_builds(eng, w, stream, torch, reps=5):
+    """For a query whose joins form a chain: the wall time (median of
+    ``reps``, host synchronisation included) of building each table, inner
+    tables first: Kernel #1 (scan + build) for a table that probes nothing,
+    Kernel #2 (scan + probe + build) for one that probes the tables built
+    before it.  The last build of each link stays cached for the plan.
+    Returns None when no join has joins of its own."""
+    if not any(j.get("joins") for j in w["query"]["joins"]):
+        return None
+    links = []
+
+    def walk(j):
+        for s in j.get("joins", []):
+            walk(s)
+        sig = (w["name"], repr(j))
+        times = []
+        for _ in range(reps):
+            old = eng.hts.pop(sig, None)
+            if old is not None:
+                eng.ctx.drop_hash(old)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ht = eng.build_join(w, j, stream)
+            torch.cuda.synchronize()
+            times.append(1e3 * (time.perf_counter() - t0))
+        links.append({"table": j["dim"], "rows": w["tables"][j["dim"]]["rows"],
+                      "kernel": "scan+probe+build" if j.get("joins") else "scan+build",
+                      "entries": eng.ctx.hash_info(ht)["entries"], "ms": statistics.median(times)})
+
+    for j in w["query"]["joins"]:
+        walk(j)
+    return links
 
 
 def time_unfused(eng, plan, stream, fused_records, reps, fused_ms):

@@ -183,8 +183,8 @@ typedef struct dpf_pred {
 /* Kernel #1 of Sec. 3.1: scans a dimension table's key column and payload
  * columns, keeps the rows passing every predicate (conjunction) and inserts
  * key -> payload into an open-addressing hash table in device memory.
- *   key_col: FOR, DELTA or DICT column; keys must be unique among the rows
- *            kept and differ from INT32_MIN
+ *   key_col: FOR or DELTA column; keys must be unique among the rows kept
+ *            and differ from INT32_MIN
  *   payload_cols: 0..2 DICT columns of the same table; field f of a probe hit
  *            is the dictionary code of payload_cols[f]
  * Asynchronous on `stream` except for one device-to-host read of the kept
@@ -203,9 +203,38 @@ dpf_status dpf_drop_hash(dpf_ctx* ctx, dpf_ht_id ht);
  * All fact columns named by a plan belong to one table.  Aggregates are
  * int64 over sign-extended int32 inputs (Sec. 4.3), wrapping on overflow. */
 typedef struct dpf_join {
-  dpf_col_id fk_col; /* fact column probed (FOR/DELTA/DICT)  */
-  dpf_ht_id ht;      /* table built by dpf_build_hash        */
+  dpf_col_id fk_col; /* column of the scanned table probed (FOR or DELTA) */
+  dpf_ht_id ht;      /* table built by dpf_build_hash or dpf_build_hash_probe */
 } dpf_join;
+
+/* ------------------------------------------------ scan, probe and build */
+/* Kernel #2 of Sec. 3.1: scans a table, probes tables built earlier and
+ * inserts the rows that pass into a new table, which a later pipeline
+ * probes.  A row is kept when it passes every predicate AND finds a match
+ * in every join (inner joins, probed through columns of the scanned table).
+ * A chain such as LINEITEM -> ORDERS -> CUSTOMER is built table by table:
+ * CUSTOMER with dpf_build_hash, then ORDERS with this call probing the
+ * CUSTOMER table, then the fused plan over LINEITEM probes the ORDERS table.
+ * Payload field f of the new table is either the dictionary code of a DICT
+ * column of the scanned table, or payload field `field` of the row's match
+ * in joins[join] (carried through the chain, so a plan over LINEITEM can
+ * group by a CUSTOMER attribute).  Keys, limits, errors and synchronisation
+ * are those of dpf_build_hash; at most DPF_MAX_JOINS joins and
+ * DPF_MAX_PREDS predicates. */
+enum dpf_payload_kind { DPF_PAYLOAD_COLUMN = 0, DPF_PAYLOAD_JOIN = 1 };
+typedef struct dpf_payload {
+  int32_t kind;      /* enum dpf_payload_kind                                 */
+  dpf_col_id col;    /* DPF_PAYLOAD_COLUMN: DICT column of the scanned table  */
+  int32_t join;      /* DPF_PAYLOAD_JOIN: index into dpf_build.joins          */
+  int32_t field;     /* DPF_PAYLOAD_JOIN: payload field of that join's table  */
+} dpf_payload;
+typedef struct dpf_build {
+  dpf_col_id key_col;                           /* FOR or DELTA             */
+  int32_t n_payload; const dpf_payload* payload; /* 0..2                    */
+  int32_t n_preds;   const dpf_pred* preds;     /* conjunction              */
+  int32_t n_joins;   const dpf_join* joins;     /* inner joins              */
+} dpf_build;
+dpf_status dpf_build_hash_probe(dpf_ctx* ctx, const dpf_build* spec, void* stream, dpf_ht_id* out);
 
 enum dpf_key_kind { DPF_KEY_COLUMN = 0, DPF_KEY_PAYLOAD = 1 };
 typedef struct dpf_key {

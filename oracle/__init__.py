@@ -64,9 +64,13 @@ class _Pred(C.Structure):
 
 
 class _Join(C.Structure):
-    _fields_ = [("fk_col", C.c_int32), ("dim", C.POINTER(_Table)), ("key_col", C.c_int32),
-                ("npreds", C.c_int32), ("preds", C.POINTER(_Pred)), ("npay", C.c_int32),
-                ("pay_cols", C.c_int32 * 2)]
+    pass
+
+
+_Join._fields_ = [("fk_col", C.c_int32), ("dim", C.POINTER(_Table)), ("key_col", C.c_int32),
+                  ("npreds", C.c_int32), ("preds", C.POINTER(_Pred)), ("npay", C.c_int32),
+                  ("pay_cols", C.c_int32 * 2), ("pay_join", C.c_int32 * 2),
+                  ("pay_field", C.c_int32 * 2), ("nsub", C.c_int32), ("sub", C.POINTER(_Join))]
 
 
 class _Key(C.Structure):
@@ -325,6 +329,40 @@ def decoded_tables(workload, from_encoded=True):
     return out
 
 
+def _joins(tables, specs, probe_names, keep, dim_tables):
+    """ctypes array of the joins ``specs`` probed from a table with columns
+    ``probe_names``; a join's own ``joins`` (a chain) are probed from its
+    dimension and become its sub joins."""
+    arr = (_Join * max(len(specs), 1))()
+    for i, j in enumerate(specs):
+        d = tables[j["dim"]]
+        dt, dnames, dkeep = _table(d["cols"], d["rows"])
+        keep += dkeep
+        dim_tables.append(dt)
+        dp = (_Pred * max(len(j["preds"]), 1))()
+        for k, pr in enumerate(j["preds"]):
+            dp[k], buf = _make_pred(pr, dnames)
+            keep.append(buf)
+        keep.append(dp)
+        subs = j.get("joins", [])
+        sub = _joins(tables, subs, dnames, keep, dim_tables)
+        arr[i].fk_col = probe_names.index(j["fk"])
+        arr[i].dim = C.pointer(dt)
+        arr[i].key_col = dnames.index(j["key"])
+        arr[i].npreds = len(j["preds"])
+        arr[i].preds = C.cast(dp, C.POINTER(_Pred))
+        arr[i].npay = len(j["payload"])
+        for f, pc in enumerate(j["payload"]):
+            if isinstance(pc, dict):
+                arr[i].pay_cols[f], arr[i].pay_join[f], arr[i].pay_field[f] = 0, pc["join"], pc["field"]
+            else:
+                arr[i].pay_cols[f], arr[i].pay_join[f], arr[i].pay_field[f] = dnames.index(pc), -1, 0
+        arr[i].nsub = len(subs)
+        arr[i].sub = C.cast(sub, C.POINTER(_Join))
+    keep.append(arr)
+    return arr
+
+
 def run_query(workload, from_encoded=True, tables=None):
     """Evaluate ``workload['query']``; returns an array of RECORD_DTYPE."""
     L = lib()
@@ -337,26 +375,8 @@ def run_query(workload, from_encoded=True, tables=None):
     for i, pr in enumerate(q["preds"]):
         preds[i], buf = _make_pred(pr, fnames)
         keep.append(buf)
-    joins = (_Join * max(len(q["joins"]), 1))()
     dim_tables = []
-    for i, j in enumerate(q["joins"]):
-        d = tables[j["dim"]]
-        dt, dnames, dkeep = _table(d["cols"], d["rows"])
-        keep += dkeep
-        dim_tables.append(dt)
-        dp = (_Pred * max(len(j["preds"]), 1))()
-        for k, pr in enumerate(j["preds"]):
-            dp[k], buf = _make_pred(pr, dnames)
-            keep.append(buf)
-        keep.append(dp)
-        joins[i].fk_col = fnames.index(j["fk"])
-        joins[i].dim = C.pointer(dt)
-        joins[i].key_col = dnames.index(j["key"])
-        joins[i].npreds = len(j["preds"])
-        joins[i].preds = C.cast(dp, C.POINTER(_Pred))
-        joins[i].npay = len(j["payload"])
-        for f, pc in enumerate(j["payload"]):
-            joins[i].pay_cols[f] = dnames.index(pc)
+    joins = _joins(tables, q["joins"], fnames, keep, dim_tables)
     keys = (_Key * max(len(q["group"]), 1))()
     for i, g in enumerate(q["group"]):
         if "col" in g:

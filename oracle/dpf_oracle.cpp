@@ -11,7 +11,9 @@
 //
 // What it computes (Sec. 3.1, Kernels #1-#3): an exact relational result
 //   SELECT keys, COUNT(*), aggs FROM fact JOIN dims WHERE conj GROUP BY keys
-// with inner equi-joins on unique dimension keys and every aggregate held
+// with inner equi-joins on unique dimension keys (a dimension may itself be
+// joined with further dimensions before it is built: a chain such as
+// LINEITEM -> ORDERS -> CUSTOMER) and every aggregate held
 // in int64 after sign-extending the int32 inputs (Sec. 4.3, DECIMAL stored
 // as 32-bit and processed as 64-bit).  The evaluator is deliberately plain:
 // it decodes whole columns first (page by page, mini block by mini block,
@@ -654,13 +656,18 @@ struct OrcPred {
 };
 
 struct OrcJoin {
-  int32_t fk_col;                 // column of the fact table
+  int32_t fk_col;                 // column of the probing table (the fact, or the
+                                  // dimension of the enclosing join)
   const OrcTable* dim;
   int32_t key_col;                // column of dim
   int32_t npreds;
   const OrcPred* preds;           // on dim
   int32_t npay;
-  int32_t pay_cols[2];            // columns of dim
+  int32_t pay_cols[2];            // payload f: column pay_cols[f] of dim when
+  int32_t pay_join[2];            //   pay_join[f] < 0, else field pay_field[f] of
+  int32_t pay_field[2];           //   the row's match in sub join pay_join[f]
+  int32_t nsub;                   // joins probed by dim's own scan (a chain:
+  const struct OrcJoin* sub;      //   scan, probe, build of Sec. 3.1 Kernel #2)
 };
 
 struct OrcKey {
@@ -709,6 +716,43 @@ static bool eval_pred(const OrcTable& t, const OrcPred& p, uint64_t r) {
   return false;
 }
 
+using OrcMap = std::unordered_map<int32_t, std::vector<int32_t>>;
+
+// The build side of one join: every row of J.dim that passes J's predicates
+// and finds a match in each of J's sub joins (an inner join: a miss drops
+// the row) maps its key to its payload values.  Sub joins are built first,
+// the same way (Sec. 3.1: Kernel #1 scans and builds, Kernel #2 scans,
+// probes the earlier table and builds the next).  Returns 0 or a status.
+static int64_t build_map(const OrcJoin& J, OrcMap& m, int depth) {
+  if (depth > 4 || J.nsub < 0 || J.nsub > 4 || J.npay < 0 || J.npay > 2) return EINVAL;
+  std::vector<OrcMap> subs(size_t(J.nsub));
+  for (int32_t s = 0; s < J.nsub; ++s) {
+    const int64_t rc = build_map(J.sub[s], subs[size_t(s)], depth + 1);
+    if (rc) return rc;
+  }
+  for (int32_t f = 0; f < J.npay; ++f)
+    if (J.pay_join[f] >= J.nsub || (J.pay_join[f] >= 0 && (J.pay_field[f] < 0 ||
+                                                           J.pay_field[f] >= J.sub[J.pay_join[f]].npay)))
+      return EINVAL;
+  for (uint64_t r = 0; r < J.dim->n; ++r) {
+    bool ok = true;
+    for (int32_t k = 0; k < J.npreds && ok; ++k) ok = eval_pred(*J.dim, J.preds[k], r);
+    std::vector<const std::vector<int32_t>*> hit(size_t(J.nsub), nullptr);
+    for (int32_t s = 0; s < J.nsub && ok; ++s) {
+      auto it = subs[size_t(s)].find(J.dim->cols[J.sub[s].fk_col].v[r]);
+      if (it == subs[size_t(s)].end()) ok = false; else hit[size_t(s)] = &it->second;
+    }
+    if (!ok) continue;
+    std::vector<int32_t> pay;
+    for (int32_t f = 0; f < J.npay; ++f)
+      pay.push_back(J.pay_join[f] < 0 ? J.dim->cols[J.pay_cols[f]].v[r]
+                                      : (*hit[size_t(J.pay_join[f])])[size_t(J.pay_field[f])]);
+    const int32_t key = J.dim->cols[J.key_col].v[r];
+    if (!m.emplace(key, pay).second) return EDUPKEY;
+  }
+  return 0;
+}
+
 // Evaluates the query.  Writes at most cap records (sorted ascending by key
 // tuple, groups with zero rows omitted, an ungrouped query always yields one
 // record) and returns the number of records, or a negative status.
@@ -717,18 +761,10 @@ int64_t orc_query(const OrcTable* fact, int32_t npreds, const OrcPred* preds, in
                   const OrcAgg* aggs, OrcRecord* out, uint64_t cap) {
   if (njoins > 8 || nkeys > 2 || naggs > 4) return EINVAL;
   // Build side: key -> payload values of the dimension rows that pass.
-  std::vector<std::unordered_map<int32_t, std::vector<int32_t>>> maps(njoins);
+  std::vector<OrcMap> maps(njoins);
   for (int32_t j = 0; j < njoins; ++j) {
-    const OrcJoin& J = joins[j];
-    for (uint64_t r = 0; r < J.dim->n; ++r) {
-      bool ok = true;
-      for (int32_t k = 0; k < J.npreds && ok; ++k) ok = eval_pred(*J.dim, J.preds[k], r);
-      if (!ok) continue;
-      std::vector<int32_t> pay;
-      for (int32_t f = 0; f < J.npay; ++f) pay.push_back(J.dim->cols[J.pay_cols[f]].v[r]);
-      const int32_t key = J.dim->cols[J.key_col].v[r];
-      if (!maps[j].emplace(key, pay).second) return EDUPKEY;
-    }
+    const int64_t rc = build_map(joins[j], maps[j], 0);
+    if (rc) return rc;
   }
   std::map<std::pair<int32_t, int32_t>, OrcRecord> groups;
   for (uint64_t r = 0; r < fact->n; ++r) {

@@ -59,6 +59,16 @@ class Join(C.Structure):
     _fields_ = [("fk_col", C.c_int32), ("ht", C.c_int32)]
 
 
+class Payload(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("col", C.c_int32), ("join", C.c_int32), ("field", C.c_int32)]
+
+
+class Build(C.Structure):
+    _fields_ = [("key_col", C.c_int32), ("n_payload", C.c_int32), ("payload", C.POINTER(Payload)),
+                ("n_preds", C.c_int32), ("preds", C.POINTER(Pred)),
+                ("n_joins", C.c_int32), ("joins", C.POINTER(Join))]
+
+
 class Key(C.Structure):
     _fields_ = [("kind", C.c_int32), ("col", C.c_int32), ("join", C.c_int32), ("field", C.c_int32)]
 
@@ -120,6 +130,7 @@ _SIGS = {
     "dpf_drop_column": (C.c_int32, [_P, C.c_int32]),
     "dpf_build_hash": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, C.POINTER(Pred), C.c_int32, _P,
                                    C.POINTER(C.c_int32)]),
+    "dpf_build_hash_probe": (C.c_int32, [_P, C.POINTER(Build), _P, C.POINTER(C.c_int32)]),
     "dpf_hash_info": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "dpf_drop_hash": (C.c_int32, [_P, C.c_int32]),
     "dpf_prepare": (C.c_int32, [_P, C.POINTER(Plan), C.c_int32, C.POINTER(Tuning), C.POINTER(C.c_int32)]),
@@ -322,6 +333,22 @@ class Context:
         out = C.c_int32()
         _check(lib().dpf_build_hash(self.h, key_col, _ptr(pay), len(payload_cols), parr, len(preds),
                                     _stream_ptr(stream), C.byref(out)))
+        return out.value
+
+    def build_hash_probe(self, key_col, payload=(), preds=(), joins=(), stream=None):
+        """Scan, probe and build (one link of a join chain).  ``payload``
+        items are a DICT column id or ``("join", j, field)``: payload
+        ``field`` of the row's match in ``joins[j]``; ``joins`` are
+        ``(fk_col, ht)`` pairs probed from the scanned table."""
+        pay = (Payload * max(len(payload), 1))()
+        for i, p in enumerate(payload):
+            pay[i] = Payload(1, 0, p[1], p[2]) if isinstance(p, tuple) else Payload(0, p, 0, 0)
+        parr = (Pred * max(len(preds), 1))(*preds)
+        jarr = (Join * max(len(joins), 1))(*[Join(fk, ht) for fk, ht in joins])
+        b = Build(key_col, len(payload), C.cast(pay, C.POINTER(Payload)), len(preds),
+                  C.cast(parr, C.POINTER(Pred)), len(joins), C.cast(jarr, C.POINTER(Join)))
+        out = C.c_int32()
+        _check(lib().dpf_build_hash_probe(self.h, C.byref(b), _stream_ptr(stream), C.byref(out)))
         return out.value
 
     def hash_info(self, ht):

@@ -1262,42 +1262,86 @@ dpf_status dpf_drop_column(dpf_ctx* c, dpf_col_id id) {
   return DPF_OK;
 }
 
-dpf_status dpf_build_hash(dpf_ctx* c, dpf_col_id key_col, const dpf_col_id* payload_cols, int32_t n_payload,
-                          const dpf_pred* preds, int32_t n_preds, void* stream, dpf_ht_id* out) {
+// Kernel #1 (no joins) and Kernel #2 (scan, probe, build) of Sec. 3.1.
+// Steps: the predicates in the given order, then one global-memory probe
+// per join (a miss drops the row; no group-id contribution).
+static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, dpf_ht_id* out) {
   if (!c || !out) return fail(DPF_EINVAL, "NULL argument");
-  if (n_payload < 0 || n_payload > 2 || (n_payload && !payload_cols)) return fail(DPF_EINVAL, "0..2 payload columns");
-  if (n_preds < 0 || n_preds > DPF_MAX_PREDS || (n_preds && !preds)) return fail(DPF_EINVAL, "bad predicates");
+  if (B.n_payload < 0 || B.n_payload > 2 || (B.n_payload && !B.payload)) return fail(DPF_EINVAL, "0..2 payload fields");
+  if (B.n_preds < 0 || B.n_preds > DPF_MAX_PREDS || (B.n_preds && !B.preds)) return fail(DPF_EINVAL, "bad predicates");
+  if (B.n_joins < 0 || B.n_joins > DPF_MAX_JOINS || (B.n_joins && !B.joins)) return fail(DPF_EINVAL, "bad joins");
   std::lock_guard<std::recursive_mutex> lk(c->mu);
   DeviceGuard g(c->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DevQuery Q;
   std::memset(&Q, 0, sizeof Q);
   ColumnSet cs{c, Q};
+  const dpf_col_id key_col = B.key_col;
   int kidx;
   dpf_status st = cs.add(key_col, &kidx);
   if (st) return st;
   const Column& kc = c->cols[key_col];
   if (kc.codec != C_FOR && kc.codec != C_DELTA) return fail(DPF_EINVAL, "key column %d must be FOR or DELTA", key_col);
   HashTable ht;
-  ht.npay = n_payload;
+  ht.npay = B.n_payload;
   ht.dim_rows = kc.nrows;
   Q.build_key = kidx;
-  Q.build_npay = n_payload;
-  for (int f = 0; f < n_payload; ++f) {
+  Q.build_npay = B.n_payload;
+  for (int i = 0; i < B.n_preds; ++i) {
     int idx;
-    if ((st = cs.add(payload_cols[f], &idx))) return st;
-    const Column& pc = c->cols[payload_cols[f]];
-    if (pc.codec != C_DICT) return fail(DPF_EINVAL, "payload column %d must be DICT", payload_cols[f]);
-    Q.build_pay[f] = idx;
-    ht.pay_dom[f] = uint32_t(pc.dict.size());
-    ht.pay_dict[f] = pc.d_dict;
+    if ((st = cs.add(B.preds[i].col, &idx))) return st;
+    if ((st = compile_pred(c->cols[B.preds[i].col], B.preds[i], Q.steps[i], idx))) return st;
   }
-  for (int i = 0; i < n_preds; ++i) {
+  std::vector<const HashTable*> probed;
+  for (int j = 0; j < B.n_joins; ++j) {
+    const dpf_join& J = B.joins[j];
+    auto it = c->hts.find(J.ht);
+    if (it == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", J.ht);
     int idx;
-    if ((st = cs.add(preds[i].col, &idx))) return st;
-    if ((st = compile_pred(c->cols[preds[i].col], preds[i], Q.steps[i], idx))) return st;
+    if ((st = cs.add(J.fk_col, &idx))) return st;
+    const int codec = c->cols[J.fk_col].codec;
+    if (codec != C_FOR && codec != C_DELTA) return fail(DPF_EINVAL, "join column %d must be FOR or DELTA", J.fk_col);
+    const HashTable& H = it->second;
+    DevStep& S = Q.steps[B.n_preds + j];
+    std::memset(&S, 0, sizeof S);
+    S.kind = ST_PROBE;
+    S.col = uint8_t(idx);
+    S.ht_kind = uint8_t(H.kind);
+    if (H.kind == HT_DIRECT) {
+      S.ht = H.direct;
+      S.kmin = H.kmin;
+      S.krange = H.capacity;
+    } else {
+      S.ht = H.slots;
+      S.ht_mask = H.capacity - 1;
+    }
+    S.zlo = H.key_lo;
+    S.zhi = H.key_hi;
+    probed.push_back(&H);
   }
-  Q.nsteps = uint32_t(n_preds);
+  for (int f = 0; f < B.n_payload; ++f) {
+    const dpf_payload& F = B.payload[f];
+    if (F.kind == DPF_PAYLOAD_COLUMN) {
+      int idx;
+      if ((st = cs.add(F.col, &idx))) return st;
+      const Column& pc = c->cols[F.col];
+      if (pc.codec != C_DICT) return fail(DPF_EINVAL, "payload column %d must be DICT", F.col);
+      Q.build_pay[f] = idx;
+      ht.pay_dom[f] = uint32_t(pc.dict.size());
+      ht.pay_dict[f] = pc.d_dict;
+    } else if (F.kind == DPF_PAYLOAD_JOIN) {
+      if (F.join < 0 || F.join >= B.n_joins) return fail(DPF_EINVAL, "payload field %d names join %d", f, F.join);
+      const HashTable& H = *probed[size_t(F.join)];
+      if (F.field < 0 || F.field >= H.npay) return fail(DPF_EINVAL, "hash table %d has no payload field %d", H.id, F.field);
+      // the build kernel decodes -1 - (2 * step + field)
+      Q.build_pay[f] = -1 - (2 * (B.n_preds + F.join) + F.field);
+      ht.pay_dom[f] = H.pay_dom[F.field];
+      ht.pay_dict[f] = H.pay_dict[F.field];
+    } else {
+      return fail(DPF_EINVAL, "unknown payload kind %d", F.kind);
+    }
+  }
+  Q.nsteps = uint32_t(B.n_preds + B.n_joins);
   Q.nrows = cs.nrows;
   Q.page_rows = cs.page_rows;
   DevQuery* dq;
@@ -1333,7 +1377,7 @@ dpf_status dpf_build_hash(dpf_ctx* c, dpf_col_id key_col, const dpf_col_id* payl
     ht.key_lo = minmax[0];
     ht.key_hi = minmax[1];
   }
-  const bool wide_payload = n_payload == 2 && ht.pay_dom[0] == 65536 && ht.pay_dom[1] == 65536;
+  const bool wide_payload = B.n_payload == 2 && ht.pay_dom[0] == 65536 && ht.pay_dom[1] == 65536;
   if (!wide_payload && range <= std::max<uint64_t>(64 * kept, 1u << 20) && range <= (1u << 26)) {
     ht.kind = HT_DIRECT;
     ht.kmin = kept ? minmax[0] : 0;
@@ -1371,6 +1415,28 @@ dpf_status dpf_build_hash(dpf_ctx* c, dpf_col_id key_col, const dpf_col_id* payl
   c->hts[ht.id] = ht;
   *out = ht.id;
   return cleanup(DPF_OK);
+}
+
+dpf_status dpf_build_hash(dpf_ctx* c, dpf_col_id key_col, const dpf_col_id* payload_cols, int32_t n_payload,
+                          const dpf_pred* preds, int32_t n_preds, void* stream, dpf_ht_id* out) {
+  if (n_payload < 0 || n_payload > 2 || (n_payload && !payload_cols)) return fail(DPF_EINVAL, "0..2 payload columns");
+  dpf_payload pay[2] = {};
+  for (int f = 0; f < n_payload; ++f) {
+    pay[f].kind = DPF_PAYLOAD_COLUMN;
+    pay[f].col = payload_cols[f];
+  }
+  dpf_build B{};
+  B.key_col = key_col;
+  B.n_payload = n_payload;
+  B.payload = pay;
+  B.n_preds = n_preds;
+  B.preds = preds;
+  return build_hash_impl(c, B, stream, out);
+}
+
+dpf_status dpf_build_hash_probe(dpf_ctx* c, const dpf_build* spec, void* stream, dpf_ht_id* out) {
+  if (!spec) return fail(DPF_EINVAL, "NULL build description");
+  return build_hash_impl(c, *spec, stream, out);
 }
 
 dpf_status dpf_hash_info(dpf_ctx* c, dpf_ht_id id, uint64_t* entries, uint64_t* capacity) {

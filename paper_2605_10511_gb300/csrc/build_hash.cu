@@ -1,15 +1,52 @@
-// Dimension scan + hash build (Kernel #1 of Sec. 3.1: scan, filter, build).
+// Table scan + hash build (Kernel #1 of Sec. 3.1: scan, filter, build) and
+// scan + probe + build (Kernel #2: the scan also probes tables built
+// earlier, so a chain of joins is built table by table).
 //
-// The dimension's columns are decoded tile by tile with the same warp tiles
-// as the fused kernel; rows passing the dimension predicates are either
-// counted (first pass, sizes the table) or inserted (second pass) into an
-// open-addressing table with linear probing.  A slot is one 64-bit word
+// The table's columns are decoded tile by tile with the same warp tiles as
+// the fused kernel, and its steps (predicates, then probes of earlier
+// tables, all in global memory) run the same dense first step and survivor
+// list code.  Rows that pass are either counted (first pass, sizes the
+// table) or inserted (second pass) into an open-addressing table with
+// linear probing or a direct table.  An open slot is one 64-bit word
 // {key, payload} claimed with a single compare-and-swap; the payload packs
-// the dictionary codes of up to two payload columns (16 bits each).
+// two 16-bit fields.
+//
+// Payload field f comes from Q.build_pay[f]: a value >= 0 is the index of
+// a DICT column of the scanned table (the field is its code); a value < 0
+// encodes code = -1 - build_pay[f], and the field is payload field
+// (code & 1) of the row's match in the table probed by step (code >> 1).
 #include "tile.cuh"
 
 namespace dpf {
 namespace {
+
+// Payload field f of a kept row (warp-uniform call; lanes with !valid
+// return 0).  A probe step's match is looked up again here; the row passed
+// that step, so a miss means a corrupt table and sets S_INTERNAL.
+template <bool kHost>
+__device__ __forceinline__ uint32_t build_payload(const DevQuery& Q, int f, const PageState& P, uint32_t i0,
+                                                  uint32_t r, bool valid, int lane, unsigned int* status) {
+  const int32_t src = Q.build_pay[f];
+  if (src >= 0) return row_value<kHost>(Q, src, P, i0, r, valid, lane, status);
+  const uint32_t code = uint32_t(-1 - src);
+  const DevStep& S = Q.steps[code >> 1];
+  const uint32_t key = row_value<kHost>(Q, S.col, P, i0, r, valid, lane, status);
+  if (!valid) return 0u;
+  uint32_t pay = 0;
+  bool hit;
+  if (S.ht_kind == HT_DIRECT) {
+    const uint32_t off = key - uint32_t(S.kmin);
+    pay = off < S.krange ? __ldg(static_cast<const uint32_t*>(S.ht) + off) : kAbsent;
+    hit = pay != kAbsent;
+  } else {
+    hit = int32_t(key) != kEmptyKey && ht_probe(static_cast<const uint2*>(S.ht), S.ht_mask, int32_t(key), &pay, status);
+  }
+  if (!hit) {
+    atomicOr(status, S_INTERNAL);
+    return 0u;
+  }
+  return (code & 1u) ? pay >> 16 : pay & 0xffffu;
+}
 
 constexpr unsigned long long kEmptySlot = 0x0000000080000000ull;  // {INT32_MIN, 0}
 
@@ -52,8 +89,8 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
       const bool valid = j0 + lane < n;
       const uint32_t r = valid ? (list[j0 + lane] & ((1u << kRowBits) - 1u)) : 0u;
       const int32_t kv = int32_t(row_value<kHost>(Q, Q.build_key, P, i0, r, valid, lane, status));
-      const uint32_t c0 = Q.build_npay > 0 ? row_value<kHost>(Q, Q.build_pay[0], P, i0, r, valid, lane, status) : 0u;
-      const uint32_t c1 = Q.build_npay > 1 ? row_value<kHost>(Q, Q.build_pay[1], P, i0, r, valid, lane, status) : 0u;
+      const uint32_t c0 = kMode != 0 && Q.build_npay > 0 ? build_payload<kHost>(Q, 0, P, i0, r, valid, lane, status) : 0u;
+      const uint32_t c1 = kMode != 0 && Q.build_npay > 1 ? build_payload<kHost>(Q, 1, P, i0, r, valid, lane, status) : 0u;
       if (!valid) continue;
       if (kMode == 0) {
         ++kept;

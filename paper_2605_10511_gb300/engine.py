@@ -2,8 +2,9 @@
 into plans (argument marshalling only; the work is done by the library).
 
 A query description has the form documented in ``synth.tables``: fact
-predicates, equi-joins against dimension tables (with dimension predicates
-and payload columns), up to two group keys and up to four aggregates.
+predicates, equi-joins against dimension tables (with dimension predicates,
+payload columns and, for a chain, joins of the dimension itself), up to two
+group keys and up to four aggregates.
 """
 
 from __future__ import annotations
@@ -60,17 +61,29 @@ class Engine:
         return total, w["tables"][w["fact"]]["rows"]
 
     # ------------------------------------------------------------------ planning
+    def build_join(self, w, j, stream=None):
+        """Builds (or reuses) the hash table of join ``j``.  A join with
+        joins of its own (a chain) has those built first; its table is then
+        built by scanning its dimension and probing theirs."""
+        sig = (w["name"], repr(j))
+        if sig not in self.hts:
+            d = j["dim"]
+            preds = [make_pred(self.col(w, d, p["col"]), p["op"], p["args"]) for p in j["preds"]]
+            subs = j.get("joins", [])
+            if not subs and all(isinstance(c, str) for c in j["payload"]):
+                pay = [self.col(w, d, c) for c in j["payload"]]
+                self.hts[sig] = self.ctx.build_hash(self.col(w, d, j["key"]), pay, preds, stream)
+            else:
+                sub_hts = [(self.col(w, d, s["fk"]), self.build_join(w, s, stream)) for s in subs]
+                pay = [("join", c["join"], c["field"]) if isinstance(c, dict) else self.col(w, d, c)
+                       for c in j["payload"]]
+                self.hts[sig] = self.ctx.build_hash_probe(self.col(w, d, j["key"]), pay, preds, sub_hts,
+                                                          stream)
+        return self.hts[sig]
+
     def build_joins(self, w, stream=None):
         """Builds (or reuses) the hash table of every join of ``w``'s query."""
-        out = []
-        for j in w["query"]["joins"]:
-            sig = (w["name"], j["dim"], j["key"], repr(j["preds"]), tuple(j["payload"]))
-            if sig not in self.hts:
-                preds = [make_pred(self.col(w, j["dim"], p["col"]), p["op"], p["args"]) for p in j["preds"]]
-                pay = [self.col(w, j["dim"], c) for c in j["payload"]]
-                self.hts[sig] = self.ctx.build_hash(self.col(w, j["dim"], j["key"]), pay, preds, stream)
-            out.append(self.hts[sig])
-        return out
+        return [self.build_join(w, j, stream) for j in w["query"]["joins"]]
 
     def plan(self, w, stream=None):
         q = w["query"]

@@ -10,9 +10,11 @@ each with its own code.
 from .tables import (  # noqa: F401
     ALPHABET,
     batched_workloads,
+    chain_join,
     date_keys,
     scan_filter_aggregate,
     star_join,
     strings,
+    tiny_chain_workload,
     tiny_random_workload,
 )

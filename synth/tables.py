@@ -18,14 +18,19 @@ A *query* is a description of the SQL it stands for::
     {"preds":  [{"col": c, "op": op, "args": [...]}, ...],   # on the fact table
      "joins":  [{"fk": c, "dim": t, "key": c,
                  "preds": [...],                              # on the dimension
-                 "payload": [c, ...]}, ...],                  # dimension columns carried
+                 "payload": [c | {"join": s, "field": f}, ...],
+                 "joins": [join, ...]}, ...],                 # optional: a chain
      "group":  [{"col": c} | {"join": j, "field": f}, ...],   # <= 2 keys
      "aggs":   [{"op": "count"} | {"op": "sum", "cols": [a]}
                 | {"op": "sum_mul", "cols": [a, b]}
                 | {"op": "sum_sub", "cols": [a, b]}, ...]}    # <= 4
 
-Predicate ops: ``lt le gt ge eq ne between in prefix`` (``between`` is
-inclusive at both ends; ``prefix`` takes one ``bytes`` argument).
+Predicate ops: ``lt le gt ge eq ne between in prefix contains`` (``between``
+is inclusive at both ends; ``prefix`` and ``contains`` take one ``bytes``
+argument).  A join's own ``joins`` (same form, ``fk`` a column of its
+dimension) make a chain: the dimension's rows must match them too, and a
+payload item ``{"join": s, "field": f}`` carries field f of the row's match
+in sub join s.
 
 Shapes, sizes and value distributions follow the workloads the method is
 evaluated on: star-schema fact tables with uniform foreign keys into small
@@ -62,6 +67,15 @@ def date_keys(first=datetime.date(1992, 1, 1), days=2556):
 
 def _int_col(values, codec="for"):
     return {"codec": codec, "values": np.ascontiguousarray(values, dtype=np.int32)}
+
+
+def _sparse_distinct(rng, count, lo, hi):
+    """``count`` distinct sorted int32 values drawn from a wide range [lo, hi)
+    (draws with replacement, drops repeats, draws again while short)."""
+    vals = np.unique(rng.integers(lo, hi, int(count * 1.05) + 64, dtype=np.int64))
+    while vals.size < count:
+        vals = np.unique(np.concatenate([vals, rng.integers(lo, hi, count, dtype=np.int64)]))
+    return np.sort(rng.permutation(vals)[:count]).astype(np.int32)
 
 
 def _distinct_values(rng, count, lo, hi):
@@ -190,6 +204,178 @@ def star_join(rows=1 << 26, seed=2, page_rows=DEFAULT_PAGE_ROWS, clustered=True,
         # the fact tables are the same as without it
         query["joins"][3]["preds"] = [{"col": "year", "op": "eq", "args": [int(date_year)]}]
     return {"name": name, "tables": tables, "fact": "fact", "query": query}
+
+
+# ---------------------------------------------------------------------------
+# Workload 2b: a chain of joins, LINEITEM -> ORDERS -> CUSTOMER
+# ---------------------------------------------------------------------------
+
+def chain_join(rows=1 << 26, seed=5, page_rows=DEFAULT_PAGE_ROWS, orders_per_row=0.25,
+               customers_per_order=0.1, sparse_orderkeys=False, segment=None):
+    """Three tables shaped like TPC-H's LINEITEM, ORDERS and CUSTOMER.
+
+    ORDERS has ``rows * orders_per_row`` rows with unique order keys drawn
+    from [1, 4 x orders] (TPC-H uses a quarter of its key space), uniform
+    customer keys, order dates over the seven-year date range and five
+    priorities.  CUSTOMER has ``orders * customers_per_order`` rows with
+    five market segments and 25 nations.  LINEITEM rows are sorted by order
+    key (about four per order, Poisson) and stored delta-coded, as a table
+    loaded in order-key order would be; ship dates fall 1..121 days after
+    the order date.  With ``sparse_orderkeys`` the order keys spread over
+    the positive int32 range (an open-addressing ORDERS table).
+
+    The query (TPC-H Q3-shaped, grouped on small keys):
+        SELECT c_nation, o_priority, COUNT(*), SUM(l_price),
+               SUM(l_price * l_discount)
+        FROM lineitem JOIN orders ON l_orderkey = o_orderkey
+                      JOIN customer ON o_custkey = c_custkey
+        WHERE c_segment = S AND o_orderdate < D AND l_shipdate > D
+        GROUP BY c_nation, o_priority
+    as a chain: CUSTOMER's table is probed by the ORDERS scan, whose table
+    carries c_nation and o_priority to the LINEITEM scan.
+    """
+    rng = _rng(seed)
+    n_orders = max(int(rows * orders_per_row), 1)
+    n_cust = max(int(n_orders * customers_per_order), 1)
+    dk = date_keys()
+    seg_vals = _distinct_values(rng, 5, 0, 100)
+    nation_vals = np.arange(25, dtype=np.int32)
+    customer = {"rows": n_cust, "page_rows": page_rows, "cols": {
+        "c_custkey": _int_col(rng.permutation(np.arange(1, n_cust + 1, dtype=np.int32))),
+        "c_segment": _int_col(seg_vals[rng.integers(0, 5, n_cust)], "dict"),
+        "c_nation": _int_col(nation_vals[rng.integers(0, 25, n_cust)], "dict"),
+    }}
+    if sparse_orderkeys:
+        okeys = _sparse_distinct(rng, n_orders, 1, 2**31 - 1)
+    else:
+        okeys = np.sort(rng.choice(np.arange(1, 4 * n_orders + 1, dtype=np.int32), n_orders, replace=False))
+    n_orders = int(okeys.size)
+    o_date_idx = rng.integers(0, dk.size - 151, n_orders)
+    prio_vals = np.arange(1, 6, dtype=np.int32)
+    operm = rng.permutation(n_orders)  # ORDERS is not stored in key order
+    orders = {"rows": n_orders, "page_rows": page_rows, "cols": {
+        "o_orderkey": _int_col(okeys[operm]),
+        "o_custkey": _int_col(rng.integers(1, n_cust + 1, n_orders, dtype=np.int32)),
+        "o_orderdate": _int_col(dk[o_date_idx[operm]]),
+        "o_priority": _int_col(prio_vals[rng.integers(0, 5, n_orders)], "dict"),
+    }}
+    l_idx = np.sort(rng.integers(0, n_orders, rows).astype(np.int32))
+    lineitem = {"rows": rows, "page_rows": page_rows, "cols": {
+        "l_orderkey": _int_col(okeys[l_idx], "delta"),
+        "l_shipdate": _int_col(dk[o_date_idx[l_idx] + rng.integers(1, 122, rows)]),
+        "l_price": _int_col(rng.integers(90_000, 10_500_001, rows, dtype=np.int32)),
+        "l_discount": _int_col(rng.integers(0, 11, rows, dtype=np.int32)),
+    }}
+    seg = int(seg_vals[int(rng.integers(0, 5))] if segment is None else segment)
+    cut = int(dk[int(dk.size * 0.45)])  # about 1995-03-15, as in TPC-H Q3
+    query = {
+        "preds": [{"col": "l_shipdate", "op": "gt", "args": [cut]}],
+        "joins": [{"fk": "l_orderkey", "dim": "orders", "key": "o_orderkey",
+                   "preds": [{"col": "o_orderdate", "op": "lt", "args": [cut]}],
+                   "payload": [{"join": 0, "field": 0}, "o_priority"],
+                   "joins": [{"fk": "o_custkey", "dim": "customer", "key": "c_custkey",
+                              "preds": [{"col": "c_segment", "op": "eq", "args": [seg]}],
+                              "payload": ["c_nation"]}]}],
+        "group": [{"join": 0, "field": 0}, {"join": 0, "field": 1}],
+        "aggs": [{"op": "count"}, {"op": "sum", "cols": ["l_price"]},
+                 {"op": "sum_mul", "cols": ["l_price", "l_discount"]}],
+    }
+    name = f"chain_join_{rows}{'_sparse' if sparse_orderkeys else ''}"
+    return {"name": name, "tables": {"customer": customer, "orders": orders, "lineitem": lineitem},
+            "fact": "lineitem", "query": query}
+
+
+def tiny_chain_workload(seed, rows=None, page_rows=None, max_dim_rows=None):
+    """A random small chain (fact -> mid -> leaf, sometimes -> leaf2 below
+    leaf, sometimes a second table probed by mid) with random predicates,
+    payload sources, dense or sparse keys and empty results.
+    ``max_dim_rows`` caps every table below the fact (and the fact at four
+    times that), for evaluators that search row by row."""
+    rng = _rng(5000 + seed)
+    if page_rows is None:
+        page_rows = int(rng.choice([128, 256, 1024]))
+    if rows is None:
+        rows = int(rng.integers(1, 5 * page_rows))
+    cap = (lambda n: n) if max_dim_rows is None else (lambda n: max(1, min(n, max_dim_rows)))
+    if max_dim_rows is not None:
+        rows = min(rows, 4 * max_dim_rows)
+
+    def keys(n):
+        if rng.integers(0, 3) == 0:  # sparse: an open-addressing table
+            return rng.permutation(_sparse_distinct(rng, n, -(2**31) + 1, 2**31 - 1))
+        return rng.permutation(np.arange(1, n + 1, dtype=np.int32) * int(rng.integers(1, 4)))
+
+    def table(n, extra):
+        cols = {"k": _int_col(keys(n), "for"),
+                "A": _int_col(rng.integers(0, 6, n, dtype=np.int32) * 5 - 7, "dict"),
+                "B": _int_col(rng.integers(0, 3, n, dtype=np.int32) + 40, "dict"),
+                "x": _int_col(rng.integers(-50, 51, n, dtype=np.int32), "delta" if rng.integers(0, 2) else "for")}
+        cols.update(extra)
+        return {"rows": n, "page_rows": page_rows, "cols": cols}
+
+    def fk_into(tab, n):
+        k = tab["cols"]["k"]["values"]
+        miss = int(k.max()) + 1 if k.max() < 2**31 - 1 else int(k.min()) - 1
+        pool = np.append(k, np.int32(miss))  # one key that never matches
+        return pool[rng.integers(0, pool.size, n)].astype(np.int32)
+
+    def dpreds():
+        out = []
+        if rng.integers(0, 2):
+            out.append({"col": "x", "op": str(rng.choice(["lt", "ge", "between"])),
+                        "args": sorted(int(v) for v in rng.integers(-60, 61, 2))})
+            if out[-1]["op"] != "between":
+                out[-1]["args"] = out[-1]["args"][:1]
+        if rng.integers(0, 3) == 0:
+            out.append({"col": "A", "op": "ne", "args": [int(rng.integers(0, 6)) * 5 - 7]})
+        return out
+
+    n_leaf = cap(int(rng.integers(1, 400)))
+    leaf = table(n_leaf, {})
+    tables = {"leaf": leaf}
+    leaf_join = {"fk": "fk_leaf", "dim": "leaf", "key": "k", "preds": dpreds(),
+                 "payload": [str(c) for c in rng.choice(["A", "B"], int(rng.integers(0, 3)), replace=False)]}
+    if rng.integers(0, 3) == 0:  # a deeper chain: leaf itself probes leaf2
+        n2 = cap(int(rng.integers(1, 200)))
+        tables["leaf2"] = table(n2, {})
+        leaf["cols"]["fk_leaf2"] = _int_col(fk_into(tables["leaf2"], n_leaf), "for")
+        leaf_join["joins"] = [{"fk": "fk_leaf2", "dim": "leaf2", "key": "k", "preds": dpreds(),
+                               "payload": ["B"]}]
+        if rng.integers(0, 2) and len(leaf_join["payload"]) < 2:
+            leaf_join["payload"].append({"join": 0, "field": 0})
+    n_mid = cap(int(rng.integers(1, 1500)))
+    mid = table(n_mid, {"fk_leaf": _int_col(fk_into(leaf, n_mid), "delta" if rng.integers(0, 2) else "for")})
+    tables["mid"] = mid
+    mid_joins = [leaf_join]
+    if rng.integers(0, 3) == 0:  # mid probes two tables
+        n_side = cap(int(rng.integers(1, 100)))
+        tables["side"] = table(n_side, {})
+        mid["cols"]["fk_side"] = _int_col(fk_into(tables["side"], n_mid), "for")
+        mid_joins.append({"fk": "fk_side", "dim": "side", "key": "k", "preds": dpreds(), "payload": ["A"]})
+    pay_choices = [{"join": s, "field": f} for s, j in enumerate(mid_joins) for f in range(len(j["payload"]))]
+    pay_choices += ["A", "B"]
+    npay = int(rng.integers(0, 3))
+    mid_pay = [pay_choices[i] for i in rng.choice(len(pay_choices), min(npay, len(pay_choices)), replace=False)]
+    fact = {"rows": rows, "page_rows": page_rows, "cols": {
+        "fk_mid": _int_col(np.sort(fk_into(mid, rows)) if rng.integers(0, 2) else fk_into(mid, rows),
+                           "delta" if rng.integers(0, 2) else "for"),
+        "m": _int_col(rng.integers(-1000, 1001, rows, dtype=np.int32)),
+        "g": _int_col(rng.integers(0, 4, rows, dtype=np.int32), "dict"),
+    }}
+    tables["fact"] = fact
+    preds = []
+    if rng.integers(0, 2):
+        preds.append({"col": "m", "op": "gt", "args": [int(rng.integers(-1000, 1001))]})
+    mid_join = {"fk": "fk_mid", "dim": "mid", "key": "k", "preds": dpreds(), "payload": mid_pay,
+                "joins": mid_joins}
+    group = []
+    for f in rng.permutation(len(mid_pay))[:int(rng.integers(0, 3))]:
+        group.append({"join": 0, "field": int(f)})
+    if len(group) < 2 and rng.integers(0, 2):
+        group.append({"col": "g"})
+    aggs = [{"op": "count"}, {"op": "sum", "cols": ["m"]}]
+    query = {"preds": preds, "joins": [mid_join], "group": group, "aggs": aggs}
+    return {"name": f"tiny_chain_{seed}", "tables": tables, "fact": "fact", "query": query}
 
 
 # ---------------------------------------------------------------------------

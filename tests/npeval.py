@@ -2,7 +2,8 @@
 
 It reads the raw generated arrays (never any encoded page) and evaluates the
 same SQL with vectorised library routines: boolean masks for predicates,
-``np.searchsorted`` over the sorted build keys for the equi-joins,
+``np.searchsorted`` over the sorted build keys for the equi-joins (applied
+recursively to a dimension that is itself joined: a chain),
 ``np.unique(..., return_inverse=True)`` for grouping and ``np.add.at`` /
 ``np.bincount`` for the int64 aggregates.  It shares nothing with the C++
 oracle beyond the query description.
@@ -62,6 +63,36 @@ def _pred_mask(cols, pred, n):
     raise ValueError(op)
 
 
+def _probe(workload, j, fk):
+    """Equi-join of the probe keys ``fk`` with join ``j``'s build side:
+    (hit mask, payload arrays aligned with ``fk``).  The build side is the
+    dimension's rows passing its predicates and matching every sub join of
+    ``j`` (a chain), its payloads taken from its columns or from those
+    sub joins' payloads."""
+    dim = workload["tables"][j["dim"]]
+    dc = dim["cols"]
+    dm = np.ones(dim["rows"], bool)
+    for p in j["preds"]:
+        dm &= _pred_mask(dc, p, dim["rows"])
+    sub_pay = []
+    for s in j.get("joins", []):
+        h, pay = _probe(workload, s, dc[s["fk"]]["values"].astype(np.int64))
+        dm &= h
+        sub_pay.append(pay)
+    pay_cols = []
+    for pc in j["payload"]:
+        pay_cols.append(sub_pay[pc["join"]][pc["field"]] if isinstance(pc, dict) else dc[pc]["values"])
+    keys = dc[j["key"]]["values"][dm].astype(np.int64)
+    order = np.argsort(keys, kind="stable")
+    skeys = keys[order]
+    assert np.all(skeys[1:] != skeys[:-1]), "duplicate build keys"
+    pos = np.searchsorted(skeys, fk)
+    pos_c = np.minimum(pos, max(skeys.size - 1, 0))
+    hit = (skeys[pos_c] == fk) if skeys.size else np.zeros(fk.size, bool)
+    pay = [np.asarray(v)[dm][order][pos_c] if skeys.size else np.zeros(fk.size, np.int32) for v in pay_cols]
+    return hit, pay
+
+
 def evaluate(workload):
     q = workload["query"]
     fact = workload["tables"][workload["fact"]]
@@ -72,21 +103,8 @@ def evaluate(workload):
         mask &= _pred_mask(fc, p, n)
     payloads = []
     for j in q["joins"]:
-        dim = workload["tables"][j["dim"]]
-        dm = np.ones(dim["rows"], bool)
-        for p in j["preds"]:
-            dm &= _pred_mask(dim["cols"], p, dim["rows"])
-        keys = dim["cols"][j["key"]]["values"][dm].astype(np.int64)
-        order = np.argsort(keys, kind="stable")
-        skeys = keys[order]
-        assert np.all(skeys[1:] != skeys[:-1]), "duplicate build keys"
-        fk = fc[j["fk"]]["values"].astype(np.int64)
-        pos = np.searchsorted(skeys, fk)
-        pos_c = np.minimum(pos, max(skeys.size - 1, 0))
-        hit = (skeys.size > 0) & (skeys[pos_c] == fk) if skeys.size else np.zeros(n, bool)
+        hit, pay = _probe(workload, j, fc[j["fk"]]["values"].astype(np.int64))
         mask &= hit
-        pay = [dim["cols"][pc]["values"][dm][order][pos_c] if skeys.size else np.zeros(n, np.int32)
-               for pc in j["payload"]]
         payloads.append(pay)
     sel = np.nonzero(mask)[0]
     kcols = []

@@ -43,6 +43,14 @@ MUTANTS = {
     "empty_ungrouped_dropped": ("if (nkeys == 0 && groups.empty()) groups.emplace",
                                 "if (false) groups.emplace"),
     "string_start_ignored": ("uint64_t s = start;", "uint64_t s = 0;"),
+    "chain_sub_preds_skipped": ("for (int32_t k = 0; k < J.npreds && ok; ++k) ok = eval_pred(*J.dim, J.preds[k], r);",
+                                "for (int32_t k = 0; k < J.npreds && ok && depth == 0; ++k) ok = eval_pred(*J.dim, J.preds[k], r);"),
+    "chain_sub_field_ignored": ("(*hit[size_t(J.pay_join[f])])[size_t(J.pay_field[f])]",
+                                "(*hit[size_t(J.pay_join[f])])[0]"),
+    "chain_payload_always_column": ("J.pay_join[f] < 0 ? J.dim->cols[J.pay_cols[f]].v[r]",
+                                    "true ? J.dim->cols[J.pay_cols[f]].v[r]"),
+    "chain_probes_own_key": ("auto it = subs[size_t(s)].find(J.dim->cols[J.sub[s].fk_col].v[r]);",
+                             "auto it = subs[size_t(s)].find(J.dim->cols[J.key_col].v[r]);"),
     "dict_rank_off_by_one": ("std::lower_bound(dict.begin(), dict.end(), values[r]) - dict.begin();",
                              "std::upper_bound(dict.begin(), dict.end(), values[r]) - dict.begin();"),
 }
@@ -79,6 +87,13 @@ def _pins_pass(o):
                 assert np.array_equal(g["key"], e["key"]), seed
                 assert np.array_equal(g["count"], e["count"]), seed
                 assert np.array_equal(g["val"], e["val"]), seed
+        for seed in range(40):
+            w = synth.tiny_chain_workload(seed)
+            e = npeval.evaluate(w)
+            g = o.run_query(w, from_encoded=bool(seed % 2))
+            assert g.shape == e.shape, ("chain", seed)
+            for f in ("key", "count", "val"):
+                assert np.array_equal(g[f], e[f]), ("chain", seed, f)
         w = synth.strings(rows=3000, seed=5, page_rows=1024)
         w["query"]["preds"] = [{"col": "s", "op": "prefix", "args": [b"a" * 45]}]
         w["query"]["group"] = []
