@@ -89,6 +89,8 @@ def _workload(name, rows):
         return synth.star_join(rows=rows or (1 << 26), clustered=True, date_year=1994)
     if name == "star_year_unsorted":
         return synth.star_join(rows=rows or (1 << 26), clustered=False, date_year=1994)
+    if name == "star_bigint":  # the measure as a BIGINT (FOR64) column
+        return synth.star_join(rows=rows or (1 << 26), clustered=True, bigint_measure=True)
     if name == "scan":
         return synth.scan_filter_aggregate(rows=rows or (1 << 20))
     # NEXT-3: LINEITEM -> ORDERS -> CUSTOMER (scan+build, scan+probe+build, fused)
@@ -412,7 +414,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="dpf", choices=["dpf", "reference"])
     ap.add_argument("--workload", default="star",
-                    choices=["star", "star_unsorted", "star_year", "star_year_unsorted", "scan", "strings",
+                    choices=["star", "star_unsorted", "star_year", "star_year_unsorted", "star_bigint", "scan",
+                             "strings",
                              "strings_text", "strings_fsst", "chain", "chain_sparse", "batched"])
     ap.add_argument("--batch-queries", type=int, default=64)
     ap.add_argument("--serve", action="store_true", help="Poisson serving run instead of the step benchmark")

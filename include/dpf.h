@@ -90,11 +90,16 @@ enum dpf_codec {
                           FOR-packed ranks (Sec. 3.4.1, short CHAR as integers)       */
   DPF_CODEC_STR = 4,   /* bytes: FOR-packed lengths + per-mini-block start + raw bytes
                           (Sec. 3.4.2 variable-length page)                           */
-  DPF_CODEC_FSST = 5   /* bytes: FSST-encoded strings (Sec. 3.4.2, Sec. 4.1) in the STR
+  DPF_CODEC_FSST = 5,  /* bytes: FSST-encoded strings (Sec. 3.4.2, Sec. 4.1) in the STR
                           page layout.  A column table of <= 255 symbols of 1..8 bytes;
                           code c < nsym stands for symbol c, code 255 for the literal
                           byte that follows.  The table travels in the dict arrays as
                           nsym int32 triples {bytes 0..3, bytes 4..7, length}         */
+  DPF_CODEC_FOR64 = 6  /* int64 (BIGINT): 64-bit GPU-FOR (Sec. 4.1): per mini block an
+                          int64 base, a bit width 0..64 and 2*bw packed 64-bit words,
+                          field j at bit j*bw (a field may cross into the next word).
+                          A plan reads FOR64 columns as aggregate operands (int64,
+                          wrapping); predicates, joins and keys take 32-bit columns */
 };
 /* Where a column's pages live: device HBM, or pinned host memory read by
  * the kernel directly through the host link (oversize tables). */
@@ -109,7 +114,8 @@ typedef struct dpf_column_desc {
 } dpf_column_desc;
 
 /* Host-side encoder (the data loader of Sec. 4.2), no device work.
- *   values: host int32[nrows] (FOR/DELTA/DICT) or host bytes (STR/FSST)
+ *   values: host int32[nrows] (FOR/DELTA/DICT), int64[nrows] (FOR64) or
+ *           host bytes (STR/FSST)
  *   str_offsets: host uint64[nrows+1] byte offsets into values (STR/FSST
  *                only, str_offsets[0] may be non-zero), else NULL
  *   out: host buffer of `cap` bytes for the page images, or NULL to size
@@ -141,8 +147,9 @@ dpf_status dpf_load_encoded(dpf_ctx* ctx, const dpf_column_desc* desc, const uin
 dpf_status dpf_load_column(dpf_ctx* ctx, const dpf_column_desc* desc, const void* values,
                            const uint64_t* str_offsets, uint64_t nrows, dpf_col_id* out);
 
-/* Rows, encoded bytes (page images) and raw bytes (4/row, or string bytes
- * + 8/row of offsets) of a loaded column; any out pointer may be NULL. */
+/* Rows, encoded bytes (page images) and raw bytes (4/row, 8/row for FOR64,
+ * or string bytes + 8/row of offsets) of a loaded column; any out pointer
+ * may be NULL. */
 dpf_status dpf_column_info(dpf_ctx* ctx, dpf_col_id col, uint64_t* rows,
                            uint64_t* encoded_bytes, uint64_t* raw_bytes);
 

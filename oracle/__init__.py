@@ -28,7 +28,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CODECS = {"for": 1, "delta": 2, "dict": 3, "str": 4, "fsst": 5}
+CODECS = {"for": 1, "delta": 2, "dict": 3, "str": 4, "fsst": 5, "for64": 6}
 STRING_CODECS = ("str", "fsst")
 PRED_OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7,
             "prefix": 8, "contains": 9}
@@ -51,7 +51,7 @@ def build(force=False):
 
 class _Column(C.Structure):
     _fields_ = [("is_str", C.c_int32), ("v", C.c_void_p), ("bytes", C.c_void_p),
-                ("offsets", C.c_void_p)]
+                ("offsets", C.c_void_p), ("v64", C.c_void_p)]
 
 
 class _Table(C.Structure):
@@ -97,6 +97,12 @@ def lib():
             L.orc_decode_int_row.restype = C.c_int64
             L.orc_decode_int_row.argtypes = [C.c_uint32, P, P, P, C.c_uint64, P, C.c_uint64,
                                              C.c_uint64, P]
+            L.orc_encode_for64.restype = C.c_int64
+            L.orc_encode_for64.argtypes = [P, C.c_uint64, C.c_uint32, P, C.c_uint64, P, P]
+            L.orc_decode_for64.restype = C.c_int64
+            L.orc_decode_for64.argtypes = [P, P, C.c_uint64, C.c_uint64, C.c_uint32, P]
+            L.orc_decode_for64_row.restype = C.c_int64
+            L.orc_decode_for64_row.argtypes = [P, P, P, C.c_uint64, C.c_uint64, P]
             L.orc_encode_str.restype = C.c_int64
             L.orc_encode_str.argtypes = [P, P, C.c_uint64, C.c_uint32, P, C.c_uint64, P, P]
             L.orc_decode_str.restype = C.c_int64
@@ -128,9 +134,9 @@ class use_library:
         global _lib
         self._saved = lib()
         L = C.CDLL(self.path)
-        for name in ("orc_encode_int", "orc_decode_int", "orc_decode_int_row",
-                     "orc_encode_str", "orc_decode_str", "orc_fsst_build", "orc_encode_fsst",
-                     "orc_decode_fsst", "orc_query"):
+        for name in ("orc_encode_int", "orc_decode_int", "orc_decode_int_row", "orc_encode_for64",
+                     "orc_decode_for64", "orc_decode_for64_row", "orc_encode_str", "orc_decode_str",
+                     "orc_fsst_build", "orc_encode_fsst", "orc_decode_fsst", "orc_query"):
             f, g = getattr(L, name), getattr(self._saved, name)
             f.restype, f.argtypes = g.restype, g.argtypes
         _lib = L
@@ -203,6 +209,19 @@ def encode_column(col, page_rows):
                                 _ptr(page_off), _ptr(row_prefix)), "encode_str")
         return {"codec": codec, "rows": n, "page_rows": page_rows, "blob": blob,
                 "page_off": page_off, "row_prefix": row_prefix, "dict": None}
+    if codec == "for64":
+        v = np.ascontiguousarray(col["values"], dtype=np.int64)
+        n = v.size
+        npages = (n + page_rows - 1) // page_rows
+        page_off = np.zeros(npages + 1, np.uint64)
+        row_prefix = np.zeros(npages, np.uint64)
+        size = _check(L.orc_encode_for64(_ptr(v), n, page_rows, None, 0, _ptr(page_off), _ptr(row_prefix)),
+                      "encode_for64")
+        blob = np.zeros(size, np.uint8)
+        _check(L.orc_encode_for64(_ptr(v), n, page_rows, _ptr(blob), size, _ptr(page_off), _ptr(row_prefix)),
+               "encode_for64")
+        return {"codec": codec, "rows": n, "page_rows": page_rows, "blob": blob,
+                "page_off": page_off, "row_prefix": row_prefix, "dict": None}
     v = np.ascontiguousarray(col["values"], dtype=np.int32)
     n = v.size
     npages = (n + page_rows - 1) // page_rows
@@ -244,6 +263,11 @@ def decode_column(enc):
                                 enc["page_rows"], _ptr(offsets), _ptr(data), data.size),
                "decode_str")
         return data[: int(offsets[-1])].copy(), offsets
+    if enc["codec"] == "for64":
+        out = np.zeros(n, np.int64)
+        _check(L.orc_decode_for64(_ptr(enc["blob"]), _ptr(enc["page_off"]), npages, n, enc["page_rows"],
+                                  _ptr(out)), "decode_for64")
+        return out
     out = np.zeros(n, np.int32)
     dct = enc["dict"]
     _check(L.orc_decode_int(CODECS[enc["codec"]], _ptr(enc["blob"]), _ptr(enc["page_off"]),
@@ -255,6 +279,11 @@ def decode_column(enc):
 def decode_row(enc, r):
     """Decode the single value at row ``r`` through the RID index."""
     L = lib()
+    if enc["codec"] == "for64":
+        out = np.zeros(1, np.int64)
+        _check(L.orc_decode_for64_row(_ptr(enc["blob"]), _ptr(enc["page_off"]), _ptr(enc["row_prefix"]),
+                                      enc["page_off"].size - 1, int(r), _ptr(out)), "decode_for64_row")
+        return int(out[0])
     out = np.zeros(1, np.int32)
     dct = enc["dict"]
     _check(L.orc_decode_int_row(CODECS[enc["codec"]], _ptr(enc["blob"]), _ptr(enc["page_off"]),
@@ -302,6 +331,11 @@ def _table(cols, n):
             arr[i].is_str = 1
             arr[i].bytes = _ptr(data) if data.size else offs.ctypes.data  # never read when empty
             arr[i].offsets = _ptr(offs)
+        elif np.asarray(c).dtype == np.int64:  # a 64-bit (FOR64) column
+            v = np.ascontiguousarray(c, np.int64)
+            keep.append(v)
+            arr[i].is_str = 0
+            arr[i].v64 = _ptr(v)
         else:
             v = np.ascontiguousarray(c, np.int32)
             keep.append(v)

@@ -6,7 +6,8 @@
 // storage-format definition (Sec. 3.4.1 fixed-length page layout with
 // mini blocks carrying a frame-of-reference base, a bit width and a byte
 // offset; Sec. 3.4.2 variable-length pages with a RID index that is a
-// prefix sum of per-page record counts; Sec. 4.1 integer decompression;
+// prefix sum of per-page record counts; Sec. 4.1 integer decompression,
+// 32-bit GPU-FOR and its 64-bit extension for BIGINT columns;
 // Sec. 4.2 data-loader metadata: page offsets and per-page row prefix).
 //
 // What it computes (Sec. 3.1, Kernels #1-#3): an exact relational result
@@ -40,7 +41,7 @@ namespace {
 constexpr uint32_t kMiniBlock = 128;           // values per mini block
 constexpr uint32_t kPageHeaderBytes = 16;      // magic|codec, nrows, payload_off, extra_off
 constexpr uint32_t kMagic = 0x00465044u;       // 'D' 'P' 'F' in the low three bytes
-enum Codec : uint32_t { FOR = 1, DELTA = 2, DICT = 3, STR = 4, FSST = 5 };
+enum Codec : uint32_t { FOR = 1, DELTA = 2, DICT = 3, STR = 4, FSST = 5, FOR64 = 6 };
 
 enum Status : int64_t {
   OK = 0,
@@ -313,6 +314,142 @@ int64_t orc_decode_int_row(uint32_t codec, const uint8_t* blob, const uint64_t* 
   }
   *out = int32_t(v);
   return OK;
+}
+
+// ---------------------------------------------------------------------------
+// 64-bit frame of reference (Sec. 4.1: GPU-FOR extended to BIGINT with 64-bit
+// reference values and bit positions taken modulo 64).  Per page: the page
+// header, one 16-byte header per mini block {base: int64, word offset: u32
+// counted in 8-byte words from the payload start, bit width: u32 in 0..64},
+// then the payload of 64-bit words.  Field j of a mini block holds x_j - base
+// (modulo 2^64) at bits [j*bw, (j+1)*bw) of its 2*bw words (128 fields of bw
+// bits fill exactly 2*bw words, so every mini block starts on a word), bit b
+// of the stream being bit b%64 of word b/64.
+// ---------------------------------------------------------------------------
+static void pack_bits64(const uint64_t* f, uint32_t bw, uint64_t* words) {
+  for (uint32_t w = 0; w < 2 * bw; ++w) words[w] = 0;
+  for (uint32_t j = 0; j < kMiniBlock; ++j)
+    for (uint32_t b = 0; b < bw; ++b)
+      if ((f[j] >> b) & 1u) {
+        const uint64_t bit = uint64_t(j) * bw + b;
+        words[bit / 64] |= uint64_t(1) << (bit % 64);
+      }
+}
+
+static uint64_t unpack_bits64(const uint64_t* words, uint32_t bw, uint32_t j) {
+  uint64_t v = 0;
+  for (uint32_t b = 0; b < bw; ++b) {
+    const uint64_t bit = uint64_t(j) * bw + b;
+    v |= ((words[bit / 64] >> (bit % 64)) & 1u) << b;
+  }
+  return v;
+}
+
+int64_t orc_encode_for64(const int64_t* values, uint64_t n, uint32_t page_rows, uint8_t* out, uint64_t cap,
+                         uint64_t* page_off, uint64_t* row_prefix) {
+  if (n == 0 || page_rows == 0 || page_rows % kMiniBlock != 0 || page_rows > (1u << 20)) return EINVAL;
+  const uint64_t npages = (n + page_rows - 1) / page_rows;
+  uint64_t off = 0;
+  for (uint64_t p = 0; p < npages; ++p) {
+    const uint64_t r0 = p * page_rows;
+    const uint32_t rows = uint32_t(std::min<uint64_t>(page_rows, n - r0));
+    const uint32_t nmb = (rows + kMiniBlock - 1) / kMiniBlock;
+    const uint32_t payload_off = uint32_t(align16(kPageHeaderBytes + uint64_t(nmb) * 16));
+    std::vector<int64_t> bases(nmb);
+    std::vector<uint32_t> bws(nmb);
+    uint64_t words = 0;
+    for (uint32_t m = 0; m < nmb; ++m) {
+      const uint64_t a = r0 + uint64_t(m) * kMiniBlock;
+      const uint32_t cnt = uint32_t(std::min<uint64_t>(kMiniBlock, r0 + rows - a));
+      int64_t mn = values[a], mx = values[a];
+      for (uint32_t j = 1; j < cnt; ++j) { mn = std::min(mn, values[a + j]); mx = std::max(mx, values[a + j]); }
+      bases[m] = mn;
+      bws[m] = bits_for_span(uint64_t(mx) - uint64_t(mn));
+      words += 2ull * bws[m];
+    }
+    if (words >= (1ull << 32)) return EINVAL;
+    const uint64_t page_bytes = align16(payload_off + words * 8);
+    if (page_off) page_off[p] = off;
+    if (row_prefix) row_prefix[p] = r0 + rows;
+    if (out) {
+      if (off + page_bytes > cap) return ETRUNC;
+      uint8_t* pg = out + off;
+      std::memset(pg, 0, page_bytes);
+      const uint32_t hdr[4] = {kMagic | (uint32_t(FOR64) << 24), rows, payload_off, 0};
+      std::memcpy(pg, hdr, sizeof hdr);
+      uint64_t* pay = reinterpret_cast<uint64_t*>(pg + payload_off);
+      uint32_t woff = 0;
+      std::vector<uint64_t> f(kMiniBlock);
+      for (uint32_t m = 0; m < nmb; ++m) {
+        const uint64_t a = r0 + uint64_t(m) * kMiniBlock;
+        const uint32_t cnt = uint32_t(std::min<uint64_t>(kMiniBlock, r0 + rows - a));
+        for (uint32_t j = 0; j < kMiniBlock; ++j)   // padding rows: offset 0
+          f[j] = j < cnt ? uint64_t(values[a + j]) - uint64_t(bases[m]) : 0;
+        pack_bits64(f.data(), bws[m], pay + woff);
+        uint8_t* h = pg + kPageHeaderBytes + uint64_t(m) * 16;
+        std::memcpy(h, &bases[m], 8);
+        std::memcpy(h + 8, &woff, 4);
+        std::memcpy(h + 12, &bws[m], 4);
+        woff += 2 * bws[m];
+      }
+    }
+    off += page_bytes;
+  }
+  if (page_off) page_off[npages] = off;
+  return int64_t(off);
+}
+
+// One value of a FOR64 page: mini block m, field j.  Returns false on a bad
+// mini block header.
+static bool for64_value(const uint8_t* pg, uint64_t pay_words, uint32_t m, uint32_t j, int64_t* v) {
+  const uint8_t* h = pg + kPageHeaderBytes + uint64_t(m) * 16;
+  int64_t base;
+  uint32_t woff, bw, poff;
+  std::memcpy(&base, h, 8);
+  std::memcpy(&woff, h + 8, 4);
+  std::memcpy(&bw, h + 12, 4);
+  std::memcpy(&poff, pg + 8, 4);
+  if (bw > 64 || uint64_t(woff) + 2ull * bw > pay_words) return false;
+  const uint64_t* pay = reinterpret_cast<const uint64_t*>(pg + poff);
+  *v = int64_t(uint64_t(base) + unpack_bits64(pay + woff, bw, j));
+  return true;
+}
+
+int64_t orc_decode_for64(const uint8_t* blob, const uint64_t* page_off, uint64_t npages, uint64_t n,
+                         uint32_t page_rows, int64_t* out) {
+  uint64_t r = 0;
+  for (uint64_t p = 0; p < npages; ++p) {
+    const uint8_t* pg = blob + page_off[p];
+    uint32_t hdr[4];
+    std::memcpy(hdr, pg, sizeof hdr);
+    if (hdr[0] != (kMagic | (uint32_t(FOR64) << 24))) return ECORRUPT;
+    const uint32_t rows = hdr[1];
+    if (rows == 0 || rows > page_rows || r + rows > n) return ECORRUPT;
+    const uint64_t pay_words = (page_off[p + 1] - page_off[p] - hdr[2]) / 8;
+    for (uint32_t i = 0; i < rows; ++i)
+      if (!for64_value(pg, pay_words, i / kMiniBlock, i % kMiniBlock, out + r + i)) return ECORRUPT;
+    r += rows;
+  }
+  return r == n ? OK : ECORRUPT;
+}
+
+// Row lookup through the RID index (binary search over the per-page row
+// prefix, as for the 32-bit codecs).
+int64_t orc_decode_for64_row(const uint8_t* blob, const uint64_t* page_off, const uint64_t* row_prefix,
+                             uint64_t npages, uint64_t r, int64_t* out) {
+  uint64_t lo = 0, hi = npages;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) / 2;
+    if (row_prefix[mid] > r) hi = mid; else lo = mid + 1;
+  }
+  if (lo >= npages) return EINVAL;
+  const uint64_t i = r - (lo == 0 ? 0 : row_prefix[lo - 1]);
+  const uint8_t* pg = blob + page_off[lo];
+  uint32_t hdr[4];
+  std::memcpy(hdr, pg, sizeof hdr);
+  if (hdr[0] != (kMagic | (uint32_t(FOR64) << 24))) return ECORRUPT;
+  const uint64_t pay_words = (page_off[lo + 1] - page_off[lo] - hdr[2]) / 8;
+  return for64_value(pg, pay_words, uint32_t(i / kMiniBlock), uint32_t(i % kMiniBlock), out) ? OK : ECORRUPT;
 }
 
 // ---------------------------------------------------------------------------
@@ -638,16 +775,26 @@ enum AggOp : int32_t { COUNT = 0, SUM, SUM_MUL, SUM_SUB };
 
 struct OrcColumn {          // one decoded column
   int32_t is_str;
-  const int32_t* v;         // int columns
+  const int32_t* v;         // 32-bit int columns (null for a 64-bit column)
   const uint8_t* bytes;     // string columns
   const uint64_t* offsets;  // n+1 byte offsets
+  const int64_t* v64;       // 64-bit int columns (null otherwise)
 };
+
+// Integer value of row r (predicates and aggregates read 32-bit and 64-bit
+// columns alike, as int64).
+static int64_t ival(const OrcColumn& c, uint64_t r) { return c.v64 ? c.v64[r] : int64_t(c.v[r]); }
 
 struct OrcTable {
   uint64_t n;
   int32_t ncols;
   const OrcColumn* cols;
 };
+
+// Joins, keys and payloads take 32-bit integer columns only.
+static bool is_i32(const OrcTable& t, int32_t col) {
+  return col >= 0 && col < t.ncols && !t.cols[col].is_str && t.cols[col].v != nullptr;
+}
 
 struct OrcPred {
   int32_t col, op, nargs, pfx_len;
@@ -699,7 +846,7 @@ static bool eval_pred(const OrcTable& t, const OrcPred& p, uint64_t r) {
       if (std::memcmp(c.bytes + c.offsets[r] + i, p.pfx, m) == 0) return true;
     return false;
   }
-  const int64_t x = c.v[r];
+  const int64_t x = ival(c, r);
   switch (p.op) {
     case LT: return x < p.args[0];
     case LE: return x <= p.args[0];
@@ -725,6 +872,11 @@ using OrcMap = std::unordered_map<int32_t, std::vector<int32_t>>;
 // probes the earlier table and builds the next).  Returns 0 or a status.
 static int64_t build_map(const OrcJoin& J, OrcMap& m, int depth) {
   if (depth > 4 || J.nsub < 0 || J.nsub > 4 || J.npay < 0 || J.npay > 2) return EINVAL;
+  if (!is_i32(*J.dim, J.key_col)) return EINVAL;
+  for (int32_t s = 0; s < J.nsub; ++s)
+    if (!is_i32(*J.dim, J.sub[s].fk_col)) return EINVAL;
+  for (int32_t f = 0; f < J.npay; ++f)
+    if (J.pay_join[f] < 0 && !is_i32(*J.dim, J.pay_cols[f])) return EINVAL;
   std::vector<OrcMap> subs(size_t(J.nsub));
   for (int32_t s = 0; s < J.nsub; ++s) {
     const int64_t rc = build_map(J.sub[s], subs[size_t(s)], depth + 1);
@@ -760,6 +912,10 @@ int64_t orc_query(const OrcTable* fact, int32_t npreds, const OrcPred* preds, in
                   const OrcJoin* joins, int32_t nkeys, const OrcKey* keys, int32_t naggs,
                   const OrcAgg* aggs, OrcRecord* out, uint64_t cap) {
   if (njoins > 8 || nkeys > 2 || naggs > 4) return EINVAL;
+  for (int32_t j = 0; j < njoins; ++j)
+    if (!is_i32(*fact, joins[j].fk_col)) return EINVAL;
+  for (int32_t k = 0; k < nkeys; ++k)
+    if (keys[k].kind == 0 && !is_i32(*fact, keys[k].col)) return EINVAL;
   // Build side: key -> payload values of the dimension rows that pass.
   std::vector<OrcMap> maps(njoins);
   for (int32_t j = 0; j < njoins; ++j) {
@@ -785,14 +941,14 @@ int64_t orc_query(const OrcTable* fact, int32_t npreds, const OrcPred* preds, in
     if (ins.second) { g.key[0] = kv[0]; g.key[1] = kv[1]; }
     g.count += 1;
     for (int32_t a = 0; a < naggs; ++a) {
-      const int64_t x = aggs[a].op == COUNT ? 0 : int64_t(fact->cols[aggs[a].a].v[r]);
-      const int64_t y = (aggs[a].op == SUM_MUL || aggs[a].op == SUM_SUB) ? int64_t(fact->cols[aggs[a].b].v[r]) : 0;
+      const int64_t x = aggs[a].op == COUNT ? 0 : ival(fact->cols[aggs[a].a], r);
+      const int64_t y = (aggs[a].op == SUM_MUL || aggs[a].op == SUM_SUB) ? ival(fact->cols[aggs[a].b], r) : 0;
       int64_t add = 0;
-      switch (aggs[a].op) {
+      switch (aggs[a].op) {   // int64 arithmetic modulo 2^64 (two's-complement wrap)
         case COUNT: add = 1; break;
         case SUM: add = x; break;
         case SUM_MUL: add = int64_t(uint64_t(x) * uint64_t(y)); break;
-        case SUM_SUB: add = x - y; break;
+        case SUM_SUB: add = int64_t(uint64_t(x) - uint64_t(y)); break;
       }
       g.val[a] = int64_t(uint64_t(g.val[a]) + uint64_t(add));   // two's-complement wrap
     }

@@ -22,7 +22,7 @@ from . import _build
 DPF_OK = 0
 STATUS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EDUPKEY", -5: "EBUSY", -6: "ETIMEOUT",
           -7: "ETRUNC", -8: "ENOTFOUND", -9: "ECORRUPT", -10: "EINTERNAL"}
-CODEC = {"for": 1, "delta": 2, "dict": 3, "str": 4, "fsst": 5}
+CODEC = {"for": 1, "delta": 2, "dict": 3, "str": 4, "fsst": 5, "for64": 6}
 STRING_CODECS = ("str", "fsst")
 PLACE = {"device": 0, "host": 1}
 OP = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7, "prefix": 8,
@@ -281,8 +281,9 @@ class Context:
 
     # ------------------------------------------------------------ columns
     def load_column(self, col, table=0, page_rows=0, placement="device"):
-        """Load one column dict (``{"codec", "values"}`` or ``{"codec": "str"
-        or "fsst", "bytes", "offsets"}``); returns its id."""
+        """Load one column dict (``{"codec", "values"}``, int64 values for
+        ``for64``, or ``{"codec": "str" or "fsst", "bytes", "offsets"}``);
+        returns its id."""
         d = ColumnDesc(CODEC[col["codec"]], PLACE[placement], int(page_rows), int(table))
         out = C.c_int32()
         if col["codec"] in STRING_CODECS:
@@ -292,7 +293,7 @@ class Context:
             _check(lib().dpf_load_column(self.h, C.byref(d), _ptr(src), _ptr(offs), offs.size - 1,
                                          C.byref(out)))
         else:
-            v = np.ascontiguousarray(col["values"], np.int32)
+            v = np.ascontiguousarray(col["values"], np.int64 if col["codec"] == "for64" else np.int32)
             _check(lib().dpf_load_column(self.h, C.byref(d), _ptr(v), None, v.size, C.byref(out)))
         return out.value
 
@@ -512,7 +513,7 @@ def encode_column(col, page_rows=0):
         values = data if data.size else np.zeros(1, np.uint8)
         n = offs.size - 1
     else:
-        values = np.ascontiguousarray(col["values"], np.int32)
+        values = np.ascontiguousarray(col["values"], np.int64 if codec == "for64" else np.int32)
         offs = None
         n = values.size
     npages = (n + P - 1) // P

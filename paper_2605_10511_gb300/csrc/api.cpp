@@ -276,6 +276,14 @@ dpf_status validate_pages(uint32_t codec, const uint8_t* pages, uint64_t size, c
     if (is_str_codec(codec) && (extra < poff || extra > pbytes || extra % 16)) return flag();
     const uint64_t pay_words = (pay_end - poff) / 4;
     const uint32_t nmb = (rows + kMB - 1) / kMB;
+    if (codec == C_FOR64) {  // {base: int64, word offset: u32, bit width: u32}, 8-byte words
+      for (uint32_t m2 = 0; m2 < nmb; ++m2) {
+        const uint8_t* h = pg + kPageHdr + uint64_t(m2) * 16;
+        const uint32_t woff = rd32(h + 8), bw = rd32(h + 12);
+        if (bw > 64 || uint64_t(woff) + 2ull * bw > pay_words / 2) return flag();
+      }
+      return;
+    }
     for (uint32_t m2 = 0; m2 < nmb; ++m2) {
       const uint8_t* h = pg + kPageHdr + uint64_t(m2) * mb_hdr_bytes(codec);
       const uint32_t wob = codec == C_DELTA ? rd32(h + 8) : rd32(h + 4);
@@ -359,6 +367,7 @@ dpf_status validate_fsst_codes(const uint8_t* pages, const uint64_t* page_off, u
 dpf_status compile_pred_body(const Column& c, const dpf_pred& p, DevStep& S, int col_index) {
   std::memset(&S, 0, sizeof S);
   S.col = uint8_t(col_index);
+  if (c.codec == C_FOR64) return fail(DPF_EINVAL, "predicates take 32-bit or string columns; column %d is FOR64", c.id);
   if (p.op == DPF_OP_PREFIX || p.op == DPF_OP_CONTAINS) {
     if (!is_str_codec(uint32_t(c.codec)))
       return fail(DPF_EINVAL, "PREFIX / CONTAINS need a STR or FSST column (column %d)", c.id);
@@ -479,7 +488,7 @@ void value_bounds(uint32_t codec, const uint8_t* pages, const uint64_t* page_off
   *vmin = 0;
   *vmax = -1;
   zones->assign(npages, make_int2(INT32_MIN, INT32_MAX));
-  if (is_str_codec(codec)) return;
+  if (is_str_codec(codec) || codec == C_FOR64) return;  // no 32-bit bounds (never a step's column)
   int64_t clo = INT64_MAX, chi = INT64_MIN;
   for (uint64_t p = 0; p < npages; ++p) {
     const uint8_t* pg = pages + page_off[p];
@@ -681,8 +690,8 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
     for (int i = 0; i < need; ++i) {
       auto it = c->cols.find(ab[i]);
       if (it == c->cols.end()) return fail(DPF_EINVAL, "unknown aggregate column %d", ab[i]);
-      if (it->second.codec != C_FOR && it->second.codec != C_DELTA)
-        return fail(DPF_EINVAL, "aggregate column %d must be FOR or DELTA", ab[i]);
+      if (it->second.codec != C_FOR && it->second.codec != C_DELTA && it->second.codec != C_FOR64)
+        return fail(DPF_EINVAL, "aggregate column %d must be FOR, DELTA or FOR64", ab[i]);
       int idx;
       dpf_status st = cs.add(ab[i], &idx);
       if (st) return st;
@@ -1113,7 +1122,7 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
   DeviceGuard g(c->device);
   const uint32_t codec = uint32_t(d->codec);
   const uint32_t P = d->page_rows ? d->page_rows : kDefaultPageRows;
-  if (codec < C_FOR || codec > C_FSST) return fail(DPF_EINVAL, "unknown codec %u", codec);
+  if (codec < C_FOR || codec > C_FOR64) return fail(DPF_EINVAL, "unknown codec %u", codec);
   if (nrows == 0 || P % kMB || P > kMaxPageRows) return fail(DPF_EINVAL, "bad nrows or page_rows");
   if (codec == C_FSST) {
     if (!dict || dict_n == 0 || dict_n % 3 || dict_n / 3 > kFsstMaxSymbols)
@@ -1154,7 +1163,7 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
     }
     col.raw_bytes = sb + 8 * nrows;
   } else {
-    col.raw_bytes = 4 * nrows;
+    col.raw_bytes = (codec == C_FOR64 ? 8 : 4) * nrows;
   }
   if (col.placement == DPF_PLACE_HOST_PINNED) {
     cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&col.host_blob), size, cudaHostAllocMapped | cudaHostAllocPortable);
@@ -1646,6 +1655,11 @@ dpf_status dpf_prepare_unfused(dpf_ctx* c, const dpf_plan* plan, dpf_prep_id* ou
     if (Q.steps[k].kind == ST_CONTAINS || Q.cols[Q.steps[k].col].codec == C_FSST) {
       dpf_release(c, p->id);
       return fail(DPF_EINVAL, "the unfused chain evaluates PREFIX on STR columns only (no FSST, no CONTAINS)");
+    }
+  for (uint32_t i = 0; i < Q.ncols; ++i)
+    if (Q.cols[i].codec == C_FOR64) {
+      dpf_release(c, p->id);
+      return fail(DPF_EINVAL, "the unfused chain decodes 32-bit columns only (no FOR64)");
     }
   const uint64_t n = Q.nrows;
   // layout: per column decoded arrays, flags, two (rid, gid) lists, counts

@@ -18,7 +18,7 @@ constexpr uint32_t kMagic = 0x00465044u;      // 'D' 'P' 'F', codec in the top b
 constexpr uint32_t kMaxPageRows = 1u << 20;
 constexpr uint32_t kDefaultPageRows = 65536;
 
-enum Codec : uint32_t { C_FOR = 1, C_DELTA = 2, C_DICT = 3, C_STR = 4, C_FSST = 5 };
+enum Codec : uint32_t { C_FOR = 1, C_DELTA = 2, C_DICT = 3, C_STR = 4, C_FSST = 5, C_FOR64 = 6 };
 // STR and FSST share the variable-length page layout (FSST pages hold the
 // encoded strings; their lengths are the encoded lengths).
 __host__ __device__ inline bool is_str_codec(uint32_t codec) { return codec == C_STR || codec == C_FSST; }
@@ -27,12 +27,14 @@ constexpr uint32_t kFsstMaxSymbols = 255;
 
 // Bytes of one mini block header in the header array that follows the
 // page header (STR: the lengths' FOR header; the u32 starts come after all
-// headers).
+// headers).  FOR64 (Sec. 4.1, 64-bit GPU-FOR): {base: int64, word offset:
+// u32 in 8-byte words, bit width: u32 in 0..64}; each mini block packs 128
+// fields into 2 * bw 64-bit words.
 __host__ __device__ inline uint32_t mb_hdr_bytes(uint32_t codec) {
-  return codec == C_DELTA ? 16u : 8u;
+  return codec == C_DELTA || codec == C_FOR64 ? 16u : 8u;
 }
 __host__ __device__ inline uint32_t mb_meta_bytes(uint32_t codec) {
-  return codec == C_DELTA ? 16u : (is_str_codec(codec) ? 12u : 8u);
+  return codec == C_DELTA || codec == C_FOR64 ? 16u : (is_str_codec(codec) ? 12u : 8u);
 }
 __host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15u) & ~uint64_t(15); }
 // Byte offset of the packed payload inside a page of `rows` rows.

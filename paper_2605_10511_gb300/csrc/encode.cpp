@@ -124,6 +124,70 @@ void write_int_page(const IntSource& src, uint32_t codec, uint64_t r0, const Pag
   }
 }
 
+// 64-bit frame of reference (Sec. 4.1, GPU-FOR extended to BIGINT): 64-bit
+// bases, fields of bw <= 64 bits at bit j*bw of a stream of 64-bit words.
+struct Mb64 {
+  int64_t base;
+  uint32_t bw, word_off;
+};
+
+inline uint32_t width_of64(uint64_t span) { return span == 0 ? 0u : 64u - uint32_t(__builtin_clzll(span)); }
+
+// Packs 128 fields q[j] (already offset by the base) of width bw into 2*bw
+// words, field j at bit j*bw, LSB first; a field crossing a word boundary
+// continues at bit 0 of the next word.
+void pack128_64(const uint64_t* q, uint32_t bw, uint64_t* out) {
+  std::memset(out, 0, size_t(2) * bw * 8);
+  if (bw == 0) return;
+  for (uint32_t j = 0; j < kMB; ++j) {
+    const uint64_t bit = uint64_t(j) * bw;
+    const uint32_t w = uint32_t(bit >> 6), s = uint32_t(bit & 63);
+    out[w] |= q[j] << s;
+    if (s + bw > 64) out[w + 1] |= q[j] >> (64 - s);
+  }
+}
+
+// Mini block plans of one FOR64 page; returns the page's byte size.
+uint64_t plan_for64_page(const int64_t* v, uint64_t r0, uint32_t rows, std::vector<Mb64>& mb) {
+  const uint32_t nmb = (rows + kMB - 1) / kMB;
+  mb.resize(nmb);
+  uint64_t words = 0;
+  for (uint32_t m = 0; m < nmb; ++m) {
+    const uint64_t a = r0 + uint64_t(m) * kMB;
+    const uint32_t cnt = std::min<uint32_t>(kMB, uint32_t(r0 + rows - a));
+    int64_t lo = v[a], hi = v[a];
+    for (uint32_t j = 1; j < cnt; ++j) {
+      lo = std::min(lo, v[a + j]);
+      hi = std::max(hi, v[a + j]);
+    }
+    mb[m].base = lo;
+    mb[m].bw = width_of64(uint64_t(hi) - uint64_t(lo));
+    mb[m].word_off = uint32_t(words);
+    words += 2ull * mb[m].bw;
+  }
+  return align16(uint64_t(payload_offset(C_FOR64, rows)) + words * 8);
+}
+
+void write_for64_page(const int64_t* v, uint64_t r0, uint32_t rows, const std::vector<Mb64>& mb,
+                      uint64_t bytes, uint8_t* pg) {
+  std::memset(pg, 0, bytes);
+  const uint32_t poff = payload_offset(C_FOR64, rows);
+  const uint32_t hdr[4] = {kMagic | (uint32_t(C_FOR64) << 24), rows, poff, 0};
+  std::memcpy(pg, hdr, sizeof hdr);
+  uint64_t* pay = reinterpret_cast<uint64_t*>(pg + poff);
+  uint64_t q[kMB];
+  for (uint32_t m = 0; m < uint32_t(mb.size()); ++m) {
+    const uint64_t a = r0 + uint64_t(m) * kMB;
+    const uint32_t cnt = std::min<uint32_t>(kMB, uint32_t(r0 + rows - a));
+    for (uint32_t j = 0; j < kMB; ++j) q[j] = j < cnt ? uint64_t(v[a + j]) - uint64_t(mb[m].base) : 0u;
+    pack128_64(q, mb[m].bw, pay + mb[m].word_off);
+    uint8_t* h = pg + kPageHdr + uint64_t(m) * 16;
+    std::memcpy(h, &mb[m].base, 8);
+    std::memcpy(h + 8, &mb[m].word_off, 4);
+    std::memcpy(h + 12, &mb[m].bw, 4);
+  }
+}
+
 void plan_str_page(const uint64_t* offs, uint64_t r0, uint32_t rows, PagePlan& pp, bool* bad) {
   // (STR and FSST pages share this layout)
   pp.rows = rows;
@@ -337,12 +401,35 @@ extern "C" dpf_status dpf_encode_column(const dpf_column_desc* desc, const void*
   const uint32_t P = desc->page_rows ? desc->page_rows : kDefaultPageRows;
   if (nrows == 0) return fail(DPF_EINVAL, "encode: nrows must be > 0");
   if (P % kMB != 0 || P > kMaxPageRows) return fail(DPF_EINVAL, "encode: page_rows %u not a multiple of 128 in [128, 2^20]", P);
-  if (codec < C_FOR || codec > C_FSST) return fail(DPF_EINVAL, "encode: unknown codec %u", codec);
+  if (codec < C_FOR || codec > C_FOR64) return fail(DPF_EINVAL, "encode: unknown codec %u", codec);
   if (!values && !is_str_codec(codec)) return fail(DPF_EINVAL, "encode: values is NULL");
   if (is_str_codec(codec) && !str_offsets) return fail(DPF_EINVAL, "encode: STR/FSST needs str_offsets");
   if (!page_off || !row_prefix || !size_out) return fail(DPF_EINVAL, "encode: page_off/row_prefix/size_out NULL");
 
   const uint64_t npages = (nrows + P - 1) / P;
+  if (codec == C_FOR64) {
+    const int64_t* v = static_cast<const int64_t*>(values);
+    std::vector<std::vector<Mb64>> mbs(npages);
+    std::vector<uint64_t> bytes(npages);
+    parallel_for(npages, [&](uint64_t p) {
+      bytes[p] = plan_for64_page(v, p * P, uint32_t(std::min<uint64_t>(P, nrows - p * P)), mbs[p]);
+    });
+    uint64_t off = 0;
+    for (uint64_t p = 0; p < npages; ++p) {
+      page_off[p] = off;
+      row_prefix[p] = std::min<uint64_t>(nrows, (p + 1) * P);
+      off += bytes[p];
+    }
+    page_off[npages] = off;
+    *size_out = off;
+    if (dict_n) *dict_n = 0;
+    if (!out) return DPF_OK;
+    if (cap < off) return fail(DPF_ETRUNC, "encode: cap %llu < %llu", (unsigned long long)cap, (unsigned long long)off);
+    parallel_for(npages, [&](uint64_t p) {
+      write_for64_page(v, p * P, uint32_t(std::min<uint64_t>(P, nrows - p * P)), mbs[p], bytes[p], out + page_off[p]);
+    });
+    return DPF_OK;
+  }
   std::vector<PagePlan> plans(npages);
   std::vector<uint32_t> codes;
   std::vector<int32_t> dvals;

@@ -166,10 +166,76 @@ __device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, 
   }
 }
 
+// Value of a FOR64 column (Sec. 4.1, 64-bit GPU-FOR) at segment row r: the
+// mini block's 16-byte header {base, word offset, bit width} and the row's
+// field at bit (r % 128) * bw of the mini block's 64-bit words, read through
+// a 128-bit window (the second word only when the field crosses into it).
+// Other integer columns are read as int32 and sign-extended.  Warp-uniform
+// call (c is uniform); lanes with !valid return 0.
+template <bool kHost>
+__device__ __forceinline__ long long value64(const DevQuery& Q, int c, const PageState& P, uint32_t seg_mb,
+                                             uint32_t r, bool valid, int lane, unsigned int* status) {
+  if (Q.cols[c].codec != C_FOR64) return (long long)int32_t(row_value<kHost>(Q, c, P, seg_mb, r, valid, lane, status));
+  const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, c));
+  if (!valid) return 0;
+  const uint4 h = ld_u4<kHost>(reinterpret_cast<const uint4*>(pg + kPageHdr + uint64_t(seg_mb + (r >> 7)) * 16));
+  const unsigned long long base = (unsigned long long)h.x | ((unsigned long long)h.y << 32);
+  const uint32_t bw = tmin<uint32_t>(h.w, 64u);  // validated at load
+  unsigned long long x = 0;
+  if (bw != 0) {
+    const uint2* pay = reinterpret_cast<const uint2*>(pg + payload_offset(C_FOR64, P.prow));
+    const uint32_t bit = (r & (kMB - 1)) * bw;
+    const uint2* p = pay + h.z + (bit >> 6);
+    const uint32_t sh = bit & 63u;
+    const uint2 lo = ld_u2<kHost>(p);
+    x = ((unsigned long long)lo.x | ((unsigned long long)lo.y << 32)) >> sh;
+    if (sh + bw > 64) {
+      const uint2 hi = ld_u2<kHost>(p + 1);
+      x |= ((unsigned long long)hi.x | ((unsigned long long)hi.y << 32)) << (64 - sh);
+    }
+    if (bw < 64) x &= (1ull << bw) - 1ull;
+  }
+  return (long long)(base + x);
+}
+
+// An aggregate with a FOR64 operand: one survivor per lane, int64 operands,
+// arithmetic modulo 2^64.  Inlined: an out-of-line call made the caller
+// spill around it, while inlined it leaves the 32-bit passes' register
+// allocation as it was.
+template <bool kHost, int kOp>
+__device__ __forceinline__ void agg_pass_wide(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
+                                           const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
+                                           uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
+  const uint32_t S1 = 1 + Q.naggs;
+  unsigned long long sum = 0;
+  for (uint32_t i0 = 0; i0 < n; i0 += 32) {
+    bool valid = i0 + lane < n;
+    const uint32_t e = valid ? list[i0 + lane] : 0u;
+    const uint32_t r = e & ((1u << kRowBits) - 1u), gid = e >> kRowBits;
+    if (!single && gid >= Q.domain) valid = false;  // reported by list_aggregate
+    const unsigned long long a = (unsigned long long)value64<kHost>(Q, ca, P, seg_mb, r, valid, lane, status);
+    unsigned long long b = 0;
+    if (kOp == DPF_AGG_SUM_MUL || kOp == DPF_AGG_SUM_SUB)
+      b = (unsigned long long)value64<kHost>(Q, cb, P, seg_mb, r, valid, lane, status);
+    const unsigned long long x = kOp == DPF_AGG_SUM ? a : (kOp == DPF_AGG_SUM_MUL ? a * b : a - b);
+    if (single) sum += valid ? x : 0ull;
+    else if (valid) atomicAdd(acc + uint64_t(gid) * S1 + slot, x);
+  }
+  if (single) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) sum += __shfl_down_sync(kFull, sum, d);
+    if (lane == 0 && sum != 0) atomicAdd(acc + slot, sum);
+  }
+}
+
 template <bool kHost, int kOp>
 __device__ __forceinline__ void agg_dispatch(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                              const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
                                              uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
+  if (Q.cols[ca].codec == C_FOR64 || (kOp != DPF_AGG_SUM && Q.cols[cb].codec == C_FOR64)) {
+    agg_pass_wide<kHost, kOp>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status);
+    return;
+  }
   const bool point = Q.cols[ca].codec != C_DELTA && (kOp == DPF_AGG_SUM || Q.cols[cb].codec != C_DELTA);
   if (point) agg_pass<kHost, kOp, true>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status);
   else agg_pass<kHost, kOp, false>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status);

@@ -9,7 +9,8 @@ A *workload* is a plain dict::
      "query": query}
 
 where a column is either ``{"codec": "for"|"delta"|"dict", "values":
-int32 ndarray}`` or ``{"codec": "str", "bytes": uint8 ndarray, "offsets":
+int32 ndarray}``, ``{"codec": "for64", "values": int64 ndarray}`` (a BIGINT
+column) or ``{"codec": "str", "bytes": uint8 ndarray, "offsets":
 uint64 ndarray of rows+1}``.  The codec names the storage encoding the
 column is to be loaded with; the generator never encodes anything itself.
 
@@ -168,7 +169,7 @@ def _star_query(rng, attrs):
 
 
 def star_join(rows=1 << 26, seed=2, page_rows=DEFAULT_PAGE_ROWS, clustered=True,
-              dim_rows=(2000, 30000, 200000), date_year=None):
+              dim_rows=(2000, 30000, 200000), date_year=None, bigint_measure=False):
     """Fact table with 4 uniform foreign keys and 2 measures, 4 dimensions.
 
     Filters three dimensions (10 %, 4 %, 8 %), joins all four and groups by
@@ -176,6 +177,8 @@ def star_join(rows=1 << 26, seed=2, page_rows=DEFAULT_PAGE_ROWS, clustered=True,
     fact rows are ordered by date key (a sorted load) and the date key is
     stored delta-coded; otherwise it is stored frame-of-reference coded.
     ``date_year`` adds a filter keeping one year of the date dimension.
+    ``bigint_measure`` stores the measure as a BIGINT (FOR64) column holding
+    m1 x 2^20 + m2 (values up to about 2^43).
     """
     rng = _rng(seed)
     dims, attrs = _star_dimensions(rng, dim_rows, page_rows)
@@ -195,10 +198,12 @@ def star_join(rows=1 << 26, seed=2, page_rows=DEFAULT_PAGE_ROWS, clustered=True,
         "fkd": _int_col(fkd, "delta" if clustered else "for"),
         "m1": _int_col(m1), "m2": _int_col(m2),
     }}
+    if bigint_measure:
+        fact["cols"]["m1"] = {"codec": "for64", "values": (m1.astype(np.int64) << 20) + m2}
     tables = dict(dims)
     tables["fact"] = fact
     query = _star_query(rng, attrs)
-    name = f"star_join_{rows}{'_clustered' if clustered else ''}"
+    name = f"star_join_{rows}{'_clustered' if clustered else ''}{'_bigint' if bigint_measure else ''}"
     if date_year is not None:
         # one year of the date dimension (an SSB Q1/Q3-style date filter);
         # the fact tables are the same as without it
@@ -589,6 +594,21 @@ def tiny_random_workload(seed, rows=None, page_rows=None):
     for p in preds:
         if p["col"] == "s" and rng2.integers(0, 2):
             p["op"] = "contains"
+    # a BIGINT measure (FOR64) from a third stream: spans from constant to the
+    # full int64 range, used by some aggregates
+    rng3 = _rng(seed + 104729)
+    if rng3.integers(0, 2):
+        spans64 = [(7, 7), (-5, 5), (-(2**40), 2**40), (-(2**63), 2**63 - 1), (2**50, 2**50 + 1000)]
+        lo, hi = spans64[int(rng3.integers(0, len(spans64)))]
+        fact["cols"]["z"] = {"codec": "for64",
+                             "values": rng3.integers(lo, hi, rows, dtype=np.int64, endpoint=True)}
+        for a in aggs[1:]:
+            if rng3.integers(0, 2):
+                a["cols"] = ["z" if rng3.integers(0, 2) else c for c in a["cols"]]
+        if len(aggs) < 4 and not any("z" in a.get("cols", []) for a in aggs):
+            aggs.append({"op": str(rng3.choice(["sum", "sum_mul", "sum_sub"])), "cols": ["z", "x"]})
+            if aggs[-1]["op"] == "sum":
+                aggs[-1]["cols"] = ["z"]
     query = {"preds": preds, "joins": joins, "group": group, "aggs": aggs}
     return {"name": f"tiny_{seed}", "tables": {"fact": fact, "dim": dim},
             "fact": "fact", "query": query}

@@ -89,10 +89,29 @@ def test_encoder_matches_oracle_on_edges(oracle_lib, codec):
             _compare({"codec": codec, "values": v}, P)
 
 
+def test_for64_encoder_matches_oracle_on_edges(oracle_lib):
+    rng = np.random.default_rng(9)
+    i64 = np.iinfo(np.int64)
+    cases = [np.array([-(1 << 40)], np.int64), np.full(129, 1 << 50, np.int64),
+             np.array([i64.min, i64.max] * 100, np.int64),
+             rng.integers(i64.min, i64.max, 3000, dtype=np.int64, endpoint=True),
+             rng.integers(0, 1 << 44, 5000, dtype=np.int64) - (1 << 43)]
+    for k in range(65):  # every bit width 0..64 in one mini block each
+        v = np.zeros(128, np.int64)
+        v[3] = np.int64(np.uint64((1 << k) - 1).astype(np.int64)) if k < 64 else np.int64(-1)
+        v[5] = i64.min if k == 64 else 0
+        cases.append(v)
+    for v in cases:
+        for P in (128, 256, 4096):
+            _compare({"codec": "for64", "values": v}, P)
+
+
 def test_encoder_matches_oracle_on_workload_columns(oracle_lib):
     for w in (synth.scan_filter_aggregate(rows=300000, page_rows=65536),
               synth.strings(rows=100000, page_rows=8192),
-              synth.star_join(rows=150000, dim_rows=(2000, 30000, 20000), clustered=True)):
+              synth.chain_join(rows=1 << 17, page_rows=16384),
+              synth.star_join(rows=150000, dim_rows=(2000, 30000, 20000), clustered=True,
+                              bigint_measure=True)):
         for t in w["tables"].values():
             for c in t["cols"].values():
                 _compare(c, t["page_rows"])

@@ -20,7 +20,8 @@ def _column(example):
         offs = np.zeros(len(example["strings"]) + 1, np.uint64)
         offs[1:] = np.cumsum([len(s) for s in example["strings"]])
         return {"codec": "str", "bytes": np.frombuffer(data, np.uint8).copy(), "offsets": offs}
-    return {"codec": example["codec"], "values": np.array(example["values"], np.int32)}
+    dt = np.int64 if example["codec"] == "for64" else np.int32
+    return {"codec": example["codec"], "values": np.array(example["values"], dt)}
 
 
 @pytest.mark.parametrize("ex", HAND_WORKED, ids=[e["name"] for e in HAND_WORKED])
@@ -31,6 +32,9 @@ def test_hand_worked_pages(oracle_lib, ex):
     assert enc["row_prefix"].tolist() == ex["row_prefix"]
     if "page_hex" in ex:
         assert enc["blob"].tobytes().hex() == ex["page_hex"]
+    if "page_header_hex" in ex:
+        hdr = bytes.fromhex(ex["page_header_hex"])
+        assert enc["blob"][:len(hdr)].tobytes() == hdr
     if "page0_payload_prefix_hex" in ex:
         pfx = bytes.fromhex(ex["page0_payload_prefix_hex"])
         assert enc["blob"][32:32 + len(pfx)].tobytes() == pfx
@@ -93,6 +97,47 @@ def test_bit_widths_are_minimal(oracle_lib):
             wob = int(np.frombuffer(enc["blob"][20:24].tobytes(), np.uint32)[0])
             assert wob & 0xFF == int(span).bit_length(), span
             assert np.array_equal(oracle_lib.decode_column(enc), v)
+
+
+def _edge_int64_columns():
+    i64 = np.iinfo(np.int64)
+    rng = np.random.default_rng(11)
+    return {
+        "one": np.array([-(1 << 40)], np.int64),
+        "full_range_128": np.array([i64.min, i64.max] * 64, np.int64),
+        "full_range_random": rng.integers(i64.min, i64.max, 1000, dtype=np.int64, endpoint=True),
+        "extremes_ragged": np.array([i64.max, i64.min, 0, -1, 1, i64.max - 1, i64.min + 1], np.int64),
+        "wide_cents": rng.integers(0, 1 << 44, 3000, dtype=np.int64) - (1 << 43),
+        "int32_like": rng.integers(-5, 5, 700, dtype=np.int64),
+        "constant": np.full(300, 1 << 50, np.int64),
+    }
+
+
+@pytest.mark.parametrize("page_rows", [128, 256, 1024])
+def test_roundtrip_for64_edges(oracle_lib, page_rows):
+    for name, v in _edge_int64_columns().items():
+        for n in sorted({v.size, min(v.size, page_rows - 1), min(v.size, page_rows + 1)}):
+            x = v[:n]
+            enc = oracle_lib.encode_column({"codec": "for64", "values": x}, page_rows)
+            assert np.array_equal(oracle_lib.decode_column(enc), x), (name, n)
+            for r in {0, n // 2, n - 1}:
+                assert oracle_lib.decode_row(enc, r) == int(x[r]), (name, n, r)
+            assert all(int(o) % 16 == 0 for o in enc["page_off"])
+
+
+def test_for64_bit_widths_are_minimal_and_pages_sized(oracle_lib):
+    """bw = bits of (max - min) for every width 0..64, and a page holds the
+    16-byte header, 16 bytes per mini block header (rounded to 16) and 2*bw
+    words of 8 bytes per mini block."""
+    for k in range(0, 65):
+        span = (1 << k) - 1
+        v = np.full(128, -(1 << 63), np.int64)
+        v[77] = np.int64(np.uint64(span).astype(np.int64)) + v[0] if k < 64 else np.iinfo(np.int64).max
+        enc = oracle_lib.encode_column({"codec": "for64", "values": v}, 128)
+        bw = int(np.frombuffer(enc["blob"][28:32].tobytes(), np.uint32)[0])
+        assert bw == k, (k, bw)
+        assert enc["page_off"].tolist() == [0, 32 + 16 * k], k
+        assert np.array_equal(oracle_lib.decode_column(enc), v)
 
 
 def test_delta_wraps_modulo_2_32(oracle_lib):

@@ -29,7 +29,8 @@ MUTANTS = {
                             "words[bit / 32] |= 1u << (31 - bit % 32);"),
     "for_base_subtracted": ("v = int32_t(uint32_t(base) + f);", "v = int32_t(uint32_t(base) - f);"),
     "delta_drops_dmin": ("running += uint32_t(base) + f;", "running += f;"),
-    "sum_sub_transposed": ("case SUM_SUB: add = x - y; break;", "case SUM_SUB: add = y - x; break;"),
+    "sum_sub_transposed": ("case SUM_SUB: add = int64_t(uint64_t(x) - uint64_t(y)); break;",
+                           "case SUM_SUB: add = int64_t(uint64_t(y) - uint64_t(x)); break;"),
     "sum_mul_wrong_operand": ("case SUM_MUL: add = int64_t(uint64_t(x) * uint64_t(y)); break;",
                               "case SUM_MUL: add = int64_t(uint64_t(x) * uint64_t(x)); break;"),
     "payload_field_ignored": ("(*hit[keys[k].join])[keys[k].field]", "(*hit[keys[k].join])[0]"),
@@ -51,6 +52,9 @@ MUTANTS = {
                                     "true ? J.dim->cols[J.pay_cols[f]].v[r]"),
     "chain_probes_own_key": ("auto it = subs[size_t(s)].find(J.dim->cols[J.sub[s].fk_col].v[r]);",
                              "auto it = subs[size_t(s)].find(J.dim->cols[J.key_col].v[r]);"),
+    "for64_bits_modulo_32": ("words[bit / 64] |= uint64_t(1) << (bit % 64);",
+                             "words[bit / 64] |= uint64_t(1) << (bit % 32);"),
+    "for64_word_offset_half": ("woff += 2 * bws[m];", "woff += bws[m];"),
     "dict_rank_off_by_one": ("std::lower_bound(dict.begin(), dict.end(), values[r]) - dict.begin();",
                              "std::upper_bound(dict.begin(), dict.end(), values[r]) - dict.begin();"),
 }
@@ -66,7 +70,8 @@ def _pins_pass(o):
                 offs[1:] = np.cumsum([len(s) for s in ex["strings"]])
                 col = {"codec": "str", "bytes": np.frombuffer(data, np.uint8).copy(), "offsets": offs}
             else:
-                col = {"codec": ex["codec"], "values": np.array(ex["values"], np.int32)}
+                col = {"codec": ex["codec"],
+                       "values": np.array(ex["values"], np.int64 if ex["codec"] == "for64" else np.int32)}
             enc = o.encode_column(col, ex["page_rows"])
             assert enc["row_prefix"].tolist() == ex["row_prefix"], ex["name"]
             if "page_hex" in ex:
