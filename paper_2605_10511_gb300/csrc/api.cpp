@@ -970,6 +970,8 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   p->L.smem_tables = max_tables;
   p->L.acc_slots = acc_slots;
   p->L.host_data = host;
+  p->L.text = false;
+  for (const DevQuery& q : p->hq) p->L.text = p->L.text || needs_string_matcher(q);
   p->fetched.assign(size_t(n), 0);
   p->id = c->next_prep++;
   *out = p.get();

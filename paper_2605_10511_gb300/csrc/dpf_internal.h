@@ -137,6 +137,16 @@ struct alignas(16) DevQuery {
   int32_t build_key, build_npay, build_pay[2];
 };
 
+// A query needs the fused kernel's general string matcher when it has a
+// CONTAINS step or a string step on an FSST column.
+inline bool needs_string_matcher(const DevQuery& Q) {
+  for (uint32_t s = 0; s < Q.nsteps && s < uint32_t(kMaxSteps); ++s) {
+    const DevStep& S = Q.steps[s];
+    if (S.kind == ST_CONTAINS || (S.kind == ST_PREFIX && Q.cols[S.col].codec == C_FSST)) return true;
+  }
+  return false;
+}
+
 struct Sched {
   unsigned long long next;     // ticket counter
   unsigned int exited;         // CTAs that left the persistent loop

@@ -290,7 +290,7 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
 // page, mini blocks whose headers miss it are skipped by the first step.
 // Each tile loads its headers as it starts (the other resident warps hide
 // the latency).
-template <bool kHost>
+template <bool kHost, bool kText>
 __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long long* acc, const uint8_t* stab,
                                uint32_t* list, int lane, unsigned int* status) {
   const uint64_t PR = Q.page_rows;
@@ -312,8 +312,6 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
     TileHdr H;
     // the list collects the survivors of consecutive tiles (a segment of at
     // most 2^kRowBits rows of this page) before the later steps run on them
-    // the list collects the survivors of consecutive tiles (a segment of at
-    // most 2^kRowBits rows of this page) before the later steps run on them
     uint32_t n = 0, seg_mb = mb0, nd = 0;
     for (uint32_t j = 0; j < ntiles; ++j) {
       const uint32_t i0 = mb0 + j * TB;
@@ -321,12 +319,12 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
       H = load_headers<kHost>(Q, P, i0, nmb, lane);
       TileState T;
       tile_init(P, i0, nmb, lane, T);
-      tile_dense_step<kHost>(Q, 0, P, H, T, stab, lane, status);
+      tile_dense_step<kHost, kText>(Q, 0, P, H, T, stab, lane, status);
       nd = 1;  // steps run densely (the first); the rest run over the list
       n = tile_compact(T, list, n, (i0 - seg_mb) * kMB, lane);
       const uint32_t next = i0 + TB;
       if (j + 1 == ntiles || n + kTileRows > kListCap || next + TB - seg_mb > kSegMbs) {
-        n = list_steps<kHost>(Q, P, seg_mb, list, n, stab, lane, status, nd);
+        n = list_steps<kHost, kText>(Q, P, seg_mb, list, n, stab, lane, status, nd);
         if (n) list_aggregate<kHost>(Q, P, seg_mb, list, n, lane, acc, status);
         n = 0;
         nd = 0;
@@ -361,7 +359,9 @@ __device__ void load_smem_tables(const DevQuery& Q, uint8_t* stab) {
   }
 }
 
-template <bool kHost, int kMinBlocks>
+// kText = false: the build without the general string matcher (CONTAINS,
+// FSST), launched for batches that have no such step.
+template <bool kHost, int kMinBlocks, bool kText>
 __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* __restrict__ queries,
                                                        const uint64_t* __restrict__ qbegin, int nq,
                                                        uint64_t total, Sched* sched, uint32_t acc_slots,
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* 
     unsigned long long* acc = Q.use_smem_acc ? sacc : Q.acc;
     uint32_t done_here = 0;
     while (hq == cur) {
-      process_ticket<kHost>(Q, held - Q.chunk_begin, acc, stab, list, lane, &sched->status);
+      process_ticket<kHost, kText>(Q, held - Q.chunk_begin, acc, stab, list, lane, &sched->status);
       ++done_here;
       hq = draw(held);
     }
@@ -444,40 +444,53 @@ size_t fused_dynamic_smem(uint32_t acc_slots, size_t smem_tables, int threads) {
 }
 
 namespace {
-template <bool kHost, int kMinBlocks>
+template <bool kHost, int kMinBlocks, bool kText>
 int occupancy_of(int threads, size_t smem) {
   int n = 0;
-  cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_kernel<kHost, kMinBlocks>, threads, smem);
+  cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks, kText>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_kernel<kHost, kMinBlocks, kText>, threads, smem);
   return n;
 }
 
-template <bool kHost, int kMinBlocks>
+template <bool kHost, int kMinBlocks, bool kText>
 cudaError_t launch_as(const FusedLaunch& L, size_t smem, uint32_t tb, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(smem));
+  cudaError_t e = cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks, kText>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  fused_kernel<kHost, kMinBlocks><<<L.grid, L.threads, smem, s>>>(L.queries, L.qbegin, L.nq, L.total_chunks,
-                                                                  L.sched, L.acc_slots, tb);
+  fused_kernel<kHost, kMinBlocks, kText><<<L.grid, L.threads, smem, s>>>(L.queries, L.qbegin, L.nq, L.total_chunks,
+                                                                         L.sched, L.acc_slots, tb);
   return cudaGetLastError();
 }
 }  // namespace
 
+// The occupancy of the string-capable build bounds the grid of both builds
+// (same launch bounds and shared memory; the lean build needs no more
+// registers).
 int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, bool host_data, int min_blocks) {
   const size_t smem = fused_dynamic_smem(acc_slots, smem_tables, threads);
   const bool hi = min_blocks == kFusedMinBlocksHi;
   if (host_data)
-    return hi ? occupancy_of<true, kFusedMinBlocksHi>(threads, smem) : occupancy_of<true, kFusedMinBlocksLo>(threads, smem);
-  return hi ? occupancy_of<false, kFusedMinBlocksHi>(threads, smem) : occupancy_of<false, kFusedMinBlocksLo>(threads, smem);
+    return hi ? occupancy_of<true, kFusedMinBlocksHi, true>(threads, smem)
+              : occupancy_of<true, kFusedMinBlocksLo, true>(threads, smem);
+  return hi ? occupancy_of<false, kFusedMinBlocksHi, true>(threads, smem)
+            : occupancy_of<false, kFusedMinBlocksLo, true>(threads, smem);
 }
 
+// Host-resident batches and batches with a CONTAINS or FSST step run the
+// string-capable build; device-resident batches without one run the lean
+// build.
 cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s) {
   const size_t smem = fused_dynamic_smem(L.acc_slots, L.smem_tables, L.threads);
   const uint32_t tb = uint32_t((L.smem_tables + 15) & ~size_t(15));
   const bool hi = L.min_blocks == kFusedMinBlocksHi;
   if (L.host_data)
-    return hi ? launch_as<true, kFusedMinBlocksHi>(L, smem, tb, s) : launch_as<true, kFusedMinBlocksLo>(L, smem, tb, s);
-  return hi ? launch_as<false, kFusedMinBlocksHi>(L, smem, tb, s) : launch_as<false, kFusedMinBlocksLo>(L, smem, tb, s);
+    return hi ? launch_as<true, kFusedMinBlocksHi, true>(L, smem, tb, s)
+              : launch_as<true, kFusedMinBlocksLo, true>(L, smem, tb, s);
+  if (L.text)
+    return hi ? launch_as<false, kFusedMinBlocksHi, true>(L, smem, tb, s)
+              : launch_as<false, kFusedMinBlocksLo, true>(L, smem, tb, s);
+  return hi ? launch_as<false, kFusedMinBlocksHi, false>(L, smem, tb, s)
+            : launch_as<false, kFusedMinBlocksLo, false>(L, smem, tb, s);
 }
 
 }  // namespace dpf

@@ -33,6 +33,8 @@ struct FusedLaunch {
   size_t smem_tables;   // bytes of the CTA's join-table region
   bool host_data;       // some column lives in mapped pinned host memory
   int min_blocks;       // kFusedMinBlocksLo or kFusedMinBlocksHi: which build runs
+  bool text;            // some query has a CONTAINS step or a string step on an FSST
+                        // column (the build with the general string matcher runs)
 };
 cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s);
 // Occupancy of the fused kernel for (threads, dynamic smem); also sets the

@@ -128,6 +128,7 @@ extern "C" dpf_status dpf_execute_noalloc(dpf_ctx* ctx, const dpf_plan* plan, vo
   L.smem_tables = smem_tables;
   L.acc_slots = Q.use_smem_acc ? uint32_t(slots) : 0u;
   L.host_data = host;
+  L.text = needs_string_matcher(Q);
   L.min_blocks = kFusedMinBlocksLo;
   const int per_sm = fused_blocks_per_sm(L.threads, L.acc_slots, smem_tables, host, L.min_blocks);
   if (per_sm < 1) return fail(DPF_EINVAL, "dpf_execute_noalloc: fused kernel does not fit on an SM");

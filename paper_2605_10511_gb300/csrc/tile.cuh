@@ -243,8 +243,11 @@ __device__ __forceinline__ bool string_match(const DevStep& S, const uint8_t* s,
 
 // PREFIX / CONTAINS step over a string column, dense: lengths decoded, their
 // exclusive scan gives each string's start, then each live row's string is
-// matched.
-template <bool kHost>
+// matched.  kText = false compiles the raw-PREFIX path only (the general
+// matcher of CONTAINS and FSST is left out of the kernel's code); the host
+// launches that build only for batches without such steps, and a step it
+// cannot run drops its rows and reports S_INTERNAL.
+template <bool kHost, bool kText = true>
 __device__ __forceinline__ void tile_prefix(const DevQuery& Q, const DevStep& S, const PageState& P,
                                             const TileHdr& Hd, TileState& T, int lane, unsigned int* status) {
   uint32_t len[TB][4];
@@ -278,9 +281,13 @@ __device__ __forceinline__ void tile_prefix(const DevQuery& Q, const DevStep& S,
           if (b[k] != want) match &= ~(1u << k);
       }
     } else {
+      if constexpr (kText) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (((T.alive >> (4 * t + k)) & 1u) && string_match<kHost>(S, mb + st[k], len[t][k], sym)) match |= 1u << k;
+        for (int k = 0; k < 4; ++k)
+          if (((T.alive >> (4 * t + k)) & 1u) && string_match<kHost>(S, mb + st[k], len[t][k], sym)) match |= 1u << k;
+      } else {
+        if (lane == 0) atomicOr(status, S_INTERNAL);
+      }
     }
     T.alive &= ~((~match & 15u) << (4 * t));
   }
@@ -493,12 +500,12 @@ static_assert(kSegMbs <= 32, "segment mini blocks must fit a 32-bit mask");
 
 // Dense step s of a tile (or none): live bits and group-id contributions.
 // The step's kind, table and codec are resolved here, once per tile.
-template <bool kHost>
+template <bool kHost, bool kText = true>
 __device__ __forceinline__ void tile_dense_step(const DevQuery& Q, uint32_t s, const PageState& P, const TileHdr& Hd,
                                                 TileState& T, const uint8_t* stab, int lane, unsigned int* status) {
   if (s >= Q.nsteps) return;
   const DevStep& S = Q.steps[s];
-  if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) tile_prefix<kHost>(Q, S, P, Hd, T, lane, status);
+  if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) tile_prefix<kHost, kText>(Q, S, P, Hd, T, lane, status);
   else if (Q.cols[S.col].codec == C_DELTA) dense_step_t<kHost, true>(Q, S, P, Hd, T, stab, lane, status);
   else dense_step_t<kHost, false>(Q, S, P, Hd, T, stab, lane, status);
 }
@@ -635,8 +642,8 @@ __device__ __forceinline__ uint32_t row_value(const DevQuery& Q, int c, const Pa
 
 // PREFIX / CONTAINS on a list: lengths and starts of the round's mini
 // blocks are decoded densely and gathered per lane, then each string is
-// matched.
-template <bool kHost>
+// matched (kText = false: raw PREFIX only, as for tile_prefix).
+template <bool kHost, bool kText = true>
 __device__ __forceinline__ bool row_prefix(const DevQuery& Q, const DevStep& S, const PageState& P,
                                            uint32_t seg_mb, uint32_t r, bool valid, int lane,
                                            unsigned int* status) {
@@ -664,7 +671,19 @@ __device__ __forceinline__ bool row_prefix(const DevQuery& Q, const DevStep& S, 
   }
   const uint8_t* bytes = pg + __shfl_sync(kFull, P.extra, c) + my_start;
   const int4* sym = Q.cols[c].codec == C_FSST ? Q.cols[c].sym : nullptr;
-  return valid && string_match<kHost>(S, bytes, my_len, sym);
+  if constexpr (kText) {
+    return valid && string_match<kHost>(S, bytes, my_len, sym);
+  } else {
+    if (!valid) return false;
+    if (S.kind != ST_PREFIX || sym != nullptr) {
+      atomicOr(status, S_INTERNAL);
+      return false;
+    }
+    if (my_len < S.plen) return false;
+    for (uint32_t i = 0; i < S.plen; ++i)
+      if (ld_u8<kHost>(bytes + i) != S.pfx[i]) return false;
+    return true;
+  }
 }
 
 // Join probe of one key; on a hit adds the join's group-id contribution.
@@ -730,7 +749,7 @@ __device__ __forceinline__ uint32_t list_step_t(const DevQuery& Q, const DevStep
 
 // A later step on a DELTA column or a PREFIX step (dense decode of the
 // round's mini blocks); kept out of line.
-template <bool kHost>
+template <bool kHost, bool kText = true>
 __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevStep& S, const PageState& P,
                                                    uint32_t seg_mb, uint32_t* list, uint32_t n,
                                                    const uint8_t* stab, int lane, unsigned int* status) {
@@ -743,7 +762,7 @@ __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevS
     uint32_t gid = e >> kRowBits;
     bool keep;
     if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) {
-      keep = row_prefix<kHost>(Q, S, P, seg_mb, r, valid, lane, status);
+      keep = row_prefix<kHost, kText>(Q, S, P, seg_mb, r, valid, lane, status);
     } else {
       const uint32_t v = row_value<kHost>(Q, S.col, P, seg_mb, r, valid, lane, status);
       if (S.kind == ST_PROBE) {
@@ -772,14 +791,14 @@ __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevS
 
 // Steps first.. of the query over the warp's list; returns the list length.  Each
 // step is resolved to its specialised loop once, outside the loop.
-template <bool kHost>
+template <bool kHost, bool kText = true>
 __device__ __forceinline__ uint32_t list_steps(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                                uint32_t* list, uint32_t n, const uint8_t* stab, int lane,
                                                unsigned int* status, uint32_t first = 1) {
   for (uint32_t s = first; s < Q.nsteps && n != 0; ++s) {
     const DevStep& S = Q.steps[s];
     if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS || Q.cols[S.col].codec == C_DELTA) {
-      n = list_step_generic<kHost>(Q, S, P, seg_mb, list, n, stab, lane, status);
+      n = list_step_generic<kHost, kText>(Q, S, P, seg_mb, list, n, stab, lane, status);
       continue;
     }
     switch (S.kind) {

@@ -286,3 +286,25 @@ def test_fsst_codes_outside_the_table_are_rejected(eng):
     with pytest.raises(dpf.DpfError) as ex:
         eng.ctx.load_encoded(bad)
     assert ex.value.status == -9  # DPF_ECORRUPT
+
+
+def test_batch_mixing_lean_and_string_matcher_queries(eng):
+    """A batch with one CONTAINS-on-FSST query runs the kernel build with the
+    general string matcher for every query in it; the same queries alone run
+    the lean build (raw PREFIX, no string step) or the matcher build.  Every
+    record equals the oracle's either way."""
+    ws = [synth.strings(rows=(1 << 16) + 5, page_rows=8192, seed=61),
+          synth.strings(rows=(1 << 16) + 5, page_rows=8192, seed=62, text=True, contains=b"ab", codec="fsst"),
+          synth.star_join(rows=(1 << 17) + 3, seed=63)]
+    for w in ws:
+        eng.load_workload(w)
+    plans = [eng.plan(w) for w in ws]
+    for i, w in enumerate(ws):
+        assert_same(eng.run(w), expect(w), w["name"])
+    prep = eng.ctx.prepare(plans)
+    try:
+        eng.ctx.launch(prep)
+        for i, w in enumerate(ws):
+            assert_same(eng.ctx.read_result(prep, i), expect(w), ("batch", w["name"]))
+    finally:
+        eng.ctx.release(prep)
