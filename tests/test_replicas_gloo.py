@@ -1,6 +1,7 @@
 """Sharded runs on CPU ranks (gloo, world size 2): each rank evaluates its
 contiguous range of fact pages, the ranks exchange their int64 group
-records, and the merge equals the whole table's result.  The oracle stands
+records, and the merge equals the whole table's result (star, strings,
+random small workloads, a join chain, a BIGINT measure).  The oracle stands
 in for each rank's fused kernel; what is tested is the host logic of
 sharding and merging (paper_2605_10511_gb300.replicas)."""
 
@@ -26,6 +27,10 @@ def _workloads():
     ws = [synth.tiny_random_workload(s, rows=9000, page_rows=1024) for s in (3, 8, 21)]
     ws.append(synth.star_join(rows=70000, seed=9, page_rows=4096))
     ws.append(synth.strings(rows=50000, seed=9, page_rows=2048))
+    # a join chain: each rank builds the whole inner tables and scans its
+    # part of LINEITEM; a BIGINT measure
+    ws.append(synth.chain_join(rows=60000, seed=9, page_rows=2048))
+    ws.append(synth.star_join(rows=40000, seed=10, page_rows=2048, bigint_measure=True))
     return ws
 
 
