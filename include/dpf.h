@@ -5,7 +5,10 @@
  * compressed columnar pages are taken through decompression, predicates,
  * hash-join probes and hash aggregation inside ONE persistent GPU kernel per
  * query batch, without materialising intermediates in global memory and
- * without host intervention during execution (Sec. 3.1, Sec. 3.2).
+ * without host intervention during execution (Sec. 3.1, Sec. 3.2).  The join
+ * tables a plan probes are built by fused scan + build (Kernel #1) and scan +
+ * probe + build (Kernel #2) kernels, so multi-table join chains run as one
+ * pipeline per table.
  *
  * Conventions for every call:
  *   - Return value: 0 (DPF_OK) or a negative dpf_status.  No C++ exception
