@@ -21,6 +21,7 @@ import oracle
 import paper_2605_10511_gb300 as dpf
 import synth
 from paper_2605_10511_gb300.engine import PlanHandle
+from _hand_worked import hand_worked_chains
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +47,11 @@ def expect(w):
     if key not in _want:
         _want[key] = oracle.run_query(w, from_encoded=False)
     return _want[key]
+
+
+def test_hand_worked_chain(eng):
+    for w, want in hand_worked_chains():
+        assert_same(eng.run(w), want, w["name"])
 
 
 @pytest.mark.parametrize("seed", range(48))

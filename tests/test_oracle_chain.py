@@ -3,6 +3,8 @@
 A chain is a join whose dimension is itself joined before its table is
 built (LINEITEM -> ORDERS -> CUSTOMER).  The oracle's result is pinned by
 
+* a chain worked by hand (tests/golden/chain_hand_worked.txt: three tiny
+  tables, the derivation and the expected records);
 * brute force on tiny chains: plain Python loops that, for every fact row,
   search every dimension row by row (no hashing, no sorting);
 * the independent numpy evaluator (``npeval``) on random chains;
@@ -21,6 +23,7 @@ import pytest
 import npeval
 import oracle
 import synth
+from _hand_worked import hand_worked_chains
 
 RECORD_DTYPE = npeval.RECORD_DTYPE
 
@@ -93,6 +96,13 @@ def _brute(w):
         out[i]["count"] = groups[k][0]
         out[i]["val"] = groups[k][1]
     return out
+
+
+def test_hand_worked_chain():
+    for w, want in hand_worked_chains():
+        _same(oracle.run_query(w, from_encoded=False), want, w["name"])
+        _same(oracle.run_query(w, from_encoded=True), want, w["name"])
+        _same(_brute(w), want, w["name"])
 
 
 @pytest.mark.parametrize("seed", range(16))
