@@ -93,14 +93,14 @@ def _workload(name, rows):
         return synth.star_join(rows=rows or (1 << 26), clustered=True, bigint_measure=True)
     if name == "scan":
         return synth.scan_filter_aggregate(rows=rows or (1 << 20))
-    # NEXT-3: LINEITEM -> ORDERS -> CUSTOMER (scan+build, scan+probe+build, fused)
+    # a join chain LINEITEM -> ORDERS -> CUSTOMER (scan+build, scan+probe+build, fused)
     if name == "chain":
         return synth.chain_join(rows=rows or (1 << 26))
     if name == "chain_sparse":
         return synth.chain_join(rows=rows or (1 << 26), sparse_orderkeys=True)
     if name == "strings":
         return synth.strings(rows=rows or (1 << 25))
-    # NEXT-2: word-based strings, LIKE '%ab%', raw bytes vs FSST
+    # word-based strings, LIKE '%ab%', raw bytes vs FSST
     if name == "strings_text":
         return synth.strings(rows=rows or (1 << 25), text=True, contains=b"ab")
     if name == "strings_fsst":

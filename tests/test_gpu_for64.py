@@ -174,3 +174,24 @@ def test_corrupt_for64_headers_are_rejected(eng):
     with pytest.raises(dpf.DpfError) as e:
         eng.ctx.load_encoded(bad)
     assert e.value.status == -9
+
+
+def test_wrapping_sums_match_their_closed_forms(eng):
+    """The library's int64 sums wrap modulo 2^64 exactly as the closed forms
+    of the oracle's pin do (4 * 2^62 -> 0, (2^32)^2 -> 0, INT64_MIN - 1 ->
+    INT64_MAX, 3 * 2^40 * -7)."""
+    i64 = np.iinfo(np.int64)
+    z = np.array([1 << 62] * 4 + [1 << 32, i64.min, 3 << 40], np.int64)
+    cols = {"z": {"codec": "for64", "values": z},
+            "x": {"codec": "for", "values": np.array([1, 1, 1, 1, 1 << 30, 1, -7], np.int32)},
+            "g": {"codec": "dict", "values": np.array([0, 0, 0, 0, 1, 2, 3], np.int32)},
+            "one": {"codec": "for", "values": np.ones(7, np.int32)}}
+    w = _table_workload("bigint_wrap", cols, 7, 128,
+                        [{"op": "sum", "cols": ["z"]}, {"op": "sum_mul", "cols": ["z", "z"]},
+                         {"op": "sum_sub", "cols": ["z", "one"]}, {"op": "sum_mul", "cols": ["z", "x"]}],
+                        [{"col": "g"}])
+    r = eng.run(w)
+    assert r["count"].tolist() == [4, 1, 1, 1]
+    assert r["val"].tolist() == [[0, 0, -4, 0], [1 << 32, 0, (1 << 32) - 1, 1 << 62],
+                                 [int(i64.min), 0, int(i64.max), int(i64.min)],
+                                 [3 << 40, 0, (3 << 40) - 1, -21 * (1 << 40)]]

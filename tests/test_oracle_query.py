@@ -137,3 +137,33 @@ def test_star_join_with_date_filter(oracle_lib, clustered):
     got = oracle_lib.run_query(w, from_encoded=True)
     _records_equal(got, npeval.evaluate(w))
     assert got.shape[0] > 0 and np.all(got["key"][:, 1] == 1995)
+
+
+def test_bigint_aggregates_wrap_modulo_2_64(oracle_lib):
+    """Closed forms for FOR64 (BIGINT) operands: four copies of 2^62 sum to
+    2^64 = 0 modulo 2^64; (2^32)^2 = 2^64 wraps to 0 as well; INT64_MIN - 1
+    wraps to INT64_MAX; and a mixed 32/64-bit product keeps all 64 bits."""
+    i64 = np.iinfo(np.int64)
+    z = np.array([1 << 62] * 4 + [1 << 32, i64.min, 3 << 40], np.int64)
+    x = np.array([1, 1, 1, 1, 1 << 30, 1, -7], np.int32)
+    g = np.array([0, 0, 0, 0, 1, 2, 3], np.int32)
+    w = {"name": "bigint_wrap", "fact": "f",
+         "tables": {"f": {"rows": 7, "page_rows": 128,
+                          "cols": {"z": {"codec": "for64", "values": z}, "x": {"codec": "for", "values": x},
+                                   "g": {"codec": "dict", "values": g},
+                                   "one": {"codec": "for", "values": np.ones(7, np.int32)}}}},
+         "query": {"preds": [], "joins": [], "group": [{"col": "g"}],
+                   "aggs": [{"op": "sum", "cols": ["z"]}, {"op": "sum_mul", "cols": ["z", "z"]},
+                            {"op": "sum_sub", "cols": ["z", "one"]}, {"op": "sum_mul", "cols": ["z", "x"]}]}}
+    for from_encoded in (False, True):
+        r = oracle_lib.run_query(w, from_encoded=from_encoded)
+        assert r["key"][:, 0].tolist() == [0, 1, 2, 3]
+        assert r["count"].tolist() == [4, 1, 1, 1]
+        # group 0: 4 * 2^62 = 2^64 -> 0; (2^62)^2 * 4 -> 0; 4 * (2^62 - 1) = 2^64 - 4 -> -4; 4 * 2^62 -> 0
+        assert r["val"][0].tolist() == [0, 0, -4, 0]
+        # group 1: 2^32; (2^32)^2 = 2^64 -> 0; 2^32 - 1; 2^32 * 2^30 = 2^62
+        assert r["val"][1].tolist() == [1 << 32, 0, (1 << 32) - 1, 1 << 62]
+        # group 2: INT64_MIN; INT64_MIN^2 = 2^126 -> 0; INT64_MIN - 1 -> INT64_MAX; INT64_MIN * 1
+        assert r["val"][2].tolist() == [int(i64.min), 0, int(i64.max), int(i64.min)]
+        # group 3: 3 * 2^40; 9 * 2^80 -> 0 mod 2^64; 3 * 2^40 - 1; -21 * 2^40
+        assert r["val"][3].tolist() == [3 << 40, 0, (3 << 40) - 1, -21 * (1 << 40)]
