@@ -1,0 +1,60 @@
+"""Host logic of bench.py on CPU: the reference arm's JSON line (the CPU
+oracle on a bounded sample), the workload table, and how the DRAM traffic of
+a committed ncu summary is looked up, scaled by rows and dropped once the
+kernel sources change."""
+
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--rows", "65536",
+                        "--steps", "2", "--warmup", "3", "--ref-budget-s", "2"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["unit"] == "rows/s" and d["higher_is_better"] is True and d["value"] > 0
+    assert d["steps"] == 2 and d["warmup"] == 3
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("star_join")
+
+
+@pytest.mark.parametrize("name", ["star", "star_unsorted", "star_year", "star_year_unsorted", "star_bigint", "scan",
+                                  "strings", "strings_text", "strings_fsst", "chain", "chain_sparse"])
+def test_every_workload_name_builds(name):
+    w = bench._workload(name, 1 << 12)
+    assert w["tables"][w["fact"]]["rows"] == 1 << 12
+    assert w["query"]["aggs"]
+
+
+def _profile(tmp_path, workload, source_hash, rows, dram):
+    d = tmp_path / "profiles"
+    d.mkdir(exist_ok=True)
+    (d / f"fused_kernel_{workload}.txt").write_text(
+        f"title line\n\nsource_hash: {source_hash}\ncaptured_rows: {rows}\n"
+        f"dram_bytes_per_launch: {dram}\n  indented: lines are notes\n")
+
+
+def test_stored_traffic_scales_by_rows_and_drops_stale_captures(tmp_path, monkeypatch):
+    h = bench.kernel_source_hash()  # of the real kernel sources
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: h)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    _profile(tmp_path, "star", h, 1 << 25, 1000)
+    traffic, src = bench.stored_traffic("star", 1 << 26)
+    assert traffic == 2000 and "scaled" in src
+    _profile(tmp_path, "star", "0" * 16, 1 << 25, 1000)
+    assert bench.stored_traffic("star", 1 << 26) == (None, "stale (kernel changed since capture)")
+    assert bench.stored_traffic("chain", 1 << 26) == (None, "no capture")
