@@ -44,7 +44,7 @@ def build(force=False):
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -119,6 +119,8 @@ def lib():
             L.orc_query.argtypes = [C.POINTER(_Table), C.c_int32, C.POINTER(_Pred), C.c_int32,
                                     C.POINTER(_Join), C.c_int32, C.POINTER(_Key), C.c_int32,
                                     C.POINTER(_Agg), P, C.c_uint64]
+            L.orc_query_threads.restype = C.c_int64
+            L.orc_query_threads.argtypes = L.orc_query.argtypes + [C.c_int32, C.c_uint64]
             _lib = L
     return _lib
 
@@ -136,7 +138,8 @@ class use_library:
         L = C.CDLL(self.path)
         for name in ("orc_encode_int", "orc_decode_int", "orc_decode_int_row", "orc_encode_for64",
                      "orc_decode_for64", "orc_decode_for64_row", "orc_encode_str", "orc_decode_str",
-                     "orc_fsst_build", "orc_encode_fsst", "orc_decode_fsst", "orc_query"):
+                     "orc_fsst_build", "orc_encode_fsst", "orc_decode_fsst", "orc_query",
+                     "orc_query_threads"):
             f, g = getattr(L, name), getattr(self._saved, name)
             f.restype, f.argtypes = g.restype, g.argtypes
         _lib = L
@@ -397,9 +400,23 @@ def _joins(tables, specs, probe_names, keep, dim_tables):
     return arr
 
 
-def run_query(workload, from_encoded=True, tables=None):
-    """Evaluate ``workload['query']``; returns an array of RECORD_DTYPE."""
+def host_threads():
+    """Host threads the oracle may use: the CPUs this process may run on."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return max(1, os.cpu_count() or 1)
+
+
+def run_query(workload, from_encoded=True, tables=None, threads=1):
+    """Evaluate ``workload['query']``; returns an array of RECORD_DTYPE.
+
+    ``threads`` > 1 evaluates the fact table's pages on that many host
+    threads (``orc_query_threads``: disjoint page ranges, per-thread group
+    maps added together); ``threads=0`` uses every CPU of the process."""
     L = lib()
+    if threads == 0:
+        threads = host_threads()
     q = workload["query"]
     if tables is None:
         tables = decoded_tables(workload, from_encoded)
@@ -423,15 +440,20 @@ def run_query(workload, from_encoded=True, tables=None):
         cols = a.get("cols", [])
         aggs[i].a = fnames.index(cols[0]) if cols else 0
         aggs[i].b = fnames.index(cols[1]) if len(cols) > 1 else 0
+    page_rows = int(workload["tables"][workload["fact"]].get("page_rows", 65536))
+
+    def call(out, cap):
+        args = (C.pointer(ft), len(q["preds"]), preds, len(q["joins"]), joins,
+                len(q["group"]), keys, len(q["aggs"]), aggs, _ptr(out), cap)
+        if threads > 1:
+            return _check(L.orc_query_threads(*args, int(threads), page_rows), "query_threads")
+        return _check(L.orc_query(*args), "query")
+
     cap = 1 << 16
     out = np.zeros(cap, RECORD_DTYPE)
-    n = _check(L.orc_query(C.pointer(ft), len(q["preds"]), preds, len(q["joins"]), joins,
-                           len(q["group"]), keys, len(q["aggs"]), aggs, _ptr(out), cap),
-               "query")
+    n = call(out, cap)
     if n > cap:
         out = np.zeros(n, RECORD_DTYPE)
-        n = _check(L.orc_query(C.pointer(ft), len(q["preds"]), preds, len(q["joins"]), joins,
-                               len(q["group"]), keys, len(q["aggs"]), aggs, _ptr(out), n),
-                   "query")
+        n = call(out, n)
     del keep, dim_tables
     return out[:n].copy()

@@ -22,6 +22,10 @@
 // up in std::unordered_map built from the rows that pass the dimension
 // predicates (the build side of Kernel #1), and accumulates groups in a
 // std::map ordered by the key tuple (the record-format result of Kernel #3).
+// orc_query_threads runs the same row walk on several host threads over
+// disjoint page ranges and adds their group records together (int64
+// addition modulo 2^64, so the records are those of the one-thread walk);
+// it exists to evaluate tables of 2^28-2^30 rows in the tests in minutes.
 //
 // Parity status of every function here: pinned by the tests under
 // tests/test_oracle_*.py (hand-worked golden bytes, encode/decode round
@@ -32,8 +36,12 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <thread>
 #include <unordered_map>
 #include <vector>
+
+// <thread> defines errno's EINVAL macro; the status names below are this file's own.
+#undef EINVAL
 
 namespace {
 
@@ -905,32 +913,39 @@ static int64_t build_map(const OrcJoin& J, OrcMap& m, int depth) {
   return 0;
 }
 
-// Evaluates the query.  Writes at most cap records (sorted ascending by key
-// tuple, groups with zero rows omitted, an ungrouped query always yields one
-// record) and returns the number of records, or a negative status.
-int64_t orc_query(const OrcTable* fact, int32_t npreds, const OrcPred* preds, int32_t njoins,
-                  const OrcJoin* joins, int32_t nkeys, const OrcKey* keys, int32_t naggs,
-                  const OrcAgg* aggs, OrcRecord* out, uint64_t cap) {
-  if (njoins > 8 || nkeys > 2 || naggs > 4) return EINVAL;
+using OrcGroups = std::map<std::pair<int32_t, int32_t>, OrcRecord>;
+
+// Checks the plan's shape and builds the join maps (the build side: key ->
+// payload values of the dimension rows that pass).  Returns 0 or a status.
+static int64_t prepare_query(const OrcTable* fact, int32_t njoins, const OrcJoin* joins, int32_t nkeys,
+                             const OrcKey* keys, int32_t naggs, std::vector<OrcMap>& maps) {
+  if (njoins < 0 || njoins > 8 || nkeys < 0 || nkeys > 2 || naggs < 0 || naggs > 4) return EINVAL;
   for (int32_t j = 0; j < njoins; ++j)
     if (!is_i32(*fact, joins[j].fk_col)) return EINVAL;
   for (int32_t k = 0; k < nkeys; ++k)
     if (keys[k].kind == 0 && !is_i32(*fact, keys[k].col)) return EINVAL;
-  // Build side: key -> payload values of the dimension rows that pass.
-  std::vector<OrcMap> maps(njoins);
+  maps.assign(size_t(njoins), OrcMap());
   for (int32_t j = 0; j < njoins; ++j) {
-    const int64_t rc = build_map(joins[j], maps[j], 0);
+    const int64_t rc = build_map(joins[j], maps[size_t(j)], 0);
     if (rc) return rc;
   }
-  std::map<std::pair<int32_t, int32_t>, OrcRecord> groups;
-  for (uint64_t r = 0; r < fact->n; ++r) {
+  return 0;
+}
+
+// The probe side, one fact row at a time, over rows [r0, r1): predicates,
+// then each join's lookup (a miss drops the row), then the row's group
+// record, whose count and aggregates grow by this row's contribution.
+static void eval_rows(const OrcTable* fact, uint64_t r0, uint64_t r1, int32_t npreds, const OrcPred* preds,
+                      int32_t njoins, const OrcJoin* joins, const std::vector<OrcMap>& maps, int32_t nkeys,
+                      const OrcKey* keys, int32_t naggs, const OrcAgg* aggs, OrcGroups& groups) {
+  for (uint64_t r = r0; r < r1; ++r) {
     bool ok = true;
     for (int32_t k = 0; k < npreds && ok; ++k) ok = eval_pred(*fact, preds[k], r);
     if (!ok) continue;
-    std::vector<const std::vector<int32_t>*> hit(njoins);
+    const std::vector<int32_t>* hit[8] = {};
     for (int32_t j = 0; j < njoins && ok; ++j) {
-      auto it = maps[j].find(fact->cols[joins[j].fk_col].v[r]);
-      if (it == maps[j].end()) ok = false; else hit[j] = &it->second;
+      auto it = maps[size_t(j)].find(fact->cols[joins[j].fk_col].v[r]);
+      if (it == maps[size_t(j)].end()) ok = false; else hit[j] = &it->second;
     }
     if (!ok) continue;
     int32_t kv[2] = {0, 0};
@@ -953,6 +968,11 @@ int64_t orc_query(const OrcTable* fact, int32_t npreds, const OrcPred* preds, in
       g.val[a] = int64_t(uint64_t(g.val[a]) + uint64_t(add));   // two's-complement wrap
     }
   }
+}
+
+// Writes the groups as records (ascending by key tuple; an ungrouped query
+// always yields one record) and returns their number.
+static int64_t emit_groups(OrcGroups& groups, int32_t nkeys, OrcRecord* out, uint64_t cap) {
   if (nkeys == 0 && groups.empty()) groups.emplace(std::make_pair(0, 0), OrcRecord{});
   uint64_t i = 0;
   for (const auto& kv : groups) {
@@ -960,6 +980,59 @@ int64_t orc_query(const OrcTable* fact, int32_t npreds, const OrcPred* preds, in
     ++i;
   }
   return int64_t(i);
+}
+
+// Evaluates the query.  Writes at most cap records (sorted ascending by key
+// tuple, groups with zero rows omitted, an ungrouped query always yields one
+// record) and returns the number of records, or a negative status.  This
+// single-threaded walk over all fact rows is the definition.
+int64_t orc_query(const OrcTable* fact, int32_t npreds, const OrcPred* preds, int32_t njoins,
+                  const OrcJoin* joins, int32_t nkeys, const OrcKey* keys, int32_t naggs,
+                  const OrcAgg* aggs, OrcRecord* out, uint64_t cap) {
+  std::vector<OrcMap> maps;
+  const int64_t rc = prepare_query(fact, njoins, joins, nkeys, keys, naggs, maps);
+  if (rc) return rc;
+  OrcGroups groups;
+  eval_rows(fact, 0, fact->n, npreds, preds, njoins, joins, maps, nkeys, keys, naggs, aggs, groups);
+  return emit_groups(groups, nkeys, out, cap);
+}
+
+// The same result from `nthreads` host threads: the fact rows are cut into
+// ranges of `range_rows` rows (the page size, so a range is a run of whole
+// pages), thread t evaluates ranges t, t + nthreads, ... into its own group
+// map exactly as orc_query does, and the maps are merged by adding counts
+// and aggregates modulo 2^64.  Integer addition is associative and
+// commutative, so the merged records equal orc_query's.
+int64_t orc_query_threads(const OrcTable* fact, int32_t npreds, const OrcPred* preds, int32_t njoins,
+                          const OrcJoin* joins, int32_t nkeys, const OrcKey* keys, int32_t naggs,
+                          const OrcAgg* aggs, OrcRecord* out, uint64_t cap, int32_t nthreads,
+                          uint64_t range_rows) {
+  if (nthreads < 1 || nthreads > 1024 || range_rows == 0) return EINVAL;
+  std::vector<OrcMap> maps;
+  const int64_t rc = prepare_query(fact, njoins, joins, nkeys, keys, naggs, maps);
+  if (rc) return rc;
+  const uint64_t nranges = (fact->n + range_rows - 1) / range_rows;
+  std::vector<OrcGroups> part(static_cast<size_t>(nthreads));
+  auto work = [&](int32_t t) {
+    for (uint64_t i = uint64_t(t); i < nranges; i += uint64_t(nthreads)) {
+      const uint64_t r0 = i * range_rows, r1 = std::min(fact->n, r0 + range_rows);
+      eval_rows(fact, r0, r1, npreds, preds, njoins, joins, maps, nkeys, keys, naggs, aggs, part[size_t(t)]);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int32_t t = 1; t < nthreads; ++t) pool.emplace_back(work, t);
+  work(0);
+  for (auto& th : pool) th.join();
+  OrcGroups groups;
+  for (const OrcGroups& p : part)
+    for (const auto& kv : p) {
+      auto ins = groups.emplace(kv.first, kv.second);
+      if (ins.second) continue;
+      OrcRecord& g = ins.first->second;
+      g.count = int64_t(uint64_t(g.count) + uint64_t(kv.second.count));
+      for (int a = 0; a < 4; ++a) g.val[a] = int64_t(uint64_t(g.val[a]) + uint64_t(kv.second.val[a]));
+    }
+  return emit_groups(groups, nkeys, out, cap);
 }
 
 }  // extern "C"

@@ -57,6 +57,14 @@ MUTANTS = {
     "for64_word_offset_half": ("woff += 2 * bws[m];", "woff += bws[m];"),
     "dict_rank_off_by_one": ("std::lower_bound(dict.begin(), dict.end(), values[r]) - dict.begin();",
                              "std::upper_bound(dict.begin(), dict.end(), values[r]) - dict.begin();"),
+    "threads_merge_drops_counts": ("g.count = int64_t(uint64_t(g.count) + uint64_t(kv.second.count));",
+                                   "g.count = int64_t(uint64_t(g.count));"),
+    "threads_merge_drops_sums": ("g.val[a] = int64_t(uint64_t(g.val[a]) + uint64_t(kv.second.val[a]));",
+                                 "g.val[a] = int64_t(uint64_t(kv.second.val[a]));"),
+    "threads_range_end_short": ("r1 = std::min(fact->n, r0 + range_rows);",
+                                "r1 = std::min(fact->n, r0 + range_rows - 1);"),
+    "threads_last_range_skipped": ("for (uint64_t i = uint64_t(t); i < nranges; i += uint64_t(nthreads)) {",
+                                   "for (uint64_t i = uint64_t(t); i + 1 < nranges; i += uint64_t(nthreads)) {"),
 }
 
 
@@ -92,6 +100,13 @@ def _pins_pass(o):
                 assert np.array_equal(g["key"], e["key"]), seed
                 assert np.array_equal(g["count"], e["count"]), seed
                 assert np.array_equal(g["val"], e["val"]), seed
+        for seed in range(40):  # the threaded walk over page ranges (3 threads)
+            w = synth.tiny_random_workload(seed)
+            e = npeval.evaluate(w)
+            g = o.run_query(w, from_encoded=False, threads=3)
+            assert g.shape == e.shape, ("threads", seed)
+            for f in ("key", "count", "val"):
+                assert np.array_equal(g[f], e[f]), ("threads", seed, f)
         for seed in range(40):
             w = synth.tiny_chain_workload(seed)
             e = npeval.evaluate(w)
@@ -117,7 +132,7 @@ def _build_variant(src_text, tmpdir, name):
     with open(path, "w") as f:
         f.write(src_text)
     so = os.path.join(tmpdir, f"lib{name}.so")
-    subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-o", so, path])
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o", so, path])
     return so
 
 
