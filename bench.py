@@ -265,33 +265,6 @@ def run_batched(args, dpf, torch, np, local):
     print(json.dumps(out), flush=True)
 
 
-def serve_variants(w, n_star, n_scan, seed):
-    """Queries over one resident star schema: star joins with the dimension
-    predicate constants re-drawn from the dimensions' own values, and
-    scan-filter-aggregates over the fact's measures."""
-    import copy
-
-    import numpy as np
-    rng = np.random.default_rng(seed)
-    out = []
-    for i in range(n_star):
-        v = copy.deepcopy(w)
-        v["tables"] = w["tables"]
-        for j in v["query"]["joins"]:
-            for p in j["preds"]:
-                vals = np.unique(w["tables"][j["dim"]]["cols"][p["col"]]["values"])
-                p["args"] = [int(x) for x in rng.choice(vals, len(p["args"]), replace=False)]
-        out.append(v)
-    for i in range(n_scan):
-        v = {k: w[k] for k in ("name", "tables", "fact")}
-        lo = int(rng.integers(1, 5_000_000))
-        v["query"] = {"preds": [{"col": "m2", "op": "lt", "args": [int(rng.integers(1000, 100_000))]},
-                                {"col": "m1", "op": "between", "args": [lo, lo + int(rng.integers(1, 5_000_000))]}],
-                      "joins": [], "group": [], "aggs": [{"op": "sum", "cols": ["m1"]}, {"op": "count"}]}
-        out.append(v)
-    return out
-
-
 def run_serve(args, dpf, torch, np, local):
     """Poisson streams of queries at several rates through the
     continuous-batching server over a resident star schema; p50/p99 latency
@@ -303,7 +276,7 @@ def run_serve(args, dpf, torch, np, local):
     t0 = time.perf_counter()
     eng.load_workload(w, fact_placement=args.serve_placement)
     load_s = time.perf_counter() - t0
-    qs = serve_variants(w, 12, 4, seed=5)
+    qs = synth.serve_variants(w, 12, 4, seed=5)
     plans = [eng.plan(v) for v in qs]
     ref = [eng.run(v) for v in qs]  # each query alone
     alg = [eng.fact_bytes(v)[0] for v in qs]

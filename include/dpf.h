@@ -372,23 +372,37 @@ dpf_status dpf_prep_stats(dpf_ctx* ctx, dpf_prep_id prep, uint32_t* launches,
  * allocator).  The paper has no counterpart; this is a library convenience.
  * Runs ONE plan through the fused kernel on `stream` and allocates nothing:
  * the kernel's scratch (scheduler counters, the compiled plan, the per-group
- * int64 accumulators) lives in a fixed 1 MiB region of device memory that is
- * part of the library image (every GPU that loads the library holds it until
- * the process exits).  The caller passes the outputs:
+ * int64 accumulators) lives in a fixed region of DPF_NOALLOC_SCRATCH_BYTES
+ * (1 MiB) of device memory that is part of the library image (every GPU
+ * that loads the library holds it until the process exits).  The caller
+ * passes the outputs:
  *   out: device dpf_record[cap], cap >= the plan's group domain (1 when
  *        ungrouped); records are written ascending by key tuple
  *   out_count: device uint32, receives the number of records
  * Asynchronous; read the outputs after synchronising `stream`.  The first
  * call on a device looks up the region's device address (a one-time set-up
- * per device); make that first call before any stream capture.  Every call
- * shares the one region per device and clears it before use, so calls whose
- * kernels overlap on the GPU (different streams, or different threads) race
- * and give wrong results: serialise them.  Device-side data checks are not
- * reported by this call.  Errors: DPF_EINVAL (a plan needing more than 1 MiB
- * of scratch: 2816 bytes + 8 x domain x (1 + aggregates); cap below the
- * domain; the dpf_prepare plan errors), DPF_ECUDA. */
+ * per device).  The call copies its compiled plan from host memory that
+ * lives only for the call, so it cannot be captured into a CUDA graph: on
+ * a capturing stream it returns DPF_EINVAL and enqueues nothing.  Every
+ * call shares the one region per device and clears it before use, so calls
+ * whose kernels overlap on the GPU (different streams, or different
+ * threads) race and give wrong results: serialise them.  Device-side data
+ * checks are read back with dpf_noalloc_status.  Errors: DPF_EINVAL (a plan
+ * needing more scratch than the region holds: DPF_NOALLOC_FIXED_BYTES +
+ * 8 x domain x (1 + aggregates) bytes; cap below the domain; a capturing
+ * stream; the dpf_prepare plan errors), DPF_ECUDA. */
+#define DPF_NOALLOC_SCRATCH_BYTES (1u << 20)
+#define DPF_NOALLOC_FIXED_BYTES 3328u /* scheduler state + compiled plan */
 dpf_status dpf_execute_noalloc(dpf_ctx* ctx, const dpf_plan* plan, void* stream, dpf_record* out,
                                uint64_t cap, uint32_t* out_count);
+/* Device status word of the last dpf_execute_noalloc kernel on the
+ * context's device, read after the caller has synchronised that call's
+ * stream (a blocking 4-byte copy; allocates nothing).  *bits = the raw word
+ * (0 = clean).  Returns DPF_OK when clean, DPF_ECORRUPT when the kernel met
+ * data that passed load validation but not its own checks (e.g. a
+ * dictionary code beyond its dictionary: such rows are dropped), or
+ * DPF_EINTERNAL (a bounded probe ran out of slots). */
+dpf_status dpf_noalloc_status(dpf_ctx* ctx, uint32_t* bits);
 
 /* One-shot form (Sec. 3.1): prepare + launch on `stream`; out_ids[i]
  * names plan i's result.  n > 1 runs every plan in one persistent launch. */

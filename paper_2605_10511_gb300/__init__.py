@@ -147,6 +147,7 @@ _SIGS = {
     "dpf_prepare_unfused": (C.c_int32, [_P, C.POINTER(Plan), C.POINTER(C.c_int32)]),
     "dpf_prep_stats": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]),
     "dpf_execute_noalloc": (C.c_int32, [_P, C.POINTER(Plan), _P, _P, C.c_uint64, _P]),
+    "dpf_noalloc_status": (C.c_int32, [_P, C.POINTER(C.c_uint32)]),
     "dpf_execute_plan": (C.c_int32, [_P, C.POINTER(Plan), C.c_int32, _P, C.POINTER(C.c_int64)]),
     "dpf_fetch_result": (C.c_int32, [_P, C.c_int64, _P, C.c_uint64, C.POINTER(C.c_uint64), C.c_int32]),
     "dpf_server_create": (C.c_int32, [_P, C.POINTER(ServerConfig), C.POINTER(_P)]),
@@ -433,6 +434,14 @@ class Context:
         buffers (dpf_record[cap], uint32)."""
         _check(lib().dpf_execute_noalloc(self.h, C.byref(plan.plan), _stream_ptr(stream),
                                          C.c_void_p(out_ptr), int(cap), C.c_void_p(count_ptr)))
+
+    def noalloc_status(self):
+        """Status word of the last allocation-free call's kernel (call after
+        synchronising its stream): raises DpfError (DPF_ECORRUPT /
+        DPF_EINTERNAL) when it is set, else returns 0."""
+        bits = C.c_uint32()
+        _check(lib().dpf_noalloc_status(self.h, C.byref(bits)))
+        return bits.value
 
     def execute(self, plans, stream=None):
         arr = (Plan * len(plans))(*[p.plan for p in plans])

@@ -11,6 +11,7 @@
 // the library image: the array below, reserved on every GPU that loads the
 // library and held until the process exits.  The caller provides the
 // output buffer.
+#include <cstddef>
 #include <mutex>
 
 #include "../../include/dpf.h"
@@ -26,7 +27,7 @@ std::recursive_mutex& ctx_mutex(dpf_ctx* c);
 
 // Capacity of the shared scratch region (1 MiB): scheduler state, the
 // compiled plan and domain x (1 + aggregates) int64 accumulators.
-constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;
+constexpr size_t kNoAllocScratchBytes = DPF_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
 
 namespace {
@@ -37,6 +38,9 @@ constexpr size_t kOffQuery = 512;
 constexpr size_t kQueryBytes = (sizeof(DevQuery) + 255) / 256 * 256;
 constexpr size_t kOffDone = kOffQuery + kQueryBytes;
 constexpr size_t kOffAcc = kOffDone + 256;
+// The header states the fixed part of the region in bytes; keep the two equal.
+static_assert(kOffAcc == DPF_NOALLOC_FIXED_BYTES, "update DPF_NOALLOC_FIXED_BYTES in dpf.h");
+static_assert(offsetof(Sched, status) % 4 == 0, "status word alignment");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
@@ -68,6 +72,17 @@ extern "C" dpf_status dpf_execute_noalloc(dpf_ctx* ctx, const dpf_plan* plan, vo
                                           uint64_t cap, uint32_t* out_count) {
   if (!ctx || !plan || !out || !out_count) return fail(DPF_EINVAL, "NULL argument");
   std::lock_guard<std::recursive_mutex> lk(ctx_mutex(ctx));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  {
+    // The call copies its plan and ticket table from host stack memory; a
+    // captured copy would keep the address of that dead frame and a replay
+    // would launch the kernel on garbage, so a capturing stream is refused.
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(s, &cap_st);
+    if (ce != cudaSuccess) return fail(DPF_ECUDA, "dpf_execute_noalloc: %s", cudaGetErrorString(ce));
+    if (cap_st != cudaStreamCaptureStatusNone)
+      return fail(DPF_EINVAL, "dpf_execute_noalloc cannot be captured into a CUDA graph (the stream is capturing)");
+  }
   DevQuery Q;
   size_t smem_tables = 0;
   bool host = false;
@@ -109,7 +124,6 @@ extern "C" dpf_status dpf_execute_noalloc(dpf_ctx* ctx, const dpf_plan* plan, vo
   Q.out_n = out_count;
   const uint64_t qbegin[2] = {0, Q.nchunks};
 
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the region keeps the previous call's contents: clear the counters and
   // accumulators, then write this call's plan
   cudaError_t e = cudaMemsetAsync(base + kOffSched, 0, sizeof(Sched), s);
@@ -135,5 +149,34 @@ extern "C" dpf_status dpf_execute_noalloc(dpf_ctx* ctx, const dpf_plan* plan, vo
   L.grid = int(std::max<uint64_t>(1, std::min<uint64_t>(uint64_t(num_sms) * per_sm, Q.nchunks)));
   e = launch_fused(L, s);
   if (e != cudaSuccess) return fail(DPF_ECUDA, "dpf_execute_noalloc launch: %s", cudaGetErrorString(e));
+  return DPF_OK;
+}
+
+extern "C" dpf_status dpf_noalloc_status(dpf_ctx* ctx, uint32_t* bits) {
+  if (!ctx || !bits) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(ctx_mutex(ctx));
+  int device = -1;
+  dpf_status st = dpf_context_device(ctx, &device);
+  if (st) return st;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device) cudaSetDevice(device);
+  struct Restore {
+    int prev, dev;
+    ~Restore() {
+      if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    }
+  } restore{prev, device};
+  uint8_t* base = nullptr;
+  if ((st = scratch_address(device, &base))) return st;
+  uint32_t word = 0;
+  const cudaError_t e = cudaMemcpy(&word, base + kOffSched + offsetof(Sched, status), sizeof word,
+                                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(DPF_ECUDA, "dpf_noalloc_status: %s", cudaGetErrorString(e));
+  *bits = word;
+  if (word & S_CORRUPT)
+    return fail(DPF_ECORRUPT, "the last dpf_execute_noalloc kernel met corrupt data (status 0x%x)", word);
+  if (word & (S_INTERNAL | S_TIMEOUT))
+    return fail(DPF_EINTERNAL, "the last dpf_execute_noalloc kernel hit a device invariant (status 0x%x)", word);
   return DPF_OK;
 }

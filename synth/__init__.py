@@ -13,6 +13,7 @@ from .tables import (  # noqa: F401
     chain_join,
     date_keys,
     scan_filter_aggregate,
+    serve_variants,
     star_join,
     strings,
     tiny_chain_workload,

@@ -500,6 +500,33 @@ def batched_workloads(n_queries=64, seed=4, log2_lo=16.0, log2_hi=26.0,
     return out
 
 
+def serve_variants(w, n_star=12, n_scan=4, seed=5):
+    """Query variants over one resident star schema ``w`` (the serving mix):
+    ``n_star`` star joins with the dimension predicate constants re-drawn
+    from the dimensions' own values, then ``n_scan`` scan-filter-aggregates
+    over the fact's measures (``m2 < x AND m1 BETWEEN lo AND hi``, SUM(m1),
+    COUNT).  Every variant shares ``w``'s tables (no copy)."""
+    import copy
+    rng = _rng(seed)
+    out = []
+    for _ in range(n_star):
+        v = copy.deepcopy({k: x for k, x in w.items() if k != "tables"})
+        v["tables"] = w["tables"]
+        for j in v["query"]["joins"]:
+            for p in j["preds"]:
+                vals = np.unique(w["tables"][j["dim"]]["cols"][p["col"]]["values"])
+                p["args"] = [int(x) for x in rng.choice(vals, len(p["args"]), replace=False)]
+        out.append(v)
+    for _ in range(n_scan):
+        v = {k: w[k] for k in ("name", "tables", "fact")}
+        lo = int(rng.integers(1, 5_000_000))
+        v["query"] = {"preds": [{"col": "m2", "op": "lt", "args": [int(rng.integers(1000, 100_000))]},
+                                {"col": "m1", "op": "between", "args": [lo, lo + int(rng.integers(1, 5_000_000))]}],
+                      "joins": [], "group": [], "aggs": [{"op": "sum", "cols": ["m1"]}, {"op": "count"}]}
+        out.append(v)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Small random workloads for property tests
 # ---------------------------------------------------------------------------
