@@ -100,6 +100,9 @@ def _workload(name, rows):
         return synth.chain_join(rows=rows or (1 << 26), sparse_orderkeys=True)
     if name == "strings":
         return synth.strings(rows=rows or (1 << 25))
+    # every row passes (an empty prefix): the group-by takes all 2^25 rows, Zipf-skewed keys
+    if name == "strings_all":
+        return synth.strings(rows=rows or (1 << 25), prefix=b"")
     # word-based strings, LIKE '%ab%', raw bytes vs FSST
     if name == "strings_text":
         return synth.strings(rows=rows or (1 << 25), text=True, contains=b"ab")
@@ -388,7 +391,7 @@ def main():
     ap.add_argument("--impl", default="dpf", choices=["dpf", "reference"])
     ap.add_argument("--workload", default="star",
                     choices=["star", "star_unsorted", "star_year", "star_year_unsorted", "star_bigint", "scan",
-                             "strings",
+                             "strings", "strings_all",
                              "strings_text", "strings_fsst", "chain", "chain_sparse", "batched"])
     ap.add_argument("--batch-queries", type=int, default=64)
     ap.add_argument("--serve", action="store_true", help="Poisson serving run instead of the step benchmark")

@@ -115,13 +115,44 @@ __device__ void finish_query(const DevQuery& Q, unsigned long long* sacc, uint32
   __syncthreads();
 }
 
+// Warp-aggregated group-by update (hash aggregation of Kernel #3, Sec. 3.1):
+// the lanes of a round that hold the same group id (`peers`, from
+// __match_any_sync) add their int64 values once.  Lanes alone in their group
+// add directly; otherwise each lane parks its value in the warp's 32-slot
+// buffer and the group's lowest lane sums its peers' values and issues the
+// group's single atomic.  Skewed keys (a Zipf head holding a fifth of the
+// rows) thus cost one atomic per distinct group per round instead of one per
+// row on the same address.  Warp-uniform call.
+__device__ __forceinline__ void warp_group_add(unsigned long long* acc, uint64_t idx, unsigned long long x,
+                                               bool valid, uint32_t peers, int lane, unsigned long long* wbuf) {
+  const uint32_t others = peers & ~(1u << lane);
+  if (!__any_sync(kFull, valid && others != 0)) {
+    if (valid) atomicAdd(acc + idx, x);
+    return;
+  }
+  wbuf[lane] = x;
+  __syncwarp();
+  if (valid && (peers & ((1u << lane) - 1u)) == 0) {
+    for (uint32_t p = others; p; p &= p - 1) x += wbuf[__ffs(p) - 1];
+    atomicAdd(acc + idx, x);
+  }
+  __syncwarp();
+}
+
+// Lanes of the round with the same group id as this one (valid lanes only;
+// invalid lanes share a key no group id takes).
+__device__ __forceinline__ uint32_t group_peers(uint32_t gid, bool valid) {
+  return __match_any_sync(kFull, valid ? gid : 0xffffffffu);
+}
+
 // One aggregate over a warp's list, specialised on its operation (dpf_agg_op)
 // and on how its operands are read: kPoint = FOR/DICT columns, one bit field
 // per row; otherwise any codec through row_value (DELTA decodes densely).
 template <bool kHost, int kOp, bool kPoint>
 __device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                          const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
-                                         uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
+                                         uint32_t slot, int ca, int cb, bool single, unsigned int* status,
+                                         unsigned long long* wbuf) {
   constexpr int U = kPoint ? kListUnroll : 1;  // rounds whose loads are issued together
   const uint32_t S1 = 1 + Q.naggs;
   long long sum = 0;
@@ -156,7 +187,9 @@ __device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, 
       else if (kOp == DPF_AGG_SUM_SUB)
         x = (long long)va[u] - (long long)vb[u];
       if (single) sum += valid[u] ? x : 0;
-      else if (valid[u]) atomicAdd(acc + uint64_t(gid[u]) * S1 + slot, (unsigned long long)x);
+      else
+        warp_group_add(acc, uint64_t(gid[u]) * S1 + slot, (unsigned long long)x, valid[u],
+                       group_peers(gid[u], valid[u]), lane, wbuf);
     }
   }
   if (single) {
@@ -205,7 +238,8 @@ __device__ __forceinline__ long long value64(const DevQuery& Q, int c, const Pag
 template <bool kHost, int kOp>
 __device__ __forceinline__ void agg_pass_wide(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                            const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
-                                           uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
+                                           uint32_t slot, int ca, int cb, bool single, unsigned int* status,
+                                           unsigned long long* wbuf) {
   const uint32_t S1 = 1 + Q.naggs;
   unsigned long long sum = 0;
   for (uint32_t i0 = 0; i0 < n; i0 += 32) {
@@ -219,7 +253,7 @@ __device__ __forceinline__ void agg_pass_wide(const DevQuery& Q, const PageState
       b = (unsigned long long)value64<kHost>(Q, cb, P, seg_mb, r, valid, lane, status);
     const unsigned long long x = kOp == DPF_AGG_SUM ? a : (kOp == DPF_AGG_SUM_MUL ? a * b : a - b);
     if (single) sum += valid ? x : 0ull;
-    else if (valid) atomicAdd(acc + uint64_t(gid) * S1 + slot, x);
+    else warp_group_add(acc, uint64_t(gid) * S1 + slot, x, valid, group_peers(gid, valid), lane, wbuf);
   }
   if (single) {
 #pragma unroll
@@ -231,34 +265,43 @@ __device__ __forceinline__ void agg_pass_wide(const DevQuery& Q, const PageState
 template <bool kHost, int kOp>
 __device__ __forceinline__ void agg_dispatch(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                              const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
-                                             uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
+                                             uint32_t slot, int ca, int cb, bool single, unsigned int* status,
+                                             unsigned long long* wbuf) {
   if (Q.cols[ca].codec == C_FOR64 || (kOp != DPF_AGG_SUM && Q.cols[cb].codec == C_FOR64)) {
-    agg_pass_wide<kHost, kOp>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status);
+    agg_pass_wide<kHost, kOp>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status, wbuf);
     return;
   }
   const bool point = Q.cols[ca].codec != C_DELTA && (kOp == DPF_AGG_SUM || Q.cols[cb].codec != C_DELTA);
-  if (point) agg_pass<kHost, kOp, true>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status);
-  else agg_pass<kHost, kOp, false>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status);
+  if (point) agg_pass<kHost, kOp, true>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status, wbuf);
+  else agg_pass<kHost, kOp, false>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status, wbuf);
 }
 
 // Aggregation over a warp's survivor list (Kernel #3 hash aggregation;
 // int64 as in Sec. 4.3): slot 0 counts rows, slot 1 + a holds aggregate a.
-// domain == 1: per-lane int64 sums reduced across the warp; otherwise int64
-// atomics into the CTA's shared accumulators (or the query's global ones for
-// large domains), indexed by the dense group id.
+// domain == 1: per-lane int64 sums reduced across the warp; otherwise
+// warp-aggregated int64 atomics (warp_group_add; COUNT adds the size of each
+// group of peers) into the CTA's shared accumulators (or the query's global
+// ones for large domains), indexed by the dense group id.
 template <bool kHost>
 __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                                const uint32_t* list, uint32_t n, int lane,
-                                               unsigned long long* acc, unsigned int* status) {
+                                               unsigned long long* acc, unsigned int* status,
+                                               unsigned long long* wbuf) {
   const uint32_t S1 = 1 + Q.naggs;
   const bool single = Q.domain == 1;
   if (single) {
     if (lane == 0) atomicAdd(acc, (unsigned long long)n);
   } else {
-    for (uint32_t i = lane; i < n; i += 32) {
-      const uint32_t gid = list[i] >> kRowBits;
-      if (gid < Q.domain) atomicAdd(acc + uint64_t(gid) * S1, 1ull);
-      else atomicOr(status, S_CORRUPT);  // a corrupt dictionary code
+    for (uint32_t i0 = 0; i0 < n; i0 += 32) {
+      bool valid = i0 + lane < n;
+      const uint32_t gid = valid ? list[i0 + lane] >> kRowBits : 0u;
+      if (valid && gid >= Q.domain) {
+        atomicOr(status, S_CORRUPT);  // a corrupt dictionary code
+        valid = false;
+      }
+      const uint32_t peers = group_peers(gid, valid);
+      if (valid && (peers & ((1u << lane) - 1u)) == 0)
+        atomicAdd(acc + uint64_t(gid) * S1, (unsigned long long)__popc(peers));
     }
   }
   for (uint32_t a = 0; a < Q.naggs; ++a) {
@@ -268,17 +311,17 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
         if (single) {
           if (lane == 0) atomicAdd(acc + 1 + a, (unsigned long long)n);
         } else {
-          agg_pass<kHost, DPF_AGG_COUNT, true>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
+          agg_pass<kHost, DPF_AGG_COUNT, true>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status, wbuf);
         }
         break;
       case DPF_AGG_SUM:
-        agg_dispatch<kHost, DPF_AGG_SUM>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        agg_dispatch<kHost, DPF_AGG_SUM>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status, wbuf);
         break;
       case DPF_AGG_SUM_MUL:
-        agg_dispatch<kHost, DPF_AGG_SUM_MUL>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        agg_dispatch<kHost, DPF_AGG_SUM_MUL>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status, wbuf);
         break;
       default:
-        agg_dispatch<kHost, DPF_AGG_SUM_SUB>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
+        agg_dispatch<kHost, DPF_AGG_SUM_SUB>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status, wbuf);
         break;
     }
   }
@@ -292,7 +335,7 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
 // the latency).
 template <bool kHost, bool kText>
 __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long long* acc, const uint8_t* stab,
-                               uint32_t* list, int lane, unsigned int* status) {
+                               uint32_t* list, int lane, unsigned int* status, unsigned long long* wbuf) {
   const uint64_t PR = Q.page_rows;
   const uint64_t r0 = chunk * Q.chunk_rows;
   const uint64_t r1 = tmin<uint64_t>(Q.nrows, r0 + Q.chunk_rows);
@@ -325,7 +368,7 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
       const uint32_t next = i0 + TB;
       if (j + 1 == ntiles || n + kTileRows > kListCap || next + TB - seg_mb > kSegMbs) {
         n = list_steps<kHost, kText>(Q, P, seg_mb, list, n, stab, lane, status, nd);
-        if (n) list_aggregate<kHost>(Q, P, seg_mb, list, n, lane, acc, status);
+        if (n) list_aggregate<kHost>(Q, P, seg_mb, list, n, lane, acc, status, wbuf);
         n = 0;
         nd = 0;
         seg_mb = next;
@@ -371,6 +414,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* 
   unsigned long long* sacc = reinterpret_cast<unsigned long long*>(dyn);
   uint8_t* stab = dyn + ((acc_slots * sizeof(unsigned long long) + 15) & ~size_t(15));
   uint32_t* lists = reinterpret_cast<uint32_t*>(stab + tables_bytes);
+  unsigned long long* wbufs = reinterpret_cast<unsigned long long*>(lists + (blockDim.x >> 5) * kListCap);
   // Warps draw tickets on their own (one ticket = chunk_rows rows of one
   // query, processed by one warp), so no CTA barrier separates tickets.  The
   // CTA meets only when its warps' tickets leave the current query: it then
@@ -379,6 +423,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* 
   // finished query's accumulators first.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t* list = lists + uint32_t(warp) * kListCap;
+  unsigned long long* wbuf = wbufs + warp * 32;
   auto draw = [&](unsigned long long& t) -> int {
     unsigned long long x = 0;
     if (lane == 0) x = atomicAdd(&sched->next, 1ull);
@@ -419,7 +464,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* 
     unsigned long long* acc = Q.use_smem_acc ? sacc : Q.acc;
     uint32_t done_here = 0;
     while (hq == cur) {
-      process_ticket<kHost, kText>(Q, held - Q.chunk_begin, acc, stab, list, lane, &sched->status);
+      process_ticket<kHost, kText>(Q, held - Q.chunk_begin, acc, stab, list, lane, &sched->status, wbuf);
       ++done_here;
       hq = draw(held);
     }
@@ -440,7 +485,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* 
 
 size_t fused_dynamic_smem(uint32_t acc_slots, size_t smem_tables, int threads) {
   return ((acc_slots * sizeof(unsigned long long) + 15) & ~size_t(15)) + ((smem_tables + 15) & ~size_t(15)) +
-         size_t(threads / 32) * kListCap * sizeof(uint32_t);
+         size_t(threads / 32) * (kListCap * sizeof(uint32_t) + 32 * sizeof(unsigned long long));
 }
 
 namespace {

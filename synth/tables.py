@@ -463,7 +463,8 @@ def strings(rows=1 << 25, seed=3, page_rows=DEFAULT_PAGE_ROWS, prefix=b"q",
         "group": [{"col": "key"}],
         "aggs": [{"op": "count"}, {"op": "sum", "cols": ["m"]}],
     }
-    name = f"strings_{rows}" + ("_text" if text else "") + ("" if codec == "str" else f"_{codec}")
+    name = (f"strings_{rows}" + ("_text" if text else "") + ("" if codec == "str" else f"_{codec}")
+            + ("_all" if contains is None and not prefix else ""))
     return {"name": name, "tables": {"fact": fact}, "fact": "fact", "query": query}
 
 
