@@ -43,7 +43,8 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("fused.cu", "tile.cuh", "dpf_device.cuh", "dpf_internal.h", "kernels.h")
+KERNEL_SOURCES = ("fused.cu", "fused_kernel.cuh", "fused_lean.cu", "fused_text.cu", "fused_host.cu", "tile.cuh",
+                  "dpf_device.cuh", "dpf_internal.h", "kernels.h")
 
 
 def kernel_source_hash():

@@ -958,6 +958,39 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
     return fail(DPF_EINVAL, "fused kernel does not fit on an SM with %u threads and %zu table bytes", t.threads, max_tables);
   }
   if (t.ctas_per_sm == 0 || int(t.ctas_per_sm) > per_sm || min_blocks == kFusedMinBlocksHi) t.ctas_per_sm = uint32_t(per_sm);
+  // Tickets are handed out in order, so the launch ends on the last query's
+  // last tickets.  Whole-size tickets there leave most warps idle while the
+  // last few finish; the final rows (about two tickets of tail_rows per warp
+  // of the grid, taken from the last queries backwards) are cut into tickets
+  // of chunk_rows / 8 rows instead.
+  {
+    const uint64_t warps = uint64_t(c->num_sms) * t.ctas_per_sm * (t.threads / 32);
+    const uint32_t tail_rows = std::max<uint32_t>(kMbPerWarpTile * kMB, t.chunk_rows / 8);
+    int64_t want = tail_rows < t.chunk_rows ? int64_t(2 * warps * tail_rows) : 0;
+    for (int i = n - 1; i >= 0 && want > 0; --i) {
+      DevQuery& Q = p->hq[i];
+      const uint64_t keep_big = Q.nrows > uint64_t(want) ? (Q.nrows - uint64_t(want)) / t.chunk_rows : 0;
+      Q.tail_first = keep_big;
+      Q.tail_rows = tail_rows;
+      const uint64_t tail = Q.nrows - keep_big * t.chunk_rows;
+      Q.nchunks = keep_big + (tail + tail_rows - 1) / tail_rows;
+      want -= int64_t(tail);
+    }
+    tickets = 0;
+    for (int i = 0; i < n; ++i) {
+      p->hq[i].chunk_begin = tickets;
+      qbegin[i] = tickets;
+      tickets += p->hq[i].nchunks;
+    }
+    qbegin[n] = tickets;
+    e = cudaMemcpyAsync(p->dq, p->hq.data(), sizeof(DevQuery) * n, cudaMemcpyHostToDevice, c->io);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->dqbegin, qbegin.data(), 8 * (n + 1), cudaMemcpyHostToDevice, c->io);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->io);
+    if (e != cudaSuccess) {
+      release_prep(c, p.get());
+      return fail(DPF_ECUDA, "prepare: %s", cudaGetErrorString(e));
+    }
+  }
   p->L.min_blocks = min_blocks;
   p->tuning = t;
   p->L.queries = p->dq;

@@ -62,6 +62,8 @@ struct DevColumn {
   uint64_t nrows;
   uint32_t codec;
   uint32_t page_rows;
+  uint32_t max_bw;            // FOR/DICT/DELTA: widest mini block (bits), from the validated headers
+  uint32_t pad_;
 };
 
 enum StepKind : uint8_t {
@@ -119,6 +121,13 @@ struct alignas(16) DevQuery {
   uint32_t chunk_rows;
   uint64_t chunk_begin;        // first global ticket of this query
   uint64_t nchunks;
+  // The launch's last tickets are cut smaller so that warps finish together:
+  // tickets from tail_first on cover tail_rows rows each, starting at row
+  // tail_first * chunk_rows (tail_rows == 0: every ticket covers chunk_rows).
+  uint64_t tail_first;
+  uint32_t tail_rows;
+  uint32_t stage;              // 1: the first step's mini blocks are staged in shared memory
+                               // (cp.async ring of the launch's stage width)
   // aggregation: slot 0 = count, slot 1 + a = aggregate a
   uint32_t domain;             // number of dense group ids
   uint32_t naggs;

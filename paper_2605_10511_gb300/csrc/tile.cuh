@@ -76,12 +76,17 @@ struct TileState {
   uint32_t gid[TB][4];    // dense group id of each row
 };
 
+// kGid = false: the tile's dense step adds no group-id contribution, so the
+// group ids stay 0 and are neither kept nor written to the list.
+template <bool kGid = true>
 __device__ __forceinline__ void tile_init(const PageState& P, uint32_t i0, uint32_t nmb, int lane,
                                           TileState& T) {
+  if (kGid) {
 #pragma unroll
-  for (int t = 0; t < TB; ++t)
+    for (int t = 0; t < TB; ++t)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) T.gid[t][k] = 0;
+      for (int k = 0; k < 4; ++k) T.gid[t][k] = 0;
+  }
   if (nmb == uint32_t(TB) && (i0 + TB) * kMB <= P.prow) {  // a full tile
     T.alive = (TB == 8) ? 0xffffffffu : ((1u << (4 * TB)) - 1u);
     return;
@@ -380,8 +385,10 @@ __device__ __forceinline__ void dense_probe(const DevStep& S, const uint8_t* sta
       }
     }
     if (pend) atomicOr(status, S_INTERNAL);
+    if (kContrib) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) T.gid[t][k] += (pay[k] & 0xffffu) * S.mul0 + (pay[k] >> 16) * S.mul1;
+      for (int k = 0; k < 4; ++k) T.gid[t][k] += (pay[k] & 0xffffu) * S.mul0 + (pay[k] >> 16) * S.mul1;
+    }
     const uint32_t live = (T.alive >> (4 * t)) & 15u;
     T.alive &= ~((live & ~hit & 15u) << (4 * t));
   }
@@ -419,7 +426,7 @@ __device__ __forceinline__ uint32_t pruned_mbs(const TileHdr& Hd, int c, int32_t
   return (__ballot_sync(kFull, out) >> (c * TB)) & ((1u << TB) - 1u);
 }
 
-template <bool kHost, bool kDelta>
+template <bool kHost, bool kDelta, bool kGid = true>
 __device__ __forceinline__ void dense_step_t(const DevQuery& Q, const DevStep& S, const PageState& P,
                                              const TileHdr& Hd, TileState& T, const uint8_t* stab, int lane,
                                              unsigned int* status) {
@@ -434,21 +441,25 @@ __device__ __forceinline__ void dense_step_t(const DevQuery& Q, const DevStep& S
   switch (S.kind) {
     case ST_PROBE:
       switch (probe_mode(S)) {
-        case PM_S1: dense_probe<PM_S1>(S, stab, v, anym, T, status); break;
-        case PM_S2: dense_probe<PM_S2>(S, stab, v, anym, T, status); break;
-        case PM_S4: dense_probe<PM_S4>(S, stab, v, anym, T, status); break;
+        case PM_S1: dense_probe<PM_S1, kGid>(S, stab, v, anym, T, status); break;
+        case PM_S2: dense_probe<PM_S2, kGid>(S, stab, v, anym, T, status); break;
+        case PM_S4: dense_probe<PM_S4, kGid>(S, stab, v, anym, T, status); break;
         case PM_GDIRECT:
-          if (S.mul0 | S.mul1) dense_probe<PM_GDIRECT, true>(S, stab, v, anym, T, status);
+          if (kGid && (S.mul0 | S.mul1)) dense_probe<PM_GDIRECT, kGid>(S, stab, v, anym, T, status);
           else dense_probe<PM_GDIRECT, false>(S, stab, v, anym, T, status);
           break;
-        default: dense_probe<PM_OPEN>(S, stab, v, anym, T, status); break;
+        default: dense_probe<PM_OPEN, kGid>(S, stab, v, anym, T, status); break;
       }
       return;
     case ST_KEY:
+      if (kGid) {
 #pragma unroll
-      for (int t = 0; t < TB; ++t)
+        for (int t = 0; t < TB; ++t)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) T.gid[t][k] += v[t][k] * S.key_mul;
+          for (int k = 0; k < 4; ++k) T.gid[t][k] += v[t][k] * S.key_mul;
+      } else if (lane == 0) {
+        atomicOr(status, S_INTERNAL);  // the kernel routes group-key first steps to kGid
+      }
       return;
     case ST_RANGE:
     case ST_NOTRANGE: {
@@ -500,14 +511,22 @@ static_assert(kSegMbs <= 32, "segment mini blocks must fit a 32-bit mask");
 
 // Dense step s of a tile (or none): live bits and group-id contributions.
 // The step's kind, table and codec are resolved here, once per tile.
-template <bool kHost, bool kText = true>
+// kGid = false compiles the step without group-id contributions (for a
+// first step that adds none: a predicate, or a probe of a table no group key
+// reads), which keeps the sixteen per-row group ids out of registers.
+template <bool kHost, bool kText = true, bool kGid = true>
 __device__ __forceinline__ void tile_dense_step(const DevQuery& Q, uint32_t s, const PageState& P, const TileHdr& Hd,
                                                 TileState& T, const uint8_t* stab, int lane, unsigned int* status) {
   if (s >= Q.nsteps) return;
   const DevStep& S = Q.steps[s];
   if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) tile_prefix<kHost, kText>(Q, S, P, Hd, T, lane, status);
-  else if (Q.cols[S.col].codec == C_DELTA) dense_step_t<kHost, true>(Q, S, P, Hd, T, stab, lane, status);
-  else dense_step_t<kHost, false>(Q, S, P, Hd, T, stab, lane, status);
+  else if (Q.cols[S.col].codec == C_DELTA) dense_step_t<kHost, true, kGid>(Q, S, P, Hd, T, stab, lane, status);
+  else dense_step_t<kHost, false, kGid>(Q, S, P, Hd, T, stab, lane, status);
+}
+
+// Whether step S adds a group-id contribution when it runs densely.
+__device__ __forceinline__ bool step_adds_gid(const DevStep& S) {
+  return S.kind == ST_KEY || (S.kind == ST_PROBE && (S.mul0 | S.mul1) != 0);
 }
 
 // Appends the tile's live rows to the warp's list after its first n0
@@ -516,6 +535,7 @@ __device__ __forceinline__ void tile_dense_step(const DevQuery& Q, uint32_t s, c
 // scan of the counts gives the lane's first slot, and the lane writes its
 // rows there in (t, k) order (the list's order is free: later steps and the
 // aggregation visit every entry once, whatever its position).
+template <bool kGid = true>
 __device__ __forceinline__ uint32_t tile_compact(const TileState& T, uint32_t* list, uint32_t n0, uint32_t row_base,
                                                  int lane) {
   const uint32_t cnt = __popc(T.alive);
@@ -532,7 +552,7 @@ __device__ __forceinline__ uint32_t tile_compact(const TileState& T, uint32_t* l
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if ((T.alive >> (4 * t + k)) & 1u) {
-        list[pos] = (row_base + uint32_t(t * kMB + k * 32 + lane)) | (T.gid[t][k] << kRowBits);
+        list[pos] = (row_base + uint32_t(t * kMB + k * 32 + lane)) | (kGid ? T.gid[t][k] << kRowBits : 0u);
         ++pos;
       }
   __syncwarp();
