@@ -405,6 +405,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ht", default="auto", choices=["auto", "smem", "global"])
     ap.add_argument("--ctas", type=int, default=0, help="CTAs per SM (4 = the 4-CTA kernel build)")
+    ap.add_argument("--stage", default="default", choices=["default", "on", "off"],
+                    help="stage the first step's mini blocks in shared memory (cp.async ring)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
@@ -455,12 +457,13 @@ def main():
     torch.cuda.synchronize()
     build_ms = 1e3 * (time.perf_counter() - t0)
     autotuned = None
-    if not (args.chunk_rows or args.threads or args.ht != "auto" or args.ctas or args.no_autotune):
+    if not (args.chunk_rows or args.threads or args.ht != "auto" or args.ctas or args.stage != "default"
+            or args.no_autotune):
         # the library's autotuner picks the launch configuration (cached
         # for this plan's signature; untimed)
         best, best_ms = eng.ctx.autotune([plan], stream, reps=3)
         autotuned = {"best": best, "best_ms": best_ms}
-    tuning = dpf.Tuning(args.chunk_rows, args.threads, dpf.HT_PLACE[args.ht], args.ctas)
+    tuning = dpf.Tuning(args.chunk_rows, args.threads, dpf.HT_PLACE[args.ht], args.ctas, dpf.STAGING[args.stage])
     prep = eng.ctx.prepare([plan], tuning)
     eng.ctx.capture_graph(prep, stream)
     for _ in range(args.warmup):

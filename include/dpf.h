@@ -299,7 +299,14 @@ typedef struct dpf_tuning {
                             kernel build for 3 resident 256-thread CTAs
                             (80 registers); >= 4 = the build for 4 (64
                             registers) when four fit, else as for 0          */
+  int32_t staging;       /* enum dpf_staging: copy the first (dense) step's
+                            compressed mini blocks into a per-warp shared-
+                            memory ring with asynchronous copies a tile ahead
+                            of their decode (Sec. 3.2 IO stage overlapped with
+                            decompression); integer first steps over device-
+                            resident pages only                              */
 } dpf_tuning;
+enum dpf_staging { DPF_STAGE_DEFAULT = 0, DPF_STAGE_ON = 1, DPF_STAGE_OFF = 2 };
 
 /* Result record: keys are dictionary values (0 when unused); count = rows
  * in the group; val[i] = aggregate i (COUNT repeats count). */
@@ -329,7 +336,8 @@ dpf_status dpf_launch_graph(dpf_ctx* ctx, dpf_prep_id prep, void* stream);
  * into DPF_ECORRUPT / DPF_EINTERNAL. */
 dpf_status dpf_read_result(dpf_ctx* ctx, dpf_prep_id prep, int32_t i, dpf_record* buf,
                            uint64_t cap, uint64_t* n_out, int32_t timeout_ms);
-/* Tuning the batch will launch with (after defaults and cache lookup). */
+/* Tuning the batch will launch with (after defaults and cache lookup;
+ * staging = DPF_STAGE_ON only when some query of the batch is staged). */
 dpf_status dpf_prep_tuning(dpf_ctx* ctx, dpf_prep_id prep, dpf_tuning* out);
 dpf_status dpf_release(dpf_ctx* ctx, dpf_prep_id prep);
 
@@ -338,7 +346,8 @@ dpf_status dpf_release(dpf_ctx* ctx, dpf_prep_id prep);
  * where the join tables live (shared memory vs device memory, Sec. 4.3) are
  * the launch configuration.  dpf_autotune prepares the n plans under each
  * configuration of a fixed grid (chunk_rows 1K..256K, threads 128/256,
- * tables AUTO/GLOBAL, kernel build for 3 or 4 CTAs per SM), times `reps` launches of each on `stream` with CUDA
+ * tables AUTO/GLOBAL, kernel build for 3 or 4 CTAs per SM, staging on/off),
+ * times `reps` launches of each on `stream` with CUDA
  * events after one warm-up launch (reps 0 = 3), and keeps the fastest in the
  * context's tuning cache under the plans' signature (the rows and encodings
  * of the columns they read, their steps, tables, groups and aggregates; not

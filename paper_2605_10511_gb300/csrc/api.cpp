@@ -61,6 +61,7 @@ struct Column {
   std::vector<uint64_t> page_off, row_prefix;
   std::vector<int32_t> dict;
   int64_t vmin = 0, vmax = -1;    // value bounds from the mini block headers (planner statistics)
+  uint32_t max_bw = 0;            // FOR/DICT/DELTA: widest mini block (bits)
 };
 
 struct HashTable {
@@ -288,7 +289,9 @@ dpf_status validate_pages(uint32_t codec, const uint8_t* pages, uint64_t size, c
       const uint8_t* h = pg + kPageHdr + uint64_t(m2) * mb_hdr_bytes(codec);
       const uint32_t wob = codec == C_DELTA ? rd32(h + 8) : rd32(h + 4);
       const uint32_t bw = wob & 0xffu, woff = wob >> 8;
-      if (bw > 32 || uint64_t(woff) + 4ull * bw > pay_words) return flag();
+      // a mini block's 4 * bw words start on a 16-byte boundary (the kernels
+      // copy them in 16-byte chunks)
+      if (bw > 32 || woff % 4 != 0 || uint64_t(woff) + 4ull * bw > pay_words) return flag();
       if (codec == C_DICT) {
         const int32_t base = int32_t(rd32(h));
         if (base < 0 || uint64_t(base) >= dict_n) return flag();
@@ -484,9 +487,10 @@ dpf_status compile_pred(const Column& c, const dpf_pred& p, DevStep& S, int col_
 // [min(0, dmin), max(0, dmin + 2^bw - 1)]; a page whose bound leaves int32
 // (values may have wrapped) gets the full range.  STR: the full range.
 void value_bounds(uint32_t codec, const uint8_t* pages, const uint64_t* page_off, uint64_t npages, uint64_t nrows,
-                  uint32_t P, int64_t* vmin, int64_t* vmax, std::vector<int2>* zones) {
+                  uint32_t P, int64_t* vmin, int64_t* vmax, std::vector<int2>* zones, uint32_t* max_bw) {
   *vmin = 0;
   *vmax = -1;
+  *max_bw = 0;
   zones->assign(npages, make_int2(INT32_MIN, INT32_MAX));
   if (is_str_codec(codec) || codec == C_FOR64) return;  // no 32-bit bounds (never a step's column)
   int64_t clo = INT64_MAX, chi = INT64_MIN;
@@ -501,11 +505,13 @@ void value_bounds(uint32_t codec, const uint8_t* pages, const uint64_t* page_off
       if (codec == C_DELTA) {
         const int64_t dmin = int32_t(rd32(h + 4));
         const uint32_t bw = std::min<uint32_t>(rd32(h + 8) & 0xffu, 32u);
+        *max_bw = std::max(*max_bw, bw);
         const int64_t span = bw >= 32 ? int64_t(0xffffffffll) : (int64_t(1) << bw) - 1;
         lo = std::min(lo, base + 127 * std::min<int64_t>(0, dmin));
         hi = std::max(hi, base + 127 * std::max<int64_t>(0, dmin + span));
       } else {
         const uint32_t bw = std::min<uint32_t>(rd32(h + 4) & 0xffu, 32u);
+        *max_bw = std::max(*max_bw, bw);
         lo = std::min(lo, base);
         hi = std::max(hi, base + (bw >= 32 ? int64_t(0xffffffffll) : (int64_t(1) << bw) - 1));
       }
@@ -571,6 +577,7 @@ struct ColumnSet {
     d.nrows = col.nrows;
     d.codec = uint32_t(col.codec);
     d.page_rows = col.page_rows;
+    d.max_bw = col.max_bw;
     host |= col.placement == DPF_PLACE_HOST_PINNED;
     *idx = int(ids.size());
     ids.push_back(id);
@@ -836,18 +843,20 @@ uint64_t plans_signature(dpf_ctx* c, const dpf_plan* plans, int32_t n) {
 // Fields left 0 take the tuning dpf_autotune stored for these plans, else the
 // defaults.
 void fill_tuning_defaults(dpf_ctx* c, dpf_tuning& t, const dpf_plan* plans, int32_t n) {
-  if (t.chunk_rows == 0 || t.threads == 0 || t.ht_placement == 0 || t.ctas_per_sm == 0) {
+  if (t.chunk_rows == 0 || t.threads == 0 || t.ht_placement == 0 || t.ctas_per_sm == 0 || t.staging == 0) {
     auto it = c->tune_cache.find(plans_signature(c, plans, n));
     if (it != c->tune_cache.end()) {
       if (t.chunk_rows == 0) t.chunk_rows = it->second.chunk_rows;
       if (t.threads == 0) t.threads = it->second.threads;
       if (t.ht_placement == 0) t.ht_placement = it->second.ht_placement;
       if (t.ctas_per_sm == 0) t.ctas_per_sm = it->second.ctas_per_sm;
+      if (t.staging == 0) t.staging = it->second.staging;
     }
   }
   if (t.chunk_rows == 0) t.chunk_rows = kDefaultChunkRows;
   if (t.threads == 0) t.threads = 256;
   if (t.ht_placement == 0) t.ht_placement = DPF_HT_AUTO;
+  if (t.staging == 0) t.staging = kDefaultStaging;
 }
 
 dpf_status release_prep(dpf_ctx* c, Prep* p) {
@@ -885,6 +894,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   if (t.chunk_rows % (kMbPerWarpTile * kMB) != 0 || t.chunk_rows > (1u << 24))
     return fail(DPF_EINVAL, "chunk_rows %u must be a multiple of %u and at most 2^24", t.chunk_rows, kMbPerWarpTile * kMB);
   if (t.threads != 128 && t.threads != 256) return fail(DPF_EINVAL, "threads must be 128 or 256");
+  if (t.staging != DPF_STAGE_ON && t.staging != DPF_STAGE_OFF) return fail(DPF_EINVAL, "staging must be 0, 1 or 2");
   bool host = false;
   uint64_t tickets = 0;
   std::vector<uint64_t> qbegin(size_t(n) + 1);
@@ -920,6 +930,24 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
     off_out[i] = scratch; scratch += align16(uint64_t(std::max<uint32_t>(Q.domain, 1)) * sizeof(dpf_record));
   }
   qbegin[n] = tickets;
+  // Staging ring: integer first steps over device-resident pages; its slots
+  // are as wide as the widest mini block of those steps' columns.
+  uint32_t stage_bw = 0;
+  if (t.staging == DPF_STAGE_ON && !host) {
+    std::vector<int> staged;
+    for (int i = 0; i < n; ++i) {
+      const DevQuery& Q = p->hq[i];
+      if (Q.nsteps == 0) continue;
+      const DevStep& S0 = Q.steps[0];
+      const DevColumn& C0 = Q.cols[S0.col];
+      const bool int_step = S0.kind != ST_PREFIX && S0.kind != ST_CONTAINS &&
+                            (C0.codec == C_FOR || C0.codec == C_DICT || C0.codec == C_DELTA);
+      if (!int_step || C0.max_bw == 0 || C0.max_bw > 32) continue;
+      staged.push_back(i);
+      stage_bw = std::max(stage_bw, C0.max_bw);
+    }
+    for (int i : staged) p->hq[i].stage = stage_bw;
+  }
   dpf_status st;
   if ((st = dev_alloc(c, scratch, reinterpret_cast<void**>(&p->scratch)))) return st;
   if ((st = dev_alloc_t(c, uint64_t(n), &p->dq)) || (st = dev_alloc_t(c, uint64_t(n) + 1, &p->dqbegin)) ||
@@ -949,10 +977,11 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   int min_blocks = kFusedMinBlocksLo;
   int per_sm = 0;
   if (t.ctas_per_sm >= uint32_t(kFusedMinBlocksHi)) {
-    per_sm = fused_blocks_per_sm(int(t.threads), acc_slots, max_tables, host, kFusedMinBlocksHi);
+    per_sm = fused_blocks_per_sm(int(t.threads), acc_slots, max_tables, host, kFusedMinBlocksHi, stage_bw);
     if (per_sm >= kFusedMinBlocksHi * 256 / int(t.threads)) min_blocks = kFusedMinBlocksHi;
   }
-  if (min_blocks == kFusedMinBlocksLo) per_sm = fused_blocks_per_sm(int(t.threads), acc_slots, max_tables, host, kFusedMinBlocksLo);
+  if (min_blocks == kFusedMinBlocksLo)
+    per_sm = fused_blocks_per_sm(int(t.threads), acc_slots, max_tables, host, kFusedMinBlocksLo, stage_bw);
   if (per_sm < 1) {
     release_prep(c, p.get());
     return fail(DPF_EINVAL, "fused kernel does not fit on an SM with %u threads and %zu table bytes", t.threads, max_tables);
@@ -965,7 +994,8 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   // of chunk_rows / 8 rows instead.
   {
     const uint64_t warps = uint64_t(c->num_sms) * t.ctas_per_sm * (t.threads / 32);
-    const uint32_t tail_rows = std::max<uint32_t>(kMbPerWarpTile * kMB, t.chunk_rows / 8);
+    const uint32_t tile_rows = kMbPerWarpTile * kMB;
+    const uint32_t tail_rows = std::max<uint32_t>(tile_rows, t.chunk_rows / 8 / tile_rows * tile_rows);
     int64_t want = tail_rows < t.chunk_rows ? int64_t(2 * warps * tail_rows) : 0;
     for (int i = n - 1; i >= 0 && want > 0; --i) {
       DevQuery& Q = p->hq[i];
@@ -1003,6 +1033,8 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   p->L.smem_tables = max_tables;
   p->L.acc_slots = acc_slots;
   p->L.host_data = host;
+  p->L.stage_bw = stage_bw;
+  p->tuning.staging = stage_bw ? DPF_STAGE_ON : DPF_STAGE_OFF;  // what the launch does
   p->L.text = false;
   for (const DevQuery& q : p->hq) p->L.text = p->L.text || needs_string_matcher(q);
   p->fetched.assign(size_t(n), 0);
@@ -1189,7 +1221,7 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
   col.row_prefix.assign(row_prefix, row_prefix + npages);
   if (codec == C_DICT) col.dict.assign(dict, dict + dict_n);
   std::vector<int2> zones;
-  value_bounds(codec, pages, page_off, npages, nrows, P, &col.vmin, &col.vmax, &zones);
+  value_bounds(codec, pages, page_off, npages, nrows, P, &col.vmin, &col.vmax, &zones, &col.max_bw);
   if (is_str_codec(codec)) {
     uint64_t sb = 0;
     for (uint64_t p = 0; p < npages; ++p) {
@@ -1543,15 +1575,18 @@ dpf_status dpf_autotune(dpf_ctx* c, const dpf_plan* plans, int32_t n, void* stre
   float top_ms = -1.f;
   dpf_status last = DPF_OK;
   static const uint32_t kCtas[] = {0, uint32_t(kFusedMinBlocksHi)};
+  static const int32_t kStage[] = {DPF_STAGE_OFF, DPF_STAGE_ON};
   for (uint32_t cr : kChunk)
     for (uint32_t th : kThreads)
       for (int32_t pl : kPlace)
-        for (uint32_t ct : kCtas) {
+        for (uint32_t ct : kCtas)
+          for (int32_t sg : kStage) {
         dpf_tuning t{};
         t.chunk_rows = cr;
         t.threads = th;
         t.ht_placement = pl;
         t.ctas_per_sm = ct;
+        t.staging = sg;
         Prep* p = nullptr;
         dpf_status st = prepare(c, plans, n, &t, &p);
         if (st) {  // e.g. the tables do not fit this configuration
@@ -1635,7 +1670,8 @@ dpf_status dpf_capture_graph(dpf_ctx* c, dpf_prep_id id, void* stream) {
   if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
   if (p->graph) { cudaGraphDestroy(p->graph); p->graph = nullptr; }
   // set the smem attribute before capture (not a stream operation)
-  fused_blocks_per_sm(p->L.threads, p->L.acc_slots, p->L.smem_tables, p->L.host_data, p->L.min_blocks);
+  fused_blocks_per_sm(p->L.threads, p->L.acc_slots, p->L.smem_tables, p->L.host_data, p->L.min_blocks,
+                      p->L.stage_bw);
   CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = launch_prep(p, s);
   cudaGraph_t graph = nullptr;

@@ -126,8 +126,8 @@ struct alignas(16) DevQuery {
   // tail_first * chunk_rows (tail_rows == 0: every ticket covers chunk_rows).
   uint64_t tail_first;
   uint32_t tail_rows;
-  uint32_t stage;              // 1: the first step's mini blocks are staged in shared memory
-                               // (cp.async ring of the launch's stage width)
+  uint32_t stage;              // > 0: the first step's mini blocks are staged in the warp's
+                               // shared-memory ring, whose slots hold up to `stage` bits a value
   // aggregation: slot 0 = count, slot 1 + a = aggregate a
   uint32_t domain;             // number of dense group ids
   uint32_t naggs;

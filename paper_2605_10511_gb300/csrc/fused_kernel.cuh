@@ -336,14 +336,31 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
 // The dense part of one tile, for one warp: the first step over all its rows
 // (kGid: the step adds group-id contributions), then its survivors appended
 // to the warp's list after the first n entries; returns the list length.
-template <bool kHost, bool kText, bool kGid>
+template <bool kHost, bool kText, bool kGid, bool kStaged = false>
 __device__ __forceinline__ uint32_t tile_first_step(const DevQuery& Q, const PageState& P, const TileHdr& H,
                                                     uint32_t i0, uint32_t nmb, uint32_t row_base, const uint8_t* stab,
-                                                    uint32_t* list, uint32_t n, int lane, unsigned int* status) {
+                                                    uint32_t* list, uint32_t n, int lane, unsigned int* status,
+                                                    StagedPay sp = StagedPay{nullptr, 0, 0}) {
   TileState T;
   tile_init<kGid>(P, i0, nmb, lane, T);
-  tile_dense_step<kHost, kText, kGid>(Q, 0, P, H, T, stab, lane, status);
+  tile_dense_step<kHost, kText, kGid, kStaged>(Q, 0, P, H, T, stab, lane, status, sp);
   return tile_compact<kGid>(T, list, n, row_base, lane);
+}
+
+// The first step's column of Q in page P: its page address and packed words.
+struct FirstCol {
+  int c;
+  uint32_t codec;
+  const uint8_t* pg;
+  const uint8_t* pay;
+};
+__device__ __forceinline__ FirstCol first_col(const DevQuery& Q, const PageState& P) {
+  FirstCol f;
+  f.c = Q.steps[0].col;
+  f.codec = Q.cols[f.c].codec;
+  f.pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, f.c));
+  f.pay = f.pg + payload_offset(f.codec, P.prow);
+  return f;
 }
 
 // One ticket: the rows [chunk*chunk_rows, +chunk_rows) of Q's fact table
@@ -357,7 +374,8 @@ __device__ __forceinline__ uint32_t tile_first_step(const DevQuery& Q, const Pag
 // the aggregation run on them.
 template <bool kHost, bool kText>
 __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long long* acc, const uint8_t* stab,
-                               uint32_t* list, int lane, unsigned int* status, unsigned long long* wbuf) {
+                               uint32_t* list, int lane, unsigned int* status, unsigned long long* wbuf,
+                               uint8_t* ring) {
   const uint64_t PR = Q.page_rows;
   uint64_t r0 = chunk * Q.chunk_rows, r1 = r0 + Q.chunk_rows;
   if (Q.tail_rows != 0 && chunk >= Q.tail_first) {  // one of the launch's small last tickets
@@ -378,14 +396,46 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
     }
     PageState P;
     page_begin<kHost>(Q, p, lane, P);
+    // staged first step (StageRing in tile.cuh): the headers of tiles 0 and 1
+    // and the words of tile 0 are in flight before the first decode
+    const uint32_t bwcap = kHost ? 0u : Q.stage;
+    if (bwcap) {
+      const FirstCol f = first_col(Q, P);
+      stage_headers(ring, 0, f.pg, f.codec, mb0, tmin<uint32_t>(TB, mb1 - mb0), lane);
+      cp_async_commit();
+      cp_async_wait_all();
+      __syncwarp();
+      stage_payload(ring, bwcap, 0, 0, f.pay, f.codec, mb0, tmin<uint32_t>(TB, mb1 - mb0), lane);
+      if (ntiles > 1) stage_headers(ring, 1, f.pg, f.codec, mb0 + TB, tmin<uint32_t>(TB, mb1 - mb0 - TB), lane);
+      cp_async_commit();
+    }
     uint32_t n = 0, seg_mb = mb0;
     for (uint32_t j = 0; j < ntiles; ++j) {
       const uint32_t i0 = mb0 + j * TB;
       const uint32_t nmb = tmin<uint32_t>(TB, mb1 - i0);
       const uint32_t row_base = (i0 - seg_mb) * kMB;
-      const TileHdr H = load_headers<kHost>(Q, P, i0, nmb, lane);
-      if (gid0) n = tile_first_step<kHost, kText, true>(Q, P, H, i0, nmb, row_base, stab, list, n, lane, status);
-      else n = tile_first_step<kHost, kText, false>(Q, P, H, i0, nmb, row_base, stab, list, n, lane, status);
+      if (bwcap) {
+        cp_async_wait_all();  // this tile's words and the next tile's headers have landed
+        __syncwarp();
+        const FirstCol f = first_col(Q, P);
+        if (j + 1 < ntiles)
+          stage_payload(ring, bwcap, (j + 1) % 3, (j + 1) % 2, f.pay, f.codec, i0 + TB,
+                        tmin<uint32_t>(TB, mb1 - i0 - TB), lane);
+        if (j + 2 < ntiles) {
+          const uint32_t n2 = tmin<uint32_t>(TB, mb1 - i0 - 2 * TB);
+          stage_headers(ring, (j + 2) % 3, f.pg, f.codec, i0 + 2 * TB, n2, lane);
+          prefetch_other_headers(Q, P, f.c, i0 + 2 * TB, n2, lane);
+        }
+        cp_async_commit();
+        const TileHdr H = staged_headers(ring, j % 3, f.c, f.codec, i0, nmb, lane);
+        const StagedPay sp{stage_words(ring, j % 2, bwcap), stage_pw(bwcap), bwcap};
+        if (gid0) n = tile_first_step<kHost, kText, true, true>(Q, P, H, i0, nmb, row_base, stab, list, n, lane, status, sp);
+        else n = tile_first_step<kHost, kText, false, true>(Q, P, H, i0, nmb, row_base, stab, list, n, lane, status, sp);
+      } else {
+        const TileHdr H = load_headers<kHost>(Q, P, i0, nmb, lane);
+        if (gid0) n = tile_first_step<kHost, kText, true>(Q, P, H, i0, nmb, row_base, stab, list, n, lane, status);
+        else n = tile_first_step<kHost, kText, false>(Q, P, H, i0, nmb, row_base, stab, list, n, lane, status);
+      }
       const uint32_t next = i0 + TB;
       if (j + 1 == ntiles || n + kTileRows > kListCap || next + TB - seg_mb > kSegMbs) {
         n = list_steps<kHost, kText>(Q, P, seg_mb, list, n, stab, lane, status, 1);
@@ -428,7 +478,7 @@ template <bool kHost, int kMinBlocks, bool kText>
 __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* __restrict__ queries,
                                                        const uint64_t* __restrict__ qbegin, int nq,
                                                        uint64_t total, Sched* sched, uint32_t acc_slots,
-                                                     uint32_t tables_bytes) {
+                                                     uint32_t tables_bytes, uint32_t stage_bw) {
   extern __shared__ __align__(16) uint8_t dyn[];
   __shared__ CtaState cs;
   unsigned long long* sacc = reinterpret_cast<unsigned long long*>(dyn);
@@ -444,6 +494,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t* list = lists + uint32_t(warp) * kListCap;
   unsigned long long* wbuf = wbufs + warp * 32;
+  uint8_t* ring = reinterpret_cast<uint8_t*>(wbufs + nw * 32) + size_t(warp) * stage_warp_bytes(stage_bw);
   auto draw = [&](unsigned long long& t) -> int {
     unsigned long long x = 0;
     if (lane == 0) x = atomicAdd(&sched->next, 1ull);
@@ -484,7 +535,7 @@ __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* 
     unsigned long long* acc = Q.use_smem_acc ? sacc : Q.acc;
     uint32_t done_here = 0;
     while (hq == cur) {
-      process_ticket<kHost, kText>(Q, held - Q.chunk_begin, acc, stab, list, lane, &sched->status, wbuf);
+      process_ticket<kHost, kText>(Q, held - Q.chunk_begin, acc, stab, list, lane, &sched->status, wbuf, ring);
       ++done_here;
       hq = draw(held);
     }
@@ -516,7 +567,7 @@ cudaError_t launch_as(const FusedLaunch& L, size_t smem, uint32_t tb, cudaStream
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   fused_kernel<kHost, kMinBlocks, kText><<<L.grid, L.threads, smem, s>>>(L.queries, L.qbegin, L.nq, L.total_chunks,
-                                                                         L.sched, L.acc_slots, tb);
+                                                                         L.sched, L.acc_slots, tb, L.stage_bw);
   return cudaGetLastError();
 }
 

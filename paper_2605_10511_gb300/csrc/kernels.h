@@ -19,6 +19,8 @@ constexpr int kFusedMinBlocksLo = 3;
 constexpr int kFusedMinBlocksHi = 4;
 // Rows of one scheduling ticket (one warp's unit of work) unless tuned.
 constexpr uint32_t kDefaultChunkRows = 4096;
+// Staging of the first step's mini blocks unless tuned (DPF_STAGE_ON / _OFF).
+constexpr int32_t kDefaultStaging = 2;
 
 // Fused persistent kernel over a batch of compiled queries (Sec. 3.2).
 // qbegin[0..nq] = first ticket of each query (qbegin[nq] = total tickets).
@@ -35,12 +37,14 @@ struct FusedLaunch {
   int min_blocks;       // kFusedMinBlocksLo or kFusedMinBlocksHi: which build runs
   bool text;            // some query has a CONTAINS step or a string step on an FSST
                         // column (the build with the general string matcher runs)
+  uint32_t stage_bw;    // bits a value of the warps' staging ring slots hold; 0 = no ring
 };
 cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s);
 // Occupancy of the fused kernel for (threads, dynamic smem); also sets the
 // kernel's dynamic shared-memory limit.
-int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, bool host_data, int min_blocks);
-size_t fused_dynamic_smem(uint32_t acc_slots, size_t smem_tables, int threads);
+int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, bool host_data, int min_blocks,
+                        uint32_t stage_bw = 0);
+size_t fused_dynamic_smem(uint32_t acc_slots, size_t smem_tables, int threads, uint32_t stage_bw = 0);
 
 // Hash build (Kernel #1 of Sec. 3.1).  `q` describes the dimension scan:
 // cols/steps as for the fused kernel, build_key/build_pay name columns.

@@ -71,6 +71,119 @@ __device__ __forceinline__ TileHdr load_headers(const DevQuery& Q, const PageSta
   return h;
 }
 
+// ------------------------------------------------------------------ staging
+// The IO stage of Sec. 3.2 overlapped with decompression: the first step's
+// compressed mini blocks are copied HBM -> shared memory with cp.async (16
+// bytes per lane, through L2 only) into a per-warp ring, one tile ahead of
+// the decode for the packed words and two tiles ahead for the mini block
+// headers (a tile's word copies need its headers' offsets and widths).  A
+// warp waits only for its own copies (cp.async.wait_group, no spinning) and
+// decodes from shared memory, so the loads of the next tile are in flight
+// while this one is decoded, probed and compacted, and hold no registers.
+// Ring of one warp, for slots of up to bwcap bits a value: 3 header slots of
+// TB headers (16 bytes each at most), then 2 word slots of TB mini blocks of
+// 4 * (bwcap + 1) words (a mini block's 4 * bw words plus one spare group).
+constexpr uint32_t kStageHdrSlot = TB * 16;
+__host__ __device__ constexpr uint32_t stage_pw(uint32_t bwcap) { return 4u * (bwcap + 1u); }
+__host__ __device__ constexpr uint32_t stage_warp_bytes(uint32_t bwcap) {
+  return bwcap == 0 ? 0u : 3u * kStageHdrSlot + 2u * TB * 4u * stage_pw(bwcap);
+}
+__device__ __forceinline__ uint8_t* stage_hdr(uint8_t* ring, uint32_t slot) { return ring + slot * kStageHdrSlot; }
+__device__ __forceinline__ uint32_t* stage_words(uint8_t* ring, uint32_t slot, uint32_t bwcap) {
+  return reinterpret_cast<uint32_t*>(ring + 3 * kStageHdrSlot) + slot * TB * stage_pw(bwcap);
+}
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
+
+// Byte offset of mini block i0's header inside its header slot: the copy
+// starts at the 16-byte boundary at or below the header (8-byte headers of
+// an odd mini block start 8 bytes into a chunk).
+__device__ __forceinline__ uint32_t stage_hdr_skew(uint32_t codec, uint32_t i0) {
+  return (kPageHdr + i0 * mb_hdr_bytes(codec)) & 15u;
+}
+
+// Copies the headers of mini blocks [i0, i0 + nmb) of a page of column
+// codec (at pg) into header slot `slot`: the 16-byte chunks that cover them,
+// from the boundary at or below the first (pages are 16-aligned) to at most
+// the 16-aligned end of the header array (the payload follows it), so every
+// chunk lies inside the page.
+__device__ __forceinline__ void stage_headers(uint8_t* ring, uint32_t slot, const uint8_t* pg, uint32_t codec,
+                                              uint32_t i0, uint32_t nmb, int lane) {
+  const uint32_t hb = mb_hdr_bytes(codec);
+  const uint64_t first = kPageHdr + uint64_t(i0) * hb;
+  const uint32_t skew = uint32_t(first & 15u);
+  const uint32_t chunks = (skew + nmb * hb + 15) / 16;  // <= 3 (8-byte) or 4 (16-byte headers)
+  if (uint32_t(lane) < chunks)
+    cp_async16(stage_hdr(ring, slot) + lane * 16, pg + (first - skew) + uint32_t(lane) * 16);
+}
+
+// Copies the packed words of the nmb mini blocks whose headers sit in header
+// slot hslot into word slot wslot: a mini block of bit width bw is 4 * bw
+// words = bw 16-byte chunks (16-aligned: load validation checks the word
+// offsets), lane i copying chunk i.  Mini blocks wider than the ring's slots
+// are left out (the decode reports them).
+__device__ __forceinline__ void stage_payload(uint8_t* ring, uint32_t bwcap, uint32_t hslot, uint32_t wslot,
+                                              const uint8_t* pay, uint32_t codec, uint32_t i0, uint32_t nmb,
+                                              int lane) {
+  const uint8_t* hs = stage_hdr(ring, hslot) + stage_hdr_skew(codec, i0);
+  uint32_t* dst = stage_words(ring, wslot, bwcap);
+  const uint32_t pw = stage_pw(bwcap);
+#pragma unroll
+  for (int t = 0; t < TB; ++t) {
+    if (t >= int(nmb)) break;
+    const uint32_t wob = codec == C_DELTA ? reinterpret_cast<const uint32_t*>(hs + t * 16)[2]
+                                          : reinterpret_cast<const uint32_t*>(hs + t * 8)[1];
+    const uint32_t bw = wob & 0xffu;
+    if (uint32_t(lane) < bw && bw <= bwcap)
+      cp_async16(dst + t * pw + uint32_t(lane) * 4, pay + uint64_t(wob >> 8) * 4 + uint32_t(lane) * 16);
+  }
+}
+
+// The tile's headers of column c from header slot hslot, laid out as
+// load_headers lays them (lane c * TB + t holds mini block t's header).
+__device__ __forceinline__ TileHdr staged_headers(uint8_t* ring, uint32_t hslot, int c, uint32_t codec, uint32_t i0,
+                                                  uint32_t nmb, int lane) {
+  TileHdr h{0, 0, 0, 0};
+  const int ht = lane % TB;
+  if (lane / TB == c && ht < int(nmb)) {
+    const uint8_t* hs = stage_hdr(ring, hslot) + stage_hdr_skew(codec, i0);
+    if (codec == C_DELTA) {
+      const uint4 v = *reinterpret_cast<const uint4*>(hs + ht * 16);
+      h.x = v.x;
+      h.y = v.y;
+      h.z = v.z;
+    } else {
+      const uint2 v = *reinterpret_cast<const uint2*>(hs + ht * 8);
+      h.x = v.x;
+      h.y = v.y;
+    }
+  }
+  return h;
+}
+
+// L2 prefetch of the headers of mini blocks [i0, i0 + nmb) of every column
+// but c (the later steps read them per survivor).
+__device__ __forceinline__ void prefetch_other_headers(const DevQuery& Q, const PageState& P, int c, uint32_t i0,
+                                                       uint32_t nmb, int lane) {
+  const int hc = lane / TB, ht = lane % TB;
+  const uint64_t hpg = __shfl_sync(kFull, P.pg, hc < int(Q.ncols) ? hc : 0);
+  if (hc < int(Q.ncols) && hc != c && ht < int(nmb))
+    prefetch_l2(reinterpret_cast<const uint8_t*>(hpg) + kPageHdr + uint64_t(i0 + ht) * mb_hdr_bytes(Q.cols[hc].codec));
+}
+
+// The staged words of the tile being decoded: mini block t's words at
+// p + t * pw (in page order), slots of up to bwcap bits.
+struct StagedPay {
+  const uint32_t* p;
+  uint32_t pw, bwcap;
+};
+
 struct TileState {
   uint32_t alive;         // bit 4t+k: row 32k+lane of mini block t is live
   uint32_t gid[TB][4];    // dense group id of each row
@@ -106,10 +219,10 @@ __device__ __forceinline__ void tile_init(const PageState& P, uint32_t i0, uint3
 // into v and decoded in place).  anym bit t = mini block t was decoded.
 // Specialised on the codec (FOR/DICT/STR lengths vs DELTA) so the unrolled
 // loops carry no per-value branch on it.
-template <bool kHost, bool kDelta>
+template <bool kHost, bool kDelta, bool kStaged = false>
 __device__ __forceinline__ void decode_t(const DevQuery& Q, int c, const PageState& P, const TileHdr& Hd,
                                          uint32_t alive, int lane, uint32_t (&v)[TB][4], uint32_t& anym,
-                                         unsigned int* status) {
+                                         unsigned int* status, StagedPay sp = StagedPay{nullptr, 0, 0}) {
   const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, c));
   const uint32_t* pay = reinterpret_cast<const uint32_t*>(pg + payload_offset(Q.cols[c].codec, P.prow));
   uint32_t hx[TB], hy[TB];
@@ -124,11 +237,21 @@ __device__ __forceinline__ void decode_t(const DevQuery& Q, int c, const PageSta
       if (lane == 0) atomicOr(status, S_CORRUPT);
       any = false;
     }
+    if (kStaged && any && bw > sp.bwcap) {  // the ring is sized from the column's widest mini block
+      if (lane == 0) atomicOr(status, S_INTERNAL);
+      any = false;
+    }
     anym |= uint32_t(any) << t;
     const bool ld = any && uint32_t(lane) < bw;
-    const uint32_t* src = pay + (hy[t] >> 8) + lane;
+    if (kStaged) {
+      const uint32_t* src = sp.p + t * sp.pw + lane;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) v[t][k] = ld ? ld_u32<kHost>(src + uint32_t(k) * bw) : 0u;
+      for (int k = 0; k < 4; ++k) v[t][k] = ld ? src[uint32_t(k) * bw] : 0u;
+    } else {
+      const uint32_t* src = pay + (hy[t] >> 8) + lane;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[t][k] = ld ? ld_u32<kHost>(src + uint32_t(k) * bw) : 0u;
+    }
   }
 #pragma unroll
   for (int t = 0; t < TB; ++t) {
@@ -426,10 +549,10 @@ __device__ __forceinline__ uint32_t pruned_mbs(const TileHdr& Hd, int c, int32_t
   return (__ballot_sync(kFull, out) >> (c * TB)) & ((1u << TB) - 1u);
 }
 
-template <bool kHost, bool kDelta, bool kGid = true>
+template <bool kHost, bool kDelta, bool kGid = true, bool kStaged = false>
 __device__ __forceinline__ void dense_step_t(const DevQuery& Q, const DevStep& S, const PageState& P,
                                              const TileHdr& Hd, TileState& T, const uint8_t* stab, int lane,
-                                             unsigned int* status) {
+                                             unsigned int* status, StagedPay sp = StagedPay{nullptr, 0, 0}) {
   // mini blocks that cannot hold a passing value are neither loaded nor decoded
   const uint32_t pruned = pruned_mbs<kDelta>(Hd, S.col, S.zlo, S.zhi, lane);
 #pragma unroll
@@ -437,7 +560,7 @@ __device__ __forceinline__ void dense_step_t(const DevQuery& Q, const DevStep& S
     if ((pruned >> t) & 1u) T.alive &= ~(15u << (4 * t));
   uint32_t v[TB][4];
   uint32_t anym;
-  decode_t<kHost, kDelta>(Q, S.col, P, Hd, T.alive, lane, v, anym, status);
+  decode_t<kHost, kDelta, kStaged>(Q, S.col, P, Hd, T.alive, lane, v, anym, status, sp);
   switch (S.kind) {
     case ST_PROBE:
       switch (probe_mode(S)) {
@@ -514,14 +637,22 @@ static_assert(kSegMbs <= 32, "segment mini blocks must fit a 32-bit mask");
 // kGid = false compiles the step without group-id contributions (for a
 // first step that adds none: a predicate, or a probe of a table no group key
 // reads), which keeps the sixteen per-row group ids out of registers.
-template <bool kHost, bool kText = true, bool kGid = true>
+// kStaged: the step's packed words come from the warp's staging ring (sp);
+// only integer first steps are staged.
+template <bool kHost, bool kText = true, bool kGid = true, bool kStaged = false>
 __device__ __forceinline__ void tile_dense_step(const DevQuery& Q, uint32_t s, const PageState& P, const TileHdr& Hd,
-                                                TileState& T, const uint8_t* stab, int lane, unsigned int* status) {
+                                                TileState& T, const uint8_t* stab, int lane, unsigned int* status,
+                                                StagedPay sp = StagedPay{nullptr, 0, 0}) {
   if (s >= Q.nsteps) return;
   const DevStep& S = Q.steps[s];
-  if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) tile_prefix<kHost, kText>(Q, S, P, Hd, T, lane, status);
-  else if (Q.cols[S.col].codec == C_DELTA) dense_step_t<kHost, true, kGid>(Q, S, P, Hd, T, stab, lane, status);
-  else dense_step_t<kHost, false, kGid>(Q, S, P, Hd, T, stab, lane, status);
+  if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) {
+    if (!kStaged) tile_prefix<kHost, kText>(Q, S, P, Hd, T, lane, status);
+    else if (lane == 0) atomicOr(status, S_INTERNAL);
+  } else if (Q.cols[S.col].codec == C_DELTA) {
+    dense_step_t<kHost, true, kGid, kStaged>(Q, S, P, Hd, T, stab, lane, status, sp);
+  } else {
+    dense_step_t<kHost, false, kGid, kStaged>(Q, S, P, Hd, T, stab, lane, status, sp);
+  }
 }
 
 // Whether step S adds a group-id contribution when it runs densely.
