@@ -12,8 +12,15 @@ ORDERS' by a scan+probe+build kernel probing it, and the timed step is the
 fused LINEITEM pipeline probing ORDERS' table; each build is timed too
 (``chain``).
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
-on a bounded sample of the same workload instead.
+Prints one JSON line (rank 0): the headline (warm graph replays; cold
+replays after an L2 flush reported beside them), the roofline against the
+measured copy peak and the 8 TB/s specification, the host-link and device
+read peaks (``link_peaks``), the end-to-end host-resident variant, the CPU
+oracle at one thread and on every CPU, and, for the default star workload,
+the other configurations measured after the headline (``extra``: strings,
+all-pass strings, the 64-query batch, a serving sweep).  ``--impl
+reference`` times the CPU oracle on a bounded sample of the same workload
+instead.
 """
 
 from __future__ import annotations
@@ -32,6 +39,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "fused rows/s & compressed GB/s vs HBM peak vs unfused chain; p50/p99 query ms"
+SPEC_HBM_GBS = 8000.0          # HBM3e bandwidth the GB300 is specified at
+L2_BYTES = 128 << 20           # at least the GB300's L2
 
 
 def _peaks():
@@ -164,38 +173,85 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_rows_per_s(w, budget_s=15.0, max_rows=None):
-    """Times the oracle (as it stands, one host thread) on a bounded prefix
-    sample of the workload's fact table; returns (rows/s, rows, seconds)."""
-    import copy
+def host_cpu():
+    """(nproc, CPU model name) of the host running the bench."""
+    n = os.cpu_count() or 1
+    try:
+        n = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        pass
+    model = "unknown"
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:  # noqa: BLE001
+        pass
+    return n, model
 
-    import numpy as np
 
+def oracle_rows_per_s(w, threads, budget_s=5.0):
+    """Times the oracle (as it stands) on a prefix sample of the workload's
+    fact table: its pages are encoded first by the oracle's own encoder (the
+    loader, untimed), then the query decodes them and evaluates the rows on
+    ``threads`` host threads.  The sample grows until one evaluation takes
+    about budget_s / 4.  Returns (rows/s, rows, seconds)."""
     import oracle
-    f = w["fact"]
-    n_total = w["tables"][f]["rows"]
-    rows = min(n_total, max_rows or (1 << 20))
+    n_total = w["tables"][w["fact"]]["rows"]
+    rows = min(n_total, 1 << 18)
     while True:
-        s = copy.deepcopy({k: v for k, v in w.items() if k != "tables"})
-        s["tables"] = dict(w["tables"])
-        t = dict(w["tables"][f])
-        cols = {}
-        for name, c in t["cols"].items():
-            if c["codec"] in ("str", "fsst"):
-                offs = c["offsets"][: rows + 1]
-                cols[name] = {"codec": "str", "bytes": c["bytes"][: int(offs[-1])], "offsets": offs}
-            else:
-                cols[name] = {"codec": c["codec"], "values": c["values"][:rows]}
-        t["cols"] = cols
-        t["rows"] = rows
-        s["tables"][f] = t
+        s = _fact_prefix(w, rows)
+        enc = oracle.encode_tables(s)
         t0 = time.perf_counter()
-        oracle.run_query(s, from_encoded=True)
+        oracle.run_query(s, encoded=enc, threads=threads)
         dt = time.perf_counter() - t0
         if dt > budget_s / 4 or rows >= n_total:
             return rows / dt, rows, dt
         rows = min(n_total, int(rows * min(8.0, max(2.0, budget_s / 2 / dt))))
-        _ = np
+
+
+def cpu_baselines(w):
+    """The oracle on the host cores: every CPU of the process and one thread."""
+    n, model = host_cpu()
+    rate_all, rows_all, dt_all = oracle_rows_per_s(w, n)
+    rate_1, rows_1, dt_1 = oracle_rows_per_s(w, 1)
+    return {"value": rate_all, "unit": "rows/s", "cores": n, "kind": "oracle",
+            "sample": f"first {rows_all} fact rows, decode + evaluate on {n} threads "
+                      f"(pages encoded beforehand, untimed), {dt_all:.2f} s",
+            "cpu_model": model, "nproc": n,
+            "one_thread": {"value": rate_1, "unit": "rows/s", "cores": 1,
+                           "sample": f"first {rows_1} fact rows, decode + evaluate, {dt_1:.2f} s"}}
+
+
+def time_graph(prep_ctx, prep, stream, torch, steps, warmup, flush=None):
+    """CUDA-event time (ms) of each of ``steps`` graph replays of ``prep``
+    after ``warmup`` untimed ones; with ``flush`` (a device buffer larger
+    than L2) the buffer is rewritten on the stream before every replay, so
+    each replay starts with a cold L2 (the write is outside the events)."""
+    for _ in range(warmup):
+        prep_ctx.launch_graph(prep, stream)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xff)
+        starts[i].record(stream)
+        prep_ctx.launch_graph(prep, stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def pcts(per):
+    v = sorted(per)
+
+    def q(p):
+        return v[min(len(v) - 1, int(round(p / 100 * (len(v) - 1))))]
+    return {"p50": q(50), "p90": q(90), "p99": q(99), "mean": statistics.mean(v), "n": len(v)}
 
 
 def run_batched(args, dpf, torch, np, local):
@@ -269,62 +325,68 @@ def run_batched(args, dpf, torch, np, local):
     print(json.dumps(out), flush=True)
 
 
-def run_serve(args, dpf, torch, np, local):
+def serve_sweep(dpf, np, local, rows, placement, rates, seconds, max_queries):
     """Poisson streams of queries at several rates through the
-    continuous-batching server over a resident star schema; p50/p99 latency
-    (submit to result on the host) and throughput per rate."""
+    continuous-batching server over a resident star schema: per rate, p50 /
+    p90 / p99 latency (submit to result on the host), achieved QPS and
+    throughput; every result is checked against the same query run alone."""
     import synth
-    rows = args.rows or (1 << 28)
-    w = synth.star_join(rows=rows, clustered=args.serve_placement == "device")
+    w = synth.star_join(rows=rows, clustered=placement == "device")
     eng = dpf.Engine(device=local)
-    t0 = time.perf_counter()
-    eng.load_workload(w, fact_placement=args.serve_placement)
-    load_s = time.perf_counter() - t0
-    qs = synth.serve_variants(w, 12, 4, seed=5)
-    plans = [eng.plan(v) for v in qs]
-    ref = [eng.run(v) for v in qs]  # each query alone
-    alg = [eng.fact_bytes(v)[0] for v in qs]
+    try:
+        t0 = time.perf_counter()
+        eng.load_workload(w, fact_placement=placement)
+        load_s = time.perf_counter() - t0
+        qs = synth.serve_variants(w, 12, 4, seed=5)
+        plans = [eng.plan(v) for v in qs]
+        ref = [eng.run(v) for v in qs]  # each query alone
+        alg = [eng.fact_bytes(v)[0] for v in qs]
+        rng = np.random.default_rng(7)
+        lines = []
+        for lam in rates:
+            n = int(min(max_queries, max(20, lam * seconds)))
+            gaps = rng.exponential(1.0 / lam, n)
+            pick = rng.integers(0, len(qs), n)
+            with dpf.Server(eng.ctx, max_batch=64, max_inflight=2) as srv:
+                tickets = []
+                t_start = time.perf_counter()
+                due = t_start
+                for k in range(n):
+                    due += gaps[k]
+                    while True:
+                        d = due - time.perf_counter()
+                        if d <= 0:
+                            break
+                        time.sleep(min(d, 0.002) if d > 0.0005 else 0)
+                    tickets.append(srv.submit(plans[pick[k]]))
+                lat, batch, mismatch = [], [], 0
+                for k, tk in enumerate(tickets):
+                    got, tm = srv.wait(tk)
+                    mismatch += int(not np.array_equal(got, ref[pick[k]]))
+                    lat.append((tm["done_us"] - tm["submit_us"]) / 1e3)
+                    batch.append(tm["batch_size"])
+                wall = time.perf_counter() - t_start
+            q = pcts(lat)
+            lines.append({"offered_qps": lam, "queries": n, "achieved_qps": n / wall,
+                          "p50_ms": q["p50"], "p90_ms": q["p90"], "p99_ms": q["p99"],
+                          "rows_per_s": rows * n / wall,
+                          "compressed_gbs": sum(alg[i] for i in pick) / wall / 1e9,
+                          "mean_batch": float(np.mean(batch)), "mismatches_vs_alone": mismatch})
+        return {"workload": w["name"], "fact_rows": rows, "fact_placement": placement,
+                "query_variants": len(qs), "load_s": load_s, "rates": lines}
+    finally:
+        eng.close()
+
+
+def run_serve(args, dpf, torch, np, local):
+    """The serving sweep as its own run (``--serve``)."""
     rates = [float(x) for x in args.serve_rates.split(",")]
-    rng = np.random.default_rng(7)
-    lines = []
-    for lam in rates:
-        n = int(min(args.serve_queries, max(20, lam * args.serve_seconds)))
-        gaps = rng.exponential(1.0 / lam, n)
-        pick = rng.integers(0, len(qs), n)
-        with dpf.Server(eng.ctx, max_batch=64, max_inflight=2) as srv:
-            tickets = []
-            t_start = time.perf_counter()
-            due = t_start
-            for k in range(n):
-                due += gaps[k]
-                while True:
-                    d = due - time.perf_counter()
-                    if d <= 0:
-                        break
-                    time.sleep(min(d, 0.002) if d > 0.0005 else 0)
-                tickets.append(srv.submit(plans[pick[k]]))
-            lat, batch, mismatch, done_last = [], [], 0, 0.0
-            for k, tk in enumerate(tickets):
-                got, tm = srv.wait(tk)
-                mismatch += int(not np.array_equal(got, ref[pick[k]]))
-                lat.append((tm["done_us"] - tm["submit_us"]) / 1e3)
-                batch.append(tm["batch_size"])
-                done_last = max(done_last, tm["done_us"])
-            wall = time.perf_counter() - t_start
-        lat_sorted = sorted(lat)
-        q_rows = sum(w["tables"]["fact"]["rows"] for _ in range(n))
-        lines.append({"offered_qps": lam, "queries": n, "achieved_qps": n / wall,
-                      "p50_ms": lat_sorted[len(lat) // 2],
-                      "p99_ms": lat_sorted[min(n - 1, int(0.99 * (n - 1) + 0.5))],
-                      "rows_per_s": q_rows / wall,
-                      "compressed_gbs": sum(alg[i] for i in pick) / wall / 1e9,
-                      "mean_batch": float(np.mean(batch)), "mismatches_vs_alone": mismatch})
+    r = serve_sweep(dpf, np, local, args.rows or (1 << 28), args.serve_placement, rates, args.serve_seconds,
+                    args.serve_queries)
     out = {"metric": METRIC, "mode": "serve", "unit": "ms", "n_gpus": 1, "higher_is_better": False,
            "dtype": "int64", "data": "synthetic (seeded star schema; Poisson arrivals)",
-           "config": {"workload": w["name"], "fact_rows": rows, "fact_placement": args.serve_placement,
-                      "query_variants": len(qs), "load_s": load_s},
-           "rates": lines}
-    eng.close()
+           "config": {k: r[k] for k in ("workload", "fact_rows", "fact_placement", "query_variants", "load_s")},
+           "rates": r["rates"]}
     print(json.dumps(out), flush=True)
 
 
@@ -348,26 +410,30 @@ def _fact_prefix(w, rows):
 
 
 def run_reference(args):
-    """The CPU oracle as the reference arm (one host thread): each step
-    evaluates a bounded prefix sample of the same workload, sized from a
-    short calibration so that the whole --warmup + --steps run takes about
-    --ref-budget-s seconds."""
+    """The CPU oracle as the reference arm, on every CPU of the process: each
+    step decodes and evaluates a bounded prefix sample of the same workload
+    (its pages encoded once beforehand by the oracle's own encoder, untimed),
+    the sample sized from a short calibration so that the whole --warmup +
+    --steps run takes about --ref-budget-s seconds."""
     import oracle
     w = _workload(args.workload, args.rows)
     n_total = w["tables"][w["fact"]]["rows"]
-    cal_rows = min(n_total, 1 << 18)
+    cores, model = host_cpu()
+    cal = _fact_prefix(w, min(n_total, 1 << 18))
+    enc = oracle.encode_tables(cal)
     t0 = time.perf_counter()
-    oracle.run_query(_fact_prefix(w, cal_rows))
-    rate = cal_rows / max(time.perf_counter() - t0, 1e-6)
+    oracle.run_query(cal, encoded=enc, threads=cores)
+    rate = cal["tables"][cal["fact"]]["rows"] / max(time.perf_counter() - t0, 1e-6)
     per_step_s = args.ref_budget_s / max(1, args.steps + args.warmup)
     rows = int(min(n_total, max(1 << 16, rate * per_step_s)))
     s = _fact_prefix(w, rows)
+    enc = oracle.encode_tables(s)
     for _ in range(args.warmup):
-        oracle.run_query(s)
+        oracle.run_query(s, encoded=enc, threads=cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.run_query(s)
+        oracle.run_query(s, encoded=enc, threads=cores)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = rows * len(times) / total
@@ -377,8 +443,9 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic (seeded; stands in for SSB/TPC-H-style star schemas)",
         "config": {"workload": w["name"], "fact_rows": n_total, "sample_rows": rows},
-        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {rows} of {n_total} fact rows per step, encode+decode+evaluate"},
+        "cpu_baseline": {"value": value, "unit": "rows/s", "cores": cores, "kind": "oracle", "cpu_model": model,
+                         "sample": f"first {rows} of {n_total} fact rows per step, decode + evaluate on {cores} "
+                                   "threads (pages encoded beforehand, untimed)"},
         "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -411,6 +478,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the strings / batch / serving measurements that follow the headline")
     ap.add_argument("--ref-budget-s", type=float, default=120.0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -499,6 +568,10 @@ def main():
         ms_step = float(t.item())
     check = eng.ctx.read_result(prep, 0)
     assert np.array_equal(check, records), "result changed across replays"
+    # cold launches: 2 x L2 of device memory rewritten before each replay
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+    cold = time_graph(eng.ctx, prep, stream, torch, max(10, min(args.steps, 30)), 1, flush=flush)
+    del flush
 
     unfused = time_unfused(eng, plan, stream, records, reps=max(3, min(args.steps, 10)),
                            fused_ms=ms_step) if not args.no_unfused else None
@@ -508,11 +581,7 @@ def main():
     traffic, traffic_src = stored_traffic(args.workload, fact_rows)
     achieved = alg_bytes / (avg_launch_ms * 1e-3) / 1e9
     value = world * fact_rows / (ms_step * 1e-3)
-    per_sorted = sorted(per)
-
-    def pct(p):
-        return per_sorted[min(len(per_sorted) - 1, int(round(p / 100 * (len(per_sorted) - 1))))]
-
+    warm = pcts(per)
     out = {
         "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -523,11 +592,16 @@ def main():
                    if alg_bytes > 129e6 else "inputs smaller than L2",
                    "tuning": eng.ctx.prep_tuning(prep)},
         "compressed_gbs": achieved, "compressed_bytes": alg_bytes,
-        "latency_ms": {"p50": pct(50), "p99": pct(99)},
+        "latency_ms": {"p50": warm["p50"], "p90": warm["p90"], "p99": warm["p99"], "mean": warm["mean"],
+                       "how": "warm: back-to-back graph replays (the timed steps)",
+                       "cold": dict(pcts(cold), how=f"{2 * L2_BYTES >> 20} MiB of device memory rewritten "
+                                                    "on the stream before each replay (L2 flushed)")},
         "build_ms": build_ms,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
-                     "peak_kind": f"{peak_kind} copy bandwidth (burst)"},
+                     "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+                     "frac_of_spec": achieved / SPEC_HBM_GBS, "spec_peak": SPEC_HBM_GBS,
+                     "frac_cold": alg_bytes / (pcts(cold)["mean"] * 1e-3) / 1e9 / peak},
         "unfused": unfused,
         "autotune": autotuned,
         "gpu_launches": args.steps,
@@ -540,18 +614,107 @@ def main():
         rows_all = fact_rows + sum(x["rows"] for x in chain)
         out["chain"] = {"links": chain, "fused_ms": ms_step, "pipeline_ms": link_ms + ms_step,
                         "pipeline_rows_per_s": rows_all / ((link_ms + ms_step) * 1e-3)}
+    eng.ctx.release(prep)
+    links = None
+    try:
+        links = {"host_read_gbs": eng.ctx.read_rate("host", 2 << 30, 5, stream),
+                 "device_read_gbs": eng.ctx.read_rate("device", 4 << 30, 5, stream),
+                 "how": "dpf_read_rate: 16-byte read-only loads by every SM over 2 GiB of mapped pinned host "
+                        "memory / 4 GiB of device memory, mean of 5 passes"}
+        out["link_peaks"] = links
+    except dpf.DpfError as e:
+        out["link_peaks"] = {"unavailable": str(e)}
+    eng.close()
     if not args.no_e2e:
         out["e2e"] = e2e_host_resident(dpf, w, args, local, tuning)
+        if links and out["e2e"].get("value"):
+            rate = out["e2e"]["h2d_bytes_per_step"] * out["e2e"]["value"] / fact_rows / 1e9
+            out["e2e"]["host_link_gbs"] = rate
+            out["e2e"]["frac_of_host_link"] = rate / links["host_read_gbs"]
     if rank == 0 and not args.no_cpu_baseline and world == 1:
-        rate, rows, dt = oracle_rows_per_s(w, budget_s=15.0)
-        out["cpu_baseline"] = {"value": rate, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                               "sample": f"first {rows} fact rows, encode+decode+evaluate, {dt:.1f} s"}
-    eng.ctx.release(prep)
-    eng.close()
+        out["cpu_baseline"] = cpu_baselines(w)
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "star":
+        out["extra"] = run_extras(args, dpf, torch, np, local)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _timed_workload(dpf, torch, np, local, w, steps, unfused_reps=3):
+    """One query of workload w, autotuned, replayed from a CUDA graph: ms per
+    launch (events on the launching stream), the fraction of the measured
+    copy peak on its compressed bytes, and the unfused chain beside it."""
+    peak, _ = _peaks()
+    eng = dpf.Engine(device=local)
+    try:
+        eng.load_workload(w)
+        stream = torch.cuda.Stream()
+        plan = eng.plan(w, stream)
+        best, _ = eng.ctx.autotune([plan], stream, reps=2)
+        prep = eng.ctx.prepare([plan])
+        eng.ctx.capture_graph(prep, stream)
+        per = time_graph(eng.ctx, prep, stream, torch, steps, 3)
+        rec = eng.ctx.read_result(prep, 0)
+        tuned = eng.ctx.prep_tuning(prep)
+        eng.ctx.release(prep)
+        alg, rows = eng.fact_bytes(w)
+        ms = statistics.mean(per)
+        out = {"workload": w["name"], "ms": ms, "p50_ms": pcts(per)["p50"], "p90_ms": pcts(per)["p90"],
+               "rows_per_s": rows / (ms * 1e-3), "compressed_gbs": alg / (ms * 1e-3) / 1e9,
+               "frac": alg / (ms * 1e-3) / 1e9 / peak, "tuning": tuned}
+        if unfused_reps:
+            u = time_unfused(eng, plan, stream, rec, reps=unfused_reps, fused_ms=ms)
+            out["unfused_ms"] = u.get("ms_per_query")
+            out["fused_speedup"] = u.get("fused_speedup")
+        return out
+    finally:
+        eng.close()
+
+
+def run_extras(args, dpf, torch, np, local):
+    """The other configurations, measured after the headline so they cannot
+    disturb it: strings 2^25 (prefix filter; and every row passing, the
+    warp-aggregated group-by under Zipf keys), the 64-query batch in one
+    launch, and a short serving sweep over a 2^28-row star schema."""
+    import synth
+    ex = {}
+    for name in ("strings", "strings_all"):
+        try:
+            ex[name] = _timed_workload(dpf, torch, np, local, _workload(name, 0), steps=20)
+        except Exception as e:  # noqa: BLE001
+            ex[name] = {"error": repr(e)}
+    try:
+        ws = synth.batched_workloads(n_queries=64, seed=4)
+        eng = dpf.Engine(device=local)
+        try:
+            for w in ws:
+                eng.load_workload(w)
+            stream = torch.cuda.Stream()
+            plans = [eng.plan(w, stream) for w in ws]
+            eng.ctx.autotune(plans, stream, reps=1)
+            prep = eng.ctx.prepare(plans)
+            eng.ctx.capture_graph(prep, stream)
+            per = time_graph(eng.ctx, prep, stream, torch, 5, 3)
+            alg = sum(eng.fact_bytes(w)[0] for w in ws)
+            rows = sum(w["tables"][w["fact"]]["rows"] for w in ws)
+            ms = statistics.mean(per)
+            peak, _ = _peaks()
+            ex["batched_64"] = {"ms": ms, "rows": rows, "rows_per_s": rows / (ms * 1e-3),
+                                "compressed_gbs": alg / (ms * 1e-3) / 1e9, "frac": alg / (ms * 1e-3) / 1e9 / peak,
+                                "tuning": eng.ctx.prep_tuning(prep), "queries": len(ws)}
+            eng.ctx.release(prep)
+        finally:
+            eng.close()
+        del ws
+    except Exception as e:  # noqa: BLE001
+        ex["batched_64"] = {"error": repr(e)}
+    try:
+        ex["serving"] = serve_sweep(dpf, np, local, rows=1 << 28, placement="device", rates=(10.0, 500.0, 1000.0),
+                                    seconds=1.5, max_queries=1500)
+    except Exception as e:  # noqa: BLE001
+        ex["serving"] = {"error": repr(e)}
+    return ex
 
 
 def time_chain_builds(eng, w, stream, torch, reps=5):

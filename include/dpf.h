@@ -413,6 +413,19 @@ dpf_status dpf_execute_noalloc(dpf_ctx* ctx, const dpf_plan* plan, void* stream,
  * DPF_EINTERNAL (a bounded probe ran out of slots). */
 dpf_status dpf_noalloc_status(dpf_ctx* ctx, uint32_t* bits);
 
+/* Measurement aid (not part of the paper's method): the read bandwidth, in
+ * GB/s (10^9 bytes/s), that a kernel on the context's device sees on a
+ * buffer of `bytes` in device memory (DPF_PLACE_DEVICE) or in mapped pinned
+ * host memory (DPF_PLACE_HOST_PINNED), read with 16-byte read-only loads by
+ * every SM as the fused kernel reads pages; mean of `reps` passes (0 = 5)
+ * after one warm-up pass, timed with CUDA events on `stream`.  The call
+ * allocates and frees the buffer itself and waits for its work.  For
+ * host-resident tables this is the roofline denominator of the fused
+ * kernel's host-resident variant.  Errors: DPF_EINVAL (bytes not a multiple
+ * of 16 in [1 MiB, 64 GiB], bad placement), DPF_ECUDA. */
+dpf_status dpf_read_rate(dpf_ctx* ctx, int32_t placement, uint64_t bytes, uint32_t reps, void* stream,
+                         double* gb_per_s);
+
 /* One-shot form (Sec. 3.1): prepare + launch on `stream`; out_ids[i]
  * names plan i's result.  n > 1 runs every plan in one persistent launch. */
 dpf_status dpf_execute_plan(dpf_ctx* ctx, const dpf_plan* plans, int32_t n, void* stream,

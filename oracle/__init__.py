@@ -245,10 +245,45 @@ def encode_column(col, page_rows):
             "page_off": page_off, "row_prefix": row_prefix, "dict": dct}
 
 
-def decode_column(enc):
-    """Decode a whole encoded column: int32 values, or (bytes, offsets)."""
+def _decode_pages_threaded(enc, threads):
+    """Integer columns: the pages cut into ``threads`` contiguous ranges, each
+    decoded by the same C decoder on its own host thread (ctypes releases the
+    interpreter lock during the call) into its slice of the output."""
+    import concurrent.futures as cf
+    L = lib()
+    n, npages, P = enc["rows"], enc["page_off"].size - 1, enc["page_rows"]
+    wide = enc["codec"] == "for64"
+    out = np.zeros(n, np.int64 if wide else np.int32)
+    item = out.itemsize
+    dct = enc["dict"]
+    bounds = np.linspace(0, npages, min(threads, npages) + 1).astype(np.int64)
+    po = enc["page_off"].ctypes.data
+
+    def work(k):
+        p0, p1 = int(bounds[k]), int(bounds[k + 1])
+        if p1 <= p0:
+            return 0
+        rows = min(n, p1 * P) - p0 * P
+        dst = out.ctypes.data + item * p0 * P
+        if wide:
+            return L.orc_decode_for64(_ptr(enc["blob"]), po + 8 * p0, p1 - p0, rows, P, dst)
+        return L.orc_decode_int(CODECS[enc["codec"]], _ptr(enc["blob"]), po + 8 * p0, p1 - p0, rows, P,
+                                _ptr(dct), 0 if dct is None else dct.size, dst)
+
+    with cf.ThreadPoolExecutor(max_workers=len(bounds) - 1) as ex:
+        for rc in ex.map(work, range(len(bounds) - 1)):
+            _check(rc, "decode (threaded)")
+    return out
+
+
+def decode_column(enc, threads=1):
+    """Decode a whole encoded column: int32 values, or (bytes, offsets).
+    ``threads`` > 1 decodes integer columns page range by page range on
+    that many host threads (the same decoder; the rows are identical)."""
     L = lib()
     n, npages = enc["rows"], enc["page_off"].size - 1
+    if threads > 1 and npages > 1 and enc["codec"] in ("for", "delta", "dict", "for64"):
+        return _decode_pages_threaded(enc, threads)
     if enc["codec"] == "fsst":
         offsets = np.zeros(n + 1, np.uint64)
         table = np.ascontiguousarray(enc["dict"], np.int32)
@@ -349,21 +384,29 @@ def _table(cols, n):
     return t, names, keep
 
 
-def decoded_tables(workload, from_encoded=True):
+def decoded_tables(workload, from_encoded=True, threads=1, encoded=None):
     """Every table's columns, decoded through the oracle's own encoder and
-    decoder (``from_encoded``) or taken raw from the generator."""
+    decoder (``from_encoded``) or taken raw from the generator.  ``encoded``
+    maps (table, column) to pages already encoded by ``encode_tables``."""
     out = {}
     for tname, t in workload["tables"].items():
         cols = {}
         for cname, c in t["cols"].items():
             if from_encoded:
-                enc = encode_column(c, t["page_rows"])
-                d = decode_column(enc)
+                enc = encoded[(tname, cname)] if encoded else encode_column(c, t["page_rows"])
+                d = decode_column(enc, threads)
                 cols[cname] = d
             else:
                 cols[cname] = (c["bytes"], c["offsets"]) if c["codec"] in STRING_CODECS else c["values"]
         out[tname] = {"rows": t["rows"], "cols": cols}
     return out
+
+
+def encode_tables(workload):
+    """Every column of every table through the oracle's encoder (the loader:
+    a step that precedes the query and is timed apart from it)."""
+    return {(tname, cname): encode_column(c, t["page_rows"])
+            for tname, t in workload["tables"].items() for cname, c in t["cols"].items()}
 
 
 def _joins(tables, specs, probe_names, keep, dim_tables):
@@ -408,7 +451,7 @@ def host_threads():
         return max(1, os.cpu_count() or 1)
 
 
-def run_query(workload, from_encoded=True, tables=None, threads=1):
+def run_query(workload, from_encoded=True, tables=None, threads=1, encoded=None):
     """Evaluate ``workload['query']``; returns an array of RECORD_DTYPE.
 
     ``threads`` > 1 evaluates the fact table's pages on that many host
@@ -417,9 +460,11 @@ def run_query(workload, from_encoded=True, tables=None, threads=1):
     L = lib()
     if threads == 0:
         threads = host_threads()
+    if tables is None and encoded is not None:
+        tables = decoded_tables(workload, True, threads, encoded)
     q = workload["query"]
     if tables is None:
-        tables = decoded_tables(workload, from_encoded)
+        tables = decoded_tables(workload, from_encoded, threads)
     fact = tables[workload["fact"]]
     ft, fnames, keep = _table(fact["cols"], fact["rows"])
     preds = (_Pred * max(len(q["preds"]), 1))()

@@ -151,6 +151,7 @@ _SIGS = {
     "dpf_prep_stats": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)]),
     "dpf_execute_noalloc": (C.c_int32, [_P, C.POINTER(Plan), _P, _P, C.c_uint64, _P]),
     "dpf_noalloc_status": (C.c_int32, [_P, C.POINTER(C.c_uint32)]),
+    "dpf_read_rate": (C.c_int32, [_P, C.c_int32, C.c_uint64, C.c_uint32, _P, C.POINTER(C.c_double)]),
     "dpf_execute_plan": (C.c_int32, [_P, C.POINTER(Plan), C.c_int32, _P, C.POINTER(C.c_int64)]),
     "dpf_fetch_result": (C.c_int32, [_P, C.c_int64, _P, C.c_uint64, C.POINTER(C.c_uint64), C.c_int32]),
     "dpf_server_create": (C.c_int32, [_P, C.POINTER(ServerConfig), C.POINTER(_P)]),
@@ -437,6 +438,14 @@ class Context:
         buffers (dpf_record[cap], uint32)."""
         _check(lib().dpf_execute_noalloc(self.h, C.byref(plan.plan), _stream_ptr(stream),
                                          C.c_void_p(out_ptr), int(cap), C.c_void_p(count_ptr)))
+
+    def read_rate(self, placement="host", nbytes=1 << 31, reps=5, stream=None):
+        """GB/s a kernel reads from device memory or mapped pinned host
+        memory (the host-link roofline for host-resident tables)."""
+        g = C.c_double()
+        _check(lib().dpf_read_rate(self.h, PLACE[placement], int(nbytes), int(reps), _stream_ptr(stream),
+                                   C.byref(g)))
+        return g.value
 
     def noalloc_status(self):
         """Status word of the last allocation-free call's kernel (call after

@@ -71,3 +71,20 @@ def test_threads_empty_result_and_wrapping_sums(oracle_lib):
                   "aggs": [{"op": "count"}]}
     r = oracle.run_query(w, from_encoded=False, threads=4)
     assert r.shape == (1,) and r["count"][0] == 0 and not r["val"].any()
+
+
+def test_threaded_decode_equals_one_thread(oracle_lib):
+    """Decoding integer columns page range by page range on several threads
+    gives the one-thread decoder's rows, for every integer codec and ragged
+    last pages; a query over pre-encoded pages agrees too."""
+    w = synth.star_join(rows=300_007, page_rows=4096, bigint_measure=True)
+    enc = oracle.encode_tables(w)
+    for (t, c), e in enc.items():
+        if e["codec"] in ("str", "fsst"):
+            continue
+        one = oracle.decode_column(e)
+        for threads in (2, 7, 1000):
+            assert np.array_equal(oracle.decode_column(e, threads=threads), one), (t, c, threads)
+    one = oracle.run_query(w, from_encoded=False)
+    _same(oracle.run_query(w, encoded=enc, threads=5), one, "encoded, threads")
+    _same(oracle.run_query(w, encoded=enc), one, "encoded")
