@@ -62,6 +62,7 @@ struct Column {
   std::vector<int32_t> dict;
   int64_t vmin = 0, vmax = -1;    // value bounds from the mini block headers (planner statistics)
   uint32_t max_bw = 0;            // FOR/DICT/DELTA: widest mini block (bits)
+  uint64_t nsym = 0;              // FSST: symbols in the table
 };
 
 struct HashTable {
@@ -578,6 +579,7 @@ struct ColumnSet {
     d.codec = uint32_t(col.codec);
     d.page_rows = col.page_rows;
     d.max_bw = col.max_bw;
+    d.nsym = col.codec == C_FSST ? uint32_t(col.nsym) : 0u;
     host |= col.placement == DPF_PLACE_HOST_PINNED;
     *idx = int(ids.size());
     ids.push_back(id);
@@ -779,6 +781,20 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
 size_t place_tables(DevQuery& Q, size_t budget, bool first_only) {
   const uint32_t width = Q.domain <= 255 ? 1u : (Q.domain <= 65535 ? 2u : 4u);
   size_t used = 0;
+  // PREFIX / CONTAINS steps on FSST columns: the code-level matcher tables
+  // (fsst_match_bytes), whichever step they are, while they fit
+  for (uint32_t s = 0; s < Q.nsteps; ++s) {
+    DevStep& S = Q.steps[s];
+    if ((S.kind != ST_PREFIX && S.kind != ST_CONTAINS) || Q.cols[S.col].codec != C_FSST) continue;
+    S.smem_width = 0;
+    if (S.plen == 0) continue;
+    const size_t bytes = fsst_match_bytes(S.plen);
+    const size_t at = (used + 15) & ~size_t(15);
+    if (at + bytes > budget) continue;
+    S.smem_width = 1;
+    S.smem_off = uint32_t(at);
+    used = at + bytes;
+  }
   for (uint32_t s = 0; s < Q.nsteps; ++s) {
     DevStep& S = Q.steps[s];
     if (S.kind != ST_PROBE) continue;
@@ -1265,6 +1281,7 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
     }
   }
   if (codec == C_FSST) {
+    col.nsym = dict_n / 3;
     std::vector<int4> sym(dict_n / 3);
     for (uint64_t i = 0; i < sym.size(); ++i) sym[i] = make_int4(dict[3 * i], dict[3 * i + 1], dict[3 * i + 2], 0);
     if ((st = dev_alloc_t(c, sym.size(), &col.d_sym)) || (st = upload(c, col.d_sym, sym.data(), sizeof(int4) * sym.size()))) {

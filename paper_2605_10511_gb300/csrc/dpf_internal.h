@@ -63,7 +63,7 @@ struct DevColumn {
   uint32_t codec;
   uint32_t page_rows;
   uint32_t max_bw;            // FOR/DICT/DELTA: widest mini block (bits), from the validated headers
-  uint32_t pad_;
+  uint32_t nsym;              // FSST: symbols in the table
 };
 
 enum StepKind : uint8_t {
@@ -97,7 +97,9 @@ struct DevStep {
   uint8_t ht_kind;
   uint8_t smem_width;     // 0: probe global memory; OPEN: 8 (slots copied);
                           // DIRECT: 1/2/4-byte entries holding this join's
-                          // group-id contribution (all ones = absent)
+                          // group-id contribution (all ones = absent);
+                          // PREFIX / CONTAINS on an FSST column: 1 = the
+                          // step's code-level matcher tables sit at smem_off
   uint16_t pad_;
   uint32_t smem_off;      // byte offset of the copy in the CTA's table region
   uint32_t mul0, mul1;    // gid multipliers of payload fields 0 and 1 (0 = unused)

@@ -449,10 +449,15 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
 
 // Copies a query's shared-memory join tables into the CTA's table region:
 // open-addressing slots as they are, direct tables as 1/2/4-byte group-id
-// contributions (all ones = absent).
+// contributions (all ones = absent); builds the code-level matcher tables
+// of string steps on FSST columns.
 __device__ void load_smem_tables(const DevQuery& Q, uint8_t* stab) {
   for (uint32_t s = 0; s < Q.nsteps; ++s) {
     const DevStep& S = Q.steps[s];
+    if ((S.kind == ST_PREFIX || S.kind == ST_CONTAINS) && S.smem_width != 0 && Q.cols[S.col].codec == C_FSST) {
+      build_fsst_matcher(S, Q.cols[S.col].sym, Q.cols[S.col].nsym, stab + S.smem_off);
+      continue;
+    }
     if (S.kind != ST_PROBE || S.smem_width == 0) continue;
     if (S.ht_kind == HT_OPEN) {
       const uint2* src = static_cast<const uint2*>(S.ht);

@@ -21,6 +21,11 @@ constexpr int kFusedMinBlocksHi = 4;
 constexpr uint32_t kDefaultChunkRows = 4096;
 // Staging of the first step's mini blocks unless tuned (DPF_STAGE_ON / _OFF).
 constexpr int32_t kDefaultStaging = 2;
+// Shared-memory bytes of the code-level matcher tables of a PREFIX / CONTAINS
+// step with a pattern of plen bytes on an FSST column: for every matcher
+// state 0..plen, the next state after one symbol code (256 entries) and
+// after one literal byte (256 entries).
+inline uint32_t fsst_match_bytes(uint32_t plen) { return (plen + 1) * 512u; }
 
 // Fused persistent kernel over a batch of compiled queries (Sec. 3.2).
 // qbegin[0..nq] = first ticket of each query (qbegin[nq] = total tickets).

@@ -358,9 +358,86 @@ __device__ __forceinline__ bool string_scan(const DevStep& S, const uint8_t* s, 
   return m.hit;
 }
 
+// Code-level matching of an FSST string (LIKE on compressed strings): the
+// matcher's state advances by one table lookup per code instead of per
+// decoded byte.  `tab` (shared memory, built by build_fsst_matcher) holds,
+// for every state q < plen, the entry after symbol code c at tab[q * 256 + c]
+// and after escaped literal byte b at tab[(plen + 1) * 256 + q * 256 + b];
+// an entry is the next state, kFsstHit (the pattern was completed inside the
+// symbol) or kFsstDead (a PREFIX mismatch).  The string's bytes are read as
+// aligned 4-byte words (inside the 16-byte padded page).
+constexpr uint8_t kFsstHit = 0x80, kFsstDead = 0x7f;
 template <bool kHost>
-__device__ __forceinline__ bool string_match(const DevStep& S, const uint8_t* s, uint32_t len, const int4* sym) {
+__device__ __forceinline__ bool fsst_table_match(const DevStep& S, const uint8_t* s, uint32_t len, const uint8_t* tab) {
+  const uint8_t* btab = tab + (uint32_t(S.plen) + 1) * 256;
+  const uint8_t* w0 = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(s) & ~uintptr_t(3));
+  const uint8_t* end = s + len;
+  uint32_t skip = uint32_t(s - w0), q = 0;
+  bool esc = false;
+  for (const uint8_t* w = w0; w < end; w += 4) {
+    uint32_t x = ld_u32<kHost>(reinterpret_cast<const uint32_t*>(w)) >> (8 * skip);
+    const uint32_t nb = tmin<uint32_t>(4u - skip, uint32_t(end - (w + skip)));
+    skip = 0;
+    for (uint32_t k = 0; k < nb; ++k, x >>= 8) {
+      const uint32_t c = x & 0xffu;
+      uint32_t e;
+      if (esc) {
+        e = btab[q * 256 + c];
+        esc = false;
+      } else if (c == kFsstEscape) {
+        esc = true;
+        continue;
+      } else {
+        e = tab[q * 256 + c];
+      }
+      if (e & kFsstHit) return true;
+      if (e == kFsstDead) return false;
+      q = e;
+    }
+  }
+  return false;
+}
+
+// The matcher state after feeding byte b in state q < plen: the next state,
+// kFsstHit when the pattern completes, kFsstDead when a PREFIX cannot match.
+__device__ __forceinline__ uint32_t matcher_feed(const DevStep& S, uint32_t q, uint32_t b) {
+  if (S.kind == ST_PREFIX) {
+    if (b != S.pfx[q]) return kFsstDead;
+  } else {  // CONTAINS: the Knuth-Morris-Pratt automaton
+    while (q > 0 && b != S.pfx[q]) q = S.kmp[q - 1];
+    if (b != S.pfx[q]) return q;
+  }
+  return q + 1 == S.plen ? uint32_t(kFsstHit) : q + 1;
+}
+
+// Builds step S's code-level tables at tab (all threads of the CTA): for
+// every state q < plen, each of the column's nsym symbols fed byte by byte
+// (codes >= nsym never occur: load validation), and each literal byte.
+__device__ __forceinline__ void build_fsst_matcher(const DevStep& S, const int4* sym, uint32_t nsym, uint8_t* tab) {
+  const uint32_t plen = S.plen, n = plen * 256;
+  uint8_t* btab = tab + (plen + 1) * 256;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint32_t q = i >> 8, c = i & 255u;
+    btab[i] = uint8_t(matcher_feed(S, q, c));
+    uint32_t e = kFsstDead;
+    if (c < nsym) {
+      const int4 y = __ldg(sym + c);
+      uint64_t w = uint32_t(y.x) | (uint64_t(uint32_t(y.y)) << 32);
+      e = q;
+      for (int k = 0; k < y.z; ++k, w >>= 8) {
+        e = matcher_feed(S, e, uint32_t(w & 0xffu));
+        if (e == kFsstHit || e == kFsstDead) break;
+      }
+    }
+    tab[i] = uint8_t(e);
+  }
+}
+
+template <bool kHost>
+__device__ __forceinline__ bool string_match(const DevStep& S, const uint8_t* s, uint32_t len, const int4* sym,
+                                             const uint8_t* tab = nullptr) {
   if (S.plen == 0) return true;                         // an empty pattern matches
+  if (tab != nullptr) return fsst_table_match<kHost>(S, s, len, tab);
   if (S.kind == ST_PREFIX) {
     if (sym == nullptr && len < S.plen) return false;
     return string_scan<kHost, ST_PREFIX>(S, s, len, sym);
@@ -377,13 +454,15 @@ __device__ __forceinline__ bool string_match(const DevStep& S, const uint8_t* s,
 // cannot run drops its rows and reports S_INTERNAL.
 template <bool kHost, bool kText = true>
 __device__ __forceinline__ void tile_prefix(const DevQuery& Q, const DevStep& S, const PageState& P,
-                                            const TileHdr& Hd, TileState& T, int lane, unsigned int* status) {
+                                            const TileHdr& Hd, TileState& T, int lane, unsigned int* status,
+                                            const uint8_t* stab) {
   uint32_t len[TB][4];
   uint32_t anym;
   tile_decode<kHost>(Q, S.col, P, Hd, T.alive, lane, len, anym, status);
   const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, S.col));
   const uint8_t* bytes = pg + __shfl_sync(kFull, P.extra, S.col);
   const int4* sym = Q.cols[S.col].codec == C_FSST ? Q.cols[S.col].sym : nullptr;
+  const uint8_t* tab = sym != nullptr && S.smem_width ? stab + S.smem_off : nullptr;
   const bool lockstep = S.kind == ST_PREFIX && sym == nullptr;
 #pragma unroll
   for (int t = 0; t < TB; ++t) {
@@ -412,7 +491,8 @@ __device__ __forceinline__ void tile_prefix(const DevQuery& Q, const DevStep& S,
       if constexpr (kText) {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          if (((T.alive >> (4 * t + k)) & 1u) && string_match<kHost>(S, mb + st[k], len[t][k], sym)) match |= 1u << k;
+          if (((T.alive >> (4 * t + k)) & 1u) && string_match<kHost>(S, mb + st[k], len[t][k], sym, tab))
+            match |= 1u << k;
       } else {
         if (lane == 0) atomicOr(status, S_INTERNAL);
       }
@@ -646,7 +726,7 @@ __device__ __forceinline__ void tile_dense_step(const DevQuery& Q, uint32_t s, c
   if (s >= Q.nsteps) return;
   const DevStep& S = Q.steps[s];
   if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) {
-    if (!kStaged) tile_prefix<kHost, kText>(Q, S, P, Hd, T, lane, status);
+    if (!kStaged) tile_prefix<kHost, kText>(Q, S, P, Hd, T, lane, status, stab);
     else if (lane == 0) atomicOr(status, S_INTERNAL);
   } else if (Q.cols[S.col].codec == C_DELTA) {
     dense_step_t<kHost, true, kGid, kStaged>(Q, S, P, Hd, T, stab, lane, status, sp);
@@ -797,7 +877,7 @@ __device__ __forceinline__ uint32_t row_value(const DevQuery& Q, int c, const Pa
 template <bool kHost, bool kText = true>
 __device__ __forceinline__ bool row_prefix(const DevQuery& Q, const DevStep& S, const PageState& P,
                                            uint32_t seg_mb, uint32_t r, bool valid, int lane,
-                                           unsigned int* status) {
+                                           unsigned int* status, const uint8_t* stab) {
   const int c = S.col;
   const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, c));
   const uint32_t* starts = reinterpret_cast<const uint32_t*>(pg + kPageHdr + uint64_t(P.nmb_page) * 8);
@@ -823,7 +903,8 @@ __device__ __forceinline__ bool row_prefix(const DevQuery& Q, const DevStep& S, 
   const uint8_t* bytes = pg + __shfl_sync(kFull, P.extra, c) + my_start;
   const int4* sym = Q.cols[c].codec == C_FSST ? Q.cols[c].sym : nullptr;
   if constexpr (kText) {
-    return valid && string_match<kHost>(S, bytes, my_len, sym);
+    const uint8_t* tab = sym != nullptr && S.smem_width ? stab + S.smem_off : nullptr;
+    return valid && string_match<kHost>(S, bytes, my_len, sym, tab);
   } else {
     if (!valid) return false;
     if (S.kind != ST_PREFIX || sym != nullptr) {
@@ -913,7 +994,7 @@ __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevS
     uint32_t gid = e >> kRowBits;
     bool keep;
     if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) {
-      keep = row_prefix<kHost, kText>(Q, S, P, seg_mb, r, valid, lane, status);
+      keep = row_prefix<kHost, kText>(Q, S, P, seg_mb, r, valid, lane, status, stab);
     } else {
       const uint32_t v = row_value<kHost>(Q, S.col, P, seg_mb, r, valid, lane, status);
       if (S.kind == ST_PROBE) {
