@@ -52,7 +52,8 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("fused.cu", "fused_kernel.cuh", "fused_lean.cu", "fused_text.cu", "fused_host.cu", "tile.cuh",
+KERNEL_SOURCES = ("fused.cu", "fused_kernel.cuh", "fused_lean.cu", "fused_text.cu", "fused_host.cu", "fused_stage.cu",
+                  "tile.cuh",
                   "dpf_device.cuh", "dpf_internal.h", "kernels.h")
 
 
@@ -113,6 +114,9 @@ def _workload(name, rows):
     # every row passes (an empty prefix): the group-by takes all 2^25 rows, Zipf-skewed keys
     if name == "strings_all":
         return synth.strings(rows=rows or (1 << 25), prefix=b"")
+    # 15 groups, one holding 97 % of the rows: the warp-aggregated group-by
+    if name == "groups_hot":
+        return synth.hot_groups(rows=rows or (1 << 25))
     # word-based strings, LIKE '%ab%', raw bytes vs FSST
     if name == "strings_text":
         return synth.strings(rows=rows or (1 << 25), text=True, contains=b"ab")
@@ -459,7 +463,7 @@ def main():
     ap.add_argument("--impl", default="dpf", choices=["dpf", "reference"])
     ap.add_argument("--workload", default="star",
                     choices=["star", "star_unsorted", "star_year", "star_year_unsorted", "star_bigint", "scan",
-                             "strings", "strings_all",
+                             "strings", "strings_all", "groups_hot",
                              "strings_text", "strings_fsst", "chain", "chain_sparse", "batched"])
     ap.add_argument("--batch-queries", type=int, default=64)
     ap.add_argument("--serve", action="store_true", help="Poisson serving run instead of the step benchmark")

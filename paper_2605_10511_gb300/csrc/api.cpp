@@ -939,6 +939,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
     tickets += Q.nchunks;
     const uint32_t S1 = 1 + Q.naggs;
     Q.use_smem_acc = uint64_t(Q.domain) * S1 <= kSmemAccSlots ? 1u : 0u;
+    Q.warp_agg = Q.domain > 1 && Q.domain <= kWarpAggMaxDomain ? 1u : 0u;
     if (Q.use_smem_acc) acc_slots = std::max<uint32_t>(acc_slots, Q.domain * S1);
     off_acc[i] = scratch; scratch += align16(uint64_t(Q.domain) * S1 * 8);
     off_done[i] = scratch; scratch += 16;
@@ -949,7 +950,9 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   // Staging ring: integer first steps over device-resident pages; its slots
   // are as wide as the widest mini block of those steps' columns.
   uint32_t stage_bw = 0;
-  if (t.staging == DPF_STAGE_ON && !host) {
+  bool text = false;
+  for (const DevQuery& q : p->hq) text = text || needs_string_matcher(q);
+  if (t.staging == DPF_STAGE_ON && !host && !text) {
     std::vector<int> staged;
     for (int i = 0; i < n; ++i) {
       const DevQuery& Q = p->hq[i];

@@ -135,6 +135,7 @@ struct alignas(16) DevQuery {
   uint32_t naggs;
   uint8_t agg_op[4], agg_a[4], agg_b[4];   // agg_a/agg_b: column indices
   uint32_t use_smem_acc;
+  uint32_t warp_agg;           // 1: warp-aggregated group-by updates (__match_any_sync peers)
   // group key reconstruction: code_k = (gid / key_div[k]) % key_dom[k]
   uint32_t nkeys;
   uint32_t key_div[2], key_dom[2];

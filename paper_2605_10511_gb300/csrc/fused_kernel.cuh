@@ -146,9 +146,12 @@ __device__ __forceinline__ void warp_group_add(unsigned long long* acc, uint64_t
 }
 
 // Lanes of the round with the same group id as this one (valid lanes only;
-// invalid lanes share a key no group id takes).
-__device__ __forceinline__ uint32_t group_peers(uint32_t gid, bool valid) {
-  return __match_any_sync(kFull, valid ? gid : 0xffffffffu);
+// invalid lanes share a key no group id takes).  Without warp aggregation
+// (Q.warp_agg == 0) every lane is its own group and adds directly:
+// __match_any_sync costs more than it saves when a round holds many distinct
+// groups (measured on 1,024 Zipf-distributed groups).
+__device__ __forceinline__ uint32_t group_peers(uint32_t gid, bool valid, bool wagg) {
+  return wagg ? __match_any_sync(kFull, valid ? gid : 0xffffffffu) : 1u << (threadIdx.x & 31);
 }
 
 // One aggregate over a warp's list, specialised on its operation (dpf_agg_op)
@@ -195,7 +198,7 @@ __device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, 
       if (single) sum += valid[u] ? x : 0;
       else
         warp_group_add(acc, uint64_t(gid[u]) * S1 + slot, (unsigned long long)x, valid[u],
-                       group_peers(gid[u], valid[u]), lane, wbuf);
+                       group_peers(gid[u], valid[u], Q.warp_agg != 0), lane, wbuf);
     }
   }
   if (single) {
@@ -259,7 +262,7 @@ __device__ __forceinline__ void agg_pass_wide(const DevQuery& Q, const PageState
       b = (unsigned long long)value64<kHost>(Q, cb, P, seg_mb, r, valid, lane, status);
     const unsigned long long x = kOp == DPF_AGG_SUM ? a : (kOp == DPF_AGG_SUM_MUL ? a * b : a - b);
     if (single) sum += valid ? x : 0ull;
-    else warp_group_add(acc, uint64_t(gid) * S1 + slot, x, valid, group_peers(gid, valid), lane, wbuf);
+    else warp_group_add(acc, uint64_t(gid) * S1 + slot, x, valid, group_peers(gid, valid, Q.warp_agg != 0), lane, wbuf);
   }
   if (single) {
 #pragma unroll
@@ -305,7 +308,7 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
         atomicOr(status, S_CORRUPT);  // a corrupt dictionary code
         valid = false;
       }
-      const uint32_t peers = group_peers(gid, valid);
+      const uint32_t peers = group_peers(gid, valid, Q.warp_agg != 0);
       if (valid && (peers & ((1u << lane) - 1u)) == 0)
         atomicAdd(acc + uint64_t(gid) * S1, (unsigned long long)__popc(peers));
     }
@@ -372,7 +375,7 @@ __device__ __forceinline__ FirstCol first_col(const DevQuery& Q, const PageState
 // the latency).  The list collects the survivors of consecutive tiles (a
 // segment of at most 2^kRowBits rows of one page) before the later steps and
 // the aggregation run on them.
-template <bool kHost, bool kText>
+template <bool kHost, bool kText, bool kStage>
 __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long long* acc, const uint8_t* stab,
                                uint32_t* list, int lane, unsigned int* status, unsigned long long* wbuf,
                                uint8_t* ring) {
@@ -398,7 +401,7 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
     page_begin<kHost>(Q, p, lane, P);
     // staged first step (StageRing in tile.cuh): the headers of tiles 0 and 1
     // and the words of tile 0 are in flight before the first decode
-    const uint32_t bwcap = kHost ? 0u : Q.stage;
+    const uint32_t bwcap = kStage && !kHost ? Q.stage : 0u;
     if (bwcap) {
       const FirstCol f = first_col(Q, P);
       stage_headers(ring, 0, f.pg, f.codec, mb0, tmin<uint32_t>(TB, mb1 - mb0), lane);
@@ -478,8 +481,10 @@ __device__ void load_smem_tables(const DevQuery& Q, uint8_t* stab) {
 }
 
 // kText = false: the build without the general string matcher (CONTAINS,
-// FSST), launched for batches that have no such step.
-template <bool kHost, int kMinBlocks, bool kText>
+// FSST), launched for batches that have no such step.  kStage: the build
+// with the staging ring (device-resident batches without such steps,
+// launched when the tuning asks for staging).
+template <bool kHost, int kMinBlocks, bool kText, bool kStage = false>
 __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* __restrict__ queries,
                                                        const uint64_t* __restrict__ qbegin, int nq,
                                                        uint64_t total, Sched* sched, uint32_t acc_slots,
@@ -540,7 +545,8 @@ __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* 
     unsigned long long* acc = Q.use_smem_acc ? sacc : Q.acc;
     uint32_t done_here = 0;
     while (hq == cur) {
-      process_ticket<kHost, kText>(Q, held - Q.chunk_begin, acc, stab, list, lane, &sched->status, wbuf, ring);
+      process_ticket<kHost, kText, kStage>(Q, held - Q.chunk_begin, acc, stab, list, lane, &sched->status, wbuf,
+                                           ring);
       ++done_here;
       hq = draw(held);
     }
@@ -558,21 +564,22 @@ __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* 
 }
 
 
-template <bool kHost, int kMinBlocks, bool kText>
+template <bool kHost, int kMinBlocks, bool kText, bool kStage = false>
 int occupancy_of(int threads, size_t smem) {
   int n = 0;
-  cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks, kText>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_kernel<kHost, kMinBlocks, kText>, threads, smem);
+  cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks, kText, kStage>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int(smem));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_kernel<kHost, kMinBlocks, kText, kStage>, threads, smem);
   return n;
 }
 
-template <bool kHost, int kMinBlocks, bool kText>
+template <bool kHost, int kMinBlocks, bool kText, bool kStage = false>
 cudaError_t launch_as(const FusedLaunch& L, size_t smem, uint32_t tb, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks, kText>,
+  cudaError_t e = cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks, kText, kStage>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  fused_kernel<kHost, kMinBlocks, kText><<<L.grid, L.threads, smem, s>>>(L.queries, L.qbegin, L.nq, L.total_chunks,
-                                                                         L.sched, L.acc_slots, tb, L.stage_bw);
+  fused_kernel<kHost, kMinBlocks, kText, kStage><<<L.grid, L.threads, smem, s>>>(
+      L.queries, L.qbegin, L.nq, L.total_chunks, L.sched, L.acc_slots, tb, L.stage_bw);
   return cudaGetLastError();
 }
 

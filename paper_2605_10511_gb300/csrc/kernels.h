@@ -21,6 +21,11 @@ constexpr int kFusedMinBlocksHi = 4;
 constexpr uint32_t kDefaultChunkRows = 4096;
 // Staging of the first step's mini blocks unless tuned (DPF_STAGE_ON / _OFF).
 constexpr int32_t kDefaultStaging = 2;
+// Group domains up to this size use warp-aggregated group-by updates: with
+// few groups the lanes of a round often share one and __match_any_sync has
+// few distinct values to sort out; with many groups (1,024 Zipf keys) plain
+// shared-memory atomics measured 1.8x faster.
+constexpr uint32_t kWarpAggMaxDomain = 32;
 // Shared-memory bytes of the code-level matcher tables of a PREFIX / CONTAINS
 // step with a pattern of plen bytes on an FSST column: for every matcher
 // state 0..plen, the next state after one symbol code (256 entries) and

@@ -12,6 +12,7 @@ from .tables import (  # noqa: F401
     batched_workloads,
     chain_join,
     date_keys,
+    hot_groups,
     scan_filter_aggregate,
     serve_variants,
     star_join,

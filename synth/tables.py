@@ -528,6 +528,28 @@ def serve_variants(w, n_star=12, n_scan=4, seed=5):
     return out
 
 
+def hot_groups(rows=1 << 25, n_groups=5, hot_frac=0.97, seed=6, page_rows=8192):
+    """A group-by stress case: group key g (n_groups values) with one value
+    taking a further hot_frac of the rows, times a 3-valued key g2; int32,
+    delta-coded and BIGINT measures; SUM, SUM of a product, SUM of a BIGINT
+    and SUM of a BIGINT minus an int32, over rows with b >= -900 (95 %)."""
+    rng = _rng(seed)
+    g = rng.integers(0, n_groups, rows).astype(np.int32)
+    g[rng.random(rows) < hot_frac] = 7 % n_groups
+    g2 = rng.integers(0, 3, rows).astype(np.int32) * 11 - 5
+    a = rng.integers(-2**31, 2**31, rows, dtype=np.int64).astype(np.int32)
+    b = rng.integers(-1000, 1000, rows).astype(np.int32)
+    big = rng.integers(-2**62, 2**62, rows, dtype=np.int64) // 3
+    return {"name": f"hot_{rows}_{n_groups}_{seed}", "fact": "f", "tables": {"f": {
+        "rows": rows, "page_rows": page_rows, "cols": {
+            "g": _int_col(g, "dict"), "g2": _int_col(g2, "dict"), "a": _int_col(a),
+            "b": _int_col(b, "delta"), "big": {"codec": "for64", "values": big}}}},
+        "query": {"preds": [{"col": "b", "op": "ge", "args": [-900]}], "joins": [],
+                  "group": [{"col": "g"}, {"col": "g2"}],
+                  "aggs": [{"op": "sum", "cols": ["a"]}, {"op": "sum_mul", "cols": ["a", "b"]},
+                           {"op": "sum", "cols": ["big"]}, {"op": "sum_sub", "cols": ["big", "a"]}]}}
+
+
 # ---------------------------------------------------------------------------
 # Small random workloads for property tests
 # ---------------------------------------------------------------------------

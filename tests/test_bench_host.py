@@ -34,7 +34,7 @@ def test_reference_arm_prints_one_contract_line():
 
 
 @pytest.mark.parametrize("name", ["star", "star_unsorted", "star_year", "star_year_unsorted", "star_bigint", "scan",
-                                  "strings", "strings_all", "strings_text", "strings_fsst", "chain", "chain_sparse"])
+                                  "strings", "strings_all", "groups_hot", "strings_text", "strings_fsst", "chain", "chain_sparse"])
 def test_every_workload_name_builds(name):
     w = bench._workload(name, 1 << 12)
     assert w["tables"][w["fact"]]["rows"] == 1 << 12

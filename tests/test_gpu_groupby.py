@@ -3,9 +3,10 @@
 The lanes of a round that hold the same group id add their values once
 (their peers found by __match_any_sync, the group's lowest lane issuing the
 atomic).  The cases that exercise it most: every row passing a filter with
-Zipf-skewed keys (the top key holds about a fifth of the rows), one hot
-group holding almost every row, groups in shared-memory and in global
-accumulators, COUNT / SUM / SUM_MUL / SUM_SUB over 32- and 64-bit operands,
+Zipf-skewed keys (the top key holds about a fifth of the rows; plain
+atomics, as for every domain above 32 groups), one hot group holding almost
+every row (warp-aggregated for domains of at most 32), groups in
+shared-memory and in global accumulators, COUNT / SUM / SUM_MUL / SUM_SUB over 32- and 64-bit operands,
 ragged tails.  Records must equal the oracle's exactly.
 """
 
@@ -43,30 +44,11 @@ def test_all_rows_pass_with_zipf_keys(eng, rows):
     assert_same(eng.run(w), want, w["name"])
 
 
-def _hot_group_workload(rows, n_groups, hot_frac, seed):
-    rng = np.random.default_rng(seed)
-    g = rng.integers(0, n_groups, rows).astype(np.int32)
-    g[rng.random(rows) < hot_frac] = 7 % n_groups
-    g2 = rng.integers(0, 3, rows).astype(np.int32) * 11 - 5
-    a = rng.integers(-2**31, 2**31, rows, dtype=np.int64).astype(np.int32)
-    b = rng.integers(-1000, 1000, rows).astype(np.int32)
-    big = rng.integers(-2**62, 2**62, rows, dtype=np.int64) // 3
-    return {"name": f"hot_{rows}_{n_groups}_{seed}", "fact": "f", "tables": {"f": {
-        "rows": rows, "page_rows": 8192, "cols": {
-            "g": {"codec": "dict", "values": g}, "g2": {"codec": "dict", "values": g2},
-            "a": {"codec": "for", "values": a}, "b": {"codec": "delta", "values": b},
-            "big": {"codec": "for64", "values": big}}}},
-        "query": {"preds": [{"col": "b", "op": "ge", "args": [-900]}], "joins": [],
-                  "group": [{"col": "g"}, {"col": "g2"}],
-                  "aggs": [{"op": "sum", "cols": ["a"]}, {"op": "sum_mul", "cols": ["a", "b"]},
-                           {"op": "sum", "cols": ["big"]}, {"op": "sum_sub", "cols": ["big", "a"]}]}}
-
-
 @pytest.mark.parametrize("n_groups,hot_frac", [(1, 0.0), (5, 0.97), (300, 0.5), (20000, 0.3)])
 def test_hot_groups_and_wide_sums(eng, n_groups, hot_frac):
     """One key holding most rows (up to all 32 lanes of a round in one
     group), int32 and int64 (FOR64) operands, products and differences that
     wrap modulo 2^64; 20,000 x 3 groups exceed the shared accumulators and
     run on global ones."""
-    w = _hot_group_workload(300_001, n_groups, hot_frac, seed=n_groups)
+    w = synth.hot_groups(300_001, n_groups, hot_frac, seed=n_groups)
     assert_same(eng.run(w), oracle.run_query(w, from_encoded=False), w["name"])
