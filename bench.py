@@ -53,7 +53,7 @@ def _peaks():
 
 
 KERNEL_SOURCES = ("fused.cu", "fused_kernel.cuh", "fused_lean.cu", "fused_text.cu", "fused_host.cu", "fused_stage.cu",
-                  "tile.cuh",
+                  "fused_wide.cu", "tile.cuh",
                   "dpf_device.cuh", "dpf_internal.h", "kernels.h")
 
 

@@ -293,7 +293,9 @@ enum dpf_ht_place { DPF_HT_AUTO = 0, DPF_HT_SMEM = 1, DPF_HT_GLOBAL = 2 };
 typedef struct dpf_tuning {
   uint32_t chunk_rows;   /* rows per scheduling ticket (one warp's unit of work):
                             multiple of 512, at most 2^24; default 2048        */
-  uint32_t threads;      /* threads per CTA: 128 or 256                          */
+  uint32_t threads;      /* threads per CTA: 128 or 256; 512 or 1024 (2 / 1 CTAs
+                            per SM) for device-resident, unstaged batches
+                            without CONTAINS / FSST steps                    */
   int32_t ht_placement;  /* enum dpf_ht_place                                     */
   uint32_t ctas_per_sm;  /* persistent CTAs per SM: 0 = as many as fit of the
                             kernel build for 3 resident 256-thread CTAs
@@ -345,7 +347,7 @@ dpf_status dpf_release(dpf_ctx* ctx, dpf_prep_id prep);
  * thread blocks process in a loop; the chunk size, the threads per block and
  * where the join tables live (shared memory vs device memory, Sec. 4.3) are
  * the launch configuration.  dpf_autotune prepares the n plans under each
- * configuration of a fixed grid (chunk_rows 1K..256K, threads 128/256,
+ * configuration of a fixed grid (chunk_rows 1K..256K, threads 128..1024,
  * tables AUTO/GLOBAL, kernel build for 3 or 4 CTAs per SM, staging on/off),
  * times `reps` launches of each on `stream` with CUDA
  * events after one warm-up launch (reps 0 = 3), and keeps the fastest in the

@@ -909,7 +909,8 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   fill_tuning_defaults(c, t, plans, n);
   if (t.chunk_rows % (kMbPerWarpTile * kMB) != 0 || t.chunk_rows > (1u << 24))
     return fail(DPF_EINVAL, "chunk_rows %u must be a multiple of %u and at most 2^24", t.chunk_rows, kMbPerWarpTile * kMB);
-  if (t.threads != 128 && t.threads != 256) return fail(DPF_EINVAL, "threads must be 128 or 256");
+  if (t.threads != 128 && t.threads != 256 && t.threads != 512 && t.threads != 1024)
+    return fail(DPF_EINVAL, "threads must be 128, 256, 512 or 1024");
   if (t.staging != DPF_STAGE_ON && t.staging != DPF_STAGE_OFF) return fail(DPF_EINVAL, "staging must be 0, 1 or 2");
   bool host = false;
   uint64_t tickets = 0;
@@ -947,26 +948,29 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
     off_out[i] = scratch; scratch += align16(uint64_t(std::max<uint32_t>(Q.domain, 1)) * sizeof(dpf_record));
   }
   qbegin[n] = tickets;
-  // Staging ring: integer first steps over device-resident pages; its slots
-  // are as wide as the widest mini block of those steps' columns.
+  // Staging ring: a launch stages all of its queries or none; a query can be
+  // staged when its first step is an integer step over device-resident
+  // pages.  The ring's slots are as wide as the widest mini block of those
+  // steps' columns.
   uint32_t stage_bw = 0;
   bool text = false;
   for (const DevQuery& q : p->hq) text = text || needs_string_matcher(q);
   if (t.staging == DPF_STAGE_ON && !host && !text) {
-    std::vector<int> staged;
-    for (int i = 0; i < n; ++i) {
-      const DevQuery& Q = p->hq[i];
-      if (Q.nsteps == 0) continue;
+    bool all = true;
+    for (const DevQuery& Q : p->hq) {
       const DevStep& S0 = Q.steps[0];
       const DevColumn& C0 = Q.cols[S0.col];
-      const bool int_step = S0.kind != ST_PREFIX && S0.kind != ST_CONTAINS &&
-                            (C0.codec == C_FOR || C0.codec == C_DICT || C0.codec == C_DELTA);
-      if (!int_step || C0.max_bw == 0 || C0.max_bw > 32) continue;
-      staged.push_back(i);
-      stage_bw = std::max(stage_bw, C0.max_bw);
+      const bool ok = Q.nsteps != 0 && S0.kind != ST_PREFIX && S0.kind != ST_CONTAINS &&
+                      (C0.codec == C_FOR || C0.codec == C_DICT || C0.codec == C_DELTA) && C0.max_bw <= 32;
+      all = all && ok;
+      if (ok) stage_bw = std::max(stage_bw, std::max<uint32_t>(C0.max_bw, 1u));
     }
-    for (int i : staged) p->hq[i].stage = stage_bw;
+    if (!all) stage_bw = 0;
+    for (DevQuery& Q : p->hq) Q.stage = stage_bw;
   }
+  if (t.threads > 256 && (host || text || stage_bw))
+    return fail(DPF_EINVAL, "CTAs of %u threads run device-resident batches without string-matcher steps, unstaged",
+                t.threads);
   dpf_status st;
   if ((st = dev_alloc(c, scratch, reinterpret_cast<void**>(&p->scratch)))) return st;
   if ((st = dev_alloc_t(c, uint64_t(n), &p->dq)) || (st = dev_alloc_t(c, uint64_t(n) + 1, &p->dqbegin)) ||
@@ -1583,7 +1587,7 @@ dpf_status dpf_autotune(dpf_ctx* c, const dpf_plan* plans, int32_t n, void* stre
   if (reps == 0) reps = 3;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   static const uint32_t kChunk[] = {1024, 2048, 4096, 16384, 65536, 262144};
-  static const uint32_t kThreads[] = {128, 256};
+  static const uint32_t kThreads[] = {128, 256, 512, 1024};
   static const int32_t kPlace[] = {DPF_HT_AUTO, DPF_HT_GLOBAL};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CUDA_TRY(cudaEventCreate(&e0));
@@ -1601,6 +1605,7 @@ dpf_status dpf_autotune(dpf_ctx* c, const dpf_plan* plans, int32_t n, void* stre
       for (int32_t pl : kPlace)
         for (uint32_t ct : kCtas)
           for (int32_t sg : kStage) {
+        if (th > 256 && (ct != 0 || sg == DPF_STAGE_ON)) continue;  // one build per wide CTA size, unstaged
         dpf_tuning t{};
         t.chunk_rows = cr;
         t.threads = th;

@@ -8,6 +8,8 @@ cudaError_t fused_lean_launch(const FusedLaunch& L, size_t smem, uint32_t tb, cu
 cudaError_t fused_text_launch(const FusedLaunch& L, size_t smem, uint32_t tb, cudaStream_t s);
 cudaError_t fused_host_launch(const FusedLaunch& L, size_t smem, uint32_t tb, cudaStream_t s);
 cudaError_t fused_stage_launch(const FusedLaunch& L, size_t smem, uint32_t tb, cudaStream_t s);
+cudaError_t fused_wide_launch(const FusedLaunch& L, size_t smem, uint32_t tb, cudaStream_t s);
+int fused_wide_occupancy(int threads, size_t smem);
 int fused_text_occupancy(int threads, size_t smem, int min_blocks);
 int fused_host_occupancy(int threads, size_t smem, int min_blocks);
 int fused_stage_occupancy(int threads, size_t smem, int min_blocks);
@@ -24,6 +26,7 @@ size_t fused_dynamic_smem(uint32_t acc_slots, size_t smem_tables, int threads, u
 int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, bool host_data, int min_blocks,
                         uint32_t stage_bw) {
   const size_t smem = fused_dynamic_smem(acc_slots, smem_tables, threads, stage_bw);
+  if (threads > 256) return fused_wide_occupancy(threads, smem);
   if (host_data) return fused_host_occupancy(threads, smem, min_blocks);
   return stage_bw ? fused_stage_occupancy(threads, smem, min_blocks) : fused_text_occupancy(threads, smem, min_blocks);
 }
@@ -34,6 +37,7 @@ int fused_blocks_per_sm(int threads, uint32_t acc_slots, size_t smem_tables, boo
 cudaError_t launch_fused(const FusedLaunch& L, cudaStream_t s) {
   const size_t smem = fused_dynamic_smem(L.acc_slots, L.smem_tables, L.threads, L.stage_bw);
   const uint32_t tb = uint32_t((L.smem_tables + 15) & ~size_t(15));
+  if (L.threads > 256) return fused_wide_launch(L, smem, tb, s);  // prepare admits lean batches only
   if (L.host_data) return fused_host_launch(L, smem, tb, s);
   if (L.text) return fused_text_launch(L, smem, tb, s);
   if (L.stage_bw) return fused_stage_launch(L, smem, tb, s);

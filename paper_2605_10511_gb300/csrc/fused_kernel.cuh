@@ -401,8 +401,13 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
     page_begin<kHost>(Q, p, lane, P);
     // staged first step (StageRing in tile.cuh): the headers of tiles 0 and 1
     // and the words of tile 0 are in flight before the first decode
+    // a staged launch stages every query (the host makes it so)
     const uint32_t bwcap = kStage && !kHost ? Q.stage : 0u;
-    if (bwcap) {
+    if (kStage && bwcap == 0) {
+      if (lane == 0) atomicOr(status, S_INTERNAL);
+      return;
+    }
+    if (kStage) {
       const FirstCol f = first_col(Q, P);
       stage_headers(ring, 0, f.pg, f.codec, mb0, tmin<uint32_t>(TB, mb1 - mb0), lane);
       cp_async_commit();
@@ -417,7 +422,7 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
       const uint32_t i0 = mb0 + j * TB;
       const uint32_t nmb = tmin<uint32_t>(TB, mb1 - i0);
       const uint32_t row_base = (i0 - seg_mb) * kMB;
-      if (bwcap) {
+      if constexpr (kStage) {
         cp_async_wait_all();  // this tile's words and the next tile's headers have landed
         __syncwarp();
         const FirstCol f = first_col(Q, P);
@@ -483,9 +488,11 @@ __device__ void load_smem_tables(const DevQuery& Q, uint8_t* stab) {
 // kText = false: the build without the general string matcher (CONTAINS,
 // FSST), launched for batches that have no such step.  kStage: the build
 // with the staging ring (device-resident batches without such steps,
-// launched when the tuning asks for staging).
-template <bool kHost, int kMinBlocks, bool kText, bool kStage = false>
-__global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* __restrict__ queries,
+// launched when the tuning asks for staging).  kThreads: the largest CTA
+// the build launches with (512- and 1,024-thread CTAs, 2 and 1 per SM, keep
+// the 64 registers of the 4 x 256-thread build).
+template <bool kHost, int kMinBlocks, bool kText, bool kStage = false, int kThreads = 256>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) fused_kernel(const DevQuery* __restrict__ queries,
                                                        const uint64_t* __restrict__ qbegin, int nq,
                                                        uint64_t total, Sched* sched, uint32_t acc_slots,
                                                      uint32_t tables_bytes, uint32_t stage_bw) {
@@ -564,21 +571,21 @@ __global__ void __launch_bounds__(256, kMinBlocks) fused_kernel(const DevQuery* 
 }
 
 
-template <bool kHost, int kMinBlocks, bool kText, bool kStage = false>
+template <bool kHost, int kMinBlocks, bool kText, bool kStage = false, int kThreads = 256>
 int occupancy_of(int threads, size_t smem) {
   int n = 0;
-  cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks, kText, kStage>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       int(smem));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fused_kernel<kHost, kMinBlocks, kText, kStage>, threads, smem);
+  auto* k = fused_kernel<kHost, kMinBlocks, kText, kStage, kThreads>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem);
   return n;
 }
 
-template <bool kHost, int kMinBlocks, bool kText, bool kStage = false>
+template <bool kHost, int kMinBlocks, bool kText, bool kStage = false, int kThreads = 256>
 cudaError_t launch_as(const FusedLaunch& L, size_t smem, uint32_t tb, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(fused_kernel<kHost, kMinBlocks, kText, kStage>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  auto* k = fused_kernel<kHost, kMinBlocks, kText, kStage, kThreads>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  fused_kernel<kHost, kMinBlocks, kText, kStage><<<L.grid, L.threads, smem, s>>>(
+  k<<<L.grid, L.threads, smem, s>>>(
       L.queries, L.qbegin, L.nq, L.total_chunks, L.sched, L.acc_slots, tb, L.stage_bw);
   return cudaGetLastError();
 }

@@ -629,6 +629,130 @@ __device__ __forceinline__ uint32_t pruned_mbs(const TileHdr& Hd, int c, int32_t
   return (__ballot_sync(kFull, out) >> (c * TB)) & ((1u << TB) - 1u);
 }
 
+// ---- staged dense step: one mini block at a time from the staging ring ----
+// With the words in shared memory, a lane extracts its four values directly
+// (value 32k + lane sits at bit (32k + lane) * bw of the mini block: two
+// shared loads and a funnel shift, no shuffles), and each mini block is
+// decoded, tested and folded into the live bits before the next, so only
+// four values per lane are live instead of sixteen.
+
+// Decodes mini block t of column c (header in Hd's lane c * TB + t) into
+// v[k] = value of row 32k + lane; false when the block has no live row (or
+// cannot be decoded: the status word says why).
+template <bool kDelta>
+__device__ __forceinline__ bool staged_mb_decode(const TileHdr& Hd, int c, int t, uint32_t alive, StagedPay sp,
+                                                 int lane, uint32_t (&v)[4], unsigned int* status) {
+  bool any = __any_sync(kFull, (alive >> (4 * t)) & 15u) != 0;
+  const uint32_t hx = __shfl_sync(kFull, Hd.x, c * TB + t);
+  const uint32_t hy = __shfl_sync(kFull, kDelta ? Hd.z : Hd.y, c * TB + t);
+  const uint32_t bw = hy & 0xffu;
+  if (any && (bw > 32 || bw > sp.bwcap)) {
+    if (lane == 0) atomicOr(status, bw > 32 ? S_CORRUPT : S_INTERNAL);
+    any = false;
+  }
+  if (!any) return false;
+  const uint32_t* src = sp.p + t * sp.pw;
+  const uint32_t bit = uint32_t(lane) * bw, w = bit >> 5, sh = bit & 31u;
+  const uint32_t mask = bw >= 32 ? 0xffffffffu : (1u << bw) - 1u;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t* q = src + uint32_t(k) * bw + w;  // the word after a block's last is inside the slot
+    v[k] = __funnelshift_r(q[0], q[1], sh) & mask;
+  }
+  if (kDelta) {
+    // x_j = first + sum_{i<=j} (dmin + p_i), modulo 2^32
+    const uint32_t dmin = __shfl_sync(kFull, Hd.y, c * TB + t);
+    uint32_t carry = hx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t sc = warp_incl_scan(v[k] + dmin, lane);
+      v[k] = carry + sc;
+      carry += __shfl_sync(kFull, sc, 31);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] += hx;
+  }
+  return true;
+}
+
+// The step's test on the four values of mini block t: bits k of the result
+// = row 32k + lane passes (and, with kGid, its group-id contribution added).
+// kOp 0..4 = probe modes, 5 = group key, 6 = RANGE, 7 = NOTRANGE, 8 = IN.
+template <int kOp, bool kGid>
+__device__ __forceinline__ uint32_t staged_mb_test(const DevStep& S, const uint8_t* stab, const uint32_t (&v)[4],
+                                                   uint32_t live, uint32_t (&gid)[4], unsigned int* status) {
+  uint32_t keep = 0;
+  if (kOp < PM_OPEN) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      keep |= uint32_t(probe_direct<kOp, kGid>(S, stab, v[k], true, gid[k])) << k;
+  } else if (kOp == PM_OPEN) {
+    const bool in_smem = S.smem_width != 0;
+    const uint2* tab = in_smem ? reinterpret_cast<const uint2*>(stab + S.smem_off) : static_cast<const uint2*>(S.ht);
+    const uint32_t mask = S.ht_mask;
+    uint32_t h[4], pend = 0, pay[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      h[k] = fmix32(v[k]) & mask;
+      pay[k] = 0;
+      if (((live >> k) & 1u) && int32_t(v[k]) != kEmptyKey) pend |= 1u << k;
+    }
+    for (uint32_t n = 0; pend && n <= mask; ++n) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!((pend >> k) & 1u)) continue;
+        const uint2 e = in_smem ? tab[h[k]] : __ldg(tab + h[k]);
+        if (e.x == v[k]) {
+          keep |= 1u << k;
+          pay[k] = e.y;
+          pend &= ~(1u << k);
+        } else if (int32_t(e.x) == kEmptyKey) {
+          pend &= ~(1u << k);
+        } else {
+          h[k] = (h[k] + 1) & mask;
+        }
+      }
+    }
+    if (pend) atomicOr(status, S_INTERNAL);
+    if (kGid) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) gid[k] += (pay[k] & 0xffffu) * S.mul0 + (pay[k] >> 16) * S.mul1;
+    }
+  } else if (kOp == 5) {
+    if (kGid) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) gid[k] += v[k] * S.key_mul;
+    }
+    keep = 15u;
+  } else if (kOp == 6 || kOp == 7) {
+    const uint32_t lo = uint32_t(S.lo), span = uint32_t(S.hi) - uint32_t(S.lo);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) keep |= uint32_t(((v[k] - lo) <= span) != (kOp == 7)) << k;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      bool hit = false;
+      for (int i = 0; i < S.nin; ++i) hit |= (int32_t(v[k]) == S.in[i]);
+      keep |= uint32_t(hit && S.kind == ST_IN) << k;
+    }
+  }
+  return keep;
+}
+
+template <bool kDelta, bool kGid, int kOp>
+__device__ __forceinline__ void staged_dense(const DevStep& S, const TileHdr& Hd, TileState& T, const uint8_t* stab,
+                                             StagedPay sp, int lane, unsigned int* status) {
+#pragma unroll
+  for (int t = 0; t < TB; ++t) {
+    uint32_t v[4];
+    if (!staged_mb_decode<kDelta>(Hd, S.col, t, T.alive, sp, lane, v, status)) continue;
+    const uint32_t live = (T.alive >> (4 * t)) & 15u;
+    const uint32_t keep = staged_mb_test<kOp, kGid>(S, stab, v, live, T.gid[t], status);
+    T.alive &= ~((~keep & 15u) << (4 * t));
+  }
+}
+
 template <bool kHost, bool kDelta, bool kGid = true, bool kStaged = false>
 __device__ __forceinline__ void dense_step_t(const DevQuery& Q, const DevStep& S, const PageState& P,
                                              const TileHdr& Hd, TileState& T, const uint8_t* stab, int lane,
@@ -638,6 +762,29 @@ __device__ __forceinline__ void dense_step_t(const DevQuery& Q, const DevStep& S
 #pragma unroll
   for (int t = 0; t < TB; ++t)
     if ((pruned >> t) & 1u) T.alive &= ~(15u << (4 * t));
+  if constexpr (kStaged) {
+    switch (S.kind) {
+      case ST_PROBE:
+        switch (probe_mode(S)) {
+          case PM_S1: staged_dense<kDelta, kGid, PM_S1>(S, Hd, T, stab, sp, lane, status); break;
+          case PM_S2: staged_dense<kDelta, kGid, PM_S2>(S, Hd, T, stab, sp, lane, status); break;
+          case PM_S4: staged_dense<kDelta, kGid, PM_S4>(S, Hd, T, stab, sp, lane, status); break;
+          case PM_GDIRECT:
+            if (kGid && (S.mul0 | S.mul1)) staged_dense<kDelta, kGid, PM_GDIRECT>(S, Hd, T, stab, sp, lane, status);
+            else staged_dense<kDelta, false, PM_GDIRECT>(S, Hd, T, stab, sp, lane, status);
+            break;
+          default: staged_dense<kDelta, kGid, PM_OPEN>(S, Hd, T, stab, sp, lane, status); break;
+        }
+        return;
+      case ST_KEY:
+        if (kGid) staged_dense<kDelta, kGid, 5>(S, Hd, T, stab, sp, lane, status);
+        else if (lane == 0) atomicOr(status, S_INTERNAL);  // the kernel routes group-key first steps to kGid
+        return;
+      case ST_RANGE: staged_dense<kDelta, kGid, 6>(S, Hd, T, stab, sp, lane, status); return;
+      case ST_NOTRANGE: staged_dense<kDelta, kGid, 7>(S, Hd, T, stab, sp, lane, status); return;
+      default: staged_dense<kDelta, kGid, 8>(S, Hd, T, stab, sp, lane, status); return;
+    }
+  }
   uint32_t v[TB][4];
   uint32_t anym;
   decode_t<kHost, kDelta, kStaged>(Q, S.col, P, Hd, T.alive, lane, v, anym, status, sp);
