@@ -69,8 +69,9 @@ struct HashTable {
   int32_t id = 0, table = 0, npay = 0;
   int kind = HT_OPEN;
   uint2* slots = nullptr;         // HT_OPEN
-  uint32_t capacity = 0;          // HT_OPEN slots, HT_DIRECT entries
+  uint32_t capacity = 0;          // HT_OPEN slots, HT_DIRECT entries, HT_RANK keys covered
   uint32_t* direct = nullptr;     // HT_DIRECT
+  uint8_t* rank = nullptr;        // HT_RANK: directory words, then payloads
   int32_t kmin = 0;
   uint64_t entries = 0;
   uint64_t dim_rows = 0;          // rows of the dimension the table was built from
@@ -626,8 +627,8 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
     S.col = uint8_t(idx);
     const HashTable& H = ht->second;
     S.ht_kind = uint8_t(H.kind);
-    if (H.kind == HT_DIRECT) {
-      S.ht = H.direct;
+    if (H.kind == HT_DIRECT || H.kind == HT_RANK) {
+      S.ht = H.kind == HT_DIRECT ? static_cast<const void*>(H.direct) : static_cast<const void*>(H.rank);
       S.kmin = H.kmin;
       S.krange = H.capacity;
     } else {
@@ -800,6 +801,7 @@ size_t place_tables(DevQuery& Q, size_t budget, bool first_only) {
     if (S.kind != ST_PROBE) continue;
     S.smem_width = 0;
     if (first_only && s != 0) continue;
+    if (S.ht_kind == HT_RANK) continue;  // probed in device memory (L2) only
     const uint32_t w = S.ht_kind == HT_DIRECT ? width : 8u;
     const size_t bytes = S.ht_kind == HT_DIRECT ? size_t(S.krange) * w : size_t(S.ht_mask + 1) * 8;
     const size_t at = (used + 15) & ~size_t(15);
@@ -1185,6 +1187,7 @@ dpf_status dpf_destroy(dpf_ctx* c) {
     for (auto& kv : c->hts) {
       dev_free(c, kv.second.slots);
       dev_free(c, kv.second.direct);
+      dev_free(c, kv.second.rank);
     }
     for (auto& kv : c->cols) free_column(c, kv.second);
     dev_free(c, c->bsched);
@@ -1407,8 +1410,8 @@ static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, 
     S.kind = ST_PROBE;
     S.col = uint8_t(idx);
     S.ht_kind = uint8_t(H.kind);
-    if (H.kind == HT_DIRECT) {
-      S.ht = H.direct;
+    if (H.kind == HT_DIRECT || H.kind == HT_RANK) {
+      S.ht = H.kind == HT_DIRECT ? static_cast<const void*>(H.direct) : static_cast<const void*>(H.rank);
       S.kmin = H.kmin;
       S.krange = H.capacity;
     } else {
@@ -1478,7 +1481,22 @@ static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, 
     ht.key_hi = minmax[1];
   }
   const bool wide_payload = B.n_payload == 2 && ht.pay_dom[0] == 65536 && ht.pay_dom[1] == 65536;
-  if (!wide_payload && range <= std::max<uint64_t>(64 * kept, 1u << 20) && range <= (1u << 26)) {
+  if (!wide_payload && kept && range > kDirectMaxRange && range <= kRankMaxRange) {
+    // a large key range: a rank directory (2 bits per key of the range) plus
+    // the kept rows' payloads, instead of one word per key of the range
+    const uint64_t nwords = (range + 63) / 64, nblocks = (nwords + 1023) / 1024;
+    ht.kind = HT_RANK;
+    ht.kmin = minmax[0];
+    ht.capacity = uint32_t(range);
+    const uint64_t bytes = 16 * nwords + 4 * kept;
+    if ((st = dev_alloc(c, bytes + 4 * nblocks, reinterpret_cast<void**>(&ht.rank)))) return cleanup(st);
+    L.rank_dir = reinterpret_cast<uint4*>(ht.rank);
+    L.rank_pay = reinterpret_cast<uint32_t*>(ht.rank + 16 * nwords);
+    L.rank_sums = reinterpret_cast<uint32_t*>(ht.rank + bytes);
+    L.kmin = ht.kmin;
+    L.krange = ht.capacity;
+    e = cudaMemsetAsync(ht.rank, 0, 16 * nwords, s);
+  } else if (!wide_payload && range <= std::max<uint64_t>(64 * kept, 1u << 20) && range <= kDirectMaxRange) {
     ht.kind = HT_DIRECT;
     ht.kmin = kept ? minmax[0] : 0;
     ht.capacity = uint32_t(range);
@@ -1505,6 +1523,7 @@ static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, 
   if (e != cudaSuccess || status) {
     dev_free(c, ht.slots);
     dev_free(c, ht.direct);
+    dev_free(c, ht.rank);
     if (e != cudaSuccess) return cleanup(fail(DPF_ECUDA, "hash build (insert): %s", cudaGetErrorString(e)));
     if (status & S_DUPKEY) return cleanup(fail(DPF_EDUPKEY, "duplicate key in hash build of column %d", key_col));
     if (status & S_CORRUPT) return cleanup(fail(DPF_EINVAL, "key column %d holds the reserved key INT32_MIN or corrupt data", key_col));
@@ -1558,6 +1577,7 @@ dpf_status dpf_drop_hash(dpf_ctx* c, dpf_ht_id id) {
   cudaDeviceSynchronize();
   dev_free(c, it->second.slots);
   dev_free(c, it->second.direct);
+  dev_free(c, it->second.rank);
   c->hts.erase(it);
   return DPF_OK;
 }

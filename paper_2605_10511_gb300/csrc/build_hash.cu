@@ -34,9 +34,11 @@ __device__ __forceinline__ uint32_t build_payload(const DevQuery& Q, int f, cons
   if (!valid) return 0u;
   uint32_t pay = 0;
   bool hit;
-  if (S.ht_kind == HT_DIRECT) {
+  if (S.ht_kind == HT_DIRECT || S.ht_kind == HT_RANK) {
     const uint32_t off = key - uint32_t(S.kmin);
-    pay = off < S.krange ? __ldg(static_cast<const uint32_t*>(S.ht) + off) : kAbsent;
+    pay = off >= S.krange ? kAbsent
+          : S.ht_kind == HT_RANK ? rank_entry(S.ht, S.krange, off)
+                                 : __ldg(static_cast<const uint32_t*>(S.ht) + off);
     hit = pay != kAbsent;
   } else {
     hit = int32_t(key) != kEmptyKey && ht_probe(static_cast<const uint2*>(S.ht), S.ht_mask, int32_t(key), &pay, status);
@@ -51,7 +53,9 @@ __device__ __forceinline__ uint32_t build_payload(const DevQuery& Q, int f, cons
 constexpr unsigned long long kEmptySlot = 0x0000000080000000ull;  // {INT32_MIN, 0}
 
 // kMode 0: count kept rows and their key range; 1: insert into an
-// open-addressing table; 2: insert into a direct table.
+// open-addressing table; 2: insert into a direct table; 3: set the rows'
+// presence bits of a rank directory (a bit already set is a duplicate key);
+// 4: store the payloads of a rank table at their ranks (after rank_scan).
 template <bool kHost, int kMode>
 __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__ qdev, BuildLaunch L,
                                                     unsigned int* status) {
@@ -103,13 +107,25 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
         continue;
       }
       const uint32_t pay = (c0 & 0xffffu) | ((c1 & 0xffffu) << 16);
-      if (kMode == 2) {
+      if (kMode == 2 || kMode == 3 || kMode == 4) {
         const uint32_t off = uint32_t(kv) - uint32_t(L.kmin);
         if (off >= L.krange) {
           atomicOr(status, S_INTERNAL);
           continue;
         }
-        if (atomicCAS(L.direct + off, kAbsent, pay) != kAbsent) atomicOr(status, S_DUPKEY);
+        if (kMode == 2) {
+          if (atomicCAS(L.direct + off, kAbsent, pay) != kAbsent) atomicOr(status, S_DUPKEY);
+        } else if (kMode == 3) {
+          unsigned int* word = reinterpret_cast<unsigned int*>(L.rank_dir + (off >> 6)) + ((off >> 5) & 1u);
+          const unsigned int bit = 1u << (off & 31u);
+          if (atomicOr(word, bit) & bit) atomicOr(status, S_DUPKEY);
+        } else {
+          const uint4 d = L.rank_dir[off >> 6];
+          const uint32_t b = off & 63u, bb = b & 31u;
+          const uint32_t below = (b < 32 ? 0u : uint32_t(__popc(d.x))) +
+                                 uint32_t(__popc((b < 32 ? d.x : d.y) & ((1u << bb) - 1u)));
+          L.rank_pay[d.z + below] = pay;
+        }
         continue;
       }
       const unsigned long long slot = (unsigned long long)uint32_t(kv) | ((unsigned long long)pay << 32);
@@ -146,6 +162,72 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
   }
 }
 
+// Ranks of a rank directory: word w's count = the present keys in words < w.
+// Pass 1: per block of 1,024 words, their total; pass 2 (one block): the
+// exclusive prefix of the block totals; pass 3: each block's words.
+constexpr uint32_t kRankBlockWords = 1024;
+__device__ __forceinline__ uint32_t word_bits(const uint4& d) { return uint32_t(__popc(d.x) + __popc(d.y)); }
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t* total) {
+  __shared__ uint32_t warp_tot[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t incl = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += y;
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+  for (int w = 0; w < nw; ++w) {
+    if (w < warp) before += warp_tot[w];
+    all += warp_tot[w];
+  }
+  __syncthreads();
+  *total = all;
+  return before + incl - x;
+}
+
+__global__ void rank_block_sums(const uint4* dir, uint32_t nwords, uint32_t* sums) {
+  uint32_t x = 0;
+  for (uint32_t k = 0; k < kRankBlockWords / 256; ++k) {
+    const uint32_t w = blockIdx.x * kRankBlockWords + k * 256 + threadIdx.x;
+    if (w < nwords) x += word_bits(dir[w]);
+  }
+  uint32_t total;
+  block_excl_scan(x, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void rank_scan_sums(uint32_t* sums, uint32_t n) {
+  uint32_t carry = 0;
+  for (uint32_t i0 = 0; i0 < n; i0 += blockDim.x) {
+    const uint32_t i = i0 + threadIdx.x;
+    const uint32_t x = i < n ? sums[i] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_excl_scan(x, &total);
+    if (i < n) sums[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void rank_fill(uint4* dir, uint32_t nwords, const uint32_t* sums) {
+  uint32_t carry = sums[blockIdx.x];
+  for (uint32_t k = 0; k < kRankBlockWords / 256; ++k) {
+    const uint32_t w = blockIdx.x * kRankBlockWords + k * 256 + threadIdx.x;
+    uint4 d = w < nwords ? dir[w] : make_uint4(0, 0, 0, 0);
+    uint32_t total;
+    const uint32_t ex = block_excl_scan(w < nwords ? word_bits(d) : 0u, &total);
+    if (w < nwords) {
+      d.z = carry + ex;
+      d.w = 0;
+      dir[w] = d;
+    }
+    carry += total;
+  }
+}
+
 __global__ void init_table_kernel(uint2* table, uint32_t slots) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += gridDim.x * blockDim.x)
     reinterpret_cast<unsigned long long*>(table)[i] = kEmptySlot;
@@ -171,6 +253,17 @@ cudaError_t launch_build_mode(const BuildLaunch& L, cudaStream_t s) {
 cudaError_t launch_build_count(const BuildLaunch& L, cudaStream_t s) { return launch_build_mode<0>(L, s); }
 
 cudaError_t launch_build_insert(const BuildLaunch& L, cudaStream_t s) {
+  if (L.rank_dir) {  // presence bits, ranks, then payloads at their ranks
+    const uint32_t nwords = uint32_t((uint64_t(L.krange) + 63) >> 6);
+    const uint32_t nblocks = (nwords + kRankBlockWords - 1) / kRankBlockWords;
+    cudaError_t e = launch_build_mode<3>(L, s);
+    if (e != cudaSuccess) return e;
+    rank_block_sums<<<nblocks, 256, 0, s>>>(L.rank_dir, nwords, L.rank_sums);
+    rank_scan_sums<<<1, 1024, 0, s>>>(L.rank_sums, nblocks);
+    rank_fill<<<nblocks, 256, 0, s>>>(L.rank_dir, nwords, L.rank_sums);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_build_mode<4>(L, s);
+  }
   return L.direct ? launch_build_mode<2>(L, s) : launch_build_mode<1>(L, s);
 }
 

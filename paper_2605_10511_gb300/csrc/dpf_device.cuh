@@ -140,6 +140,20 @@ __device__ __forceinline__ bool step_pred(const DevStep& S, int32_t x) {
   }
 }
 
+// Payload of key kmin + off (off < krange) in a rank-directory table, or
+// kAbsent: the key's presence bit in its directory word, then the payload
+// at the word's count of earlier keys plus the set bits below the key's.
+__device__ __forceinline__ uint32_t rank_entry(const void* tab, uint32_t krange, uint32_t off) {
+  const uint4* dir = static_cast<const uint4*>(tab);
+  const uint4 d = __ldg(dir + (off >> 6));
+  const uint32_t b = off & 63u, bb = b & 31u;
+  const uint32_t w = b < 32 ? d.x : d.y;
+  if (!((w >> bb) & 1u)) return kAbsent;
+  const uint32_t below = (b < 32 ? 0u : uint32_t(__popc(d.x))) + uint32_t(__popc(w & ((1u << bb) - 1u)));
+  const uint32_t* pay = reinterpret_cast<const uint32_t*>(dir + ((uint64_t(krange) + 63) >> 6));
+  return __ldg(pay + d.z + below);
+}
+
 // Bounded linear probe of an open-addressing table of capacity mask+1.
 // Returns true and the payload on a hit; a probe that meets neither the key
 // nor an empty slot within capacity steps sets S_INTERNAL.

@@ -79,9 +79,13 @@ enum StepKind : uint8_t {
 
 // Join tables (Sec. 3.1 hash tables; representation chosen at build):
 //  HT_OPEN   open addressing, slots {key, payload}, linear probing;
-//  HT_DIRECT dense key range: entry[key - kmin] = payload or kAbsent.
+//  HT_DIRECT dense key range: entry[key - kmin] = payload or kAbsent;
+//  HT_RANK   large, sparsely filled key range: a rank directory of 16-byte
+//            words {presence bits of 64 consecutive keys (two u32), number
+//            of present keys before the word, 0}, followed by the payloads
+//            of the present keys in key order (rank_entry).
 // payload = code0 | code1 << 16 (dictionary codes of the payload columns).
-enum HtKind : uint8_t { HT_OPEN = 0, HT_DIRECT = 1 };
+enum HtKind : uint8_t { HT_OPEN = 0, HT_DIRECT = 1, HT_RANK = 2 };
 constexpr uint32_t kAbsent = 0xffffffffu;
 
 struct DevStep {
@@ -90,10 +94,10 @@ struct DevStep {
   int32_t in[kMaxIn];     // IN operands; ST_CONTAINS: in[0..1] = a pattern of <= 8 bytes
                           // packed for the sliding-window compare
   // ST_PROBE
-  const void* ht;         // OPEN: uint2 slots; DIRECT: uint32 entries (global)
+  const void* ht;         // OPEN: uint2 slots; DIRECT: uint32 entries; RANK: directory + payloads (global)
   uint32_t ht_mask;       // OPEN: capacity - 1 (power of two)
-  int32_t kmin;           // DIRECT: smallest key
-  uint32_t krange;        // DIRECT: number of entries
+  int32_t kmin;           // DIRECT / RANK: smallest key
+  uint32_t krange;        // DIRECT / RANK: keys covered (kmin + [0, krange))
   uint8_t ht_kind;
   uint8_t smem_width;     // 0: probe global memory; OPEN: 8 (slots copied);
                           // DIRECT: 1/2/4-byte entries holding this join's

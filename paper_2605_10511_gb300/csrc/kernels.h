@@ -26,6 +26,12 @@ constexpr int32_t kDefaultStaging = 2;
 // few distinct values to sort out; with many groups (1,024 Zipf keys) plain
 // shared-memory atomics measured 1.8x faster.
 constexpr uint32_t kWarpAggMaxDomain = 32;
+// Join-table representation by the key range of the kept rows (R8): a
+// direct table of one word per key up to 2^22 keys (16 MB), a rank
+// directory (2 bits per key plus the kept payloads) up to 2^28 keys, open
+// addressing beyond.
+constexpr uint64_t kDirectMaxRange = uint64_t(1) << 22;
+constexpr uint64_t kRankMaxRange = uint64_t(1) << 28;
 // Shared-memory bytes of the code-level matcher tables of a PREFIX / CONTAINS
 // step with a pattern of plen bytes on an FSST column: for every matcher
 // state 0..plen, the next state after one symbol code (256 entries) and
@@ -65,6 +71,9 @@ struct BuildLaunch {
   uint32_t* direct;           // direct table: krange entries (or nullptr)
   int32_t kmin;
   uint32_t krange;
+  uint4* rank_dir;            // rank table: (krange + 63) / 64 directory words (or nullptr)
+  uint32_t* rank_pay;         //   payloads of the present keys, in key order
+  uint32_t* rank_sums;        //   scratch: one count per 1,024 directory words
   unsigned long long* count;  // device counter (count pass)
   int32_t* kminmax;           // device {min, max} of kept keys (count pass)
   Sched* sched;               // status word

@@ -502,8 +502,8 @@ __device__ __forceinline__ void tile_prefix(const DevQuery& Q, const DevStep& S,
 }
 
 // Probe modes: direct table copied into shared memory as 1/2/4-byte group-id
-// contributions, direct table in global memory, open addressing (shared or
-// global slots).
+// contributions, direct or rank-directory table in global memory, open
+// addressing (shared or global slots).
 enum ProbeMode : int { PM_S1 = 0, PM_S2 = 1, PM_S4 = 2, PM_GDIRECT = 3, PM_OPEN = 4 };
 __device__ __forceinline__ int probe_mode(const DevStep& S) {
   if (S.ht_kind == HT_OPEN) return PM_OPEN;
@@ -528,8 +528,9 @@ __device__ __forceinline__ bool probe_direct(const DevStep& S, const uint8_t* st
   } else if (kMode == PM_S4) {
     e = look ? reinterpret_cast<const uint32_t*>(stab + S.smem_off)[off] : kAbsent;
     hit = e != kAbsent;
-  } else {
-    e = look ? __ldg(static_cast<const uint32_t*>(S.ht) + off) : kAbsent;
+  } else {  // a table in device memory: direct, or a rank directory
+    if (S.ht_kind == HT_RANK) e = look ? rank_entry(S.ht, S.krange, off) : kAbsent;
+    else e = look ? __ldg(static_cast<const uint32_t*>(S.ht) + off) : kAbsent;
     hit = e != kAbsent;
     e = kContrib ? (e & 0xffffu) * S.mul0 + (e >> 16) * S.mul1 : 0u;
   }

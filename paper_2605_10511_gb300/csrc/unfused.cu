@@ -149,10 +149,10 @@ __global__ void probe_kernel(const uint32_t* rid_in, const uint32_t* gid_in, con
       r = rid_in[i];
       g = gid_in[i];
       const int32_t key = fk[r];
-      if (S.ht_kind == HT_DIRECT) {
+      if (S.ht_kind == HT_DIRECT || S.ht_kind == HT_RANK) {
         const uint32_t off = uint32_t(key) - uint32_t(S.kmin);
         if (off < S.krange) {
-          pay = __ldg(static_cast<const uint32_t*>(S.ht) + off);
+          pay = S.ht_kind == HT_RANK ? rank_entry(S.ht, S.krange, off) : __ldg(static_cast<const uint32_t*>(S.ht) + off);
           hit = pay != kAbsent;
         }
       } else if (key != kEmptyKey) {

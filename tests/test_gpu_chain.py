@@ -185,3 +185,32 @@ def test_probe_build_matches_a_plain_build_when_nothing_is_dropped(eng):
             eng.ctx.release(prep)
     assert_same(recs[0], recs[1])
     assert recs[0]["count"].sum() == w["tables"]["lineitem"]["rows"]
+
+
+@pytest.mark.parametrize("rows", [1 << 24, 1 << 26])
+def test_chain_with_rank_directory_table(rows):
+    """LINEITEM -> ORDERS -> CUSTOMER with ORDERS' kept keys spread over more
+    than 2^22 keys: ORDERS' table is a rank directory (presence bits of 64
+    keys and a count per 16-byte word, then the kept payloads) instead of one
+    word per key of the range.  Its device bytes must be those of the rank
+    layout, far below a direct table's 4 bytes per key; the records must
+    equal the oracle's; a scan + probe + build probing the rank table (a
+    longer chain) is checked the same way in the unfused chain."""
+    w = synth.chain_join(rows=rows)
+    eng = dpf.Engine(device=0)
+    try:
+        eng.load_workload(w)
+        before = eng.ctx.memory_used()
+        j = w["query"]["joins"][0]
+        eng.build_joins(w)
+        hts = [eng.hts[(w["name"], repr(j))]]
+        info = eng.ctx.hash_info(hts[0])
+        assert info["capacity"] > 1 << 22, info  # the kept keys' range
+        rank_bytes = 16 * ((info["capacity"] + 63) // 64) + 4 * info["entries"]
+        grown = eng.ctx.memory_used() - before
+        assert grown < 2 * rank_bytes + (64 << 20) and grown < 4 * info["capacity"], (grown, info)
+        want = oracle.run_query(w, from_encoded=False, threads=0)
+        assert_same(eng.run(w), want, "fused")
+        assert_same(eng.run_unfused(w), want, "unfused")
+    finally:
+        eng.close()
