@@ -31,7 +31,7 @@ _lib = None
 CODECS = {"for": 1, "delta": 2, "dict": 3, "str": 4, "fsst": 5, "for64": 6}
 STRING_CODECS = ("str", "fsst")
 PRED_OPS = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7,
-            "prefix": 8, "contains": 9}
+            "prefix": 8, "contains": 9, "like": 10}
 AGG_OPS = {"count": 0, "sum": 1, "sum_mul": 2, "sum_sub": 3}
 
 RECORD_DTYPE = np.dtype([("key", np.int32, (2,)), ("count", np.int64), ("val", np.int64, (4,))])
@@ -339,7 +339,7 @@ def _make_pred(pred, names):
     p = _Pred()
     p.col = names.index(pred["col"])
     p.op = PRED_OPS[pred["op"]]
-    if pred["op"] in ("prefix", "contains"):
+    if pred["op"] in ("prefix", "contains", "like"):
         pfx = bytes(pred["args"][0])
         buf = C.create_string_buffer(pfx, max(len(pfx), 1))
         p.pfx = C.cast(buf, C.c_void_p)

@@ -778,7 +778,7 @@ int64_t orc_decode_fsst(const uint8_t* blob, const uint64_t* page_off, uint64_t 
 // Query evaluation over decoded columns.
 // ---------------------------------------------------------------------------
 
-enum PredOp : int32_t { LT = 0, LE, GT, GE, EQ, NE, BETWEEN, IN, PREFIX, CONTAINS };
+enum PredOp : int32_t { LT = 0, LE, GT, GE, EQ, NE, BETWEEN, IN, PREFIX, CONTAINS, LIKE };
 enum AggOp : int32_t { COUNT = 0, SUM, SUM_MUL, SUM_SUB };
 
 struct OrcColumn {          // one decoded column
@@ -840,8 +840,29 @@ struct OrcRecord {
   int64_t val[4];
 };
 
+// SQL LIKE over bytes, the whole string against the whole pattern: '%'
+// stands for any run of bytes (possibly empty), '_' for any one byte, every
+// other byte for itself (no escape character).  The textbook dynamic
+// program: m[i][j] = the first i string bytes match the first j pattern
+// bytes.
+static bool like_match(const uint8_t* s, uint64_t n, const uint8_t* p, uint64_t k) {
+  std::vector<std::vector<char>> m(n + 1, std::vector<char>(k + 1, 0));
+  m[0][0] = 1;
+  for (uint64_t j = 1; j <= k; ++j) m[0][j] = p[j - 1] == '%' && m[0][j - 1];
+  for (uint64_t i = 1; i <= n; ++i)
+    for (uint64_t j = 1; j <= k; ++j) {
+      if (p[j - 1] == '%') m[i][j] = m[i][j - 1] || m[i - 1][j];             // empty run, or one more byte
+      else m[i][j] = m[i - 1][j - 1] && (p[j - 1] == '_' || p[j - 1] == s[i - 1]);
+    }
+  return m[n][k] != 0;
+}
+
 static bool eval_pred(const OrcTable& t, const OrcPred& p, uint64_t r) {
   const OrcColumn& c = t.cols[p.col];
+  if (p.op == LIKE) {
+    const uint64_t len = c.offsets[r + 1] - c.offsets[r];
+    return like_match(c.bytes + c.offsets[r], len, p.pfx, uint64_t(p.pfx_len));
+  }
   if (p.op == PREFIX) {
     const uint64_t len = c.offsets[r + 1] - c.offsets[r];
     if (len < uint64_t(p.pfx_len)) return false;

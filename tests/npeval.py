@@ -26,6 +26,16 @@ def _pred_mask(cols, pred, n):
             idx = np.where(ok, offs[:-1] + i, 0)
             ok &= (data[idx] == pfx[i]) if data.size else np.zeros(n, bool)
         return ok
+    if op == "like":
+        # SQL LIKE as a regular expression ('%' -> any run, '_' -> any byte)
+        # matched over the whole string by Python's own regex engine
+        import re
+        pat = bytes(args[0])
+        rx = re.compile(b"".join(b".*" if ch == 0x25 else b"." if ch == 0x5F else re.escape(bytes([ch]))
+                                 for ch in pat), re.DOTALL)
+        data, offs = c["bytes"], c["offsets"].astype(np.int64)
+        raw = np.asarray(data, np.uint8).tobytes()
+        return np.array([rx.fullmatch(raw[offs[r]:offs[r + 1]]) is not None for r in range(n)], bool)
     if op == "contains":
         # vectorised over candidate start positions: row r matches if the
         # pattern equals bytes [offs[r] + i, offs[r] + i + m) for some i
