@@ -172,9 +172,14 @@ enum dpf_op {
   DPF_OP_PREFIX = 8,  /* STR/FSST: string starts with prefix[0..prefix_len); a
                          prefix longer than the string does not match; an empty
                          prefix matches every row (Sec. 4.1 variable-length scan) */
-  DPF_OP_CONTAINS = 9 /* STR/FSST: prefix[0..prefix_len) occurs anywhere in the
+  DPF_OP_CONTAINS = 9,/* STR/FSST: prefix[0..prefix_len) occurs anywhere in the
                          string (LIKE '%pattern%'; Sec. 4.1 names KMP matching);
                          an empty pattern matches every row                       */
+  DPF_OP_LIKE = 10    /* SQL LIKE: the whole string against prefix[0..prefix_len)
+                         where '%' stands for any run of bytes and '_' for any
+                         one byte (no escape character).  'p%' and '%p%' with a
+                         wildcard-free p run as PREFIX / CONTAINS (STR or FSST);
+                         other patterns need a STR column                        */
 };
 #define DPF_MAX_IN 8
 #define DPF_MAX_PREFIX 32

@@ -26,7 +26,7 @@ CODEC = {"for": 1, "delta": 2, "dict": 3, "str": 4, "fsst": 5, "for64": 6}
 STRING_CODECS = ("str", "fsst")
 PLACE = {"device": 0, "host": 1}
 OP = {"lt": 0, "le": 1, "gt": 2, "ge": 3, "eq": 4, "ne": 5, "between": 6, "in": 7, "prefix": 8,
-      "contains": 9}
+      "contains": 9, "like": 10}
 AGG = {"count": 0, "sum": 1, "sum_mul": 2, "sum_sub": 3}
 HT_PLACE = {"auto": 0, "smem": 1, "global": 2}
 MAX_IN = 8
@@ -220,7 +220,7 @@ def make_pred(col_id, op, args):
     p = Pred()
     p.col = col_id
     p.op = OP[op]
-    if op in ("prefix", "contains"):
+    if op in ("prefix", "contains", "like"):
         pfx = bytes(args[0])
         if len(pfx) > MAX_PREFIX:
             raise ValueError(f"pattern longer than {MAX_PREFIX} bytes")

@@ -373,13 +373,35 @@ dpf_status compile_pred_body(const Column& c, const dpf_pred& p, DevStep& S, int
   std::memset(&S, 0, sizeof S);
   S.col = uint8_t(col_index);
   if (c.codec == C_FOR64) return fail(DPF_EINVAL, "predicates take 32-bit or string columns; column %d is FOR64", c.id);
-  if (p.op == DPF_OP_PREFIX || p.op == DPF_OP_CONTAINS) {
+  if (p.op == DPF_OP_PREFIX || p.op == DPF_OP_CONTAINS || p.op == DPF_OP_LIKE) {
     if (!is_str_codec(uint32_t(c.codec)))
-      return fail(DPF_EINVAL, "PREFIX / CONTAINS need a STR or FSST column (column %d)", c.id);
+      return fail(DPF_EINVAL, "PREFIX / CONTAINS / LIKE need a STR or FSST column (column %d)", c.id);
     if (p.prefix_len < 0 || p.prefix_len > DPF_MAX_PREFIX) return fail(DPF_EINVAL, "prefix_len %d out of range", p.prefix_len);
-    S.kind = p.op == DPF_OP_PREFIX ? ST_PREFIX : ST_CONTAINS;
-    S.plen = uint8_t(p.prefix_len);
-    std::memcpy(S.pfx, p.prefix, size_t(p.prefix_len));
+    int32_t op = p.op;
+    const uint8_t* pat = p.prefix;
+    int32_t plen = p.prefix_len;
+    if (op == DPF_OP_LIKE) {
+      // 'p%' is PREFIX p and '%p%' is CONTAINS p when p has no wildcard
+      bool inner_wild = false;
+      const bool lead = plen > 0 && pat[0] == '%', trail = plen > (lead ? 1 : 0) && pat[plen - 1] == '%';
+      for (int32_t i = lead ? 1 : 0; i < plen - (trail ? 1 : 0); ++i) inner_wild |= pat[i] == '%' || pat[i] == '_';
+      bool all_pct = plen > 0;
+      for (int32_t i = 0; i < plen; ++i) all_pct = all_pct && pat[i] == '%';
+      if (all_pct) {  // only '%': every string matches
+        op = DPF_OP_CONTAINS;
+        plen = 0;
+      } else if (!inner_wild && trail) {
+        op = lead ? DPF_OP_CONTAINS : DPF_OP_PREFIX;
+        pat += lead ? 1 : 0;
+        plen -= (lead ? 1 : 0) + 1;
+      } else if (c.codec != C_STR) {
+        return fail(DPF_EINVAL, "LIKE patterns other than 'p%%' and '%%p%%' need a STR column (column %d is FSST)",
+                    c.id);
+      }
+    }
+    S.kind = op == DPF_OP_PREFIX ? ST_PREFIX : op == DPF_OP_CONTAINS ? ST_CONTAINS : ST_LIKE;
+    S.plen = uint8_t(plen);
+    std::memcpy(S.pfx, pat, size_t(plen));
     if (S.kind == ST_CONTAINS) {
       // a pattern of <= 8 bytes packed for the sliding-window compare: byte k
       // of the pattern at bits 8 * (plen - 1 - k) (the newest byte lowest)
@@ -399,7 +421,8 @@ dpf_status compile_pred_body(const Column& c, const dpf_pred& p, DevStep& S, int
     }
     return DPF_OK;
   }
-  if (is_str_codec(uint32_t(c.codec))) return fail(DPF_EINVAL, "only PREFIX and CONTAINS apply to string column %d", c.id);
+  if (is_str_codec(uint32_t(c.codec)))
+    return fail(DPF_EINVAL, "only PREFIX, CONTAINS and LIKE apply to string column %d", c.id);
   const int64_t MN = INT32_MIN, MX = INT32_MAX;
   int64_t lo, hi;
   bool neg = false;
@@ -540,6 +563,11 @@ double step_selectivity(const DevStep& S, const Column* col, const HashTable* ht
     case ST_PROBE: return ht && ht->dim_rows ? double(ht->entries) / double(ht->dim_rows) : 1.0;
     case ST_PREFIX: return std::pow(0.1, double(S.plen));
     case ST_CONTAINS: return std::min(1.0, 30.0 * std::pow(0.1, double(S.plen)));
+    case ST_LIKE: {
+      double lits = 0;
+      for (uint32_t i = 0; i < S.plen; ++i) lits += S.pfx[i] != '%' && S.pfx[i] != '_';
+      return std::min(1.0, 30.0 * std::pow(0.1, lits));
+    }
     default: break;
   }
   if (!col || col->vmax < col->vmin) return 0.5;
@@ -962,7 +990,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
     for (const DevQuery& Q : p->hq) {
       const DevStep& S0 = Q.steps[0];
       const DevColumn& C0 = Q.cols[S0.col];
-      const bool ok = Q.nsteps != 0 && S0.kind != ST_PREFIX && S0.kind != ST_CONTAINS &&
+      const bool ok = Q.nsteps != 0 && S0.kind != ST_PREFIX && S0.kind != ST_CONTAINS && S0.kind != ST_LIKE &&
                       (C0.codec == C_FOR || C0.codec == C_DICT || C0.codec == C_DELTA) && C0.max_bw <= 32;
       all = all && ok;
       if (ok) stage_bw = std::max(stage_bw, std::max<uint32_t>(C0.max_bw, 1u));
@@ -1768,7 +1796,7 @@ dpf_status dpf_prepare_unfused(dpf_ctx* c, const dpf_plan* plan, dpf_prep_id* ou
     return fail(DPF_EINVAL, "the unfused chain reads device-resident columns only");
   }
   for (uint32_t k = 0; k < Q.nsteps; ++k)
-    if (Q.steps[k].kind == ST_CONTAINS || Q.cols[Q.steps[k].col].codec == C_FSST) {
+    if (Q.steps[k].kind == ST_CONTAINS || Q.steps[k].kind == ST_LIKE || Q.cols[Q.steps[k].col].codec == C_FSST) {
       dpf_release(c, p->id);
       return fail(DPF_EINVAL, "the unfused chain evaluates PREFIX on STR columns only (no FSST, no CONTAINS)");
     }

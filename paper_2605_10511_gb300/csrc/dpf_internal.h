@@ -72,6 +72,7 @@ enum StepKind : uint8_t {
   ST_IN = 3,        // x in in[0..nin)
   ST_FALSE = 4,     // no row passes (e.g. an equality on a value absent from a dictionary)
   ST_CONTAINS = 9,  // the string contains pfx[0..plen) (LIKE '%pattern%'), matched by KMP
+  ST_LIKE = 10,     // SQL LIKE of the whole string against pfx[0..plen) ('%', '_' wildcards)
   ST_PREFIX = 5,    // STR column starts with pfx[0..plen)
   ST_PROBE = 6,     // hash probe; a miss drops the row, a hit adds payload fields to gid
   ST_KEY = 7,       // DICT column code added to gid
@@ -154,11 +155,12 @@ struct alignas(16) DevQuery {
 };
 
 // A query needs the fused kernel's general string matcher when it has a
-// CONTAINS step or a string step on an FSST column.
+// CONTAINS or LIKE step or a string step on an FSST column.
 inline bool needs_string_matcher(const DevQuery& Q) {
   for (uint32_t s = 0; s < Q.nsteps && s < uint32_t(kMaxSteps); ++s) {
     const DevStep& S = Q.steps[s];
-    if (S.kind == ST_CONTAINS || (S.kind == ST_PREFIX && Q.cols[S.col].codec == C_FSST)) return true;
+    if (S.kind == ST_CONTAINS || S.kind == ST_LIKE || (S.kind == ST_PREFIX && Q.cols[S.col].codec == C_FSST))
+      return true;
   }
   return false;
 }

@@ -433,9 +433,38 @@ __device__ __forceinline__ void build_fsst_matcher(const DevStep& S, const int4*
   }
 }
 
+// SQL LIKE of a raw string s[0..n) against pfx[0..plen): '%' any run of
+// bytes, '_' any one byte.  The iterative greedy wildcard matcher: literals
+// and '_' advance both sides; a '%' records where it stands and first
+// matches nothing; on a mismatch the last '%' takes one more byte and the
+// match resumes after it.  O(n * plen) at worst, no recursion.
+template <bool kHost>
+__device__ __forceinline__ bool like_match(const DevStep& S, const uint8_t* s, uint32_t n) {
+  const uint32_t m = S.plen, none = 0xffffffffu;
+  uint32_t i = 0, j = 0, star_j = none, star_i = 0;
+  while (i < n) {
+    const uint32_t pc = j < m ? S.pfx[j] : 0u;
+    if (j < m && pc != '%' && (pc == '_' || pc == ld_u8<kHost>(s + i))) {
+      ++i;
+      ++j;
+    } else if (j < m && pc == '%') {
+      star_j = j++;
+      star_i = i;
+    } else if (star_j != none) {
+      j = star_j + 1;
+      i = ++star_i;
+    } else {
+      return false;
+    }
+  }
+  while (j < m && S.pfx[j] == '%') ++j;
+  return j == m;
+}
+
 template <bool kHost>
 __device__ __forceinline__ bool string_match(const DevStep& S, const uint8_t* s, uint32_t len, const int4* sym,
                                              const uint8_t* tab = nullptr) {
+  if (S.kind == ST_LIKE) return sym == nullptr && like_match<kHost>(S, s, len);  // STR columns only
   if (S.plen == 0) return true;                         // an empty pattern matches
   if (tab != nullptr) return fsst_table_match<kHost>(S, s, len, tab);
   if (S.kind == ST_PREFIX) {
@@ -873,7 +902,7 @@ __device__ __forceinline__ void tile_dense_step(const DevQuery& Q, uint32_t s, c
                                                 StagedPay sp = StagedPay{nullptr, 0, 0}) {
   if (s >= Q.nsteps) return;
   const DevStep& S = Q.steps[s];
-  if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) {
+  if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS || S.kind == ST_LIKE) {
     if (!kStaged) tile_prefix<kHost, kText>(Q, S, P, Hd, T, lane, status, stab);
     else if (lane == 0) atomicOr(status, S_INTERNAL);
   } else if (Q.cols[S.col].codec == C_DELTA) {
@@ -1141,7 +1170,7 @@ __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevS
     const uint32_t r = e & ((1u << kRowBits) - 1u);
     uint32_t gid = e >> kRowBits;
     bool keep;
-    if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS) {
+    if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS || S.kind == ST_LIKE) {
       keep = row_prefix<kHost, kText>(Q, S, P, seg_mb, r, valid, lane, status, stab);
     } else {
       const uint32_t v = row_value<kHost>(Q, S.col, P, seg_mb, r, valid, lane, status);
@@ -1177,7 +1206,7 @@ __device__ __forceinline__ uint32_t list_steps(const DevQuery& Q, const PageStat
                                                unsigned int* status, uint32_t first = 1) {
   for (uint32_t s = first; s < Q.nsteps && n != 0; ++s) {
     const DevStep& S = Q.steps[s];
-    if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS || Q.cols[S.col].codec == C_DELTA) {
+    if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS || S.kind == ST_LIKE || Q.cols[S.col].codec == C_DELTA) {
       n = list_step_generic<kHost, kText>(Q, S, P, seg_mb, list, n, stab, lane, status);
       continue;
     }
