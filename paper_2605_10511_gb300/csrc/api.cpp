@@ -794,6 +794,13 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
   }
   Q.nsteps = uint32_t(steps.size());
   for (size_t i = 0; i < steps.size(); ++i) Q.steps[i] = steps[order[i]];
+  // When the first step keeps enough rows (>= 3 % estimated), most 32-byte
+  // sectors of step 1's column hold a survivor's field anyway: prefetch its
+  // mini blocks into L2 while the dense tiles run, so that step's
+  // per-survivor reads hit L2 instead of waiting on DRAM.
+  if (steps.size() > 1 && sel[order[0]] >= kPrefetchMinSel && Q.steps[1].kind != ST_PREFIX &&
+      Q.steps[1].kind != ST_CONTAINS && Q.steps[1].kind != ST_LIKE)
+    Q.pf_step = 1;
   Q.nrows = cs.nrows;
   Q.page_rows = cs.page_rows;
   *host = cs.host;

@@ -122,7 +122,10 @@ struct DevStep {
 struct alignas(16) DevQuery {
   DevColumn cols[kMaxCols];
   DevStep steps[kMaxSteps];
-  uint32_t ncols, nsteps, smem_table_bytes, pad0_;
+  uint32_t ncols, nsteps, smem_table_bytes;
+  uint32_t pf_step;            // 1: while a segment's tiles run the first step, their mini
+                               // blocks of step 1's column are prefetched into L2 (step 1
+                               // then reads them per survivor); 0: no prefetch
   uint64_t nrows;
   uint32_t page_rows;
   uint32_t chunk_rows;

@@ -441,6 +441,7 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
         else n = tile_first_step<kHost, kText, false, true>(Q, P, H, i0, nmb, row_base, stab, list, n, lane, status, sp);
       } else {
         const TileHdr H = load_headers<kHost>(Q, P, i0, nmb, lane);
+        if (!kHost && Q.pf_step) prefetch_words(Q, P, H, Q.steps[1].col, nmb, lane);
         if (gid0) n = tile_first_step<kHost, kText, true>(Q, P, H, i0, nmb, row_base, stab, list, n, lane, status);
         else n = tile_first_step<kHost, kText, false>(Q, P, H, i0, nmb, row_base, stab, list, n, lane, status);
       }

@@ -19,6 +19,9 @@ constexpr int kFusedMinBlocksLo = 3;
 constexpr int kFusedMinBlocksHi = 4;
 // Rows of one scheduling ticket (one warp's unit of work) unless tuned.
 constexpr uint32_t kDefaultChunkRows = 4096;
+// Estimated selectivity of the first step from which step 1's mini blocks
+// are prefetched into L2 during the dense tiles (DevQuery::pf_step).
+constexpr double kPrefetchMinSel = 0.03;
 // Staging of the first step's mini blocks unless tuned (DPF_STAGE_ON / _OFF).
 constexpr int32_t kDefaultStaging = 2;
 // Group domains up to this size use warp-aggregated group-by updates: with

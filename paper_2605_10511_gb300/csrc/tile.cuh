@@ -184,6 +184,20 @@ struct StagedPay {
   uint32_t pw, bwcap;
 };
 
+// L2 prefetch of the packed words of mini blocks [i0, i0 + nmb) of column
+// c (its headers in Hd, lanes c * TB + t): every 128-byte line of each block.
+__device__ __forceinline__ void prefetch_words(const DevQuery& Q, const PageState& P, const TileHdr& Hd, int c,
+                                               uint32_t nmb, int lane) {
+  const int t = lane % TB, part = lane / TB;  // up to 8 lanes per block: lines part, part + 8, ...
+  const uint32_t codec = Q.cols[c].codec;
+  const uint32_t wob = __shfl_sync(kFull, codec == C_DELTA ? Hd.z : Hd.y, c * TB + t);
+  const uint64_t pg = __shfl_sync(kFull, P.pg, c);
+  if (t >= int(nmb) || codec == C_FOR64 || is_str_codec(codec)) return;
+  const uint32_t bw = tmin<uint32_t>(wob & 0xffu, 32u), bytes = 16 * bw;
+  const uint8_t* w = reinterpret_cast<const uint8_t*>(pg) + payload_offset(codec, P.prow) + uint64_t(wob >> 8) * 4;
+  for (uint32_t off = uint32_t(part) * 128; off < bytes; off += (32 / TB) * 128) prefetch_l2(w + off);
+}
+
 struct TileState {
   uint32_t alive;         // bit 4t+k: row 32k+lane of mini block t is live
   uint32_t gid[TB][4];    // dense group id of each row
