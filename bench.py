@@ -478,6 +478,8 @@ def main():
     ap.add_argument("--ctas", type=int, default=0, help="CTAs per SM (4 = the 4-CTA kernel build)")
     ap.add_argument("--stage", default="default", choices=["default", "on", "off"],
                     help="stage the first step's mini blocks in shared memory (cp.async ring)")
+    ap.add_argument("--group-agg", default="default", choices=["default", "warp", "atomic"],
+                    help="grouped aggregates: warp-aggregated or one atomic per row")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
@@ -531,12 +533,13 @@ def main():
     build_ms = 1e3 * (time.perf_counter() - t0)
     autotuned = None
     if not (args.chunk_rows or args.threads or args.ht != "auto" or args.ctas or args.stage != "default"
-            or args.no_autotune):
+            or args.group_agg != "default" or args.no_autotune):
         # the library's autotuner picks the launch configuration (cached
         # for this plan's signature; untimed)
         best, best_ms = eng.ctx.autotune([plan], stream, reps=3)
         autotuned = {"best": best, "best_ms": best_ms}
-    tuning = dpf.Tuning(args.chunk_rows, args.threads, dpf.HT_PLACE[args.ht], args.ctas, dpf.STAGING[args.stage])
+    tuning = dpf.Tuning(args.chunk_rows, args.threads, dpf.HT_PLACE[args.ht], args.ctas, dpf.STAGING[args.stage],
+                        dpf.GROUP_AGG[args.group_agg])
     prep = eng.ctx.prepare([plan], tuning)
     eng.ctx.capture_graph(prep, stream)
     for _ in range(args.warmup):

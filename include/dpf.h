@@ -312,8 +312,13 @@ typedef struct dpf_tuning {
                             of their decode (Sec. 3.2 IO stage overlapped with
                             decompression); integer first steps over device-
                             resident pages only                              */
+  int32_t group_agg;     /* enum dpf_group_agg: how grouped aggregates are added
+                            into the accumulators: one int64 atomic per row,
+                            or warp-aggregated (lanes of a round holding the
+                            same group, found by __match_any_sync, add once) */
 } dpf_tuning;
 enum dpf_staging { DPF_STAGE_DEFAULT = 0, DPF_STAGE_ON = 1, DPF_STAGE_OFF = 2 };
+enum dpf_group_agg { DPF_GROUP_AGG_DEFAULT = 0, DPF_GROUP_AGG_WARP = 1, DPF_GROUP_AGG_ATOMIC = 2 };
 
 /* Result record: keys are dictionary values (0 when unused); count = rows
  * in the group; val[i] = aggregate i (COUNT repeats count). */
@@ -344,7 +349,8 @@ dpf_status dpf_launch_graph(dpf_ctx* ctx, dpf_prep_id prep, void* stream);
 dpf_status dpf_read_result(dpf_ctx* ctx, dpf_prep_id prep, int32_t i, dpf_record* buf,
                            uint64_t cap, uint64_t* n_out, int32_t timeout_ms);
 /* Tuning the batch will launch with (after defaults and cache lookup;
- * staging = DPF_STAGE_ON only when some query of the batch is staged). */
+ * staging = DPF_STAGE_ON only when the batch is staged, group_agg =
+ * DPF_GROUP_AGG_WARP only when some grouped query uses it). */
 dpf_status dpf_prep_tuning(dpf_ctx* ctx, dpf_prep_id prep, dpf_tuning* out);
 dpf_status dpf_release(dpf_ctx* ctx, dpf_prep_id prep);
 
@@ -353,8 +359,9 @@ dpf_status dpf_release(dpf_ctx* ctx, dpf_prep_id prep);
  * where the join tables live (shared memory vs device memory, Sec. 4.3) are
  * the launch configuration.  dpf_autotune prepares the n plans under each
  * configuration of a fixed grid (chunk_rows 1K..256K, threads 128..1024,
- * tables AUTO/GLOBAL, kernel build for 3 or 4 CTAs per SM, staging on/off),
- * times `reps` launches of each on `stream` with CUDA
+ * tables AUTO/GLOBAL, kernel build for 3 or 4 CTAs per SM), then, at the
+ * fastest point, staging on and warp-aggregated group-by; it times `reps`
+ * launches of each on `stream` with CUDA
  * events after one warm-up launch (reps 0 = 3), and keeps the fastest in the
  * context's tuning cache under the plans' signature (the rows and encodings
  * of the columns they read, their steps, tables, groups and aggregates; not

@@ -86,10 +86,11 @@ class Plan(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("chunk_rows", C.c_uint32), ("threads", C.c_uint32), ("ht_placement", C.c_int32),
-                ("ctas_per_sm", C.c_uint32), ("staging", C.c_int32)]
+                ("ctas_per_sm", C.c_uint32), ("staging", C.c_int32), ("group_agg", C.c_int32)]
 
 
 STAGING = {"default": 0, "on": 1, "off": 2}
+GROUP_AGG = {"default": 0, "warp": 1, "atomic": 2}
 
 
 class ServerConfig(C.Structure):
@@ -398,7 +399,7 @@ class Context:
         t = Tuning()
         _check(lib().dpf_prep_tuning(self.h, prep, C.byref(t)))
         return {"chunk_rows": t.chunk_rows, "threads": t.threads, "ht_placement": t.ht_placement,
-                "ctas_per_sm": t.ctas_per_sm, "staging": t.staging}
+                "ctas_per_sm": t.ctas_per_sm, "staging": t.staging, "group_agg": t.group_agg}
 
     def autotune(self, plans, stream=None, reps=3):
         """Times the plans under the library's grid of launch configurations
@@ -407,7 +408,7 @@ class Context:
         t, ms = Tuning(), C.c_float()
         _check(lib().dpf_autotune(self.h, arr, len(plans), _stream_ptr(stream), reps, C.byref(t), C.byref(ms)))
         return ({"chunk_rows": t.chunk_rows, "threads": t.threads, "ht_placement": t.ht_placement,
-                 "ctas_per_sm": t.ctas_per_sm, "staging": t.staging}, ms.value)
+                 "ctas_per_sm": t.ctas_per_sm, "staging": t.staging, "group_agg": t.group_agg}, ms.value)
 
     def plan_footprint(self, plan):
         b = C.c_uint64()

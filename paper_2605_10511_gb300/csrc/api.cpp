@@ -896,7 +896,8 @@ uint64_t plans_signature(dpf_ctx* c, const dpf_plan* plans, int32_t n) {
 // Fields left 0 take the tuning dpf_autotune stored for these plans, else the
 // defaults.
 void fill_tuning_defaults(dpf_ctx* c, dpf_tuning& t, const dpf_plan* plans, int32_t n) {
-  if (t.chunk_rows == 0 || t.threads == 0 || t.ht_placement == 0 || t.ctas_per_sm == 0 || t.staging == 0) {
+  if (t.chunk_rows == 0 || t.threads == 0 || t.ht_placement == 0 || t.ctas_per_sm == 0 || t.staging == 0 ||
+      t.group_agg == 0) {
     auto it = c->tune_cache.find(plans_signature(c, plans, n));
     if (it != c->tune_cache.end()) {
       if (t.chunk_rows == 0) t.chunk_rows = it->second.chunk_rows;
@@ -904,12 +905,14 @@ void fill_tuning_defaults(dpf_ctx* c, dpf_tuning& t, const dpf_plan* plans, int3
       if (t.ht_placement == 0) t.ht_placement = it->second.ht_placement;
       if (t.ctas_per_sm == 0) t.ctas_per_sm = it->second.ctas_per_sm;
       if (t.staging == 0) t.staging = it->second.staging;
+      if (t.group_agg == 0) t.group_agg = it->second.group_agg;
     }
   }
   if (t.chunk_rows == 0) t.chunk_rows = kDefaultChunkRows;
   if (t.threads == 0) t.threads = 256;
   if (t.ht_placement == 0) t.ht_placement = DPF_HT_AUTO;
   if (t.staging == 0) t.staging = kDefaultStaging;
+  if (t.group_agg == 0) t.group_agg = kDefaultGroupAgg;
 }
 
 dpf_status release_prep(dpf_ctx* c, Prep* p) {
@@ -949,6 +952,9 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   if (t.threads != 128 && t.threads != 256 && t.threads != 512 && t.threads != 1024)
     return fail(DPF_EINVAL, "threads must be 128, 256, 512 or 1024");
   if (t.staging != DPF_STAGE_ON && t.staging != DPF_STAGE_OFF) return fail(DPF_EINVAL, "staging must be 0, 1 or 2");
+  if (t.group_agg != DPF_GROUP_AGG_WARP && t.group_agg != DPF_GROUP_AGG_ATOMIC)
+    return fail(DPF_EINVAL, "group_agg must be 0, 1 or 2");
+  bool any_warp_agg = false;
   bool host = false;
   uint64_t tickets = 0;
   std::vector<uint64_t> qbegin(size_t(n) + 1);
@@ -977,7 +983,8 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
     tickets += Q.nchunks;
     const uint32_t S1 = 1 + Q.naggs;
     Q.use_smem_acc = uint64_t(Q.domain) * S1 <= kSmemAccSlots ? 1u : 0u;
-    Q.warp_agg = Q.domain > 1 && Q.domain <= kWarpAggMaxDomain ? 1u : 0u;
+    Q.warp_agg = t.group_agg == DPF_GROUP_AGG_WARP && Q.domain > 1 ? 1u : 0u;
+    any_warp_agg = any_warp_agg || Q.warp_agg;
     if (Q.use_smem_acc) acc_slots = std::max<uint32_t>(acc_slots, Q.domain * S1);
     off_acc[i] = scratch; scratch += align16(uint64_t(Q.domain) * S1 * 8);
     off_done[i] = scratch; scratch += 16;
@@ -1095,6 +1102,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   p->L.host_data = host;
   p->L.stage_bw = stage_bw;
   p->tuning.staging = stage_bw ? DPF_STAGE_ON : DPF_STAGE_OFF;  // what the launch does
+  p->tuning.group_agg = any_warp_agg ? DPF_GROUP_AGG_WARP : DPF_GROUP_AGG_ATOMIC;
   p->L.text = false;
   for (const DevQuery& q : p->hq) p->L.text = p->L.text || needs_string_matcher(q);
   p->fetched.assign(size_t(n), 0);
@@ -1644,6 +1652,7 @@ dpf_status dpf_autotune(dpf_ctx* c, const dpf_plan* plans, int32_t n, void* stre
   static const uint32_t kChunk[] = {1024, 2048, 4096, 16384, 65536, 262144};
   static const uint32_t kThreads[] = {128, 256, 512, 1024};
   static const int32_t kPlace[] = {DPF_HT_AUTO, DPF_HT_GLOBAL};
+  static const uint32_t kCtas[] = {0, uint32_t(kFusedMinBlocksHi)};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CUDA_TRY(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1653,58 +1662,69 @@ dpf_status dpf_autotune(dpf_ctx* c, const dpf_plan* plans, int32_t n, void* stre
   dpf_tuning top{};
   float top_ms = -1.f;
   dpf_status last = DPF_OK;
-  static const uint32_t kCtas[] = {0, uint32_t(kFusedMinBlocksHi)};
-  static const int32_t kStage[] = {DPF_STAGE_OFF, DPF_STAGE_ON};
+  // Times one configuration; keeps it when it is the fastest so far.
+  // Returns a status only for errors that end the search.
+  auto trial = [&](dpf_tuning t) -> dpf_status {
+    Prep* p = nullptr;
+    dpf_status st = prepare(c, plans, n, &t, &p);
+    if (st) {  // e.g. the tables do not fit this configuration
+      last = st;
+      return DPF_OK;
+    }
+    const int32_t id = p->id;
+    cudaError_t e = launch_prep(p, s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (uint32_t r = 0; r < reps && e == cudaSuccess; ++r) e = launch_prep(p, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    uint32_t status = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&status, &p->sched->status, 4, cudaMemcpyDeviceToHost);
+    dpf_tuning used = p->tuning;
+    release_prep(c, p);
+    c->preps.erase(id);
+    if (e != cudaSuccess) return fail(DPF_ECUDA, "autotune: %s", cudaGetErrorString(e));
+    if (status) return fail(status & S_CORRUPT ? DPF_ECORRUPT : DPF_EINTERNAL, "autotune: device status %u", status);
+    ms /= float(reps);
+    if (top_ms < 0.f || ms < top_ms) {
+      top_ms = ms;
+      used.ctas_per_sm = t.ctas_per_sm;  // 0: the 3-CTA build at its occupancy; 4: the 4-CTA build
+      top = used;
+    }
+    return DPF_OK;
+  };
+  dpf_status st = DPF_OK;
+  // the launch grid (unstaged, one atomic per row)
   for (uint32_t cr : kChunk)
     for (uint32_t th : kThreads)
       for (int32_t pl : kPlace)
-        for (uint32_t ct : kCtas)
-          for (int32_t sg : kStage) {
-        if (th > 256 && (ct != 0 || sg == DPF_STAGE_ON)) continue;  // one build per wide CTA size, unstaged
-        dpf_tuning t{};
-        t.chunk_rows = cr;
-        t.threads = th;
-        t.ht_placement = pl;
-        t.ctas_per_sm = ct;
-        t.staging = sg;
-        Prep* p = nullptr;
-        dpf_status st = prepare(c, plans, n, &t, &p);
-        if (st) {  // e.g. the tables do not fit this configuration
-          last = st;
-          continue;
+        for (uint32_t ct : kCtas) {
+          if (st || (th > 256 && ct != 0)) continue;  // one build per wide CTA size
+          dpf_tuning t{};
+          t.chunk_rows = cr;
+          t.threads = th;
+          t.ht_placement = pl;
+          t.ctas_per_sm = ct;
+          t.staging = DPF_STAGE_OFF;
+          t.group_agg = DPF_GROUP_AGG_ATOMIC;
+          st = trial(t);
         }
-        const int32_t id = p->id;
-        cudaError_t e = launch_prep(p, s);  // warm-up
-        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-        for (uint32_t r = 0; r < reps && e == cudaSuccess; ++r) e = launch_prep(p, s);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        uint32_t status = 0;
-        if (e == cudaSuccess) e = cudaMemcpy(&status, &p->sched->status, 4, cudaMemcpyDeviceToHost);
-        const dpf_tuning used = p->tuning;
-        release_prep(c, p);
-        c->preps.erase(id);
-        if (e != cudaSuccess) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          return fail(DPF_ECUDA, "autotune: %s", cudaGetErrorString(e));
-        }
-        if (status) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          return fail(status & S_CORRUPT ? DPF_ECORRUPT : DPF_EINTERNAL, "autotune: device status %u", status);
-        }
-        ms /= float(reps);
-        if (top_ms < 0.f || ms < top_ms) {
-          top_ms = ms;
-          top = used;
-          top.ctas_per_sm = ct;  // 0: the 3-CTA build at its occupancy; 4: the 4-CTA build
-        }
-      }
+  // then, at the fastest point, the staging ring and warp-aggregated group-by
+  if (!st && top_ms >= 0.f) {
+    dpf_tuning t = top;
+    t.staging = DPF_STAGE_ON;
+    if (t.threads > 256) t.threads = 256;  // the staging builds take 256-thread CTAs
+    st = trial(t);
+  }
+  if (!st && top_ms >= 0.f) {
+    dpf_tuning t = top;
+    t.group_agg = DPF_GROUP_AGG_WARP;
+    st = trial(t);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (st) return st;
   if (top_ms < 0.f) return fail(last ? last : DPF_EINVAL, "autotune: no configuration could be prepared");
   c->tune_cache[plans_signature(c, plans, n)] = top;
   if (best) *best = top;

@@ -24,11 +24,11 @@ constexpr uint32_t kDefaultChunkRows = 4096;
 constexpr double kPrefetchMinSel = 0.03;
 // Staging of the first step's mini blocks unless tuned (DPF_STAGE_ON / _OFF).
 constexpr int32_t kDefaultStaging = 2;
-// Group domains up to this size use warp-aggregated group-by updates: with
-// few groups the lanes of a round often share one and __match_any_sync has
-// few distinct values to sort out; with many groups (1,024 Zipf keys) plain
-// shared-memory atomics measured 1.8x faster.
-constexpr uint32_t kWarpAggMaxDomain = 32;
+// Grouped aggregates are added with one int64 atomic per row unless tuned
+// (DPF_GROUP_AGG_*): warp aggregation measured slower on GB300 both with
+// 1,024 Zipf groups (1.8x) and with 15 groups, one holding 97 % of the rows
+// (1.3x); the autotuner tries it per plan signature.
+constexpr int32_t kDefaultGroupAgg = 2;
 // Join-table representation by the key range of the kept rows (R8): a
 // direct table of one word per key up to 2^22 keys (16 MB), a rank
 // directory (2 bits per key plus the kept payloads) up to 2^28 keys, open

@@ -3,10 +3,10 @@
 The lanes of a round that hold the same group id add their values once
 (their peers found by __match_any_sync, the group's lowest lane issuing the
 atomic).  The cases that exercise it most: every row passing a filter with
-Zipf-skewed keys (the top key holds about a fifth of the rows; plain
-atomics, as for every domain above 32 groups), one hot group holding almost
-every row (warp-aggregated for domains of at most 32), groups in
-shared-memory and in global accumulators, COUNT / SUM / SUM_MUL / SUM_SUB over 32- and 64-bit operands,
+Zipf-skewed keys (the top key holds about a fifth of the rows), one hot
+group holding almost every row, groups in shared-memory and in global
+accumulators, each with warp aggregation and with one atomic per row (the
+two group_agg tunings), COUNT / SUM / SUM_MUL / SUM_SUB over 32- and 64-bit operands,
 ragged tails.  Records must equal the oracle's exactly.
 """
 
@@ -41,7 +41,9 @@ def test_all_rows_pass_with_zipf_keys(eng, rows):
     want = oracle.run_query(w, from_encoded=False, threads=0)
     assert int(want["count"].sum()) == rows
     assert int(want["count"].max()) > rows // 8  # the Zipf head: many lanes of a round share it
-    assert_same(eng.run(w), want, w["name"])
+    for mode in ("atomic", "warp"):
+        t = dpf.Tuning(0, 0, 0, 0, 0, dpf.GROUP_AGG[mode])
+        assert_same(eng.run(w, tuning=t), want, (w["name"], mode))
 
 
 @pytest.mark.parametrize("n_groups,hot_frac", [(1, 0.0), (5, 0.97), (300, 0.5), (20000, 0.3)])
@@ -51,4 +53,8 @@ def test_hot_groups_and_wide_sums(eng, n_groups, hot_frac):
     wrap modulo 2^64; 20,000 x 3 groups exceed the shared accumulators and
     run on global ones."""
     w = synth.hot_groups(300_001, n_groups, hot_frac, seed=n_groups)
-    assert_same(eng.run(w), oracle.run_query(w, from_encoded=False), w["name"])
+    want = oracle.run_query(w, from_encoded=False)
+    for mode in ("atomic", "warp"):
+        for threads in (256, 1024):
+            t = dpf.Tuning(2048, threads, 0, 0, 0, dpf.GROUP_AGG[mode])
+            assert_same(eng.run(w, tuning=t), want, (w["name"], mode, threads))
