@@ -359,7 +359,7 @@ dpf_status dpf_release(dpf_ctx* ctx, dpf_prep_id prep);
  * where the join tables live (shared memory vs device memory, Sec. 4.3) are
  * the launch configuration.  dpf_autotune prepares the n plans under each
  * configuration of a fixed grid (chunk_rows 1K..256K, threads 128..1024,
- * tables AUTO/GLOBAL, kernel build for 3 or 4 CTAs per SM), then, at the
+ * tables AUTO/SMEM/GLOBAL, kernel build for 3 or 4 CTAs per SM), then, at the
  * fastest point, staging on and warp-aggregated group-by; it times `reps`
  * launches of each on `stream` with CUDA
  * events after one warm-up launch (reps 0 = 3), and keeps the fastest in the

@@ -963,9 +963,12 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   uint64_t scratch = 0;
   size_t max_tables = 0;
   uint32_t acc_slots = 0;
+  // SMEM placement: what the opt-in shared memory leaves after the largest
+  // accumulator region, the warps' lists and group buffers, and the plan
+  const int per_cta_fixed = int(kSmemAccSlots * 8) + int(t.threads / 32) * int(kListBytesPerWarp) + 4096;
   const size_t table_budget =
       t.ht_placement == DPF_HT_GLOBAL ? 0
-      : t.ht_placement == DPF_HT_SMEM ? size_t(std::max(0, c->smem_optin - int(kSmemAccSlots * 8) - 4096))
+      : t.ht_placement == DPF_HT_SMEM ? size_t(std::max(0, c->smem_optin - per_cta_fixed))
                                       : size_t(48 * 1024);
   for (int i = 0; i < n; ++i) {
     DevQuery& Q = p->hq[i];
@@ -1651,7 +1654,7 @@ dpf_status dpf_autotune(dpf_ctx* c, const dpf_plan* plans, int32_t n, void* stre
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   static const uint32_t kChunk[] = {1024, 2048, 4096, 16384, 65536, 262144};
   static const uint32_t kThreads[] = {128, 256, 512, 1024};
-  static const int32_t kPlace[] = {DPF_HT_AUTO, DPF_HT_GLOBAL};
+  static const int32_t kPlace[] = {DPF_HT_AUTO, DPF_HT_SMEM, DPF_HT_GLOBAL};
   static const uint32_t kCtas[] = {0, uint32_t(kFusedMinBlocksHi)};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CUDA_TRY(cudaEventCreate(&e0));

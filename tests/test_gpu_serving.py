@@ -56,7 +56,7 @@ def test_autotune_caches_a_grid_point_and_keeps_results(eng, mix, expected):
     assert ms > 0
     assert best["chunk_rows"] in (1024, 2048, 4096, 16384, 65536, 262144)
     assert best["threads"] in (128, 256, 512, 1024)
-    assert best["ht_placement"] in (dpf.HT_PLACE["auto"], dpf.HT_PLACE["global"])
+    assert best["ht_placement"] in (dpf.HT_PLACE["auto"], dpf.HT_PLACE["smem"], dpf.HT_PLACE["global"])
     prep = eng.ctx.prepare(plans)  # tuning fields 0: the cached choice
     try:
         t = eng.ctx.prep_tuning(prep)
