@@ -69,10 +69,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def stored_traffic(workload, fact_rows):
+def stored_traffic(workload, fact_rows, alg_bytes=None):
     """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary of this workload (scaled by rows when it was captured on a
-    smaller case), or None when absent or taken on other kernel sources."""
+    summary of this workload, or None when absent or taken on other kernel
+    sources.  A capture of a smaller case is scaled by rows, or (with
+    ``alg_bytes``: a batch whose queries differ) by algorithmic bytes."""
     path = os.path.join(ROOT, "profiles", f"fused_kernel_{workload}.txt")
     try:
         kv = {}
@@ -84,6 +85,9 @@ def stored_traffic(workload, fact_rows):
         if kv.get("source_hash") != kernel_source_hash():
             return None, "stale (kernel changed since capture)"
         b = float(kv["dram_bytes_per_launch"])
+        if alg_bytes is not None:
+            a = float(kv["algorithmic_bytes_per_launch"])
+            return b * alg_bytes / a, f"ncu capture at {int(a)} algorithmic bytes, scaled by algorithmic bytes"
         rows = float(kv["captured_rows"])
         return b * fact_rows / rows, f"ncu capture at {int(rows)} rows, scaled by rows"
     except Exception:  # noqa: BLE001
@@ -258,12 +262,19 @@ def pcts(per):
     return {"p50": q(50), "p90": q(90), "p99": q(99), "mean": statistics.mean(v), "n": len(v)}
 
 
+def _explicit_tuning(args):
+    """True when the command line fixes the launch configuration (or turns
+    the autotuner off): the library's defaults fill what it leaves at 0."""
+    return bool(args.chunk_rows or args.threads or args.ht != "auto" or args.ctas or args.stage != "default"
+                or args.group_agg != "default" or args.no_autotune)
+
+
 def run_batched(args, dpf, torch, np, local):
     """64 queries of the three shapes over fact tables of log-uniform size
     (2^16..2^26 rows) in ONE persistent launch replayed from a CUDA graph,
     under the launch configuration the library's autotuner picks."""
     import synth
-    ws = synth.batched_workloads(n_queries=args.batch_queries, seed=4)
+    ws = synth.batched_workloads(n_queries=args.batch_queries, seed=4, max_rows=args.batch_max_rows)
     eng = dpf.Engine(device=local)
     for w in ws:
         eng.load_workload(w)
@@ -271,9 +282,14 @@ def run_batched(args, dpf, torch, np, local):
     plans = [eng.plan(w, stream) for w in ws]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    best, tune_ms = eng.ctx.autotune(plans, stream, reps=2)
+    best, tune_ms, tuning = None, None, None
+    if _explicit_tuning(args):
+        tuning = dpf.Tuning(args.chunk_rows, args.threads, dpf.HT_PLACE[args.ht], args.ctas, dpf.STAGING[args.stage],
+                            dpf.GROUP_AGG[args.group_agg])
+    else:
+        best, tune_ms = eng.ctx.autotune(plans, stream, reps=2)
     tune_s = time.perf_counter() - t0
-    prep = eng.ctx.prepare(plans)
+    prep = eng.ctx.prepare(plans, tuning)
     eng.ctx.capture_graph(prep, stream)
     for _ in range(args.warmup):
         eng.ctx.launch_graph(prep, stream)
@@ -308,17 +324,19 @@ def run_batched(args, dpf, torch, np, local):
             unf_bytes += r["intermediate_bytes"]
     peak, peak_kind = _peaks()
     achieved = alg / (statistics.mean(per) * 1e-3) / 1e9
+    traffic, traffic_src = stored_traffic("batched", rows, alg_bytes=alg)
     out = {
         "metric": METRIC, "value": rows / (ms_step * 1e-3), "unit": "rows/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded; 64 queries of the scan / star / strings shapes)",
         "config": {"workload": f"batched_{len(ws)}_queries", "fact_rows_total": rows,
+                   "max_rows_per_query": args.batch_max_rows,
                    "queries": len(ws), "l2": "inputs larger than L2", "tuning": tuned},
         "autotune": {"best": best, "best_ms": tune_ms, "search_s": tune_s},
         "compressed_gbs": achieved, "compressed_bytes": alg,
         "latency_ms": {"p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(0.99 * (len(per) - 1) + 0.5))]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "traffic_source": "no capture for the batch",
+                     "traffic": traffic, "traffic_source": traffic_src,
                      "peak_kind": f"{peak_kind} copy bandwidth (burst)"},
         "unfused": None if args.no_unfused else {
             "ms_per_batch": unf_ms, "launches_per_batch": unf_launches, "intermediate_bytes": unf_bytes,
@@ -466,6 +484,8 @@ def main():
                              "strings", "strings_all", "groups_hot",
                              "strings_text", "strings_fsst", "chain", "chain_sparse", "batched"])
     ap.add_argument("--batch-queries", type=int, default=64)
+    ap.add_argument("--batch-max-rows", type=int, default=None,
+                    help="cap every batched query's fact rows (a smaller batch for profiling)")
     ap.add_argument("--serve", action="store_true", help="Poisson serving run instead of the step benchmark")
     ap.add_argument("--serve-rates", default="10,100,500,1000,2000")
     ap.add_argument("--serve-seconds", type=float, default=2.0)
@@ -532,8 +552,7 @@ def main():
     torch.cuda.synchronize()
     build_ms = 1e3 * (time.perf_counter() - t0)
     autotuned = None
-    if not (args.chunk_rows or args.threads or args.ht != "auto" or args.ctas or args.stage != "default"
-            or args.group_agg != "default" or args.no_autotune):
+    if not _explicit_tuning(args):
         # the library's autotuner picks the launch configuration (cached
         # for this plan's signature; untimed)
         best, best_ms = eng.ctx.autotune([plan], stream, reps=3)
@@ -616,12 +635,16 @@ def main():
         "wall_s": wall,
     }
 
+    eng.ctx.release(prep)
     if chain:
         link_ms = sum(x["ms"] for x in chain)
         rows_all = fact_rows + sum(x["rows"] for x in chain)
         out["chain"] = {"links": chain, "fused_ms": ms_step, "pipeline_ms": link_ms + ms_step,
                         "pipeline_rows_per_s": rows_all / ((link_ms + ms_step) * 1e-3)}
-    eng.ctx.release(prep)
+        for mode in ("exact", "async"):
+            p = time_chain_pipeline(eng, w, stream, torch, np, records, asynchronous=mode == "async")
+            p["rows_per_s"] = rows_all / (p["wall_ms"] * 1e-3)
+            out["chain"][f"pipeline_{mode}"] = p
     links = None
     try:
         links = {"host_read_gbs": eng.ctx.read_rate("host", 2 << 30, 5, stream),
@@ -756,6 +779,58 @@ def time_chain_builds(eng, w, stream, torch, reps=5):
     for j in w["query"]["joins"]:
         walk(j)
     return links
+
+
+def time_chain_pipeline(eng, w, stream, torch, np, want, asynchronous, reps=9):
+    """A whole chain query from its tables to its records, as a user runs it
+    once per query: the chain's tables are dropped, then built (with
+    ``asynchronous``, enqueue-only builds sized from load-time bounds; else
+    the exactly sized builds, which read each kept count back), the fused
+    plan over the last table is prepared and launched on the same stream,
+    its records are read and (async) every build's status is checked.
+    ``wall_ms``: median host time of ``reps`` such queries; ``gpu_ms``:
+    CUDA events from before the first build to after the fused launch.  An
+    untimed first query autotunes the plan (the tuning is cached for its
+    signature) and every query's records must equal ``want``."""
+    def drop():
+        for sig in [k for k in eng.hts if k[0] == w["name"]]:
+            eng.ctx.drop_hash(eng.hts.pop(sig))
+
+    walls, gpus = [], []
+    for r in range(reps + 1):
+        drop()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        plan = eng.plan(w, stream, asynchronous=asynchronous)
+        if r == 0:
+            eng.ctx.autotune([plan], stream, reps=2)
+        prep = eng.ctx.prepare([plan])
+        try:
+            eng.ctx.launch(prep, stream)
+            e1.record(stream)
+            got = eng.ctx.read_result(prep, 0)
+        finally:
+            eng.ctx.release(prep)
+        if asynchronous:
+            eng.wait_joins(w)
+        t1 = time.perf_counter()
+        assert np.array_equal(got, want), "chain pipeline records differ"
+        if r:
+            walls.append(1e3 * (t1 - t0))
+            gpus.append(e0.elapsed_time(e1))
+    tables = []
+
+    def walk(j):
+        for s in j.get("joins", []):
+            walk(s)
+        tables.append(dict(eng.ctx.hash_info(eng.hts[(w["name"], repr(j))]), table=j["dim"]))
+    for j in w["query"]["joins"]:
+        walk(j)
+    return {"wall_ms": statistics.median(walls), "gpu_ms": statistics.median(gpus), "reps": reps,
+            "builds": "enqueue-only, sized from load-time bounds" if asynchronous else "exact (kept count read back)",
+            "tables": tables}
 
 
 def time_unfused(eng, plan, stream, fused_records, reps, fused_ms):

@@ -208,7 +208,8 @@ typedef struct dpf_pred {
 dpf_status dpf_build_hash(dpf_ctx* ctx, dpf_col_id key_col, const dpf_col_id* payload_cols,
                           int32_t n_payload, const dpf_pred* preds, int32_t n_preds,
                           void* stream, dpf_ht_id* out);
-/* Entries and slot capacity of a built table. */
+/* Entries and slot capacity of a built table (waits for an asynchronous
+ * build, see dpf_build_hash_async, and returns its error if it failed). */
 dpf_status dpf_hash_info(dpf_ctx* ctx, dpf_ht_id ht, uint64_t* entries, uint64_t* capacity);
 dpf_status dpf_drop_hash(dpf_ctx* ctx, dpf_ht_id ht);
 
@@ -250,6 +251,36 @@ typedef struct dpf_build {
   int32_t n_joins;   const dpf_join* joins;     /* inner joins              */
 } dpf_build;
 dpf_status dpf_build_hash_probe(dpf_ctx* ctx, const dpf_build* spec, void* stream, dpf_ht_id* out);
+
+/* Kernels #1 / #2 of Sec. 3.1 without any device-to-host read, so a chain's
+ * builds and the plan that probes the last table can be enqueued back to
+ * back on one stream (the paper launches its three kernels in sequence).
+ * The same scan as dpf_build_hash_probe (spec->n_joins may be 0), but the
+ * table is sized from what is known at load time: the key column's value
+ * bounds from its mini block headers and its row count as the bound on
+ * the rows kept.  Such a table can be larger than an exactly sized one
+ * (open addressing: 2 x the scanned rows; a rank directory: one payload
+ * word per scanned row).
+ *   stream: every kernel and copy of the build is enqueued on it, and the
+ *           call returns once they are; the table is ready when the stream
+ *           reaches that point, so plans and builds that probe it must run
+ *           on the same stream (or wait on an event recorded after it).
+ *           It cannot be captured into a CUDA graph (DPF_EINVAL): the call
+ *           allocates the table and copies its compiled scan from host
+ *           memory.
+ * Errors that only the kernels can find (a duplicate key: DPF_EDUPKEY; the
+ * reserved key INT32_MIN: DPF_EINVAL) are reported by dpf_hash_wait or
+ * dpf_hash_info, which wait for the build; a table whose build failed
+ * stays allocated (plans already enqueued may read it; every access stays
+ * within it) and is refused by later dpf_prepare and build calls.  Until
+ * then dpf_prepare uses an estimate of its entry count for step ordering.
+ * Errors at the call: DPF_EINVAL, DPF_ENOMEM, DPF_ECUDA. */
+dpf_status dpf_build_hash_async(dpf_ctx* ctx, const dpf_build* spec, void* stream, dpf_ht_id* out);
+/* Waits for a table's build (returns at once for tables built by the
+ * synchronous calls) and reports its outcome: DPF_OK, DPF_EDUPKEY,
+ * DPF_EINVAL (the reserved key or corrupt pages), DPF_EINTERNAL or
+ * DPF_ECUDA.  The same error is returned again by later calls. */
+dpf_status dpf_hash_wait(dpf_ctx* ctx, dpf_ht_id ht);
 
 enum dpf_key_kind { DPF_KEY_COLUMN = 0, DPF_KEY_PAYLOAD = 1 };
 typedef struct dpf_key {

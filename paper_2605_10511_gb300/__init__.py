@@ -135,6 +135,8 @@ _SIGS = {
     "dpf_build_hash": (C.c_int32, [_P, C.c_int32, _P, C.c_int32, C.POINTER(Pred), C.c_int32, _P,
                                    C.POINTER(C.c_int32)]),
     "dpf_build_hash_probe": (C.c_int32, [_P, C.POINTER(Build), _P, C.POINTER(C.c_int32)]),
+    "dpf_build_hash_async": (C.c_int32, [_P, C.POINTER(Build), _P, C.POINTER(C.c_int32)]),
+    "dpf_hash_wait": (C.c_int32, [_P, C.c_int32]),
     "dpf_hash_info": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "dpf_drop_hash": (C.c_int32, [_P, C.c_int32]),
     "dpf_prepare": (C.c_int32, [_P, C.POINTER(Plan), C.c_int32, C.POINTER(Tuning), C.POINTER(C.c_int32)]),
@@ -342,11 +344,14 @@ class Context:
                                     _stream_ptr(stream), C.byref(out)))
         return out.value
 
-    def build_hash_probe(self, key_col, payload=(), preds=(), joins=(), stream=None):
+    def build_hash_probe(self, key_col, payload=(), preds=(), joins=(), stream=None, asynchronous=False):
         """Scan, probe and build (one link of a join chain).  ``payload``
         items are a DICT column id or ``("join", j, field)``: payload
         ``field`` of the row's match in ``joins[j]``; ``joins`` are
-        ``(fk_col, ht)`` pairs probed from the scanned table."""
+        ``(fk_col, ht)`` pairs probed from the scanned table.  With
+        ``asynchronous`` the table is sized from load-time bounds and the
+        call only enqueues (``dpf_build_hash_async``; ``hash_wait`` reports
+        what the kernels found)."""
         pay = (Payload * max(len(payload), 1))()
         for i, p in enumerate(payload):
             pay[i] = Payload(1, 0, p[1], p[2]) if isinstance(p, tuple) else Payload(0, p, 0, 0)
@@ -355,8 +360,15 @@ class Context:
         b = Build(key_col, len(payload), C.cast(pay, C.POINTER(Payload)), len(preds),
                   C.cast(parr, C.POINTER(Pred)), len(joins), C.cast(jarr, C.POINTER(Join)))
         out = C.c_int32()
-        _check(lib().dpf_build_hash_probe(self.h, C.byref(b), _stream_ptr(stream), C.byref(out)))
+        call = lib().dpf_build_hash_async if asynchronous else lib().dpf_build_hash_probe
+        _check(call(self.h, C.byref(b), _stream_ptr(stream), C.byref(out)))
         return out.value
+
+    def build_hash_async(self, key_col, payload=(), preds=(), joins=(), stream=None):
+        return self.build_hash_probe(key_col, payload, preds, joins, stream, asynchronous=True)
+
+    def hash_wait(self, ht):
+        _check(lib().dpf_hash_wait(self.h, ht))
 
     def hash_info(self, ht):
         e, c = C.c_uint64(), C.c_uint64()

@@ -78,6 +78,13 @@ struct HashTable {
   int32_t key_lo = 1, key_hi = 0; // smallest and largest stored key (empty: lo > hi)
   uint32_t pay_dom[2] = {0, 0};
   const int32_t* pay_dict[2] = {nullptr, nullptr};
+  // asynchronous builds (dpf_build_hash_async) until finish_build
+  bool pending = false;
+  cudaEvent_t done = nullptr;     // recorded after the build's last kernel
+  DevQuery* bq = nullptr;         // the build's compiled scan
+  BuildStat* bstat = nullptr;     // its status word and inserted-row count
+  dpf_col_id key_col = 0;
+  dpf_status failed = DPF_OK;     // the error a finished build reported
 };
 
 struct Prep {
@@ -217,6 +224,22 @@ void dev_free(dpf_ctx* c, void* p) {
   } else {
     cudaFree(p);
   }
+}
+
+// Frees a table's device blocks (and an asynchronous build's launch buffers).
+static void free_table(dpf_ctx* c, HashTable& ht) {
+  dev_free(c, ht.slots);
+  dev_free(c, ht.direct);
+  dev_free(c, ht.rank);
+  dev_free(c, ht.bq);
+  dev_free(c, ht.bstat);
+  if (ht.done) cudaEventDestroy(ht.done);
+  ht.slots = nullptr;
+  ht.direct = nullptr;
+  ht.rank = nullptr;
+  ht.bq = nullptr;
+  ht.bstat = nullptr;
+  ht.done = nullptr;
 }
 
 template <class T>
@@ -644,6 +667,7 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
     const dpf_join& J = P.joins[j];
     auto ht = c->hts.find(J.ht);
     if (ht == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", J.ht);
+    if (ht->second.failed) return fail(DPF_EINVAL, "hash table %d failed to build", J.ht);
     int idx;
     dpf_status st = cs.add(J.fk_col, &idx);
     if (st) return st;
@@ -1230,11 +1254,7 @@ dpf_status dpf_destroy(dpf_ctx* c) {
     cudaDeviceSynchronize();
     for (auto& kv : c->preps) release_prep(c, kv.second.get());
     c->preps.clear();
-    for (auto& kv : c->hts) {
-      dev_free(c, kv.second.slots);
-      dev_free(c, kv.second.direct);
-      dev_free(c, kv.second.rank);
-    }
+    for (auto& kv : c->hts) free_table(c, kv.second);
     for (auto& kv : c->cols) free_column(c, kv.second);
     dev_free(c, c->bsched);
     dev_free(c, c->bcount);
@@ -1411,18 +1431,25 @@ dpf_status dpf_drop_column(dpf_ctx* c, dpf_col_id id) {
   return DPF_OK;
 }
 
-// Kernel #1 (no joins) and Kernel #2 (scan, probe, build) of Sec. 3.1.
-// Steps: the predicates in the given order, then one global-memory probe
-// per join (a miss drops the row; no group-id contribution).
-static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, dpf_ht_id* out) {
-  if (!c || !out) return fail(DPF_EINVAL, "NULL argument");
+// A hash build compiled on the host (Kernel #1 with no joins, Kernel #2
+// with joins; Sec. 3.1): the scan's steps are the predicates in the given
+// order, then one global-memory probe per join (a miss drops the row; no
+// group-id contribution).  est_kept is the planner's estimate of the rows
+// kept (the scanned rows times each step's estimated selectivity).
+struct BuildSpec {
+  DevQuery Q;
+  HashTable ht;
+  bool host = false;
+  bool wide_payload = false;
+  double est_kept = 0;
+};
+
+static dpf_status compile_build(dpf_ctx* c, const dpf_build& B, BuildSpec& bs) {
   if (B.n_payload < 0 || B.n_payload > 2 || (B.n_payload && !B.payload)) return fail(DPF_EINVAL, "0..2 payload fields");
   if (B.n_preds < 0 || B.n_preds > DPF_MAX_PREDS || (B.n_preds && !B.preds)) return fail(DPF_EINVAL, "bad predicates");
   if (B.n_joins < 0 || B.n_joins > DPF_MAX_JOINS || (B.n_joins && !B.joins)) return fail(DPF_EINVAL, "bad joins");
-  std::lock_guard<std::recursive_mutex> lk(c->mu);
-  DeviceGuard g(c->device);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  DevQuery Q;
+  DevQuery& Q = bs.Q;
+  HashTable& ht = bs.ht;
   std::memset(&Q, 0, sizeof Q);
   ColumnSet cs{c, Q};
   const dpf_col_id key_col = B.key_col;
@@ -1431,21 +1458,23 @@ static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, 
   if (st) return st;
   const Column& kc = c->cols[key_col];
   if (kc.codec != C_FOR && kc.codec != C_DELTA) return fail(DPF_EINVAL, "key column %d must be FOR or DELTA", key_col);
-  HashTable ht;
   ht.npay = B.n_payload;
   ht.dim_rows = kc.nrows;
   Q.build_key = kidx;
   Q.build_npay = B.n_payload;
+  double sel = 1.0;
   for (int i = 0; i < B.n_preds; ++i) {
     int idx;
     if ((st = cs.add(B.preds[i].col, &idx))) return st;
     if ((st = compile_pred(c->cols[B.preds[i].col], B.preds[i], Q.steps[i], idx))) return st;
+    sel *= std::min(1.0, step_selectivity(Q.steps[i], &c->cols[B.preds[i].col], nullptr));
   }
   std::vector<const HashTable*> probed;
   for (int j = 0; j < B.n_joins; ++j) {
     const dpf_join& J = B.joins[j];
     auto it = c->hts.find(J.ht);
     if (it == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", J.ht);
+    if (it->second.failed) return fail(DPF_EINVAL, "hash table %d failed to build", J.ht);
     int idx;
     if ((st = cs.add(J.fk_col, &idx))) return st;
     const int codec = c->cols[J.fk_col].codec;
@@ -1466,6 +1495,7 @@ static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, 
     }
     S.zlo = H.key_lo;
     S.zhi = H.key_hi;
+    sel *= std::min(1.0, step_selectivity(S, nullptr, &H));
     probed.push_back(&H);
   }
   for (int f = 0; f < B.n_payload; ++f) {
@@ -1493,15 +1523,92 @@ static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, 
   Q.nsteps = uint32_t(B.n_preds + B.n_joins);
   Q.nrows = cs.nrows;
   Q.page_rows = cs.page_rows;
+  bs.host = cs.host;
+  bs.wide_payload = B.n_payload == 2 && ht.pay_dom[0] == 65536 && ht.pay_dom[1] == 65536;
+  bs.est_kept = double(kc.nrows) * sel;
+  ht.table = kc.table;
+  return DPF_OK;
+}
+
+// Chooses the layout of a table for at most `kept` rows whose keys lie in
+// [lo, hi], allocates it and enqueues its initialisation on s: a direct
+// table (one word per key of the range, one load per probe) for dense
+// ranges; a rank directory (presence bits and a running count per 64 keys,
+// then the payloads in key order: 2 bits per key of the range plus a word
+// per row) for large ranges; open addressing (a power of two >= 2 x kept
+// slots) otherwise.
+static dpf_status alloc_table(dpf_ctx* c, const BuildSpec& bs, uint64_t kept, int64_t lo, int64_t hi, HashTable& ht,
+                              BuildLaunch& L, cudaStream_t s) {
+  const uint64_t range = kept && lo <= hi ? uint64_t(hi - lo + 1) : 0;
+  if (range) {
+    ht.key_lo = int32_t(lo);
+    ht.key_hi = int32_t(hi);
+  }
+  dpf_status st;
+  cudaError_t e;
+  if (!bs.wide_payload && range > kDirectMaxRange && range <= kRankMaxRange) {
+    const uint64_t nwords = (range + 63) / 64, nblocks = (nwords + 1023) / 1024;
+    ht.kind = HT_RANK;
+    ht.kmin = int32_t(lo);
+    ht.capacity = uint32_t(range);
+    const uint64_t bytes = 16 * nwords + 4 * kept;
+    if ((st = dev_alloc(c, bytes + 4 * nblocks, reinterpret_cast<void**>(&ht.rank)))) return st;
+    L.rank_dir = reinterpret_cast<uint4*>(ht.rank);
+    L.rank_pay = reinterpret_cast<uint32_t*>(ht.rank + 16 * nwords);
+    L.rank_sums = reinterpret_cast<uint32_t*>(ht.rank + bytes);
+    L.kmin = ht.kmin;
+    L.krange = ht.capacity;
+    e = cudaMemsetAsync(ht.rank, 0, 16 * nwords, s);
+  } else if (!bs.wide_payload && range <= std::max<uint64_t>(64 * kept, 1u << 20) && range <= kDirectMaxRange) {
+    ht.kind = HT_DIRECT;
+    ht.kmin = range ? int32_t(lo) : 0;
+    ht.capacity = uint32_t(range);
+    if ((st = dev_alloc_t(c, std::max<uint64_t>(range, 1), &ht.direct))) return st;
+    L.direct = ht.direct;
+    L.kmin = ht.kmin;
+    L.krange = ht.capacity;
+    e = launch_init_direct(ht.direct, uint32_t(std::max<uint64_t>(range, 1)), s);
+  } else {
+    uint64_t cap = 16;
+    while (cap < 2 * kept) cap <<= 1;
+    if (cap > (1ull << 31)) return fail(DPF_ENOMEM, "hash table of %llu entries is too large", (unsigned long long)kept);
+    if ((st = dev_alloc_t(c, cap, &ht.slots))) return st;
+    ht.kind = HT_OPEN;
+    ht.capacity = uint32_t(cap);
+    L.table = ht.slots;
+    L.mask = uint32_t(cap - 1);
+    e = launch_init_table(ht.slots, uint32_t(cap), s);
+  }
+  if (e != cudaSuccess) return fail(DPF_ECUDA, "hash table initialisation: %s", cudaGetErrorString(e));
+  return DPF_OK;
+}
+
+static dpf_status build_status_error(uint32_t status, dpf_col_id key_col) {
+  if (status & S_DUPKEY) return fail(DPF_EDUPKEY, "duplicate key in hash build of column %d", key_col);
+  if (status & S_CORRUPT) return fail(DPF_EINVAL, "key column %d holds the reserved key INT32_MIN or corrupt data", key_col);
+  return fail(DPF_EINTERNAL, "hash build status %u", status);
+}
+
+// Exact sizing: a count pass finds the kept rows and their key range, the
+// host reads them back and sizes the table, then the insert pass fills it.
+static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, dpf_ht_id* out) {
+  if (!c || !out) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BuildSpec bs;
+  dpf_status st = compile_build(c, B, bs);
+  if (st) return st;
+  HashTable& ht = bs.ht;
   DevQuery* dq;
   if ((st = dev_alloc_t(c, 1, &dq))) return st;
   BuildLaunch L{};
   L.q = dq;
   L.count = c->bcount;
   L.sched = c->bsched;
-  L.nrows = Q.nrows;
-  L.page_rows = Q.page_rows;
-  L.host_data = cs.host;
+  L.nrows = bs.Q.nrows;
+  L.page_rows = bs.Q.page_rows;
+  L.host_data = bs.host;
   L.kminmax = c->bkminmax;
   unsigned long long kept = 0;
   int32_t minmax[2] = {INT32_MAX, INT32_MIN};
@@ -1510,7 +1617,7 @@ static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, 
     dev_free(c, dq);
     return r;
   };
-  cudaError_t e = cudaMemcpyAsync(dq, &Q, sizeof Q, cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(dq, &bs.Q, sizeof bs.Q, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->bcount, 0, 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->bsched, 0, sizeof(Sched), s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->bkminmax, minmax, 8, cudaMemcpyHostToDevice, s);
@@ -1519,67 +1626,109 @@ static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, 
   if (e == cudaSuccess) e = cudaMemcpyAsync(minmax, c->bkminmax, 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cleanup(fail(DPF_ECUDA, "hash build (count): %s", cudaGetErrorString(e)));
-  // dense key ranges get a direct table (one load per probe); others open
-  // addressing with capacity a power of two >= 2 x entries
-  const uint64_t range = kept ? uint64_t(int64_t(minmax[1]) - int64_t(minmax[0]) + 1) : 0;
-  if (kept) {
-    ht.key_lo = minmax[0];
-    ht.key_hi = minmax[1];
-  }
-  const bool wide_payload = B.n_payload == 2 && ht.pay_dom[0] == 65536 && ht.pay_dom[1] == 65536;
-  if (!wide_payload && kept && range > kDirectMaxRange && range <= kRankMaxRange) {
-    // a large key range: a rank directory (2 bits per key of the range) plus
-    // the kept rows' payloads, instead of one word per key of the range
-    const uint64_t nwords = (range + 63) / 64, nblocks = (nwords + 1023) / 1024;
-    ht.kind = HT_RANK;
-    ht.kmin = minmax[0];
-    ht.capacity = uint32_t(range);
-    const uint64_t bytes = 16 * nwords + 4 * kept;
-    if ((st = dev_alloc(c, bytes + 4 * nblocks, reinterpret_cast<void**>(&ht.rank)))) return cleanup(st);
-    L.rank_dir = reinterpret_cast<uint4*>(ht.rank);
-    L.rank_pay = reinterpret_cast<uint32_t*>(ht.rank + 16 * nwords);
-    L.rank_sums = reinterpret_cast<uint32_t*>(ht.rank + bytes);
-    L.kmin = ht.kmin;
-    L.krange = ht.capacity;
-    e = cudaMemsetAsync(ht.rank, 0, 16 * nwords, s);
-  } else if (!wide_payload && range <= std::max<uint64_t>(64 * kept, 1u << 20) && range <= kDirectMaxRange) {
-    ht.kind = HT_DIRECT;
-    ht.kmin = kept ? minmax[0] : 0;
-    ht.capacity = uint32_t(range);
-    if ((st = dev_alloc_t(c, std::max<uint64_t>(range, 1), &ht.direct))) return cleanup(st);
-    L.direct = ht.direct;
-    L.kmin = ht.kmin;
-    L.krange = ht.capacity;
-    e = launch_init_direct(ht.direct, uint32_t(std::max<uint64_t>(range, 1)), s);
-  } else {
-    uint64_t cap = 16;
-    while (cap < 2 * kept) cap <<= 1;
-    if (cap > (1ull << 31)) return cleanup(fail(DPF_ENOMEM, "hash table of %llu entries is too large", kept));
-    if ((st = dev_alloc_t(c, cap, &ht.slots))) return cleanup(st);
-    ht.kind = HT_OPEN;
-    ht.capacity = uint32_t(cap);
-    L.table = ht.slots;
-    L.mask = uint32_t(cap - 1);
-    e = launch_init_table(ht.slots, uint32_t(cap), s);
+  if ((st = alloc_table(c, bs, kept, minmax[0], minmax[1], ht, L, s))) {
+    free_table(c, ht);
+    return cleanup(st);
   }
   ht.entries = kept;
-  if (e == cudaSuccess) e = launch_build_insert(L, s);
+  e = launch_build_insert(L, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&status, &c->bsched->status, 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess || status) {
-    dev_free(c, ht.slots);
-    dev_free(c, ht.direct);
-    dev_free(c, ht.rank);
+    free_table(c, ht);
     if (e != cudaSuccess) return cleanup(fail(DPF_ECUDA, "hash build (insert): %s", cudaGetErrorString(e)));
-    if (status & S_DUPKEY) return cleanup(fail(DPF_EDUPKEY, "duplicate key in hash build of column %d", key_col));
-    if (status & S_CORRUPT) return cleanup(fail(DPF_EINVAL, "key column %d holds the reserved key INT32_MIN or corrupt data", key_col));
-    return cleanup(fail(DPF_EINTERNAL, "hash build status %u", status));
+    return cleanup(build_status_error(status, B.key_col));
   }
-  ht.table = kc.table;
   ht.id = c->next_ht++;
   c->hts[ht.id] = ht;
   *out = ht.id;
   return cleanup(DPF_OK);
+}
+
+// Sizing from what is known at load time, so nothing is read back: the key
+// column's bounds from its mini block headers and its row count as the
+// bound on the kept rows.  Everything is enqueued on the stream; the
+// table's device-side status and inserted-row count are read by
+// finish_build once the stream has passed the build.
+static dpf_status build_hash_async_impl(dpf_ctx* c, const dpf_build& B, void* stream, dpf_ht_id* out) {
+  if (!c || !out) return fail(DPF_EINVAL, "NULL argument");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return fail(DPF_EINVAL, "dpf_build_hash_async allocates and copies from host memory: it cannot be captured");
+  }
+  BuildSpec bs;
+  dpf_status st = compile_build(c, B, bs);
+  if (st) return st;
+  HashTable& ht = bs.ht;
+  const Column& kc = c->cols[B.key_col];
+  BuildLaunch L{};
+  if ((st = dev_alloc_t(c, 1, &ht.bq)) || (st = dev_alloc(c, sizeof(BuildStat), reinterpret_cast<void**>(&ht.bstat)))) {
+    free_table(c, ht);
+    return st;
+  }
+  L.q = ht.bq;
+  L.sched = &ht.bstat->sched;
+  L.inserted = &ht.bstat->inserted;
+  L.nrows = bs.Q.nrows;
+  L.page_rows = bs.Q.page_rows;
+  L.host_data = bs.host;
+  cudaError_t e = cudaMemcpyAsync(ht.bq, &bs.Q, sizeof bs.Q, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ht.bstat, 0, sizeof(BuildStat), s);
+  if (e != cudaSuccess) {
+    free_table(c, ht);
+    return fail(DPF_ECUDA, "hash build: %s", cudaGetErrorString(e));
+  }
+  if ((st = alloc_table(c, bs, kc.nrows, kc.vmin, kc.vmax, ht, L, s))) {
+    cudaStreamSynchronize(s);  // the copies above write blocks that free_table returns to the cache
+    free_table(c, ht);
+    return st;
+  }
+  e = launch_build_insert(L, s);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ht.done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ht.done, s);
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s);  // nothing of the failed build may still be running when its blocks are freed
+    free_table(c, ht);
+    return fail(DPF_ECUDA, "hash build: %s", cudaGetErrorString(e));
+  }
+  ht.pending = true;
+  ht.key_col = B.key_col;
+  ht.entries = uint64_t(std::llround(bs.est_kept));  // an estimate until finish_build
+  ht.id = c->next_ht++;
+  c->hts[ht.id] = ht;
+  *out = ht.id;
+  return DPF_OK;
+}
+
+// Completes an asynchronous build: waits for it, reads its status and the
+// rows it inserted, and releases its launch buffers.  A failed build keeps
+// its error: the table stays allocated (plans already enqueued may read
+// it) but no new plan or build may use it.
+static dpf_status finish_build(dpf_ctx* c, HashTable& ht) {
+  if (!ht.pending) return ht.failed ? fail(ht.failed, "hash table %d failed to build", ht.id) : DPF_OK;
+  BuildStat bs{};
+  cudaError_t e = cudaEventSynchronize(ht.done);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bs, ht.bstat, sizeof bs, cudaMemcpyDeviceToHost, c->io);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->io);
+  if (e != cudaSuccess) return fail(DPF_ECUDA, "hash build: %s", cudaGetErrorString(e));
+  ht.pending = false;
+  dev_free(c, ht.bq);
+  dev_free(c, ht.bstat);
+  cudaEventDestroy(ht.done);
+  ht.bq = nullptr;
+  ht.bstat = nullptr;
+  ht.done = nullptr;
+  ht.entries = bs.inserted;
+  if (bs.sched.status) {
+    const dpf_status r = build_status_error(bs.sched.status, ht.key_col);
+    ht.failed = r;
+    return r;
+  }
+  return DPF_OK;
 }
 
 dpf_status dpf_build_hash(dpf_ctx* c, dpf_col_id key_col, const dpf_col_id* payload_cols, int32_t n_payload,
@@ -1604,11 +1753,27 @@ dpf_status dpf_build_hash_probe(dpf_ctx* c, const dpf_build* spec, void* stream,
   return build_hash_impl(c, *spec, stream, out);
 }
 
+dpf_status dpf_build_hash_async(dpf_ctx* c, const dpf_build* spec, void* stream, dpf_ht_id* out) {
+  if (!spec) return fail(DPF_EINVAL, "NULL build description");
+  return build_hash_async_impl(c, *spec, stream, out);
+}
+
+dpf_status dpf_hash_wait(dpf_ctx* c, dpf_ht_id id) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  auto it = c->hts.find(id);
+  if (it == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", id);
+  return finish_build(c, it->second);
+}
+
 dpf_status dpf_hash_info(dpf_ctx* c, dpf_ht_id id, uint64_t* entries, uint64_t* capacity) {
   if (!c) return fail(DPF_EINVAL, "ctx is NULL");
   std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
   auto it = c->hts.find(id);
   if (it == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", id);
+  if (dpf_status st = finish_build(c, it->second)) return st;
   if (entries) *entries = it->second.entries;
   if (capacity) *capacity = it->second.capacity;
   return DPF_OK;
@@ -1621,9 +1786,7 @@ dpf_status dpf_drop_hash(dpf_ctx* c, dpf_ht_id id) {
   auto it = c->hts.find(id);
   if (it == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", id);
   cudaDeviceSynchronize();
-  dev_free(c, it->second.slots);
-  dev_free(c, it->second.direct);
-  dev_free(c, it->second.rank);
+  free_table(c, it->second);
   c->hts.erase(it);
   return DPF_OK;
 }

@@ -56,6 +56,8 @@ constexpr unsigned long long kEmptySlot = 0x0000000080000000ull;  // {INT32_MIN,
 // open-addressing table; 2: insert into a direct table; 3: set the rows'
 // presence bits of a rank directory (a bit already set is a duplicate key);
 // 4: store the payloads of a rank table at their ranks (after rank_scan).
+// Modes 1-3 also add the rows they insert to L.inserted when it is set (a
+// table sized before its scan learns its entry count that way).
 template <bool kHost, int kMode>
 __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__ qdev, BuildLaunch L,
                                                     unsigned int* status) {
@@ -106,6 +108,7 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
         atomicOr(status, S_CORRUPT);
         continue;
       }
+      if (kMode != 4) ++kept;  // rows inserted (read only when L.inserted is set)
       const uint32_t pay = (c0 & 0xffffu) | ((c1 & 0xffffu) << 16);
       if (kMode == 2 || kMode == 3 || kMode == 4) {
         const uint32_t off = uint32_t(kv) - uint32_t(L.kmin);
@@ -159,6 +162,10 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
       atomicMin(L.kminmax, kmin);
       atomicMax(L.kminmax + 1, kmax);
     }
+  } else if (kMode != 4 && L.inserted) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) kept += __shfl_down_sync(kFull, kept, d);
+    if (lane == 0 && kept) atomicAdd(L.inserted, kept);
   }
 }
 

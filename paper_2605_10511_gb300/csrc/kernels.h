@@ -81,9 +81,16 @@ struct BuildLaunch {
   uint32_t* rank_sums;        //   scratch: one count per 1,024 directory words
   unsigned long long* count;  // device counter (count pass)
   int32_t* kminmax;           // device {min, max} of kept keys (count pass)
+  unsigned long long* inserted;  // tables sized before the scan: rows the insert pass kept (or nullptr)
   Sched* sched;               // status word
   uint64_t nrows, page_rows;
   bool host_data;
+};
+// Device-side outcome of a table sized before its scan: the build kernels'
+// status bits and the rows the insert pass kept.
+struct BuildStat {
+  Sched sched;
+  unsigned long long inserted;
 };
 cudaError_t launch_build_count(const BuildLaunch& L, cudaStream_t s);
 cudaError_t launch_build_insert(const BuildLaunch& L, cudaStream_t s);

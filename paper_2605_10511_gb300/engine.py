@@ -61,34 +61,36 @@ class Engine:
         return total, w["tables"][w["fact"]]["rows"]
 
     # ------------------------------------------------------------------ planning
-    def build_join(self, w, j, stream=None):
+    def build_join(self, w, j, stream=None, asynchronous=False):
         """Builds (or reuses) the hash table of join ``j``.  A join with
         joins of its own (a chain) has those built first; its table is then
-        built by scanning its dimension and probing theirs."""
+        built by scanning its dimension and probing theirs.  With
+        ``asynchronous`` every table of the chain is only enqueued on
+        ``stream`` (``dpf_build_hash_async``)."""
         sig = (w["name"], repr(j))
         if sig not in self.hts:
             d = j["dim"]
             preds = [make_pred(self.col(w, d, p["col"]), p["op"], p["args"]) for p in j["preds"]]
             subs = j.get("joins", [])
-            if not subs and all(isinstance(c, str) for c in j["payload"]):
+            if not subs and not asynchronous and all(isinstance(c, str) for c in j["payload"]):
                 pay = [self.col(w, d, c) for c in j["payload"]]
                 self.hts[sig] = self.ctx.build_hash(self.col(w, d, j["key"]), pay, preds, stream)
             else:
-                sub_hts = [(self.col(w, d, s["fk"]), self.build_join(w, s, stream)) for s in subs]
+                sub_hts = [(self.col(w, d, s["fk"]), self.build_join(w, s, stream, asynchronous)) for s in subs]
                 pay = [("join", c["join"], c["field"]) if isinstance(c, dict) else self.col(w, d, c)
                        for c in j["payload"]]
-                self.hts[sig] = self.ctx.build_hash_probe(self.col(w, d, j["key"]), pay, preds, sub_hts,
-                                                          stream)
+                build = self.ctx.build_hash_async if asynchronous else self.ctx.build_hash_probe
+                self.hts[sig] = build(self.col(w, d, j["key"]), pay, preds, sub_hts, stream)
         return self.hts[sig]
 
-    def build_joins(self, w, stream=None):
+    def build_joins(self, w, stream=None, asynchronous=False):
         """Builds (or reuses) the hash table of every join of ``w``'s query."""
-        return [self.build_join(w, j, stream) for j in w["query"]["joins"]]
+        return [self.build_join(w, j, stream, asynchronous) for j in w["query"]["joins"]]
 
-    def plan(self, w, stream=None):
+    def plan(self, w, stream=None, asynchronous=False):
         q = w["query"]
         f = w["fact"]
-        hts = self.build_joins(w, stream)
+        hts = self.build_joins(w, stream, asynchronous)
         preds = (Pred * max(len(q["preds"]), 1))(
             *[make_pred(self.col(w, f, p["col"]), p["op"], p["args"]) for p in q["preds"]])
         joins = (Join * max(len(q["joins"]), 1))(
@@ -110,16 +112,31 @@ class Engine:
                     self.col(w, f, next(iter(w["tables"][f]["cols"]))))
         return PlanHandle(plan, (preds, joins, keys, aggs))
 
-    def run(self, w, stream=None, tuning=None):
-        """Loads (if needed), plans, launches and reads one query's records."""
+    def run(self, w, stream=None, tuning=None, asynchronous=False):
+        """Loads (if needed), plans, launches and reads one query's records
+        (with ``asynchronous``, its tables are built by enqueue-only builds
+        on ``stream``, checked by ``hash_wait`` after the records are read)."""
         self.load_workload(w)
-        h = self.plan(w, stream)
+        h = self.plan(w, stream, asynchronous)
         prep = self.ctx.prepare([h], tuning)
         try:
             self.ctx.launch(prep, stream)
-            return self.ctx.read_result(prep, 0)
+            rec = self.ctx.read_result(prep, 0)
         finally:
             self.ctx.release(prep)
+        if asynchronous:
+            self.wait_joins(w)
+        return rec
+
+    def wait_joins(self, w):
+        """``hash_wait`` on every table of ``w``'s query, inner tables first
+        (raises the first build error)."""
+        def walk(j):
+            for s in j.get("joins", []):
+                walk(s)
+            self.ctx.hash_wait(self.hts[(w["name"], repr(j))])
+        for j in w["query"]["joins"]:
+            walk(j)
 
     def run_unfused(self, w, stream=None):
         """The same query through the unfused per-operator chain."""
