@@ -61,6 +61,7 @@ struct Column {
   std::vector<uint64_t> page_off, row_prefix;
   std::vector<int32_t> dict;
   int64_t vmin = 0, vmax = -1;    // value bounds from the mini block headers (planner statistics)
+  std::vector<int2> zones;        // host copy of the zone map (planner statistics)
   uint32_t max_bw = 0;            // FOR/DICT/DELTA: widest mini block (bits)
   uint64_t nsym = 0;              // FSST: symbols in the table
 };
@@ -575,6 +576,21 @@ void value_bounds(uint32_t codec, const uint8_t* pages, const uint64_t* page_off
   }
 }
 
+// Fraction of a column's rows in pages whose zone map meets [lo, hi]: the
+// rows a first step over that range decodes (the kernel skips the other
+// pages unread).
+double zone_fraction(const Column& col, int32_t lo, int32_t hi) {
+  if (col.nrows == 0 || col.zones.empty()) return 1.0;
+  if (lo > hi) return 0.0;
+  uint64_t kept = 0;
+  for (uint64_t p = 0; p < col.zones.size(); ++p) {
+    const int2 z = col.zones[p];
+    if (z.y < lo || z.x > hi) continue;
+    kept += std::min<uint64_t>(col.page_rows, col.nrows - p * uint64_t(col.page_rows));
+  }
+  return double(kept) / double(col.nrows);
+}
+
 // Estimated fraction of rows a step keeps, for ordering the steps: range
 // predicates assume values spread evenly over the column's bounds; a join
 // keeps the fraction of dimension rows that passed its build predicates
@@ -769,12 +785,14 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
   if (steps.size() > size_t(kMaxSteps)) return fail(DPF_EINVAL, "plan compiles to more than %d steps", kMaxSteps);
   // Step order from a small cost model (the result does not depend on it: a
   // conjunction, and group-id contributions add).  The first step runs
-  // densely over every row at a cost of about its column's bits per row; every
-  // later step runs over the survivors of the steps before it at about
-  // kSparseCost bit-equivalents per survivor (a sector read and a probe).  For
-  // a given first step, later filters go most selective first; group keys
-  // come last.  The plan's own first filter is kept unless another first
-  // step is estimated 5 % cheaper.
+  // densely over the rows of the pages its zone map keeps (the pages whose
+  // value bounds meet the step's range; the kernel skips the others
+  // unread) at a cost of about its column's bits per row; every later step
+  // runs over the survivors of the steps before it at about kSparseCost
+  // bit-equivalents per survivor (a sector read and a probe).  For a given
+  // first step, later filters go most selective first; group keys come
+  // last.  The plan's own first filter is kept unless another first step is
+  // estimated 5 % cheaper.
   constexpr double kSparseCost = 64.0;
   std::vector<size_t> filters, keys;
   for (size_t i = 0; i < steps.size(); ++i) (steps[i].kind == ST_KEY ? keys : filters).push_back(i);
@@ -782,6 +800,7 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
   for (size_t i = 0; i < steps.size(); ++i) {
     const Column& col = c->cols[cs.ids[steps[i].col]];
     if (col.nrows) bits[i] = 8.0 * double(col.bytes) / double(col.nrows) + (steps[i].kind == ST_PROBE ? 4.0 : 0.0);
+    bits[i] *= zone_fraction(col, steps[i].zlo, steps[i].zhi);
   }
   auto plan_cost = [&](size_t first, std::vector<size_t>* out) {
     std::vector<size_t> rest;
@@ -1350,6 +1369,7 @@ dpf_status dpf_load_encoded(dpf_ctx* c, const dpf_column_desc* d, const uint8_t*
     free_column(c, col);
     return st;
   }
+  col.zones = std::move(zones);
   if (codec == C_DICT) {
     if ((st = dev_alloc_t(c, dict_n, &col.d_dict)) || (st = upload(c, col.d_dict, dict, 4 * dict_n))) {
       free_column(c, col);
