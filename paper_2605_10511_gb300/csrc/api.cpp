@@ -73,6 +73,7 @@ struct HashTable {
   uint32_t capacity = 0;          // HT_OPEN slots, HT_DIRECT entries, HT_RANK keys covered
   uint32_t* direct = nullptr;     // HT_DIRECT
   uint8_t* rank = nullptr;        // HT_RANK: directory words, then payloads
+  uint8_t* stage = nullptr;       // HT_RANK while building: pair count, then the staged pairs
   int32_t kmin = 0;
   uint64_t entries = 0;
   uint64_t dim_rows = 0;          // rows of the dimension the table was built from
@@ -232,12 +233,14 @@ static void free_table(dpf_ctx* c, HashTable& ht) {
   dev_free(c, ht.slots);
   dev_free(c, ht.direct);
   dev_free(c, ht.rank);
+  dev_free(c, ht.stage);
   dev_free(c, ht.bq);
   dev_free(c, ht.bstat);
   if (ht.done) cudaEventDestroy(ht.done);
   ht.slots = nullptr;
   ht.direct = nullptr;
   ht.rank = nullptr;
+  ht.stage = nullptr;
   ht.bq = nullptr;
   ht.bstat = nullptr;
   ht.done = nullptr;
@@ -1572,13 +1575,20 @@ static dpf_status alloc_table(dpf_ctx* c, const BuildSpec& bs, uint64_t kept, in
     ht.kmin = int32_t(lo);
     ht.capacity = uint32_t(range);
     const uint64_t bytes = 16 * nwords + 4 * kept;
-    if ((st = dev_alloc(c, bytes + 4 * nblocks, reinterpret_cast<void**>(&ht.rank)))) return st;
+    if (kept > UINT32_MAX) return fail(DPF_ENOMEM, "rank table of %llu rows is too large", (unsigned long long)kept);
+    if ((st = dev_alloc(c, bytes + 4 * nblocks, reinterpret_cast<void**>(&ht.rank))) ||
+        (st = dev_alloc(c, 16 + 8 * kept, reinterpret_cast<void**>(&ht.stage))))
+      return st;
     L.rank_dir = reinterpret_cast<uint4*>(ht.rank);
     L.rank_pay = reinterpret_cast<uint32_t*>(ht.rank + 16 * nwords);
     L.rank_sums = reinterpret_cast<uint32_t*>(ht.rank + bytes);
+    L.stage_n = reinterpret_cast<unsigned long long*>(ht.stage);
+    L.rank_stage = reinterpret_cast<uint2*>(ht.stage + 16);
+    L.rank_cap = uint32_t(kept);
     L.kmin = ht.kmin;
     L.krange = ht.capacity;
     e = cudaMemsetAsync(ht.rank, 0, 16 * nwords, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ht.stage, 0, 16, s);
   } else if (!bs.wide_payload && range <= std::max<uint64_t>(64 * kept, 1u << 20) && range <= kDirectMaxRange) {
     ht.kind = HT_DIRECT;
     ht.kmin = range ? int32_t(lo) : 0;
@@ -1659,6 +1669,8 @@ static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, 
     if (e != cudaSuccess) return cleanup(fail(DPF_ECUDA, "hash build (insert): %s", cudaGetErrorString(e)));
     return cleanup(build_status_error(status, B.key_col));
   }
+  dev_free(c, ht.stage);  // the build has finished with it
+  ht.stage = nullptr;
   ht.id = c->next_ht++;
   c->hts[ht.id] = ht;
   *out = ht.id;
@@ -1738,9 +1750,11 @@ static dpf_status finish_build(dpf_ctx* c, HashTable& ht) {
   ht.pending = false;
   dev_free(c, ht.bq);
   dev_free(c, ht.bstat);
+  dev_free(c, ht.stage);
   cudaEventDestroy(ht.done);
   ht.bq = nullptr;
   ht.bstat = nullptr;
+  ht.stage = nullptr;
   ht.done = nullptr;
   ht.entries = bs.inserted;
   if (bs.sched.status) {

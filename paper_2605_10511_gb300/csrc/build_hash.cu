@@ -54,10 +54,11 @@ constexpr unsigned long long kEmptySlot = 0x0000000080000000ull;  // {INT32_MIN,
 
 // kMode 0: count kept rows and their key range; 1: insert into an
 // open-addressing table; 2: insert into a direct table; 3: set the rows'
-// presence bits of a rank directory (a bit already set is a duplicate key);
-// 4: store the payloads of a rank table at their ranks (after rank_scan).
-// Modes 1-3 also add the rows they insert to L.inserted when it is set (a
-// table sized before its scan learns its entry count that way).
+// presence bits of a rank directory (a bit already set is a duplicate key)
+// and append {key offset, payload} to the staging list, from which
+// rank_scatter places the payloads once the ranks are known.  Modes 1-3
+// also add the rows they insert to L.inserted when it is set (a table sized
+// before its scan learns its entry count that way).
 template <bool kHost, int kMode>
 __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__ qdev, BuildLaunch L,
                                                     unsigned int* status) {
@@ -108,9 +109,9 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
         atomicOr(status, S_CORRUPT);
         continue;
       }
-      if (kMode != 4) ++kept;  // rows inserted (read only when L.inserted is set)
+      ++kept;  // rows inserted (read only when L.inserted is set)
       const uint32_t pay = (c0 & 0xffffu) | ((c1 & 0xffffu) << 16);
-      if (kMode == 2 || kMode == 3 || kMode == 4) {
+      if (kMode == 2 || kMode == 3) {
         const uint32_t off = uint32_t(kv) - uint32_t(L.kmin);
         if (off >= L.krange) {
           atomicOr(status, S_INTERNAL);
@@ -118,16 +119,18 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
         }
         if (kMode == 2) {
           if (atomicCAS(L.direct + off, kAbsent, pay) != kAbsent) atomicOr(status, S_DUPKEY);
-        } else if (kMode == 3) {
+        } else {
           unsigned int* word = reinterpret_cast<unsigned int*>(L.rank_dir + (off >> 6)) + ((off >> 5) & 1u);
           const unsigned int bit = 1u << (off & 31u);
           if (atomicOr(word, bit) & bit) atomicOr(status, S_DUPKEY);
-        } else {
-          const uint4 d = L.rank_dir[off >> 6];
-          const uint32_t b = off & 63u, bb = b & 31u;
-          const uint32_t below = (b < 32 ? 0u : uint32_t(__popc(d.x))) +
-                                 uint32_t(__popc((b < 32 ? d.x : d.y) & ((1u << bb) - 1u)));
-          L.rank_pay[d.z + below] = pay;
+          // one atomic per group of lanes appending together
+          const unsigned int m = __activemask();
+          const int leader = __ffs(m) - 1;
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(L.stage_n, (unsigned long long)__popc(m));
+          base = __shfl_sync(m, base, leader) + uint32_t(__popc(m & ((1u << lane) - 1u)));
+          if (base < L.rank_cap) L.rank_stage[base] = make_uint2(off, pay);
+          else atomicOr(status, S_INTERNAL);
         }
         continue;
       }
@@ -162,14 +165,15 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
       atomicMin(L.kminmax, kmin);
       atomicMax(L.kminmax + 1, kmax);
     }
-  } else if (kMode != 4 && L.inserted) {
+  } else if (L.inserted) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) kept += __shfl_down_sync(kFull, kept, d);
     if (lane == 0 && kept) atomicAdd(L.inserted, kept);
   }
 }
 
-// Ranks of a rank directory: word w's count = the present keys in words < w.
+// Ranks of a rank directory: word w's counts = the present keys in words
+// < w (z), and that plus the word's keys 0-31 (w).
 // Pass 1: per block of 1,024 words, their total; pass 2 (one block): the
 // exclusive prefix of the block totals; pass 3: each block's words.
 constexpr uint32_t kRankBlockWords = 1024;
@@ -228,10 +232,25 @@ __global__ void rank_fill(uint4* dir, uint32_t nwords, const uint32_t* sums) {
     const uint32_t ex = block_excl_scan(w < nwords ? word_bits(d) : 0u, &total);
     if (w < nwords) {
       d.z = carry + ex;
-      d.w = 0;
+      d.w = d.z + uint32_t(__popc(d.x));
       dir[w] = d;
     }
     carry += total;
+  }
+}
+
+// Payloads of a rank table at their ranks: each staged {key offset,
+// payload} goes to the word's running count plus the set bits below it.
+__global__ void rank_scatter(const uint4* dir, const uint2* stage, const unsigned long long* n, uint32_t* pay,
+                             uint32_t cap, unsigned int* status) {
+  const uint64_t cnt = tmin<uint64_t>(*n, cap);
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < cnt; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint2 e = stage[i];
+    const uint4 d = dir[e.x >> 6];
+    const uint32_t b = e.x & 63u, bb = b & 31u;
+    const uint32_t idx = (b < 32 ? d.z : d.w) + uint32_t(__popc((b < 32 ? d.x : d.y) & ((1u << bb) - 1u)));
+    if (idx < cap) pay[idx] = e.y;
+    else atomicOr(status, S_INTERNAL);
   }
 }
 
@@ -260,7 +279,7 @@ cudaError_t launch_build_mode(const BuildLaunch& L, cudaStream_t s) {
 cudaError_t launch_build_count(const BuildLaunch& L, cudaStream_t s) { return launch_build_mode<0>(L, s); }
 
 cudaError_t launch_build_insert(const BuildLaunch& L, cudaStream_t s) {
-  if (L.rank_dir) {  // presence bits, ranks, then payloads at their ranks
+  if (L.rank_dir) {  // presence bits and staged pairs, ranks, then payloads at their ranks
     const uint32_t nwords = uint32_t((uint64_t(L.krange) + 63) >> 6);
     const uint32_t nblocks = (nwords + kRankBlockWords - 1) / kRankBlockWords;
     cudaError_t e = launch_build_mode<3>(L, s);
@@ -268,8 +287,9 @@ cudaError_t launch_build_insert(const BuildLaunch& L, cudaStream_t s) {
     rank_block_sums<<<nblocks, 256, 0, s>>>(L.rank_dir, nwords, L.rank_sums);
     rank_scan_sums<<<1, 1024, 0, s>>>(L.rank_sums, nblocks);
     rank_fill<<<nblocks, 256, 0, s>>>(L.rank_dir, nwords, L.rank_sums);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_build_mode<4>(L, s);
+    const int g = int(tmax<uint32_t>(1u, tmin<uint32_t>((L.rank_cap + 255) / 256, 2048u)));
+    rank_scatter<<<g, 256, 0, s>>>(L.rank_dir, L.rank_stage, L.stage_n, L.rank_pay, L.rank_cap, &L.sched->status);
+    return cudaGetLastError();
   }
   return L.direct ? launch_build_mode<2>(L, s) : launch_build_mode<1>(L, s);
 }

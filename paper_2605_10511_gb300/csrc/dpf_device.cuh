@@ -140,18 +140,26 @@ __device__ __forceinline__ bool step_pred(const DevStep& S, int32_t x) {
   }
 }
 
+// A rank-directory table: one 16-byte word per 64 keys of the range,
+// {presence bits of keys 0-31, of keys 32-63, present keys before the word,
+// present keys before its key 32}, then the present keys' payloads in key
+// order.  Key offset off's bits live in 32-bit word rank_bits_word(off) of
+// the directory and its running count two words later.
+__device__ __forceinline__ uint32_t rank_bits_word(uint32_t off) {
+  const uint32_t q = off >> 5;
+  return (q >> 1) * 4u + (q & 1u);
+}
+
 // Payload of key kmin + off (off < krange) in a rank-directory table, or
-// kAbsent: the key's presence bit in its directory word, then the payload
-// at the word's count of earlier keys plus the set bits below the key's.
+// kAbsent: the key's presence bit, then the payload at the half word's
+// running count plus the set bits below the key's.
 __device__ __forceinline__ uint32_t rank_entry(const void* tab, uint32_t krange, uint32_t off) {
-  const uint4* dir = static_cast<const uint4*>(tab);
-  const uint4 d = __ldg(dir + (off >> 6));
-  const uint32_t b = off & 63u, bb = b & 31u;
-  const uint32_t w = b < 32 ? d.x : d.y;
-  if (!((w >> bb) & 1u)) return kAbsent;
-  const uint32_t below = (b < 32 ? 0u : uint32_t(__popc(d.x))) + uint32_t(__popc(w & ((1u << bb) - 1u)));
-  const uint32_t* pay = reinterpret_cast<const uint32_t*>(dir + ((uint64_t(krange) + 63) >> 6));
-  return __ldg(pay + d.z + below);
+  const uint32_t* dw = static_cast<const uint32_t*>(tab);
+  const uint32_t wi = rank_bits_word(off), bb = off & 31u;
+  const uint32_t bits = __ldg(dw + wi);
+  if (!((bits >> bb) & 1u)) return kAbsent;
+  const uint32_t* pay = dw + 4 * ((uint64_t(krange) + 63) >> 6);
+  return __ldg(pay + __ldg(dw + wi + 2) + uint32_t(__popc(bits & ((1u << bb) - 1u))));
 }
 
 // Bounded linear probe of an open-addressing table of capacity mask+1.

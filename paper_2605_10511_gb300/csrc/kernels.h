@@ -79,6 +79,9 @@ struct BuildLaunch {
   uint4* rank_dir;            // rank table: (krange + 63) / 64 directory words (or nullptr)
   uint32_t* rank_pay;         //   payloads of the present keys, in key order
   uint32_t* rank_sums;        //   scratch: one count per 1,024 directory words
+  uint2* rank_stage;          //   scratch: {key offset, payload} of each inserted row, in insertion order
+  unsigned long long* stage_n;  //   its count
+  uint32_t rank_cap;          //   payload words (= staged pairs) the table holds
   unsigned long long* count;  // device counter (count pass)
   int32_t* kminmax;           // device {min, max} of kept keys (count pass)
   unsigned long long* inserted;  // tables sized before the scan: rows the insert pass kept (or nullptr)

@@ -581,6 +581,38 @@ __device__ __forceinline__ bool probe_direct(const DevStep& S, const uint8_t* st
   return hit;
 }
 
+// Dense probe of a rank-directory table: the presence-bit words of the
+// tile's rows are loaded first, all independent of one another; then, only
+// when the step adds group-id contributions, each hit's running count and
+// its payload.  Dead and out-of-range rows read directory word 0 and count
+// as misses; a miss reads no count and no payload.
+template <bool kContrib>
+__device__ __forceinline__ void dense_probe_rank(const DevStep& S, const uint32_t (&v)[TB][4], uint32_t anym,
+                                                 TileState& T) {
+  const uint32_t* dw = static_cast<const uint32_t*>(S.ht);
+  const uint32_t* pay = dw + 4 * ((uint64_t(S.krange) + 63) >> 6);
+#pragma unroll
+  for (int t = 0; t < TB; ++t) {
+    if (!((anym >> t) & 1u)) continue;
+    uint32_t keep = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint32_t off = v[t][k] - uint32_t(S.kmin);
+      const bool look = off < S.krange;
+      const uint32_t wi = look ? rank_bits_word(off) : 0u;
+      const uint32_t bits = __ldg(dw + wi);
+      const bool hit = look && ((bits >> (off & 31u)) & 1u);
+      keep |= uint32_t(hit) << k;
+      if (kContrib) {
+        const uint32_t idx = hit ? __ldg(dw + wi + 2) + uint32_t(__popc(bits & ((1u << (off & 31u)) - 1u))) : 0u;
+        const uint32_t e = hit ? __ldg(pay + idx) : 0u;
+        T.gid[t][k] += hit ? (e & 0xffffu) * S.mul0 + (e >> 16) * S.mul1 : 0u;
+      }
+    }
+    T.alive &= ~((~keep & 15u) << (4 * t));
+  }
+}
+
 // Join probe step over a decoded tile: live rows that miss are dropped;
 // hits add this join's group-id contribution.
 template <int kMode, bool kContrib = true>
@@ -839,8 +871,14 @@ __device__ __forceinline__ void dense_step_t(const DevQuery& Q, const DevStep& S
         case PM_S2: dense_probe<PM_S2, kGid>(S, stab, v, anym, T, status); break;
         case PM_S4: dense_probe<PM_S4, kGid>(S, stab, v, anym, T, status); break;
         case PM_GDIRECT:
-          if (kGid && (S.mul0 | S.mul1)) dense_probe<PM_GDIRECT, kGid>(S, stab, v, anym, T, status);
-          else dense_probe<PM_GDIRECT, false>(S, stab, v, anym, T, status);
+          if (S.ht_kind == HT_RANK) {
+            if (kGid && (S.mul0 | S.mul1)) dense_probe_rank<kGid>(S, v, anym, T);
+            else dense_probe_rank<false>(S, v, anym, T);
+          } else if (kGid && (S.mul0 | S.mul1)) {
+            dense_probe<PM_GDIRECT, kGid>(S, stab, v, anym, T, status);
+          } else {
+            dense_probe<PM_GDIRECT, false>(S, stab, v, anym, T, status);
+          }
           break;
         default: dense_probe<PM_OPEN, kGid>(S, stab, v, anym, T, status); break;
       }
