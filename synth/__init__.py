@@ -10,6 +10,7 @@ each with its own code.
 from .tables import (  # noqa: F401
     ALPHABET,
     batched_workloads,
+    bigint_filter_star,
     chain_join,
     date_keys,
     hot_groups,

@@ -290,6 +290,26 @@ def chain_join(rows=1 << 26, seed=5, page_rows=DEFAULT_PAGE_ROWS, orders_per_row
             "fact": "lineitem", "query": query}
 
 
+def bigint_filter_star(rows=1 << 16, seed=7, page_rows=DEFAULT_PAGE_ROWS, preds=None, joins=True):
+    """The star join with its measure m1 stored as a BIGINT (FOR64) column
+    (m1 x 2^20 + m2, values up to about 2^43) and predicates on that
+    measure, so bounds above and below 2^32 are compared in 64 bits.
+    ``preds`` defaults to m1 BETWEEN 2^35 AND 2^42.  With ``joins=False``
+    the joins and group keys are dropped and only the fact table is kept:
+    the 64-bit predicates are then the plan's only filters (COUNT(*) and
+    SUM(m1) over the fact alone)."""
+    w = star_join(rows, seed, page_rows, clustered=False, bigint_measure=True)
+    q = w["query"]
+    q["preds"] = list(preds) if preds is not None else [{"col": "m1", "op": "between", "args": [1 << 35, 1 << 42]}]
+    if not joins:
+        q["joins"] = []
+        q["group"] = []
+        q["aggs"] = [{"op": "count"}, {"op": "sum", "cols": ["m1"]}]
+        w["tables"] = {"fact": w["tables"]["fact"]}
+    w["name"] = f"star_bigint_filter_{rows}_{seed}{'' if joins else '_alone'}"
+    return w
+
+
 def tiny_chain_workload(seed, rows=None, page_rows=None, max_dim_rows=None):
     """A random small chain (fact -> mid -> leaf, sometimes -> leaf2 below
     leaf, sometimes a second table probed by mid) with random predicates,
