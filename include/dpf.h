@@ -102,7 +102,8 @@ enum dpf_codec {
                           int64 base, a bit width 0..64 and 2*bw packed 64-bit words,
                           field j at bit j*bw (a field may cross into the next word).
                           A plan reads FOR64 columns as aggregate operands (int64,
-                          wrapping); predicates, joins and keys take 32-bit columns */
+                          wrapping) and in predicates (int64 compares; see dpf_op);
+                          joins and group keys take 32-bit columns                  */
 };
 /* Where a column's pages live: device HBM, or pinned host memory read by
  * the kernel directly through the host link (oversize tables). */
@@ -164,6 +165,10 @@ dpf_status dpf_column_read(dpf_ctx* ctx, dpf_col_id col, uint64_t offset, uint64
 dpf_status dpf_drop_column(dpf_ctx* ctx, dpf_col_id col);
 
 /* --------------------------------------------------------- predicates */
+/* On a FOR64 (BIGINT) column the comparisons, BETWEEN and IN with one
+ * operand compare the int64 value with the int64 operands (other ops:
+ * DPF_EINVAL).  Such a predicate runs over the rows that pass the other
+ * steps; when every filter of a scan is one, every row is decoded for it. */
 enum dpf_op {
   DPF_OP_LT = 0, DPF_OP_LE = 1, DPF_OP_GT = 2, DPF_OP_GE = 3, DPF_OP_EQ = 4,
   DPF_OP_NE = 5,

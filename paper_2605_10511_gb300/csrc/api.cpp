@@ -399,7 +399,38 @@ dpf_status validate_fsst_codes(const uint8_t* pages, const uint64_t* page_off, u
 dpf_status compile_pred_body(const Column& c, const dpf_pred& p, DevStep& S, int col_index) {
   std::memset(&S, 0, sizeof S);
   S.col = uint8_t(col_index);
-  if (c.codec == C_FOR64) return fail(DPF_EINVAL, "predicates take 32-bit or string columns; column %d is FOR64", c.id);
+  if (c.codec == C_FOR64) {
+    // BIGINT (Sec. 4.1, 64-bit GPU-FOR): the int64 value against int64
+    // operands, as an int64 range or its complement
+    int64_t lo = INT64_MIN, hi = INT64_MAX;
+    bool neg = false;
+    switch (p.op) {
+      case DPF_OP_LT:
+        if (p.v[0] == INT64_MIN) lo = 1, hi = 0;
+        else hi = p.v[0] - 1;
+        break;
+      case DPF_OP_LE: hi = p.v[0]; break;
+      case DPF_OP_GT:
+        if (p.v[0] == INT64_MAX) lo = 1, hi = 0;
+        else lo = p.v[0] + 1;
+        break;
+      case DPF_OP_GE: lo = p.v[0]; break;
+      case DPF_OP_EQ: lo = hi = p.v[0]; break;
+      case DPF_OP_NE: lo = hi = p.v[0]; neg = true; break;
+      case DPF_OP_BETWEEN: lo = p.v[0]; hi = p.v[1]; break;
+      case DPF_OP_IN:
+        if (p.n != 1) return fail(DPF_EINVAL, "IN on FOR64 column %d takes one operand (got %d)", c.id, p.n);
+        lo = hi = p.v[0];
+        break;
+      default: return fail(DPF_EINVAL, "predicate op %d does not apply to FOR64 column %d", p.op, c.id);
+    }
+    S.kind = neg ? ST_NOTRANGE64 : ST_RANGE64;
+    S.in[0] = int32_t(uint32_t(uint64_t(lo)));
+    S.in[1] = int32_t(uint32_t(uint64_t(lo) >> 32));
+    S.in[2] = int32_t(uint32_t(uint64_t(hi)));
+    S.in[3] = int32_t(uint32_t(uint64_t(hi) >> 32));
+    return DPF_OK;
+  }
   if (p.op == DPF_OP_PREFIX || p.op == DPF_OP_CONTAINS || p.op == DPF_OP_LIKE) {
     if (!is_str_codec(uint32_t(c.codec)))
       return fail(DPF_EINVAL, "PREFIX / CONTAINS / LIKE need a STR or FSST column (column %d)", c.id);
@@ -603,6 +634,9 @@ double step_selectivity(const DevStep& S, const Column* col, const HashTable* ht
     case ST_FALSE: return 0.0;
     case ST_KEY: return 2.0;  // not a filter: after every filter
     case ST_PROBE: return ht && ht->dim_rows ? double(ht->entries) / double(ht->dim_rows) : 1.0;
+    case ST_RANGE64:
+    case ST_NOTRANGE64: return 0.5;  // no 64-bit value bounds are kept
+    case ST_ALL: return 1.0;
     case ST_PREFIX: return std::pow(0.1, double(S.plen));
     case ST_CONTAINS: return std::min(1.0, 30.0 * std::pow(0.1, double(S.plen)));
     case ST_LIKE: {
@@ -823,13 +857,33 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
     }
     return cost;
   };
+  // A 64-bit range (a FOR64 column) runs only over survivors, never as the
+  // dense first step; when every filter is one, a pass-all first step that
+  // reads nothing leads.
+  std::vector<size_t> leads;
+  for (size_t f : filters)
+    if (!is_step64(steps[f].kind)) leads.push_back(f);
+  if (!filters.empty() && leads.empty()) {
+    DevStep A;
+    std::memset(&A, 0, sizeof A);
+    A.kind = ST_ALL;
+    A.col = steps[filters[0]].col;
+    A.zlo = INT32_MIN;
+    A.zhi = INT32_MAX;
+    steps.push_back(A);
+    sel.push_back(1.0);
+    bits.push_back(0.0);
+    leads.push_back(steps.size() - 1);
+    filters.push_back(steps.size() - 1);
+    if (steps.size() > size_t(kMaxSteps)) return fail(DPF_EINVAL, "plan compiles to more than %d steps", kMaxSteps);
+  }
   std::vector<size_t> order(steps.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = i;
   if (!filters.empty()) {
-    size_t best = filters[0];
+    size_t best = leads[0];
     double best_cost = plan_cost(best, nullptr);
     const double own = best_cost;
-    for (size_t f : filters) {
+    for (size_t f : leads) {
       const double cst = plan_cost(f, nullptr);
       if (cst < best_cost && cst < 0.95 * own) {
         best = f;
@@ -845,7 +899,8 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
   // mini blocks into L2 while the dense tiles run, so that step's
   // per-survivor reads hit L2 instead of waiting on DRAM.
   if (steps.size() > 1 && sel[order[0]] >= kPrefetchMinSel && Q.steps[1].kind != ST_PREFIX &&
-      Q.steps[1].kind != ST_CONTAINS && Q.steps[1].kind != ST_LIKE)
+      Q.steps[1].kind != ST_CONTAINS && Q.steps[1].kind != ST_LIKE && !is_step64(Q.steps[1].kind) &&
+      Q.steps[0].kind != ST_ALL)
     Q.pf_step = 1;
   Q.nrows = cs.nrows;
   Q.page_rows = cs.page_rows;
@@ -1054,6 +1109,7 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
       const DevStep& S0 = Q.steps[0];
       const DevColumn& C0 = Q.cols[S0.col];
       const bool ok = Q.nsteps != 0 && S0.kind != ST_PREFIX && S0.kind != ST_CONTAINS && S0.kind != ST_LIKE &&
+                      S0.kind != ST_ALL &&
                       (C0.codec == C_FOR || C0.codec == C_DICT || C0.codec == C_DELTA) && C0.max_bw <= 32;
       all = all && ok;
       if (ok) stage_bw = std::max(stage_bw, std::max<uint32_t>(C0.max_bw, 1u));
@@ -1485,12 +1541,38 @@ static dpf_status compile_build(dpf_ctx* c, const dpf_build& B, BuildSpec& bs) {
   ht.dim_rows = kc.nrows;
   Q.build_key = kidx;
   Q.build_npay = B.n_payload;
-  double sel = 1.0;
+  // Predicates in the given order, 32-bit ones first: a 64-bit range (a
+  // FOR64 column) runs over survivors only, and when every predicate is one
+  // a pass-all step that reads nothing leads (base = 1).
+  std::vector<int> porder;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int i = 0; i < B.n_preds; ++i) {
+      auto it = c->cols.find(B.preds[i].col);
+      const bool wide = it != c->cols.end() && it->second.codec == C_FOR64;
+      if (wide == (pass == 1)) porder.push_back(i);
+    }
+  bool all_wide = B.n_preds > 0;
   for (int i = 0; i < B.n_preds; ++i) {
+    auto it = c->cols.find(B.preds[i].col);
+    all_wide = all_wide && it != c->cols.end() && it->second.codec == C_FOR64;
+  }
+  const int base = all_wide ? 1 : 0;
+  if (base + B.n_preds + B.n_joins > kMaxSteps) return fail(DPF_EINVAL, "build compiles to more than %d steps", kMaxSteps);
+  double sel = 1.0;
+  for (int k = 0; k < B.n_preds; ++k) {
+    const dpf_pred& pr = B.preds[porder[size_t(k)]];
     int idx;
-    if ((st = cs.add(B.preds[i].col, &idx))) return st;
-    if ((st = compile_pred(c->cols[B.preds[i].col], B.preds[i], Q.steps[i], idx))) return st;
-    sel *= std::min(1.0, step_selectivity(Q.steps[i], &c->cols[B.preds[i].col], nullptr));
+    if ((st = cs.add(pr.col, &idx))) return st;
+    if ((st = compile_pred(c->cols[pr.col], pr, Q.steps[base + k], idx))) return st;
+    sel *= std::min(1.0, step_selectivity(Q.steps[base + k], &c->cols[pr.col], nullptr));
+  }
+  if (base) {
+    DevStep& A = Q.steps[0];
+    std::memset(&A, 0, sizeof A);
+    A.kind = ST_ALL;
+    A.col = Q.steps[1].col;
+    A.zlo = INT32_MIN;
+    A.zhi = INT32_MAX;
   }
   std::vector<const HashTable*> probed;
   for (int j = 0; j < B.n_joins; ++j) {
@@ -1503,7 +1585,7 @@ static dpf_status compile_build(dpf_ctx* c, const dpf_build& B, BuildSpec& bs) {
     const int codec = c->cols[J.fk_col].codec;
     if (codec != C_FOR && codec != C_DELTA) return fail(DPF_EINVAL, "join column %d must be FOR or DELTA", J.fk_col);
     const HashTable& H = it->second;
-    DevStep& S = Q.steps[B.n_preds + j];
+    DevStep& S = Q.steps[base + B.n_preds + j];
     std::memset(&S, 0, sizeof S);
     S.kind = ST_PROBE;
     S.col = uint8_t(idx);
@@ -1536,14 +1618,14 @@ static dpf_status compile_build(dpf_ctx* c, const dpf_build& B, BuildSpec& bs) {
       const HashTable& H = *probed[size_t(F.join)];
       if (F.field < 0 || F.field >= H.npay) return fail(DPF_EINVAL, "hash table %d has no payload field %d", H.id, F.field);
       // the build kernel decodes -1 - (2 * step + field)
-      Q.build_pay[f] = -1 - (2 * (B.n_preds + F.join) + F.field);
+      Q.build_pay[f] = -1 - (2 * (base + B.n_preds + F.join) + F.field);
       ht.pay_dom[f] = H.pay_dom[F.field];
       ht.pay_dict[f] = H.pay_dict[F.field];
     } else {
       return fail(DPF_EINVAL, "unknown payload kind %d", F.kind);
     }
   }
-  Q.nsteps = uint32_t(B.n_preds + B.n_joins);
+  Q.nsteps = uint32_t(base + B.n_preds + B.n_joins);
   Q.nrows = cs.nrows;
   Q.page_rows = cs.page_rows;
   bs.host = cs.host;

@@ -76,15 +76,26 @@ enum StepKind : uint8_t {
   ST_PREFIX = 5,    // STR column starts with pfx[0..plen)
   ST_PROBE = 6,     // hash probe; a miss drops the row, a hit adds payload fields to gid
   ST_KEY = 7,       // DICT column code added to gid
+  ST_RANGE64 = 11,     // FOR64 column: lo64 <= x <= hi64 (int64 bounds in in[0..3]); never a first step
+  ST_NOTRANGE64 = 12,  // FOR64 column: !(lo64 <= x <= hi64)
+  ST_ALL = 13,      // every row passes, nothing decoded: the first step of a scan whose filters are all 64-bit
 };
+
+// int64 bounds of an ST_RANGE64 / ST_NOTRANGE64 step, kept in the IN
+// operand words: in[0..1] = lo64 (low word first), in[2..3] = hi64.
+__host__ __device__ inline int64_t step_bound64(const int32_t* in, int i) {
+  return int64_t((uint64_t(uint32_t(in[2 * i + 1])) << 32) | uint64_t(uint32_t(in[2 * i])));
+}
+__host__ __device__ inline bool is_step64(uint8_t kind) { return kind == 11 || kind == 12; }
 
 // Join tables (Sec. 3.1 hash tables; representation chosen at build):
 //  HT_OPEN   open addressing, slots {key, payload}, linear probing;
 //  HT_DIRECT dense key range: entry[key - kmin] = payload or kAbsent;
 //  HT_RANK   large, sparsely filled key range: a rank directory of 16-byte
-//            words {presence bits of 64 consecutive keys (two u32), number
-//            of present keys before the word, 0}, followed by the payloads
-//            of the present keys in key order (rank_entry).
+//            words {presence bits of keys 0-31 and of keys 32-63 of 64
+//            consecutive keys, present keys before the word, present keys
+//            before its key 32}, followed by the payloads of the present
+//            keys in key order (rank_entry).
 // payload = code0 | code1 << 16 (dictionary codes of the payload columns).
 enum HtKind : uint8_t { HT_OPEN = 0, HT_DIRECT = 1, HT_RANK = 2 };
 constexpr uint32_t kAbsent = 0xffffffffu;

@@ -208,38 +208,6 @@ __device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, 
   }
 }
 
-// Value of a FOR64 column (Sec. 4.1, 64-bit GPU-FOR) at segment row r: the
-// mini block's 16-byte header {base, word offset, bit width} and the row's
-// field at bit (r % 128) * bw of the mini block's 64-bit words, read through
-// a 128-bit window (the second word only when the field crosses into it).
-// Other integer columns are read as int32 and sign-extended.  Warp-uniform
-// call (c is uniform); lanes with !valid return 0.
-template <bool kHost>
-__device__ __forceinline__ long long value64(const DevQuery& Q, int c, const PageState& P, uint32_t seg_mb,
-                                             uint32_t r, bool valid, int lane, unsigned int* status) {
-  if (Q.cols[c].codec != C_FOR64) return (long long)int32_t(row_value<kHost>(Q, c, P, seg_mb, r, valid, lane, status));
-  const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, c));
-  if (!valid) return 0;
-  const uint4 h = ld_u4<kHost>(reinterpret_cast<const uint4*>(pg + kPageHdr + uint64_t(seg_mb + (r >> 7)) * 16));
-  const unsigned long long base = (unsigned long long)h.x | ((unsigned long long)h.y << 32);
-  const uint32_t bw = tmin<uint32_t>(h.w, 64u);  // validated at load
-  unsigned long long x = 0;
-  if (bw != 0) {
-    const uint2* pay = reinterpret_cast<const uint2*>(pg + payload_offset(C_FOR64, P.prow));
-    const uint32_t bit = (r & (kMB - 1)) * bw;
-    const uint2* p = pay + h.z + (bit >> 6);
-    const uint32_t sh = bit & 63u;
-    const uint2 lo = ld_u2<kHost>(p);
-    x = ((unsigned long long)lo.x | ((unsigned long long)lo.y << 32)) >> sh;
-    if (sh + bw > 64) {
-      const uint2 hi = ld_u2<kHost>(p + 1);
-      x |= ((unsigned long long)hi.x | ((unsigned long long)hi.y << 32)) << (64 - sh);
-    }
-    if (bw < 64) x &= (1ull << bw) - 1ull;
-  }
-  return (long long)(base + x);
-}
-
 // An aggregate with a FOR64 operand: one survivor per lane, int64 operands,
 // arithmetic modulo 2^64.  Inlined: an out-of-line call made the caller
 // spill around it, while inlined it leaves the 32-bit passes' register

@@ -955,6 +955,7 @@ __device__ __forceinline__ void tile_dense_step(const DevQuery& Q, uint32_t s, c
                                                 StagedPay sp = StagedPay{nullptr, 0, 0}) {
   if (s >= Q.nsteps) return;
   const DevStep& S = Q.steps[s];
+  if (S.kind == ST_ALL) return;  // every row passes; its column is never read
   if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS || S.kind == ST_LIKE) {
     if (!kStaged) tile_prefix<kHost, kText>(Q, S, P, Hd, T, lane, status, stab);
     else if (lane == 0) atomicOr(status, S_INTERNAL);
@@ -1209,8 +1210,41 @@ __device__ __forceinline__ uint32_t list_step_t(const DevQuery& Q, const DevStep
   return out;
 }
 
-// A later step on a DELTA column or a PREFIX step (dense decode of the
-// round's mini blocks); kept out of line.
+// Value of a FOR64 column (Sec. 4.1, 64-bit GPU-FOR) at segment row r: the
+// mini block's 16-byte header {base, word offset, bit width} and the row's
+// field at bit (r % 128) * bw of the mini block's 64-bit words, read through
+// a 128-bit window (the second word only when the field crosses into it).
+// Other integer columns are read as int32 and sign-extended.  Warp-uniform
+// call (c is uniform); lanes with !valid return 0.
+template <bool kHost>
+__device__ __forceinline__ long long value64(const DevQuery& Q, int c, const PageState& P, uint32_t seg_mb,
+                                             uint32_t r, bool valid, int lane, unsigned int* status) {
+  if (Q.cols[c].codec != C_FOR64) return (long long)int32_t(row_value<kHost>(Q, c, P, seg_mb, r, valid, lane, status));
+  const uint8_t* pg = reinterpret_cast<const uint8_t*>(__shfl_sync(kFull, P.pg, c));
+  if (!valid) return 0;
+  const uint4 h = ld_u4<kHost>(reinterpret_cast<const uint4*>(pg + kPageHdr + uint64_t(seg_mb + (r >> 7)) * 16));
+  const unsigned long long base = (unsigned long long)h.x | ((unsigned long long)h.y << 32);
+  const uint32_t bw = tmin<uint32_t>(h.w, 64u);  // validated at load
+  unsigned long long x = 0;
+  if (bw != 0) {
+    const uint2* pay = reinterpret_cast<const uint2*>(pg + payload_offset(C_FOR64, P.prow));
+    const uint32_t bit = (r & (kMB - 1)) * bw;
+    const uint2* p = pay + h.z + (bit >> 6);
+    const uint32_t sh = bit & 63u;
+    const uint2 lo = ld_u2<kHost>(p);
+    x = ((unsigned long long)lo.x | ((unsigned long long)lo.y << 32)) >> sh;
+    if (sh + bw > 64) {
+      const uint2 hi = ld_u2<kHost>(p + 1);
+      x |= ((unsigned long long)hi.x | ((unsigned long long)hi.y << 32)) << (64 - sh);
+    }
+    if (bw < 64) x &= (1ull << bw) - 1ull;
+  }
+  return (long long)(base + x);
+}
+
+// A later step on a DELTA column, a string step (dense decode of the
+// round's mini blocks) or a 64-bit range over a FOR64 column (one field per
+// survivor, value64); kept out of line.
 template <bool kHost, bool kText = true>
 __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevStep& S, const PageState& P,
                                                    uint32_t seg_mb, uint32_t* list, uint32_t n,
@@ -1225,6 +1259,10 @@ __device__ __noinline__ uint32_t list_step_generic(const DevQuery& Q, const DevS
     bool keep;
     if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS || S.kind == ST_LIKE) {
       keep = row_prefix<kHost, kText>(Q, S, P, seg_mb, r, valid, lane, status, stab);
+    } else if (is_step64(S.kind)) {
+      const int64_t x = value64<kHost>(Q, S.col, P, seg_mb, r, valid, lane, status);
+      const bool in = step_bound64(S.in, 0) <= x && x <= step_bound64(S.in, 1);
+      keep = valid && (in != (S.kind == ST_NOTRANGE64));
     } else {
       const uint32_t v = row_value<kHost>(Q, S.col, P, seg_mb, r, valid, lane, status);
       if (S.kind == ST_PROBE) {
@@ -1259,7 +1297,8 @@ __device__ __forceinline__ uint32_t list_steps(const DevQuery& Q, const PageStat
                                                unsigned int* status, uint32_t first = 1) {
   for (uint32_t s = first; s < Q.nsteps && n != 0; ++s) {
     const DevStep& S = Q.steps[s];
-    if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS || S.kind == ST_LIKE || Q.cols[S.col].codec == C_DELTA) {
+    if (S.kind == ST_PREFIX || S.kind == ST_CONTAINS || S.kind == ST_LIKE || Q.cols[S.col].codec == C_DELTA ||
+        is_step64(S.kind)) {
       n = list_step_generic<kHost, kText>(Q, S, P, seg_mb, list, n, stab, lane, status);
       continue;
     }

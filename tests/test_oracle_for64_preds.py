@@ -64,3 +64,35 @@ def test_bounds_cut_values_above_2_32(oracle_lib):
     assert int(got["count"][0]) == int((v > (1 << 40)).sum())
     assert int(got["val"][0][0]) == int((v > (1 << 40)).sum())  # the COUNT aggregate
     assert int(got["val"][0][1]) == int(v[v > (1 << 40)].sum())
+
+
+def with_dim_bigint(w, preds, seed=3):
+    """w with a BIGINT column ``big`` (values up to about 2^41) added to
+    dim1 and ``preds`` on it added to dim1's build predicates."""
+    rng = np.random.default_rng(seed)
+    d = w["tables"]["dim1"]
+    d["cols"]["big"] = {"codec": "for64",
+                        "values": rng.integers(-(1 << 40), 1 << 41, d["rows"], dtype=np.int64)}
+    j = w["query"]["joins"][0]
+    j["preds"] = list(j["preds"]) + list(preds)
+    return w
+
+
+DIM_CASES = {
+    "with_a_32_bit_predicate": lambda: [{"col": "big", "op": "gt", "args": [0]}],
+    "only_64_bit": "only",
+    "ne": lambda: [{"col": "big", "op": "ne", "args": [7]}],
+}
+
+
+@pytest.mark.parametrize("case", sorted(DIM_CASES))
+def test_dimension_build_with_a_bigint_predicate(oracle_lib, case):
+    w = synth.bigint_filter_star(ROWS, 9, 4096)
+    if DIM_CASES[case] == "only":
+        w["query"]["joins"][0]["preds"] = []
+        w = with_dim_bigint(w, [{"col": "big", "op": "between", "args": [-(1 << 35), 1 << 39]}])
+    else:
+        w = with_dim_bigint(w, DIM_CASES[case]())
+    want = npeval.evaluate(w)
+    _records_equal(oracle_lib.run_query(w, from_encoded=False), want)
+    _records_equal(oracle_lib.run_query(w, from_encoded=True), want)
