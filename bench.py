@@ -94,6 +94,27 @@ def stored_traffic(workload, fact_rows, alg_bytes=None):
         return None, "no capture"
 
 
+def stored_link_bytes(workload, fact_rows):
+    """Bytes the host-resident variant's fused kernel received over the host
+    link per launch (ncu ctc__rx_bytes_data_user.sum from the committed
+    summary of that capture, scaled by rows), or None when absent or taken
+    on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"fused_kernel_{workload}_host.txt")
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and not line.startswith(" "):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_hash") != kernel_source_hash():
+            return None, "stale (kernel changed since capture)"
+        rows = float(kv["captured_rows"])
+        return float(kv["link_bytes_per_launch"]) * fact_rows / rows, f"ncu capture at {int(rows)} rows, scaled by rows"
+    except Exception:  # noqa: BLE001
+        return None, "no capture"
+
+
 def _workload(name, rows):
     import synth
     if name == "star":
@@ -658,9 +679,19 @@ def main():
     if not args.no_e2e:
         out["e2e"] = e2e_host_resident(dpf, w, args, local, tuning)
         if links and out["e2e"].get("value"):
-            rate = out["e2e"]["h2d_bytes_per_step"] * out["e2e"]["value"] / fact_rows / 1e9
-            out["e2e"]["host_link_gbs"] = rate
-            out["e2e"]["frac_of_host_link"] = rate / links["host_read_gbs"]
+            e = out["e2e"]
+            step_s = fact_rows / e["value"]
+            rate = e["h2d_bytes_per_step"] / step_s / 1e9
+            e["page_bytes_gbs"] = rate
+            e["page_bytes_frac_of_host_link"] = rate / links["host_read_gbs"]
+            link, src = stored_link_bytes(args.workload, fact_rows)
+            if link is not None:
+                # the kernel reads only the sectors holding a survivor's field of
+                # the later steps' columns: the bytes that crossed the link
+                e["link_bytes_per_step"] = link
+                e["link_gbs"] = link / step_s / 1e9
+                e["frac_of_host_link"] = e["link_gbs"] / links["host_read_gbs"]
+                e["link_bytes_source"] = src
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baselines(w)
     if rank == 0 and world == 1 and not args.no_extras and args.workload == "star":
@@ -874,6 +905,8 @@ def e2e_host_resident(dpf, w, args, device, tuning):
     import torch
     w2 = copy.copy(w)
     w2["name"] = w["name"] + "_host"
+    if tuning is not None and tuning.threads > 256:  # the wide CTAs take device-resident pages only
+        tuning = dpf.Tuning(tuning.chunk_rows, 0, tuning.ht_placement, 0, tuning.staging, tuning.group_agg)
     eng = dpf.Engine(device=device)
     try:
         eng.load_workload(w2, fact_placement="host")

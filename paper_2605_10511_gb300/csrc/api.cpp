@@ -153,8 +153,8 @@ struct DeviceGuard {
   }
 };
 
-constexpr uint64_t kCacheMaxBytes = uint64_t(1) << 30;  // freed bytes kept for reuse
-constexpr uint64_t kCacheMaxBlock = uint64_t(64) << 20; // larger blocks are returned at once
+constexpr uint64_t kCacheMaxBytes = uint64_t(8) << 30;  // freed bytes kept for reuse
+constexpr uint64_t kCacheMaxBlock = uint64_t(1) << 30;  // larger blocks are returned at once
 
 void drop_cache(dpf_ctx* c) {
   for (auto& kv : c->cache) cudaFree(kv.second);
