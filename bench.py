@@ -57,15 +57,40 @@ KERNEL_SOURCES = ("fused.cu", "fused_kernel.cuh", "fused_lean.cu", "fused_text.c
                   "dpf_device.cuh", "dpf_internal.h", "kernels.h")
 
 
-def kernel_source_hash():
-    """Hash of the sources that define the fused kernel: ties stored ncu
-    counters to the kernel build they were taken on."""
+def _code_only(src):
+    """C++ source without its comments and blank lines (string and character
+    literals kept as they are): what the compiler sees."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            while i < n and src[i] != "\n":
+                i += 1
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(line.rstrip() for line in "".join(out).splitlines() if line.strip())
+
+
+def kernel_source_hash(root=None):
+    """Hash of the code (comments and blank lines left out) of the sources
+    that define the fused kernel: ties stored ncu counters to the kernel
+    build they were taken on."""
     import hashlib
-    d = os.path.join(ROOT, "paper_2605_10511_gb300", "csrc")
+    d = os.path.join(root or ROOT, "paper_2605_10511_gb300", "csrc")
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(d, name), "rb") as f:
-            h.update(name.encode() + b"\0" + f.read())
+        with open(os.path.join(d, name), encoding="utf-8") as f:
+            h.update(name.encode() + b"\0" + _code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

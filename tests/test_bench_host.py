@@ -68,3 +68,15 @@ def test_cpu_baselines_and_percentiles():
     assert cb["cores"] == cb["nproc"] >= 1 and cb["value"] > 0 and cb["one_thread"]["cores"] == 1
     q = bench.pcts([3.0, 1.0, 2.0, 4.0, 5.0])
     assert q["p50"] == 3.0 and q["p90"] == 5.0 and q["mean"] == 3.0 and q["n"] == 5
+
+
+def test_kernel_source_hash_ignores_comments_only():
+    """The hash that ties stored ncu counters to the kernel code changes with
+    the code and not with comments or blank lines."""
+    a = "int f(int x) {  // doubles x\n  return 2 * x; /* no overflow check */\n}\n"
+    b = "// a header comment\nint f(int x) {\n\n  return 2 * x;\n}\n"
+    c = "int f(int x) {\n  return 3 * x;\n}\n"
+    s = 'const char* p = "// not a comment"; char q = \'"\';\n'
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
+    assert bench._code_only(s) == s.rstrip("\n")
