@@ -17,6 +17,7 @@
 
 #include "dpf_internal.h"
 #include "host_common.h"
+#include "build_pay.h"
 #include "kernels.h"
 
 namespace dpf {
@@ -1626,6 +1627,39 @@ static dpf_status compile_build(dpf_ctx* c, const dpf_build& B, BuildSpec& bs) {
     }
   }
   Q.nsteps = uint32_t(base + B.n_preds + B.n_joins);
+  // The payload fields through the survivor entries' group-id bits when
+  // they fit there (the entries hold 32 - kRowBits bits of group id): a
+  // probed table's field by its probe step's multiplier, a DICT column's
+  // code by a key step after the filters.  The build kernel then reads each
+  // kept row's fields from its entry instead of probing or decoding again.
+  {
+    uint32_t fbits[2] = {0, 0}, total = 0, keys = 0;
+    for (int f = 0; f < B.n_payload; ++f) {
+      while ((uint64_t(1) << fbits[f]) < uint64_t(std::max<uint32_t>(ht.pay_dom[f], 1u))) ++fbits[f];
+      total += fbits[f];
+      keys += B.payload[f].kind == DPF_PAYLOAD_COLUMN;
+    }
+    if (B.n_payload > 0 && total <= 20 && Q.nsteps + keys <= uint32_t(kMaxSteps)) {
+      uint32_t shift = 0;
+      for (int f = 0; f < B.n_payload; ++f) {
+        const dpf_payload& F = B.payload[f];
+        if (F.kind == DPF_PAYLOAD_COLUMN) {
+          DevStep& K = Q.steps[Q.nsteps++];
+          std::memset(&K, 0, sizeof K);
+          K.kind = ST_KEY;
+          K.col = uint8_t(Q.build_pay[f]);
+          K.key_mul = 1u << shift;
+          K.zlo = INT32_MIN;
+          K.zhi = INT32_MAX;
+        } else {
+          DevStep& S = Q.steps[base + B.n_preds + F.join];
+          (F.field == 0 ? S.mul0 : S.mul1) += 1u << shift;
+        }
+        Q.build_pay[f] = kPayFromGid | int32_t(shift << 8) | int32_t(fbits[f]);
+        shift += fbits[f];
+      }
+    }
+  }
   Q.nrows = cs.nrows;
   Q.page_rows = cs.page_rows;
   bs.host = cs.host;

@@ -11,10 +11,16 @@
 // {key, payload} claimed with a single compare-and-swap; the payload packs
 // two 16-bit fields.
 //
-// Payload field f comes from Q.build_pay[f]: a value >= 0 is the index of
-// a DICT column of the scanned table (the field is its code); a value < 0
+// Payload field f comes from Q.build_pay[f]: a value >= kPayFromGid holds
+// {shift << 8 | bits}, and the field is bits [shift, shift + bits) of the
+// row's group id, which the scan's steps built (a probe step adds its
+// match's payload fields times their multipliers, a key step a DICT code
+// times its multiplier: the fused kernel's group-id machinery carries the
+// fields through the survivor list); another value >= 0 is the index of a
+// DICT column of the scanned table (the field is its code); a value < 0
 // encodes code = -1 - build_pay[f], and the field is payload field
 // (code & 1) of the row's match in the table probed by step (code >> 1).
+#include "build_pay.h"
 #include "tile.cuh"
 
 namespace dpf {
@@ -25,8 +31,13 @@ namespace {
 // that step, so a miss means a corrupt table and sets S_INTERNAL.
 template <bool kHost>
 __device__ __forceinline__ uint32_t build_payload(const DevQuery& Q, int f, const PageState& P, uint32_t i0,
-                                                  uint32_t r, bool valid, int lane, unsigned int* status) {
+                                                  uint32_t r, uint32_t gid, bool valid, int lane,
+                                                  unsigned int* status) {
   const int32_t src = Q.build_pay[f];
+  if (src >= kPayFromGid) {
+    const uint32_t sh = (uint32_t(src) >> 8) & 0xffu, bits = uint32_t(src) & 0xffu;
+    return valid ? (gid >> sh) & ((1u << bits) - 1u) : 0u;
+  }
   if (src >= 0) return row_value<kHost>(Q, src, P, i0, r, valid, lane, status);
   const uint32_t code = uint32_t(-1 - src);
   const DevStep& S = Q.steps[code >> 1];
@@ -94,10 +105,13 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
     n = list_steps<kHost>(Q, P, i0, list, n, nullptr, lane, status);
     for (uint32_t j0 = 0; j0 < n; j0 += 32) {
       const bool valid = j0 + lane < n;
-      const uint32_t r = valid ? (list[j0 + lane] & ((1u << kRowBits) - 1u)) : 0u;
+      const uint32_t e = valid ? list[j0 + lane] : 0u;
+      const uint32_t r = e & ((1u << kRowBits) - 1u), gid = e >> kRowBits;
       const int32_t kv = int32_t(row_value<kHost>(Q, Q.build_key, P, i0, r, valid, lane, status));
-      const uint32_t c0 = kMode != 0 && Q.build_npay > 0 ? build_payload<kHost>(Q, 0, P, i0, r, valid, lane, status) : 0u;
-      const uint32_t c1 = kMode != 0 && Q.build_npay > 1 ? build_payload<kHost>(Q, 1, P, i0, r, valid, lane, status) : 0u;
+      const uint32_t c0 =
+          kMode != 0 && Q.build_npay > 0 ? build_payload<kHost>(Q, 0, P, i0, r, gid, valid, lane, status) : 0u;
+      const uint32_t c1 =
+          kMode != 0 && Q.build_npay > 1 ? build_payload<kHost>(Q, 1, P, i0, r, gid, valid, lane, status) : 0u;
       if (!valid) continue;
       if (kMode == 0) {
         ++kept;

@@ -164,7 +164,8 @@ struct alignas(16) DevQuery {
   unsigned int* done;          // chunks flushed so far, zero between launches
   void* out;                   // dpf_record[domain]
   unsigned int* out_n;
-  // dimension scans (hash build): key column and payload columns
+  // dimension scans (hash build): key column and the sources of the payload
+  // fields (a DICT column, a probed table's field, or group-id bits)
   int32_t build_key, build_npay, build_pay[2];
 };
 

@@ -142,13 +142,13 @@ def test_loaded_pages_equal_the_oracle_pages(eng):
     eng.ctx.drop_column(cid)
 
 
-def test_uses_other_than_aggregation_are_rejected(eng):
+def test_join_keys_and_group_keys_are_rejected(eng):
+    """FOR64 columns serve as aggregate operands and in predicates
+    (tests/test_gpu_for64_preds.py); as a join's probe column they are
+    refused, and the unfused chain refuses FOR64 columns altogether."""
     base = synth.star_join(rows=1 << 14, bigint_measure=True, seed=41)
     eng.load_workload(base)
     cases = []
-    w = copy.deepcopy(base)
-    w["query"]["preds"] = [{"col": "m1", "op": "gt", "args": [5]}]
-    cases.append(w)
     w = copy.deepcopy(base)
     w["query"]["joins"][0]["fk"] = "m1"
     cases.append(w)
