@@ -681,6 +681,7 @@ def main():
         "wall_s": wall,
     }
 
+    tuned = eng.ctx.prep_tuning(prep)
     eng.ctx.release(prep)
     if chain:
         link_ms = sum(x["ms"] for x in chain)
@@ -691,6 +692,9 @@ def main():
             p = time_chain_pipeline(eng, w, stream, torch, np, records, asynchronous=mode == "async")
             p["rows_per_s"] = rows_all / (p["wall_ms"] * 1e-3)
             out["chain"][f"pipeline_{mode}"] = p
+        p = time_chain_graph(eng, w, stream, torch, np, records, tuned)
+        p["rows_per_s"] = rows_all / (p["wall_ms"] * 1e-3)
+        out["chain"]["pipeline_graph"] = p
     links = None
     try:
         links = {"host_read_gbs": eng.ctx.read_rate("host", 2 << 30, 5, stream),
@@ -887,6 +891,49 @@ def time_chain_pipeline(eng, w, stream, torch, np, want, asynchronous, reps=9):
     return {"wall_ms": statistics.median(walls), "gpu_ms": statistics.median(gpus), "reps": reps,
             "builds": "enqueue-only, sized from load-time bounds" if asynchronous else "exact (kept count read back)",
             "tables": tables}
+
+
+def time_chain_graph(eng, w, stream, torch, np, want, tuning, reps=20):
+    """The whole chain query as one prepared chain replayed from one CUDA
+    graph: every replay rebuilds CUSTOMER's and ORDERS' tables (Kernels #1
+    and #2, enqueue-only sizing) and runs the fused plan over LINEITEM
+    (Kernel #3), then the records are read and each build's status checked.
+    ``wall_ms``: median host time from the replay to the checked records;
+    ``gpu_ms``: CUDA events around the replay.  The plan runs at ``tuning``
+    (the headline plan's autotuned configuration)."""
+    prep = eng.prepare_chain(w, dpf_tuning(tuning))
+    try:
+        eng.ctx.launch(prep, stream)
+        assert np.array_equal(eng.ctx.read_result(prep, 0), want), "prepared chain records differ"
+        eng.wait_joins(w, deferred=True)
+        eng.ctx.capture_graph(prep, stream)
+        walls, gpus = [], []
+        for r in range(reps + 2):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            e0.record(stream)
+            eng.ctx.launch_graph(prep, stream)
+            e1.record(stream)
+            got = eng.ctx.read_result(prep, 0)
+            eng.wait_joins(w, deferred=True)
+            t1 = time.perf_counter()
+            assert np.array_equal(got, want), "prepared chain records differ"
+            if r >= 2:
+                walls.append(1e3 * (t1 - t0))
+                gpus.append(e0.elapsed_time(e1))
+        tables = [dict(eng.ctx.hash_info(h)) for h in eng.chain_tables(w, deferred=True)]
+    finally:
+        eng.ctx.release(prep)
+    return {"wall_ms": statistics.median(walls), "gpu_ms": statistics.median(gpus), "reps": reps,
+            "builds": "deferred tables rebuilt by every replay of one CUDA graph", "tables": tables}
+
+
+def dpf_tuning(t):
+    """A Tuning structure from the dict dpf_prep_tuning returns."""
+    import paper_2605_10511_gb300 as dpf
+    return dpf.Tuning(t["chunk_rows"], t["threads"], t["ht_placement"], t["ctas_per_sm"], t["staging"],
+                      t["group_agg"])
 
 
 def time_unfused(eng, plan, stream, fused_records, reps, fused_ms):

@@ -287,6 +287,14 @@ dpf_status dpf_build_hash_async(dpf_ctx* ctx, const dpf_build* spec, void* strea
  * DPF_ECUDA.  The same error is returned again by later calls. */
 dpf_status dpf_hash_wait(dpf_ctx* ctx, dpf_ht_id ht);
 
+/* Kernel #1 / #2 of Sec. 3.1 prepared but not run: the scan is compiled
+ * and uploaded and the table allocated, sized as dpf_build_hash_async
+ * sizes it, and left empty (every probe misses) until a chain prepared by
+ * dpf_prepare_chain runs the build.  The call waits for its own set-up on
+ * the library's private stream and enqueues nothing on the caller's.
+ * Errors: DPF_EINVAL, DPF_ENOMEM, DPF_ECUDA. */
+dpf_status dpf_build_hash_deferred(dpf_ctx* ctx, const dpf_build* spec, dpf_ht_id* out);
+
 enum dpf_key_kind { DPF_KEY_COLUMN = 0, DPF_KEY_PAYLOAD = 1 };
 typedef struct dpf_key {
   int32_t kind;      /* DPF_KEY_COLUMN: fact DICT column `col`;
@@ -370,6 +378,23 @@ typedef struct dpf_record {
  * domain above DPF_MAX_GROUPS), DPF_ENOMEM, DPF_ECUDA. */
 dpf_status dpf_prepare(dpf_ctx* ctx, const dpf_plan* plans, int32_t n, const dpf_tuning* tuning,
                        dpf_prep_id* out);
+/* A join chain as one prepared batch (Sec. 3.1: Kernels #1 / #2 build the
+ * tables, Kernel #3 probes them): every launch of the batch (dpf_launch,
+ * or a graph captured by dpf_capture_graph and replayed by
+ * dpf_launch_graph) first rebuilds the deferred tables builds[0..n_builds)
+ * in that order (each emptied, then scanned, probing the tables built
+ * before it), then runs the plans, all on one stream with no host work in
+ * between.  Inner tables come first.  A launch's build status and entry
+ * counts are read by dpf_hash_wait(builds[i]) after it; a failed build is
+ * sticky (later dpf_prepare and build calls refuse the table).  The
+ * tables stay referenced while the batch exists: dpf_drop_hash refuses
+ * them until dpf_release.  Two batches rebuilding the same table must not
+ * run at the same time.  Tune (dpf_autotune) after a launch has filled
+ * the tables.  Errors: DPF_EINVAL (unknown, non-deferred, failed or
+ * repeated table; the errors of dpf_prepare), DPF_ENOMEM, DPF_ECUDA. */
+dpf_status dpf_prepare_chain(dpf_ctx* ctx, const dpf_ht_id* builds, int32_t n_builds,
+                             const dpf_plan* plans, int32_t n_plans, const dpf_tuning* tuning,
+                             dpf_prep_id* out);
 /* Enqueues ONE persistent fused kernel for all plans of the batch on
  * `stream` (no host synchronisation, capturable into a CUDA graph).  The
  * kernel leaves its scratch state zeroed, so launches can be replayed. */

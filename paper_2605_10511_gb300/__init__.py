@@ -137,6 +137,9 @@ _SIGS = {
     "dpf_build_hash_probe": (C.c_int32, [_P, C.POINTER(Build), _P, C.POINTER(C.c_int32)]),
     "dpf_build_hash_async": (C.c_int32, [_P, C.POINTER(Build), _P, C.POINTER(C.c_int32)]),
     "dpf_hash_wait": (C.c_int32, [_P, C.c_int32]),
+    "dpf_build_hash_deferred": (C.c_int32, [_P, C.POINTER(Build), C.POINTER(C.c_int32)]),
+    "dpf_prepare_chain": (C.c_int32, [_P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(Plan), C.c_int32,
+                                      C.POINTER(Tuning), C.POINTER(C.c_int32)]),
     "dpf_hash_info": (C.c_int32, [_P, C.c_int32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "dpf_drop_hash": (C.c_int32, [_P, C.c_int32]),
     "dpf_prepare": (C.c_int32, [_P, C.POINTER(Plan), C.c_int32, C.POINTER(Tuning), C.POINTER(C.c_int32)]),
@@ -344,7 +347,8 @@ class Context:
                                     _stream_ptr(stream), C.byref(out)))
         return out.value
 
-    def build_hash_probe(self, key_col, payload=(), preds=(), joins=(), stream=None, asynchronous=False):
+    def build_hash_probe(self, key_col, payload=(), preds=(), joins=(), stream=None, asynchronous=False,
+                         deferred=False):
         """Scan, probe and build (one link of a join chain).  ``payload``
         items are a DICT column id or ``("join", j, field)``: payload
         ``field`` of the row's match in ``joins[j]``; ``joins`` are
@@ -360,12 +364,20 @@ class Context:
         b = Build(key_col, len(payload), C.cast(pay, C.POINTER(Payload)), len(preds),
                   C.cast(parr, C.POINTER(Pred)), len(joins), C.cast(jarr, C.POINTER(Join)))
         out = C.c_int32()
-        call = lib().dpf_build_hash_async if asynchronous else lib().dpf_build_hash_probe
-        _check(call(self.h, C.byref(b), _stream_ptr(stream), C.byref(out)))
+        if deferred:
+            _check(lib().dpf_build_hash_deferred(self.h, C.byref(b), C.byref(out)))
+        else:
+            call = lib().dpf_build_hash_async if asynchronous else lib().dpf_build_hash_probe
+            _check(call(self.h, C.byref(b), _stream_ptr(stream), C.byref(out)))
         return out.value
 
     def build_hash_async(self, key_col, payload=(), preds=(), joins=(), stream=None):
         return self.build_hash_probe(key_col, payload, preds, joins, stream, asynchronous=True)
+
+    def build_hash_deferred(self, key_col, payload=(), preds=(), joins=()):
+        """A table prepared but not built (``dpf_build_hash_deferred``): empty
+        until a chain prepared with ``prepare_chain`` runs it."""
+        return self.build_hash_probe(key_col, payload, preds, joins, deferred=True)
 
     def hash_wait(self, ht):
         _check(lib().dpf_hash_wait(self.h, ht))
@@ -384,6 +396,16 @@ class Context:
         out = C.c_int32()
         _check(lib().dpf_prepare(self.h, arr, len(plans), C.byref(tuning) if tuning else None,
                                  C.byref(out)))
+        return out.value
+
+    def prepare_chain(self, builds, plans, tuning=None):
+        """A batch whose every launch rebuilds the deferred tables ``builds``
+        (inner tables first) and then runs ``plans`` (``dpf_prepare_chain``)."""
+        ids = (C.c_int32 * len(builds))(*builds)
+        arr = (Plan * len(plans))(*[p.plan for p in plans])
+        out = C.c_int32()
+        _check(lib().dpf_prepare_chain(self.h, ids, len(builds), arr, len(plans),
+                                       C.byref(tuning) if tuning else None, C.byref(out)))
         return out.value
 
     def launch(self, prep, stream=None):

@@ -88,6 +88,11 @@ struct HashTable {
   BuildStat* bstat = nullptr;     // its status word and inserted-row count
   dpf_col_id key_col = 0;
   dpf_status failed = DPF_OK;     // the error a finished build reported
+  // tables sized before their scan keep their launch (dpf_build_hash_deferred:
+  // rebuilt by every launch of the prepared chains that name them)
+  bool deferred = false;
+  int32_t refs = 0;               // prepared chains that rebuild the table
+  BuildLaunch bl{};
 };
 
 struct Prep {
@@ -112,6 +117,9 @@ struct Prep {
   uint8_t* unf_scratch = nullptr;
   uint32_t launches = 1;
   uint64_t fixed_inter_bytes = 0;   // decoded columns + flags per run
+  // a prepared chain: these deferred tables are rebuilt, in order, before the
+  // fused kernel of every launch (dpf_prepare_chain)
+  std::vector<HashTable*> chain;
 };
 
 struct dpf_ctx {
@@ -245,6 +253,26 @@ static void free_table(dpf_ctx* c, HashTable& ht) {
   ht.bq = nullptr;
   ht.bstat = nullptr;
   ht.done = nullptr;
+}
+
+// Enqueues the build of a table sized before its scan on s: its status
+// zeroed, the table emptied (absent entries, no presence bits, no staged
+// pairs), the insert pass(es), then the event dpf_hash_wait waits on.
+static cudaError_t enqueue_table_build(HashTable& ht, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ht.bstat, 0, sizeof(BuildStat), s);
+  if (e == cudaSuccess) {
+    if (ht.kind == HT_RANK) {
+      e = cudaMemsetAsync(ht.rank, 0, 16 * ((uint64_t(ht.capacity) + 63) / 64), s);
+      if (e == cudaSuccess) e = cudaMemsetAsync(ht.stage, 0, 16, s);
+    } else if (ht.kind == HT_DIRECT) {
+      e = launch_init_direct(ht.direct, std::max<uint32_t>(ht.capacity, 1u), s);
+    } else {
+      e = launch_init_table(ht.slots, ht.capacity, s);
+    }
+  }
+  if (e == cudaSuccess) e = launch_build_insert(ht.bl, s);
+  if (e == cudaSuccess) e = cudaEventRecord(ht.done, s);
+  return e;
 }
 
 template <class T>
@@ -1019,6 +1047,8 @@ void fill_tuning_defaults(dpf_ctx* c, dpf_tuning& t, const dpf_plan* plans, int3
 
 dpf_status release_prep(dpf_ctx* c, Prep* p) {
   if (p->launched && p->ev) cudaEventSynchronize(p->ev);
+  for (HashTable* h : p->chain) --h->refs;
+  p->chain.clear();
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->graph) cudaGraphDestroy(p->graph);
   if (p->ev) cudaEventDestroy(p->ev);
@@ -1032,6 +1062,11 @@ dpf_status release_prep(dpf_ctx* c, Prep* p) {
 
 // Launch of a prepared batch (fused kernel or unfused chain) on s.
 cudaError_t launch_prep(Prep* p, cudaStream_t s) {
+  for (HashTable* h : p->chain) {
+    const cudaError_t e = enqueue_table_build(*h, s);
+    if (e != cudaSuccess) return e;
+    h->pending = true;
+  }
   if (p->unfused) {
     uint32_t n = 0;
     cudaError_t e = launch_unfused(p->U, s, &n);
@@ -1798,11 +1833,13 @@ static dpf_status build_hash_impl(dpf_ctx* c, const dpf_build& B, void* stream, 
 // bound on the kept rows.  Everything is enqueued on the stream; the
 // table's device-side status and inserted-row count are read by
 // finish_build once the stream has passed the build.
-static dpf_status build_hash_async_impl(dpf_ctx* c, const dpf_build& B, void* stream, dpf_ht_id* out) {
+static dpf_status build_hash_async_impl(dpf_ctx* c, const dpf_build& B, void* stream, bool deferred,
+                                        dpf_ht_id* out) {
   if (!c || !out) return fail(DPF_EINVAL, "NULL argument");
   std::lock_guard<std::recursive_mutex> lk(c->mu);
   DeviceGuard g(c->device);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // a deferred table is set up on the private stream and left empty
+  cudaStream_t s = deferred ? c->io : static_cast<cudaStream_t>(stream);
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
     cudaGetLastError();
@@ -1835,15 +1872,21 @@ static dpf_status build_hash_async_impl(dpf_ctx* c, const dpf_build& B, void* st
     free_table(c, ht);
     return st;
   }
-  e = launch_build_insert(L, s);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ht.done, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventRecord(ht.done, s);
+  e = cudaEventCreateWithFlags(&ht.done, cudaEventDisableTiming);
+  if (!deferred) {
+    if (e == cudaSuccess) e = launch_build_insert(L, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ht.done, s);
+  } else if (e == cudaSuccess) {
+    e = cudaStreamSynchronize(s);  // an empty table, scan uploaded, until a chain runs the build
+  }
   if (e != cudaSuccess) {
     cudaStreamSynchronize(s);  // nothing of the failed build may still be running when its blocks are freed
     free_table(c, ht);
     return fail(DPF_ECUDA, "hash build: %s", cudaGetErrorString(e));
   }
-  ht.pending = true;
+  ht.bl = L;
+  ht.deferred = deferred;
+  ht.pending = !deferred;
   ht.key_col = B.key_col;
   ht.entries = uint64_t(std::llround(bs.est_kept));  // an estimate until finish_build
   ht.id = c->next_ht++;
@@ -1864,14 +1907,16 @@ static dpf_status finish_build(dpf_ctx* c, HashTable& ht) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->io);
   if (e != cudaSuccess) return fail(DPF_ECUDA, "hash build: %s", cudaGetErrorString(e));
   ht.pending = false;
-  dev_free(c, ht.bq);
-  dev_free(c, ht.bstat);
-  dev_free(c, ht.stage);
-  cudaEventDestroy(ht.done);
-  ht.bq = nullptr;
-  ht.bstat = nullptr;
-  ht.stage = nullptr;
-  ht.done = nullptr;
+  if (!ht.deferred) {  // a deferred table keeps its launch buffers for the next chain launch
+    dev_free(c, ht.bq);
+    dev_free(c, ht.bstat);
+    dev_free(c, ht.stage);
+    cudaEventDestroy(ht.done);
+    ht.bq = nullptr;
+    ht.bstat = nullptr;
+    ht.stage = nullptr;
+    ht.done = nullptr;
+  }
   ht.entries = bs.inserted;
   if (bs.sched.status) {
     const dpf_status r = build_status_error(bs.sched.status, ht.key_col);
@@ -1905,7 +1950,37 @@ dpf_status dpf_build_hash_probe(dpf_ctx* c, const dpf_build* spec, void* stream,
 
 dpf_status dpf_build_hash_async(dpf_ctx* c, const dpf_build* spec, void* stream, dpf_ht_id* out) {
   if (!spec) return fail(DPF_EINVAL, "NULL build description");
-  return build_hash_async_impl(c, *spec, stream, out);
+  return build_hash_async_impl(c, *spec, stream, false, out);
+}
+
+dpf_status dpf_build_hash_deferred(dpf_ctx* c, const dpf_build* spec, dpf_ht_id* out) {
+  if (!spec) return fail(DPF_EINVAL, "NULL build description");
+  return build_hash_async_impl(c, *spec, nullptr, true, out);
+}
+
+dpf_status dpf_prepare_chain(dpf_ctx* c, const dpf_ht_id* builds, int32_t n_builds, const dpf_plan* plans,
+                             int32_t n, const dpf_tuning* tuning, dpf_prep_id* out) {
+  if (!c || !out || !builds) return fail(DPF_EINVAL, "NULL argument");
+  if (n_builds < 1 || n_builds > 64) return fail(DPF_EINVAL, "need 1..64 deferred tables");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  std::vector<HashTable*> hs;
+  for (int32_t i = 0; i < n_builds; ++i) {
+    auto it = c->hts.find(builds[i]);
+    if (it == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", builds[i]);
+    if (!it->second.deferred) return fail(DPF_EINVAL, "hash table %d was not made by dpf_build_hash_deferred", builds[i]);
+    if (it->second.failed) return fail(DPF_EINVAL, "hash table %d failed to build", builds[i]);
+    if (std::find(hs.begin(), hs.end(), &it->second) != hs.end())
+      return fail(DPF_EINVAL, "hash table %d is named twice", builds[i]);
+    hs.push_back(&it->second);
+  }
+  Prep* p;
+  dpf_status st = prepare(c, plans, n, tuning, &p);
+  if (st) return st;
+  p->chain = hs;
+  for (HashTable* h : hs) ++h->refs;
+  *out = p->id;
+  return DPF_OK;
 }
 
 dpf_status dpf_hash_wait(dpf_ctx* c, dpf_ht_id id) {
@@ -1935,6 +2010,7 @@ dpf_status dpf_drop_hash(dpf_ctx* c, dpf_ht_id id) {
   DeviceGuard g(c->device);
   auto it = c->hts.find(id);
   if (it == c->hts.end()) return fail(DPF_EINVAL, "unknown hash table %d", id);
+  if (it->second.refs > 0) return fail(DPF_EINVAL, "hash table %d is rebuilt by a prepared chain", id);
   cudaDeviceSynchronize();
   free_table(c, it->second);
   c->hts.erase(it);
@@ -2110,6 +2186,7 @@ dpf_status dpf_launch_graph(dpf_ctx* c, dpf_prep_id id, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CUDA_TRY(cudaGraphLaunch(p->gexec, s));
   CUDA_TRY(cudaEventRecord(p->ev, s));
+  for (HashTable* h : p->chain) h->pending = true;
   p->launched = true;
   return DPF_OK;
 }

@@ -28,6 +28,7 @@ class Engine:
         self.cols = {}       # (workload name, table, column) -> column id
         self.tables = {}     # (workload name, table) -> table id
         self.hts = {}        # join signature -> hash table id
+        self.dhts = {}       # join signature -> deferred hash table id (prepared chains)
 
     def close(self):
         self.ctx.close()
@@ -61,36 +62,65 @@ class Engine:
         return total, w["tables"][w["fact"]]["rows"]
 
     # ------------------------------------------------------------------ planning
-    def build_join(self, w, j, stream=None, asynchronous=False):
+    def build_join(self, w, j, stream=None, asynchronous=False, deferred=False):
         """Builds (or reuses) the hash table of join ``j``.  A join with
         joins of its own (a chain) has those built first; its table is then
         built by scanning its dimension and probing theirs.  With
         ``asynchronous`` every table of the chain is only enqueued on
-        ``stream`` (``dpf_build_hash_async``)."""
+        ``stream`` (``dpf_build_hash_async``); with ``deferred`` it is
+        prepared, empty, for a prepared chain (``dpf_build_hash_deferred``,
+        kept apart from the built tables)."""
         sig = (w["name"], repr(j))
-        if sig not in self.hts:
+        cache = self.dhts if deferred else self.hts
+        if sig not in cache:
             d = j["dim"]
             preds = [make_pred(self.col(w, d, p["col"]), p["op"], p["args"]) for p in j["preds"]]
             subs = j.get("joins", [])
-            if not subs and not asynchronous and all(isinstance(c, str) for c in j["payload"]):
+            if not subs and not asynchronous and not deferred and all(isinstance(c, str) for c in j["payload"]):
                 pay = [self.col(w, d, c) for c in j["payload"]]
-                self.hts[sig] = self.ctx.build_hash(self.col(w, d, j["key"]), pay, preds, stream)
+                cache[sig] = self.ctx.build_hash(self.col(w, d, j["key"]), pay, preds, stream)
             else:
-                sub_hts = [(self.col(w, d, s["fk"]), self.build_join(w, s, stream, asynchronous)) for s in subs]
+                sub_hts = [(self.col(w, d, s["fk"]), self.build_join(w, s, stream, asynchronous, deferred))
+                           for s in subs]
                 pay = [("join", c["join"], c["field"]) if isinstance(c, dict) else self.col(w, d, c)
                        for c in j["payload"]]
-                build = self.ctx.build_hash_async if asynchronous else self.ctx.build_hash_probe
-                self.hts[sig] = build(self.col(w, d, j["key"]), pay, preds, sub_hts, stream)
-        return self.hts[sig]
+                key = self.col(w, d, j["key"])
+                if deferred:
+                    cache[sig] = self.ctx.build_hash_deferred(key, pay, preds, sub_hts)
+                else:
+                    build = self.ctx.build_hash_async if asynchronous else self.ctx.build_hash_probe
+                    cache[sig] = build(key, pay, preds, sub_hts, stream)
+        return cache[sig]
 
-    def build_joins(self, w, stream=None, asynchronous=False):
+    def build_joins(self, w, stream=None, asynchronous=False, deferred=False):
         """Builds (or reuses) the hash table of every join of ``w``'s query."""
-        return [self.build_join(w, j, stream, asynchronous) for j in w["query"]["joins"]]
+        return [self.build_join(w, j, stream, asynchronous, deferred) for j in w["query"]["joins"]]
 
-    def plan(self, w, stream=None, asynchronous=False):
+    def chain_tables(self, w, deferred=False):
+        """Table ids of ``w``'s joins, inner tables first."""
+        cache = self.dhts if deferred else self.hts
+        out = []
+
+        def walk(j):
+            for s in j.get("joins", []):
+                walk(s)
+            out.append(cache[(w["name"], repr(j))])
+        for j in w["query"]["joins"]:
+            walk(j)
+        return out
+
+    def prepare_chain(self, w, tuning=None):
+        """``w``'s query as one prepared chain: deferred tables for every join
+        (inner first) and the plan over them; every launch of the returned
+        batch rebuilds the tables and runs the plan."""
+        self.load_workload(w)
+        h = self.plan(w, deferred=True)
+        return self.ctx.prepare_chain(self.chain_tables(w, deferred=True), [h], tuning)
+
+    def plan(self, w, stream=None, asynchronous=False, deferred=False):
         q = w["query"]
         f = w["fact"]
-        hts = self.build_joins(w, stream, asynchronous)
+        hts = self.build_joins(w, stream, asynchronous, deferred)
         preds = (Pred * max(len(q["preds"]), 1))(
             *[make_pred(self.col(w, f, p["col"]), p["op"], p["args"]) for p in q["preds"]])
         joins = (Join * max(len(q["joins"]), 1))(
@@ -128,15 +158,11 @@ class Engine:
             self.wait_joins(w)
         return rec
 
-    def wait_joins(self, w):
+    def wait_joins(self, w, deferred=False):
         """``hash_wait`` on every table of ``w``'s query, inner tables first
         (raises the first build error)."""
-        def walk(j):
-            for s in j.get("joins", []):
-                walk(s)
-            self.ctx.hash_wait(self.hts[(w["name"], repr(j))])
-        for j in w["query"]["joins"]:
-            walk(j)
+        for ht in self.chain_tables(w, deferred):
+            self.ctx.hash_wait(ht)
 
     def run_unfused(self, w, stream=None):
         """The same query through the unfused per-operator chain."""
