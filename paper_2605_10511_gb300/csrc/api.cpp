@@ -1199,20 +1199,33 @@ dpf_status prepare(dpf_ctx* c, const dpf_plan* plans, int32_t n, const dpf_tunin
   // last tickets.  Whole-size tickets there leave most warps idle while the
   // last few finish; the final rows (about two tickets of tail_rows per warp
   // of the grid, taken from the last queries backwards) are cut into tickets
-  // of chunk_rows / 8 rows instead.
+  // of chunk_rows / 8 rows instead.  In a batch the same holds at every query
+  // switch: a CTA's warps meet when their tickets leave a query (its plan,
+  // tables and accumulators sit in shared memory), so each query's last rows
+  // (one small ticket per warp of the grid) are cut small as well.
   {
     const uint64_t warps = uint64_t(c->num_sms) * t.ctas_per_sm * (t.threads / 32);
     const uint32_t tile_rows = kMbPerWarpTile * kMB;
     const uint32_t tail_rows = std::max<uint32_t>(tile_rows, t.chunk_rows / 8 / tile_rows * tile_rows);
-    int64_t want = tail_rows < t.chunk_rows ? int64_t(2 * warps * tail_rows) : 0;
-    for (int i = n - 1; i >= 0 && want > 0; --i) {
+    std::vector<uint64_t> tail_len(size_t(n), 0);
+    if (tail_rows < t.chunk_rows) {
+      if (n > 1)
+        for (int i = 0; i < n; ++i) tail_len[size_t(i)] = std::min<uint64_t>(p->hq[i].nrows, warps * tail_rows);
+      uint64_t want = 2 * warps * tail_rows;
+      for (int i = n - 1; i >= 0 && want > 0; --i) {
+        const uint64_t rows = std::min<uint64_t>(p->hq[i].nrows, want);
+        tail_len[size_t(i)] = std::max(tail_len[size_t(i)], rows);
+        want -= rows;
+      }
+    }
+    for (int i = 0; i < n; ++i) {
       DevQuery& Q = p->hq[i];
-      const uint64_t keep_big = Q.nrows > uint64_t(want) ? (Q.nrows - uint64_t(want)) / t.chunk_rows : 0;
+      if (tail_len[size_t(i)] == 0) continue;
+      const uint64_t keep_big = (Q.nrows - tail_len[size_t(i)]) / t.chunk_rows;
       Q.tail_first = keep_big;
       Q.tail_rows = tail_rows;
       const uint64_t tail = Q.nrows - keep_big * t.chunk_rows;
       Q.nchunks = keep_big + (tail + tail_rows - 1) / tail_rows;
-      want -= int64_t(tail);
     }
     tickets = 0;
     for (int i = 0; i < n; ++i) {
