@@ -271,7 +271,15 @@ static cudaError_t enqueue_table_build(HashTable& ht, cudaStream_t s) {
     }
   }
   if (e == cudaSuccess) e = launch_build_insert(ht.bl, s);
-  if (e == cudaSuccess) e = cudaEventRecord(ht.done, s);
+  if (e == cudaSuccess) {
+    // captured into a graph, the record must be an external event node for
+    // the host to wait on it after a replay
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e == cudaSuccess)
+      e = cap == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ht.done, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(ht.done, s);
+  }
   return e;
 }
 
