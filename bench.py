@@ -714,6 +714,11 @@ def main():
             e["page_bytes_gbs"] = rate
             e["page_bytes_frac_of_host_link"] = rate / links["host_read_gbs"]
             link, src = stored_link_bytes(args.workload, fact_rows)
+            if link is None:
+                t, tsrc = stored_traffic(args.workload, fact_rows)
+                if t is not None:
+                    link, src = t, ("estimate: the DRAM bytes of the HBM-resident kernel's capture of this query "
+                                    f"({tsrc}); the host-resident kernel reads the same sectors over the link")
             if link is not None:
                 # the kernel reads only the sectors holding a survivor's field of
                 # the later steps' columns: the bytes that crossed the link
