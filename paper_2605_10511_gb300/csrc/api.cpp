@@ -93,6 +93,7 @@ struct HashTable {
   bool deferred = false;
   int32_t refs = 0;               // prepared chains that rebuild the table
   BuildLaunch bl{};
+  BuildStat* hstat = nullptr;     // deferred: pinned host copy of bstat, written by each chain launch
 };
 
 struct Prep {
@@ -245,6 +246,7 @@ static void free_table(dpf_ctx* c, HashTable& ht) {
   dev_free(c, ht.stage);
   dev_free(c, ht.bq);
   dev_free(c, ht.bstat);
+  if (ht.hstat) cudaFreeHost(ht.hstat);
   if (ht.done) cudaEventDestroy(ht.done);
   ht.slots = nullptr;
   ht.direct = nullptr;
@@ -252,6 +254,7 @@ static void free_table(dpf_ctx* c, HashTable& ht) {
   ht.stage = nullptr;
   ht.bq = nullptr;
   ht.bstat = nullptr;
+  ht.hstat = nullptr;
   ht.done = nullptr;
 }
 
@@ -271,6 +274,7 @@ static cudaError_t enqueue_table_build(HashTable& ht, cudaStream_t s) {
     }
   }
   if (e == cudaSuccess) e = launch_build_insert(ht.bl, s);
+  if (e == cudaSuccess && ht.hstat) e = cudaMemcpyAsync(ht.hstat, ht.bstat, sizeof(BuildStat), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) {
     // captured into a graph, the record must be an external event node for
     // the host to wait on it after a replay
@@ -1898,7 +1902,9 @@ static dpf_status build_hash_async_impl(dpf_ctx* c, const dpf_build& B, void* st
     if (e == cudaSuccess) e = launch_build_insert(L, s);
     if (e == cudaSuccess) e = cudaEventRecord(ht.done, s);
   } else if (e == cudaSuccess) {
-    e = cudaStreamSynchronize(s);  // an empty table, scan uploaded, until a chain runs the build
+    e = cudaHostAlloc(reinterpret_cast<void**>(&ht.hstat), sizeof(BuildStat), cudaHostAllocDefault);
+    if (e == cudaSuccess) std::memset(ht.hstat, 0, sizeof(BuildStat));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // an empty table, scan uploaded, until a chain runs the build
   }
   if (e != cudaSuccess) {
     cudaStreamSynchronize(s);  // nothing of the failed build may still be running when its blocks are freed
@@ -1924,8 +1930,12 @@ static dpf_status finish_build(dpf_ctx* c, HashTable& ht) {
   if (!ht.pending) return ht.failed ? fail(ht.failed, "hash table %d failed to build", ht.id) : DPF_OK;
   BuildStat bs{};
   cudaError_t e = cudaEventSynchronize(ht.done);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&bs, ht.bstat, sizeof bs, cudaMemcpyDeviceToHost, c->io);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->io);
+  if (e == cudaSuccess && ht.hstat) {
+    bs = *ht.hstat;  // the launch copied it there before the event
+  } else {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bs, ht.bstat, sizeof bs, cudaMemcpyDeviceToHost, c->io);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->io);
+  }
   if (e != cudaSuccess) return fail(DPF_ECUDA, "hash build: %s", cudaGetErrorString(e));
   ht.pending = false;
   if (!ht.deferred) {  // a deferred table keeps its launch buffers for the next chain launch

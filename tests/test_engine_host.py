@@ -35,6 +35,20 @@ class RecordingCtx:
         self.calls.append(("probe_build", key_col, list(payload), len(preds), list(joins), self.next_ht))
         return self.next_ht
 
+    def build_hash_async(self, key_col, payload=(), preds=(), joins=(), stream=None):
+        self.next_ht += 1
+        self.calls.append(("async", key_col, list(payload), len(preds), list(joins), self.next_ht))
+        return self.next_ht
+
+    def build_hash_deferred(self, key_col, payload=(), preds=(), joins=()):
+        self.next_ht += 1
+        self.calls.append(("deferred", key_col, list(payload), len(preds), list(joins), self.next_ht))
+        return self.next_ht
+
+    def prepare_chain(self, builds, plans, tuning=None):
+        self.calls.append(("chain", list(builds), len(plans)))
+        return 7
+
     def close(self):
         pass
 
@@ -116,3 +130,27 @@ def test_plain_joins_use_the_scan_and_build_call():
     eng, ctx = _engine(w)
     eng.build_joins(w)
     assert [c[0] for c in ctx.calls] == ["build"] * 4
+
+
+def test_enqueue_only_and_deferred_builds_route_every_table():
+    """With ``asynchronous`` or ``deferred`` every table of a chain, the
+    inner one included, goes through the scan + probe + build form of that
+    mode (a table without joins is the same call with no joins); deferred
+    tables are kept apart from built ones, and a prepared chain names them
+    inner first."""
+    w = synth.chain_join(rows=1 << 12, page_rows=1024)
+    for mode in ("async", "deferred"):
+        eng, ctx = _engine(w)
+        hts = eng.build_joins(w, asynchronous=mode == "async", deferred=mode == "deferred")
+        assert [c[0] for c in ctx.calls] == [mode, mode]
+        cust, orders = ctx.calls
+        assert cust[1] == eng.col(w, "customer", "c_custkey") and cust[4] == []
+        assert cust[2] == [eng.col(w, "customer", "c_nation")]
+        assert orders[4] == [(eng.col(w, "orders", "o_custkey"), cust[5])]
+        assert hts == [orders[5]]
+        assert eng.chain_tables(w, deferred=mode == "deferred") == [cust[5], orders[5]]
+        if mode == "deferred":
+            assert eng.hts == {}  # built tables untouched
+            assert eng.prepare_chain(w) == 7
+            assert ctx.calls[-1] == ("chain", [cust[5], orders[5]], 1)
+            assert [c[0] for c in ctx.calls[:-1]] == ["deferred", "deferred"]  # the plan reused them
