@@ -704,6 +704,16 @@ struct ColumnSet {
   uint64_t nrows = 0;
   uint32_t page_rows = 0;
   bool host = false;
+  // The table checks of add without adding the column (a column a plan
+  // names but never reads).
+  dpf_status check(int32_t id) const {
+    auto it = c->cols.find(id);
+    if (it == c->cols.end()) return fail(DPF_EINVAL, "unknown column %d", id);
+    const Column& col = it->second;
+    if (!ids.empty() && (col.table != table || col.nrows != nrows || col.page_rows != page_rows))
+      return fail(DPF_EINVAL, "column %d is not in the same table (table/rows/page_rows differ)", id);
+    return DPF_OK;
+  }
   dpf_status add(int32_t id, int* idx) {
     auto it = c->cols.find(id);
     if (it == c->cols.end()) return fail(DPF_EINVAL, "unknown column %d", id);
@@ -745,13 +755,26 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
     return fail(DPF_EINVAL, "plan array pointer is NULL");
   std::vector<DevStep> steps;
   std::vector<double> sel;  // estimated selectivity of each step
+  // A predicate every row passes (an empty PREFIX or CONTAINS pattern, LIKE
+  // '%', a range over the whole int32 or int64 domain) compiles to no step:
+  // its column is checked but not read.
+  std::vector<int32_t> unread;
   for (int i = 0; i < P.n_preds; ++i) {
-    int idx;
-    dpf_status st = cs.add(P.preds[i].col, &idx);
-    if (st) return st;
+    if (c->cols.find(P.preds[i].col) == c->cols.end()) return fail(DPF_EINVAL, "unknown column %d", P.preds[i].col);
     DevStep S;
-    st = compile_pred(c->cols[P.preds[i].col], P.preds[i], S, idx);
+    dpf_status st = compile_pred(c->cols[P.preds[i].col], P.preds[i], S, 0);
     if (st) return st;
+    const bool all = ((S.kind == ST_PREFIX || S.kind == ST_CONTAINS) && S.plen == 0) ||
+                     (S.kind == ST_RANGE && S.lo == INT32_MIN && S.hi == INT32_MAX) ||
+                     (S.kind == ST_RANGE64 && step_bound64(S.in, 0) == INT64_MIN && step_bound64(S.in, 1) == INT64_MAX) ||
+                     (S.kind == ST_NOTRANGE64 && step_bound64(S.in, 0) > step_bound64(S.in, 1));
+    if (all) {
+      unread.push_back(P.preds[i].col);
+      continue;
+    }
+    int idx;
+    if ((st = cs.add(P.preds[i].col, &idx))) return st;
+    S.col = uint8_t(idx);
     sel.push_back(step_selectivity(S, &c->cols[P.preds[i].col], nullptr));
     steps.push_back(S);
   }
@@ -853,6 +876,11 @@ dpf_status compile_plan(dpf_ctx* c, const dpf_plan& P, DevQuery& Q, bool* host,
       if (st) return st;
       (i == 0 ? Q.agg_a : Q.agg_b)[a] = uint8_t(idx);
     }
+  }
+  for (int32_t id : unread) {
+    int idx;
+    dpf_status st = cs.ids.empty() ? cs.add(id, &idx) : cs.check(id);
+    if (st) return st;
   }
   if (cs.ids.empty() && P.scan_col != 0) {
     int idx;
