@@ -68,11 +68,19 @@ def test_workload_shapes(eng, shapes, name):
 
 
 @pytest.mark.parametrize("seed", range(0, 40, 3))
+def _a_step(p):
+    """False for a predicate every row passes: the planner compiles it to no step."""
+    if p["op"] in ("prefix", "contains") and len(bytes(p["args"][0])) == 0:
+        return False
+    return not (p["op"] == "like" and all(b == 0x25 for b in bytes(p["args"][0])))
+
+
 def test_unfused_chain_random_small(eng, seed):
     w = synth.tiny_random_workload(seed)
     q = w["query"]
-    if w["tables"]["fact"]["cols"]["s"]["codec"] == "fsst" and any(p["col"] == "s" for p in q["preds"]) \
-            or any(p["op"] == "contains" for p in q["preds"]) \
+    preds = [p for p in q["preds"] if _a_step(p)]
+    if w["tables"]["fact"]["cols"]["s"]["codec"] == "fsst" and any(p["col"] == "s" for p in preds) \
+            or any(p["op"] == "contains" for p in preds) \
             or any("z" in a.get("cols", []) for a in q["aggs"]):
         # the unfused baseline evaluates PREFIX on STR columns only and
         # decodes 32-bit columns only
