@@ -341,7 +341,7 @@ typedef struct dpf_plan {
 enum dpf_ht_place { DPF_HT_AUTO = 0, DPF_HT_SMEM = 1, DPF_HT_GLOBAL = 2 };
 typedef struct dpf_tuning {
   uint32_t chunk_rows;   /* rows per scheduling ticket (one warp's unit of work):
-                            multiple of 512, at most 2^24; default 2048        */
+                            multiple of 512, at most 2^24; default 4096        */
   uint32_t threads;      /* threads per CTA: 128 or 256; 512 or 1024 (2 / 1 CTAs
                             per SM) for device-resident, unstaged batches
                             without CONTAINS / FSST steps                    */
@@ -363,6 +363,20 @@ typedef struct dpf_tuning {
 } dpf_tuning;
 enum dpf_staging { DPF_STAGE_DEFAULT = 0, DPF_STAGE_ON = 1, DPF_STAGE_OFF = 2 };
 enum dpf_group_agg { DPF_GROUP_AGG_DEFAULT = 0, DPF_GROUP_AGG_WARP = 1, DPF_GROUP_AGG_ATOMIC = 2 };
+/* The context's default launch configuration: the fields a dpf_prepare
+ * leaves 0 (or a NULL tuning) and dpf_autotune has not chosen for its
+ * plans take these before the library's defaults.  json is a flat JSON
+ * object with any of the keys of dpf_tuning: "chunk_rows", "threads",
+ * "ctas_per_sm" (non-negative integers, as dpf_tuning constrains them),
+ * "ht_placement" ("auto" | "smem" | "global"), "staging" ("default" | "on"
+ * | "off"), "group_agg" ("default" | "warp" | "atomic"); the enums may also
+ * be given by their values.  NULL or "" resets to the library's defaults.
+ * Errors: DPF_EINVAL (a syntax error, an unknown key, a bad value; the
+ * previous defaults stay). */
+dpf_status dpf_set_tuning(dpf_ctx* ctx, const char* json);
+/* The parse of dpf_set_tuning alone (no context, no device): json (NULL or
+ * "" gives all zeros) into *out.  Errors: DPF_EINVAL. */
+dpf_status dpf_parse_tuning(const char* json, dpf_tuning* out);
 
 /* Result record: keys are dictionary values (0 when unused); count = rows
  * in the group; val[i] = aggregate i (COUNT repeats count). */

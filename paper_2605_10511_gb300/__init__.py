@@ -137,6 +137,8 @@ _SIGS = {
     "dpf_build_hash_probe": (C.c_int32, [_P, C.POINTER(Build), _P, C.POINTER(C.c_int32)]),
     "dpf_build_hash_async": (C.c_int32, [_P, C.POINTER(Build), _P, C.POINTER(C.c_int32)]),
     "dpf_hash_wait": (C.c_int32, [_P, C.c_int32]),
+    "dpf_set_tuning": (C.c_int32, [_P, C.c_char_p]),
+    "dpf_parse_tuning": (C.c_int32, [C.c_char_p, C.POINTER(Tuning)]),
     "dpf_build_hash_deferred": (C.c_int32, [_P, C.POINTER(Build), C.POINTER(C.c_int32)]),
     "dpf_prepare_chain": (C.c_int32, [_P, C.POINTER(C.c_int32), C.c_int32, C.POINTER(Plan), C.c_int32,
                                       C.POINTER(Tuning), C.POINTER(C.c_int32)]),
@@ -220,6 +222,14 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return C.c_void_p(stream)
     return C.c_void_p(stream.cuda_stream)
+
+
+def parse_tuning(text):
+    """The launch configuration a JSON object string gives (``dpf_parse_tuning``,
+    host only): a dict of the dpf_tuning fields."""
+    t = Tuning()
+    _check(lib().dpf_parse_tuning(None if text is None else text.encode(), C.byref(t)))
+    return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
 
 def make_pred(col_id, op, args):
@@ -397,6 +407,13 @@ class Context:
         _check(lib().dpf_prepare(self.h, arr, len(plans), C.byref(tuning) if tuning else None,
                                  C.byref(out)))
         return out.value
+
+    def set_tuning(self, tuning=None):
+        """The context's default launch configuration (``dpf_set_tuning``):
+        a dict or a JSON object string; None resets."""
+        import json
+        text = None if tuning is None else (tuning if isinstance(tuning, str) else json.dumps(tuning))
+        _check(lib().dpf_set_tuning(self.h, None if text is None else text.encode()))
 
     def prepare_chain(self, builds, plans, tuning=None):
         """A batch whose every launch rebuilds the deferred tables ``builds``

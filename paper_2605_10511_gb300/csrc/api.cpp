@@ -141,6 +141,7 @@ struct dpf_ctx {
   int num_sms = 0;
   int smem_optin = 0;
   std::map<uint64_t, dpf_tuning> tune_cache;  // plan-set signature -> tuning chosen by dpf_autotune
+  dpf_tuning defaults{};          // dpf_set_tuning: fields a prepare and the autotuner leave open
   // Freed device blocks kept for reuse (without allocation hooks): a batch's
   // scratch is allocated at dpf_prepare and freed at dpf_release, and
   // cudaFree would wait for every kernel on the device, serialising a
@@ -1078,11 +1079,112 @@ void fill_tuning_defaults(dpf_ctx* c, dpf_tuning& t, const dpf_plan* plans, int3
       if (t.group_agg == 0) t.group_agg = it->second.group_agg;
     }
   }
+  const dpf_tuning& d = c->defaults;  // the context's defaults (dpf_set_tuning)
+  if (t.chunk_rows == 0) t.chunk_rows = d.chunk_rows;
+  if (t.threads == 0) t.threads = d.threads;
+  if (t.ht_placement == 0) t.ht_placement = d.ht_placement;
+  if (t.ctas_per_sm == 0) t.ctas_per_sm = d.ctas_per_sm;
+  if (t.staging == 0) t.staging = d.staging;
+  if (t.group_agg == 0) t.group_agg = d.group_agg;
   if (t.chunk_rows == 0) t.chunk_rows = kDefaultChunkRows;
   if (t.threads == 0) t.threads = 256;
   if (t.ht_placement == 0) t.ht_placement = DPF_HT_AUTO;
   if (t.staging == 0) t.staging = kDefaultStaging;
   if (t.group_agg == 0) t.group_agg = kDefaultGroupAgg;
+}
+
+// A flat JSON object of launch-configuration fields (dpf_set_tuning): the
+// keys of dpf_tuning with non-negative integers, or for the three enums
+// their names ("auto" / "smem" / "global", "default" / "on" / "off",
+// "default" / "warp" / "atomic").  Returns false on anything else.
+bool parse_tuning_json(const char* js, dpf_tuning* out, std::string* why) {
+  dpf_tuning t{};
+  const char* p = js;
+  auto ws = [&] { while (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r') ++p; };
+  auto str = [&](std::string* v) {
+    if (*p != '"') return false;
+    ++p;
+    v->clear();
+    while (*p && *p != '"') {
+      if (*p == '\\' || v->size() > 32) return false;
+      v->push_back(*p++);
+    }
+    if (*p != '"') return false;
+    ++p;
+    return true;
+  };
+  ws();
+  if (*p != '{') { *why = "expected '{'"; return false; }
+  ++p;
+  ws();
+  bool first = true;
+  while (*p != '}') {
+    if (!first) {
+      if (*p != ',') { *why = "expected ',' or '}'"; return false; }
+      ++p;
+      ws();
+    }
+    first = false;
+    std::string key, sval;
+    if (!str(&key)) { *why = "expected a quoted key"; return false; }
+    ws();
+    if (*p != ':') { *why = "expected ':' after \"" + key + "\""; return false; }
+    ++p;
+    ws();
+    int64_t num = -1;
+    if (*p == '"') {
+      if (!str(&sval)) { *why = "bad string value for \"" + key + "\""; return false; }
+    } else if (*p >= '0' && *p <= '9') {
+      num = 0;
+      while (*p >= '0' && *p <= '9') {
+        num = num * 10 + (*p++ - '0');
+        if (num > (int64_t(1) << 31)) { *why = "value of \"" + key + "\" too large"; return false; }
+      }
+    } else {
+      *why = "value of \"" + key + "\" must be a non-negative integer or a name";
+      return false;
+    }
+    ws();
+    auto pick = [&](std::initializer_list<const char*> names, int32_t* dst) {
+      if (num >= 0) {
+        if (num >= int64_t(names.size())) return false;
+        *dst = int32_t(num);
+        return true;
+      }
+      int32_t i = 0;
+      for (const char* nm : names) {
+        if (sval == nm) { *dst = i; return true; }
+        ++i;
+      }
+      return false;
+    };
+    bool ok = true;
+    if (key == "chunk_rows") {
+      ok = num >= 0 && num % 512 == 0 && num <= (int64_t(1) << 24);
+      t.chunk_rows = uint32_t(num);
+    } else if (key == "threads") {
+      ok = num == 0 || num == 128 || num == 256 || num == 512 || num == 1024;
+      t.threads = uint32_t(num);
+    } else if (key == "ctas_per_sm") {
+      ok = num >= 0 && num <= 32;
+      t.ctas_per_sm = uint32_t(num);
+    } else if (key == "ht_placement") {
+      ok = pick({"auto", "smem", "global"}, &t.ht_placement);
+    } else if (key == "staging") {
+      ok = pick({"default", "on", "off"}, &t.staging);
+    } else if (key == "group_agg") {
+      ok = pick({"default", "warp", "atomic"}, &t.group_agg);
+    } else {
+      *why = "unknown key \"" + key + "\"";
+      return false;
+    }
+    if (!ok) { *why = "bad value for \"" + key + "\""; return false; }
+  }
+  ++p;
+  ws();
+  if (*p) { *why = "text after the object"; return false; }
+  *out = t;
+  return true;
 }
 
 dpf_status release_prep(dpf_ctx* c, Prep* p) {
@@ -2355,6 +2457,24 @@ dpf_status dpf_prep_stats(dpf_ctx* c, dpf_prep_id id, uint32_t* launches, uint64
       }
     }
   }
+  return DPF_OK;
+}
+
+dpf_status dpf_parse_tuning(const char* json, dpf_tuning* out) {
+  if (!out) return fail(DPF_EINVAL, "NULL argument");
+  dpf_tuning t{};
+  std::string why;
+  if (json && *json && !parse_tuning_json(json, &t, &why)) return fail(DPF_EINVAL, "tuning: %s", why.c_str());
+  *out = t;
+  return DPF_OK;
+}
+
+dpf_status dpf_set_tuning(dpf_ctx* c, const char* json) {
+  if (!c) return fail(DPF_EINVAL, "ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(c->mu);
+  dpf_tuning t{};
+  if (dpf_status st = dpf_parse_tuning(json, &t)) return st;
+  c->defaults = t;
   return DPF_OK;
 }
 

@@ -1,4 +1,5 @@
-"""GPU parity of plans with predicates every row passes.
+"""GPU parity of plans with predicates every row passes, and the context's
+default launch configuration.
 
 The planner compiles an empty PREFIX or CONTAINS pattern, LIKE '%', and a
 range over a column's whole int32 or int64 domain to no step at all (the
@@ -106,3 +107,39 @@ def test_a_dropped_predicate_is_still_checked(eng, strings_w):
     with pytest.raises(dpf.DpfError) as e:
         eng.ctx.prepare([h])
     assert e.value.status == -1
+
+
+def test_context_default_tuning(strings_w):
+    """dpf_set_tuning: a prepare without a tuning takes the context's
+    defaults (the fields it leaves open), an explicit tuning overrides them,
+    a reset restores the library's; records stay the oracle's."""
+    w = copy.deepcopy(strings_w)
+    w["query"]["preds"] = [{"col": "s", "op": "prefix", "args": [b"q"]}]
+    want = oracle.run_query(w, from_encoded=False, threads=0)
+    e = dpf.Engine(device=0)
+    try:
+        e.load_workload(w)
+        h = e.plan(w)
+
+        def run(tuning=None):
+            prep = e.ctx.prepare([h], tuning)
+            try:
+                e.ctx.launch(prep)
+                assert_same(e.ctx.read_result(prep, 0), want)
+                return e.ctx.prep_tuning(prep)
+            finally:
+                e.ctx.release(prep)
+        e.ctx.set_tuning({"chunk_rows": 8192, "threads": 128, "ht_placement": "global"})
+        t = run()
+        assert (t["chunk_rows"], t["threads"], t["ht_placement"]) == (8192, 128, 2)
+        t = run(dpf.Tuning(2048, 256, 0, 0, 0, 0))
+        assert (t["chunk_rows"], t["threads"], t["ht_placement"]) == (2048, 256, 2)
+        with pytest.raises(dpf.DpfError):
+            e.ctx.set_tuning('{"threads": 300}')
+        t = run()  # a refused object leaves the defaults as they were
+        assert (t["chunk_rows"], t["threads"]) == (8192, 128)
+        e.ctx.set_tuning(None)
+        t = run()
+        assert (t["chunk_rows"], t["threads"], t["ht_placement"]) == (4096, 256, 0)
+    finally:
+        e.close()
