@@ -121,37 +121,52 @@ __device__ void finish_query(const DevQuery& Q, unsigned long long* sacc, uint32
   __syncthreads();
 }
 
-// Warp-aggregated group-by update (hash aggregation of Kernel #3, Sec. 3.1):
-// the lanes of a round that hold the same group id (`peers`, from
-// __match_any_sync) add their int64 values once.  Lanes alone in their group
-// add directly; otherwise each lane parks its value in the warp's 32-slot
-// buffer and the group's lowest lane sums its peers' values and issues the
-// group's single atomic.  Skewed keys (a Zipf head holding a fifth of the
-// rows) thus cost one atomic per distinct group per round instead of one per
-// row on the same address.  Warp-uniform call.
-__device__ __forceinline__ void warp_group_add(unsigned long long* acc, uint64_t idx, unsigned long long x,
-                                               bool valid, uint32_t peers, int lane, unsigned long long* wbuf) {
-  const uint32_t others = peers & ~(1u << lane);
-  if (!__any_sync(kFull, valid && others != 0)) {
-    if (valid) atomicAdd(acc + idx, x);
-    return;
+// Warp-aggregated group-by update (hash aggregation of Kernel #3, Sec. 3.1),
+// by the round's leading group: the lanes holding the group id of the
+// round's first valid lane combine their values with warp reductions and
+// that lane issues the group's single atomic; every other valid lane adds
+// its own value.  A hot group (a Zipf head, or one key holding most rows)
+// thus costs one atomic per round instead of one per row on the same
+// address.  The sum is exact modulo 2^64: a value is split into 16-bit parts
+// whose sums over 32 lanes stay below 2^21 (kWide: four unsigned parts of
+// the 64-bit value; otherwise the value is an int32, whose low 16 bits and
+// signed high 16 bits are summed).  Warp-uniform call.
+template <bool kWide>
+__device__ __forceinline__ void lead_group_add(unsigned long long* acc, uint32_t gid, uint32_t S1, uint32_t slot,
+                                               unsigned long long x, bool valid, int lane) {
+  const uint32_t vm = __ballot_sync(kFull, valid);
+  if (vm == 0) return;
+  const int lead = __ffs(vm) - 1;
+  const uint32_t g0 = __shfl_sync(kFull, gid, lead);
+  const bool mine = valid && gid == g0;
+  const uint32_t m = __ballot_sync(kFull, mine);
+  if (mine) {
+    unsigned long long t;
+    if (kWide) {
+      const uint32_t lo = uint32_t(x), hi = uint32_t(x >> 32);
+      t = (unsigned long long)__reduce_add_sync(m, lo & 0xffffu) +
+          ((unsigned long long)__reduce_add_sync(m, lo >> 16) << 16) +
+          ((unsigned long long)__reduce_add_sync(m, hi & 0xffffu) << 32) +
+          ((unsigned long long)__reduce_add_sync(m, hi >> 16) << 48);
+    } else {
+      const int32_t v = int32_t(uint32_t(x));
+      const uint32_t s_lo = __reduce_add_sync(m, uint32_t(v) & 0xffffu);
+      const int32_t s_hi = int32_t(__reduce_add_sync(m, uint32_t(v >> 16)));  // |sum| < 2^20
+      t = (unsigned long long)((long long)s_lo + (long long)s_hi * 65536ll);
+    }
+    if (lane == lead) atomicAdd(acc + uint64_t(g0) * S1 + slot, t);
+  } else if (valid) {
+    atomicAdd(acc + uint64_t(gid) * S1 + slot, x);
   }
-  wbuf[lane] = x;
-  __syncwarp();
-  if (valid && (peers & ((1u << lane) - 1u)) == 0) {
-    for (uint32_t p = others; p; p &= p - 1) x += wbuf[__ffs(p) - 1];
-    atomicAdd(acc + idx, x);
-  }
-  __syncwarp();
 }
 
-// Lanes of the round with the same group id as this one (valid lanes only;
-// invalid lanes share a key no group id takes).  Without warp aggregation
-// (Q.warp_agg == 0) every lane is its own group and adds directly:
-// __match_any_sync costs more than it saves when a round holds many distinct
-// groups (measured on 1,024 Zipf-distributed groups).
-__device__ __forceinline__ uint32_t group_peers(uint32_t gid, bool valid, bool wagg) {
-  return wagg ? __match_any_sync(kFull, valid ? gid : 0xffffffffu) : 1u << (threadIdx.x & 31);
+// A grouped update: warp-aggregated by the leading group (Q.warp_agg) or one
+// atomic per row.
+template <bool kWide>
+__device__ __forceinline__ void group_add(const DevQuery& Q, unsigned long long* acc, uint32_t gid, uint32_t S1,
+                                          uint32_t slot, unsigned long long x, bool valid, int lane) {
+  if (Q.warp_agg) lead_group_add<kWide>(acc, gid, S1, slot, x, valid, lane);
+  else if (valid) atomicAdd(acc + uint64_t(gid) * S1 + slot, x);
 }
 
 // One aggregate over a warp's list, specialised on its operation (dpf_agg_op)
@@ -196,9 +211,8 @@ __device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, 
       else if (kOp == DPF_AGG_SUM_SUB)
         x = (long long)va[u] - (long long)vb[u];
       if (single) sum += valid[u] ? x : 0;
-      else
-        warp_group_add(acc, uint64_t(gid[u]) * S1 + slot, (unsigned long long)x, valid[u],
-                       group_peers(gid[u], valid[u], Q.warp_agg != 0), lane, wbuf);
+      else group_add<kOp == DPF_AGG_SUM_MUL || kOp == DPF_AGG_SUM_SUB>(Q, acc, gid[u], S1, slot,
+                                                                      (unsigned long long)x, valid[u], lane);
     }
   }
   if (single) {
@@ -230,7 +244,7 @@ __device__ __forceinline__ void agg_pass_wide(const DevQuery& Q, const PageState
       b = (unsigned long long)value64<kHost>(Q, cb, P, seg_mb, r, valid, lane, status);
     const unsigned long long x = kOp == DPF_AGG_SUM ? a : (kOp == DPF_AGG_SUM_MUL ? a * b : a - b);
     if (single) sum += valid ? x : 0ull;
-    else warp_group_add(acc, uint64_t(gid) * S1 + slot, x, valid, group_peers(gid, valid, Q.warp_agg != 0), lane, wbuf);
+    else group_add<true>(Q, acc, gid, S1, slot, x, valid, lane);
   }
   if (single) {
 #pragma unroll
@@ -256,9 +270,9 @@ __device__ __forceinline__ void agg_dispatch(const DevQuery& Q, const PageState&
 // Aggregation over a warp's survivor list (Kernel #3 hash aggregation;
 // int64 as in Sec. 4.3): slot 0 counts rows, slot 1 + a holds aggregate a.
 // domain == 1: per-lane int64 sums reduced across the warp; otherwise
-// warp-aggregated int64 atomics (warp_group_add; COUNT adds the size of each
-// group of peers) into the CTA's shared accumulators (or the query's global
-// ones for large domains), indexed by the dense group id.
+// int64 atomics (one per row, or warp-aggregated by the round's leading
+// group: group_add) into the CTA's shared accumulators (or the query's
+// global ones for large domains), indexed by the dense group id.
 template <bool kHost>
 __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                                const uint32_t* list, uint32_t n, int lane,
@@ -276,9 +290,7 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
         atomicOr(status, S_CORRUPT);  // a corrupt dictionary code
         valid = false;
       }
-      const uint32_t peers = group_peers(gid, valid, Q.warp_agg != 0);
-      if (valid && (peers & ((1u << lane) - 1u)) == 0)
-        atomicAdd(acc + uint64_t(gid) * S1, (unsigned long long)__popc(peers));
+      group_add<false>(Q, acc, gid, S1, 0, 1ull, valid, lane);
     }
   }
   for (uint32_t a = 0; a < Q.naggs; ++a) {
