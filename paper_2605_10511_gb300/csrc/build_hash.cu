@@ -66,8 +66,9 @@ constexpr unsigned long long kEmptySlot = 0x0000000080000000ull;  // {INT32_MIN,
 // kMode 0: count kept rows and their key range; 1: insert into an
 // open-addressing table; 2: insert into a direct table; 3: set the rows'
 // presence bits of a rank directory (a bit already set is a duplicate key)
-// and append {key offset, payload} to the staging list, from which
-// rank_scatter places the payloads once the ranks are known.  Modes 1-3
+// and write {key offset, payload} to the staging list (a tile reserves one
+// slot per kept row with one atomic), from which rank_scatter places the
+// payloads once the ranks are known.  Modes 1-3
 // also add the rows they insert to L.inserted when it is set (a table sized
 // before its scan learns its entry count that way).
 template <bool kHost, int kMode>
@@ -103,6 +104,12 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
     tile_dense_step<kHost>(Q, 0, P, H, T, nullptr, lane, status);
     uint32_t n = tile_compact(T, list, 0, 0, lane);
     n = list_steps<kHost>(Q, P, i0, list, n, nullptr, lane, status);
+    // rank builds: one staging slot per kept row of the tile, reserved at once
+    unsigned long long sbase = 0;
+    if (kMode == 3 && n != 0) {
+      if (lane == 0) sbase = atomicAdd(L.stage_n, (unsigned long long)n);
+      sbase = __shfl_sync(kFull, sbase, 0);
+    }
     for (uint32_t j0 = 0; j0 < n; j0 += 32) {
       const bool valid = j0 + lane < n;
       const uint32_t e = valid ? list[j0 + lane] : 0u;
@@ -119,8 +126,12 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
         kmax = max(kmax, kv);
         continue;
       }
+      // a rank build's slot of a row that inserts nothing holds a pair the
+      // scatter skips (its key offset is out of range)
+      const unsigned long long sslot = sbase + j0 + lane;
       if (kv == kEmptyKey) {
         atomicOr(status, S_CORRUPT);
+        if (kMode == 3 && sslot < L.rank_cap) L.rank_stage[sslot] = make_uint2(0xffffffffu, 0u);
         continue;
       }
       ++kept;  // rows inserted (read only when L.inserted is set)
@@ -129,6 +140,7 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
         const uint32_t off = uint32_t(kv) - uint32_t(L.kmin);
         if (off >= L.krange) {
           atomicOr(status, S_INTERNAL);
+          if (kMode == 3 && sslot < L.rank_cap) L.rank_stage[sslot] = make_uint2(0xffffffffu, 0u);
           continue;
         }
         if (kMode == 2) {
@@ -137,13 +149,7 @@ __global__ void __launch_bounds__(256) build_kernel(const DevQuery* __restrict__
           unsigned int* word = reinterpret_cast<unsigned int*>(L.rank_dir + (off >> 6)) + ((off >> 5) & 1u);
           const unsigned int bit = 1u << (off & 31u);
           if (atomicOr(word, bit) & bit) atomicOr(status, S_DUPKEY);
-          // one atomic per group of lanes appending together
-          const unsigned int m = __activemask();
-          const int leader = __ffs(m) - 1;
-          unsigned long long base = 0;
-          if (lane == leader) base = atomicAdd(L.stage_n, (unsigned long long)__popc(m));
-          base = __shfl_sync(m, base, leader) + uint32_t(__popc(m & ((1u << lane) - 1u)));
-          if (base < L.rank_cap) L.rank_stage[base] = make_uint2(off, pay);
+          if (sslot < L.rank_cap) L.rank_stage[sslot] = make_uint2(off, pay);
           else atomicOr(status, S_INTERNAL);
         }
         continue;
@@ -254,12 +260,15 @@ __global__ void rank_fill(uint4* dir, uint32_t nwords, const uint32_t* sums) {
 }
 
 // Payloads of a rank table at their ranks: each staged {key offset,
-// payload} goes to the word's running count plus the set bits below it.
+// payload} goes to the word's running count plus the set bits below it
+// (a pair whose offset is outside the key range marks a row that inserted
+// nothing).
 __global__ void rank_scatter(const uint4* dir, const uint2* stage, const unsigned long long* n, uint32_t* pay,
-                             uint32_t cap, unsigned int* status) {
+                             uint32_t cap, uint32_t krange, unsigned int* status) {
   const uint64_t cnt = tmin<uint64_t>(*n, cap);
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < cnt; i += uint64_t(gridDim.x) * blockDim.x) {
     const uint2 e = stage[i];
+    if (e.x >= krange) continue;
     const uint4 d = dir[e.x >> 6];
     const uint32_t b = e.x & 63u, bb = b & 31u;
     const uint32_t idx = (b < 32 ? d.z : d.w) + uint32_t(__popc((b < 32 ? d.x : d.y) & ((1u << bb) - 1u)));
@@ -302,7 +311,8 @@ cudaError_t launch_build_insert(const BuildLaunch& L, cudaStream_t s) {
     rank_scan_sums<<<1, 1024, 0, s>>>(L.rank_sums, nblocks);
     rank_fill<<<nblocks, 256, 0, s>>>(L.rank_dir, nwords, L.rank_sums);
     const int g = int(tmax<uint32_t>(1u, tmin<uint32_t>((L.rank_cap + 255) / 256, 2048u)));
-    rank_scatter<<<g, 256, 0, s>>>(L.rank_dir, L.rank_stage, L.stage_n, L.rank_pay, L.rank_cap, &L.sched->status);
+    rank_scatter<<<g, 256, 0, s>>>(L.rank_dir, L.rank_stage, L.stage_n, L.rank_pay, L.rank_cap, L.krange,
+                                   &L.sched->status);
     return cudaGetLastError();
   }
   return L.direct ? launch_build_mode<2>(L, s) : launch_build_mode<1>(L, s);
