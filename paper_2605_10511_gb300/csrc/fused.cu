@@ -16,8 +16,7 @@ int fused_stage_occupancy(int threads, size_t smem, int min_blocks);
 
 size_t fused_dynamic_smem(uint32_t acc_slots, size_t smem_tables, int threads, uint32_t stage_bw) {
   return ((acc_slots * sizeof(unsigned long long) + 15) & ~size_t(15)) + ((smem_tables + 15) & ~size_t(15)) +
-         size_t(threads / 32) * (kListCap * sizeof(uint32_t) + 32 * sizeof(unsigned long long) +
-                                 stage_warp_bytes(stage_bw));
+         size_t(threads / 32) * (kListCap * sizeof(uint32_t) + stage_warp_bytes(stage_bw));
 }
 
 // The occupancy of the string-capable build bounds the grid of both builds

@@ -175,8 +175,7 @@ __device__ __forceinline__ void group_add(const DevQuery& Q, unsigned long long*
 template <bool kHost, int kOp, bool kPoint>
 __device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                          const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
-                                         uint32_t slot, int ca, int cb, bool single, unsigned int* status,
-                                         unsigned long long* wbuf) {
+                                         uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
   constexpr int U = kPoint ? kListUnroll : 1;  // rounds whose loads are issued together
   const uint32_t S1 = 1 + Q.naggs;
   long long sum = 0;
@@ -229,8 +228,7 @@ __device__ __forceinline__ void agg_pass(const DevQuery& Q, const PageState& P, 
 template <bool kHost, int kOp>
 __device__ __forceinline__ void agg_pass_wide(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                            const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
-                                           uint32_t slot, int ca, int cb, bool single, unsigned int* status,
-                                           unsigned long long* wbuf) {
+                                           uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
   const uint32_t S1 = 1 + Q.naggs;
   unsigned long long sum = 0;
   for (uint32_t i0 = 0; i0 < n; i0 += 32) {
@@ -256,15 +254,14 @@ __device__ __forceinline__ void agg_pass_wide(const DevQuery& Q, const PageState
 template <bool kHost, int kOp>
 __device__ __forceinline__ void agg_dispatch(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                              const uint32_t* list, uint32_t n, int lane, unsigned long long* acc,
-                                             uint32_t slot, int ca, int cb, bool single, unsigned int* status,
-                                             unsigned long long* wbuf) {
+                                             uint32_t slot, int ca, int cb, bool single, unsigned int* status) {
   if (Q.cols[ca].codec == C_FOR64 || (kOp != DPF_AGG_SUM && Q.cols[cb].codec == C_FOR64)) {
-    agg_pass_wide<kHost, kOp>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status, wbuf);
+    agg_pass_wide<kHost, kOp>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status);
     return;
   }
   const bool point = Q.cols[ca].codec != C_DELTA && (kOp == DPF_AGG_SUM || Q.cols[cb].codec != C_DELTA);
-  if (point) agg_pass<kHost, kOp, true>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status, wbuf);
-  else agg_pass<kHost, kOp, false>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status, wbuf);
+  if (point) agg_pass<kHost, kOp, true>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status);
+  else agg_pass<kHost, kOp, false>(Q, P, seg_mb, list, n, lane, acc, slot, ca, cb, single, status);
 }
 
 // Aggregation over a warp's survivor list (Kernel #3 hash aggregation;
@@ -276,8 +273,7 @@ __device__ __forceinline__ void agg_dispatch(const DevQuery& Q, const PageState&
 template <bool kHost>
 __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageState& P, uint32_t seg_mb,
                                                const uint32_t* list, uint32_t n, int lane,
-                                               unsigned long long* acc, unsigned int* status,
-                                               unsigned long long* wbuf) {
+                                               unsigned long long* acc, unsigned int* status) {
   const uint32_t S1 = 1 + Q.naggs;
   const bool single = Q.domain == 1;
   if (single) {
@@ -300,17 +296,17 @@ __device__ __forceinline__ void list_aggregate(const DevQuery& Q, const PageStat
         if (single) {
           if (lane == 0) atomicAdd(acc + 1 + a, (unsigned long long)n);
         } else {
-          agg_pass<kHost, DPF_AGG_COUNT, true>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status, wbuf);
+          agg_pass<kHost, DPF_AGG_COUNT, true>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
         }
         break;
       case DPF_AGG_SUM:
-        agg_dispatch<kHost, DPF_AGG_SUM>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status, wbuf);
+        agg_dispatch<kHost, DPF_AGG_SUM>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
         break;
       case DPF_AGG_SUM_MUL:
-        agg_dispatch<kHost, DPF_AGG_SUM_MUL>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status, wbuf);
+        agg_dispatch<kHost, DPF_AGG_SUM_MUL>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
         break;
       default:
-        agg_dispatch<kHost, DPF_AGG_SUM_SUB>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status, wbuf);
+        agg_dispatch<kHost, DPF_AGG_SUM_SUB>(Q, P, seg_mb, list, n, lane, acc, 1 + a, ca, cb, single, status);
         break;
     }
   }
@@ -357,7 +353,7 @@ __device__ __forceinline__ FirstCol first_col(const DevQuery& Q, const PageState
 // the aggregation run on them.
 template <bool kHost, bool kText, bool kStage>
 __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long long* acc, const uint8_t* stab,
-                               uint32_t* list, int lane, unsigned int* status, unsigned long long* wbuf,
+                               uint32_t* list, int lane, unsigned int* status,
                                uint8_t* ring) {
   const uint64_t PR = Q.page_rows;
   uint64_t r0 = chunk * Q.chunk_rows, r1 = r0 + Q.chunk_rows;
@@ -428,7 +424,7 @@ __device__ void process_ticket(const DevQuery& Q, uint64_t chunk, unsigned long 
       const uint32_t next = i0 + TB;
       if (j + 1 == ntiles || n + kTileRows > kListCap || next + TB - seg_mb > kSegMbs) {
         n = list_steps<kHost, kText>(Q, P, seg_mb, list, n, stab, lane, status, 1);
-        if (n) list_aggregate<kHost>(Q, P, seg_mb, list, n, lane, acc, status, wbuf);
+        if (n) list_aggregate<kHost>(Q, P, seg_mb, list, n, lane, acc, status);
         n = 0;
         seg_mb = next;
       }
@@ -482,7 +478,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) fused_kernel(const DevQu
   unsigned long long* sacc = reinterpret_cast<unsigned long long*>(dyn);
   uint8_t* stab = dyn + ((acc_slots * sizeof(unsigned long long) + 15) & ~size_t(15));
   uint32_t* lists = reinterpret_cast<uint32_t*>(stab + tables_bytes);
-  unsigned long long* wbufs = reinterpret_cast<unsigned long long*>(lists + (blockDim.x >> 5) * kListCap);
   // Warps draw tickets on their own (one ticket = chunk_rows rows of one
   // query, processed by one warp), so no CTA barrier separates tickets.  The
   // CTA meets only when its warps' tickets leave the current query: it then
@@ -491,8 +486,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) fused_kernel(const DevQu
   // finished query's accumulators first.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   uint32_t* list = lists + uint32_t(warp) * kListCap;
-  unsigned long long* wbuf = wbufs + warp * 32;
-  uint8_t* ring = reinterpret_cast<uint8_t*>(wbufs + nw * 32) + size_t(warp) * stage_warp_bytes(stage_bw);
+  uint8_t* ring = reinterpret_cast<uint8_t*>(lists + nw * kListCap) + size_t(warp) * stage_warp_bytes(stage_bw);
   auto draw = [&](unsigned long long& t) -> int {
     unsigned long long x = 0;
     if (lane == 0) x = atomicAdd(&sched->next, 1ull);
@@ -533,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) fused_kernel(const DevQu
     unsigned long long* acc = Q.use_smem_acc ? sacc : Q.acc;
     uint32_t done_here = 0;
     while (hq == cur) {
-      process_ticket<kHost, kText, kStage>(Q, held - Q.chunk_begin, acc, stab, list, lane, &sched->status, wbuf,
+      process_ticket<kHost, kText, kStage>(Q, held - Q.chunk_begin, acc, stab, list, lane, &sched->status,
                                            ring);
       ++done_here;
       hq = draw(held);

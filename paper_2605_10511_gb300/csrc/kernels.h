@@ -19,8 +19,8 @@ constexpr int kFusedMinBlocksLo = 3;
 constexpr int kFusedMinBlocksHi = 4;
 // Rows of one scheduling ticket (one warp's unit of work) unless tuned.
 constexpr uint32_t kDefaultChunkRows = 4096;
-// Shared memory of one warp's survivor list (1,024 entries) and group buffer.
-constexpr uint32_t kListBytesPerWarp = 1024 * 4 + 32 * 8;
+// Shared memory of one warp's survivor list (1,024 entries).
+constexpr uint32_t kListBytesPerWarp = 1024 * 4;
 // Estimated selectivity of the first step from which step 1's mini blocks
 // are prefetched into L2 during the dense tiles (DevQuery::pf_step).
 constexpr double kPrefetchMinSel = 0.03;

@@ -939,7 +939,7 @@ constexpr uint32_t kListCap = 1024;                    // entries per warp list
 constexpr int kListUnroll = 1;  // survivor rounds whose loads are issued together (measured best at 1)
 static_assert(kTileRows <= (1u << kRowBits), "row index field too narrow");
 static_assert(kListCap >= kTileRows, "a list must hold one tile");
-static_assert(kListBytesPerWarp == kListCap * 4 + 32 * 8, "the host's per-warp shared-memory figure");
+static_assert(kListBytesPerWarp == kListCap * 4, "the host's per-warp shared-memory figure");
 static_assert(kSegMbs <= 32, "segment mini blocks must fit a 32-bit mask");
 
 // Dense step s of a tile (or none): live bits and group-id contributions.
