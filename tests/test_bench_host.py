@@ -80,3 +80,26 @@ def test_kernel_source_hash_ignores_comments_only():
     assert bench._code_only(a) == bench._code_only(b)
     assert bench._code_only(a) != bench._code_only(c)
     assert bench._code_only(s) == s.rstrip("\n")
+
+
+def test_stored_traffic_by_algorithmic_bytes_and_link_bytes(tmp_path, monkeypatch):
+    """A batch's capture scales by algorithmic bytes; the host-resident
+    variant's link bytes come from its own capture when present, and the
+    lookup reports a missing or stale one."""
+    h = "ab" * 8
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda *a: h)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir(exist_ok=True)
+    (tmp_path / "profiles" / "fused_kernel_batched.txt").write_text(
+        f"source_hash: {h}\ncaptured_rows: 100\ndram_bytes_per_launch: 900\n"
+        "algorithmic_bytes_per_launch: 1000\n")
+    traffic, src = bench.stored_traffic("batched", 0, alg_bytes=4000)
+    assert traffic == 3600 and "algorithmic bytes" in src
+    assert bench.stored_link_bytes("star", 1 << 26) == (None, "no capture")
+    (tmp_path / "profiles" / "fused_kernel_star_host.txt").write_text(
+        f"source_hash: {h}\ncaptured_rows: {1 << 25}\nlink_bytes_per_launch: 1000\n")
+    link, src = bench.stored_link_bytes("star", 1 << 26)
+    assert link == 2000 and "scaled" in src
+    (tmp_path / "profiles" / "fused_kernel_star_host.txt").write_text(
+        f"source_hash: {'0' * 16}\ncaptured_rows: 1\nlink_bytes_per_launch: 1\n")
+    assert bench.stored_link_bytes("star", 1 << 26) == (None, "stale (kernel changed since capture)")
