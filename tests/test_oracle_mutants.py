@@ -65,6 +65,7 @@ MUTANTS = {
                                 "r1 = std::min(fact->n, r0 + range_rows - 1);"),
     "threads_last_range_skipped": ("for (uint64_t i = uint64_t(t); i < nranges; i += uint64_t(nthreads)) {",
                                    "for (uint64_t i = uint64_t(t); i + 1 < nranges; i += uint64_t(nthreads)) {"),
+    "bigint_predicate_in_32_bits": ("  const int64_t x = ival(c, r);", "  const int64_t x = int32_t(ival(c, r));"),
 }
 
 
@@ -122,6 +123,13 @@ def _pins_pass(o):
         e = npeval.evaluate(w)
         g = o.run_query(w)
         assert np.array_equal(g["val"], e["val"]) and np.array_equal(g["count"], e["count"])
+        for preds in ([{"col": "m1", "op": "gt", "args": [1 << 40]}],
+                      [{"col": "m1", "op": "between", "args": [3 << 30, 1 << 41]}]):  # BIGINT predicates
+            w = synth.bigint_filter_star(5000, 7, 1024, preds=preds, joins=False)
+            e = npeval.evaluate(w)
+            g = o.run_query(w, from_encoded=True)
+            for f in ("key", "count", "val"):
+                assert np.array_equal(g[f], e[f]), ("bigint", f)
     except Exception as exc:  # noqa: BLE001 - any failure counts as a caught mutant
         return False, f"{type(exc).__name__}: {exc}"
     return True, ""
